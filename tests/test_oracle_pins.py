@@ -1,0 +1,283 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself:
+closed-form integrals and potentials, polynomial exactness, symmetry, brute
+force on tiny meshes and invariances. None of these needs a GPU.
+
+The paper prints no worked numbers for the Poisson / exchange path, so every
+pin here is a closed form, an invariant or an independent construction.
+"""
+
+import math
+
+import numpy as np
+import pytest
+from scipy.special import erf
+
+import oracle
+from oracle import dg_oracle as O
+from paper_2510_21213_gb300 import inputs
+
+
+# ---------------------------------------------------------------------------
+# Quadrature and the nodal basis (Sec. 5.2: degree-q nodal GL elements whose
+# nodes double as the quadrature rule)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("p", [1, 2, 4, 7])
+def test_gl_exact_on_box_monomials(p):
+    m = oracle.Mesh([-1.3, -0.4, 0.2], [0.9, 1.6, 2.2], (2, 3, 2), p)
+    x = oracle.node_coords(m)
+    W = oracle.quad_weights(m)
+    assert abs(W.sum() - np.prod(m.hi - m.lo)) < 1e-13 * np.prod(m.hi - m.lo)
+
+    def exact(a, b, c):
+        val = 1.0
+        for d, k in enumerate((a, b, c)):
+            val *= (m.hi[d] ** (k + 1) - m.lo[d] ** (k + 1)) / (k + 1)
+        return val
+
+    for (a, b, c) in [(2 * p + 1, 0, 0), (0, 2 * p + 1, 1), (p, p + 1, 2 * p + 1), (2 * p + 1,) * 3]:
+        got = np.sum(W * x[:, 0] ** a * x[:, 1] ** b * x[:, 2] ** c)
+        ref = exact(a, b, c)
+        assert abs(got - ref) <= 1e-11 * max(1.0, abs(ref)), (a, b, c, got, ref)
+    # one degree more is not integrated exactly (the rule is not over-exact)
+    a = 2 * p + 2
+    m1 = oracle.Mesh([0.0] * 3, [1.0] * 3, (1, 1, 1), p)
+    got = np.sum(oracle.quad_weights(m1) * oracle.node_coords(m1)[:, 0] ** a)
+    assert abs(got - 1.0 / (a + 1)) > 1e-10
+
+
+@pytest.mark.parametrize("p", [1, 3, 6, 8])
+def test_lagrange_interpolates_and_differentiates_polynomials(p):
+    xi, _ = oracle.gauss_legendre(p + 1)
+    L, dL = oracle.lagrange_eval(xi, xi)
+    assert np.allclose(L, np.eye(p + 1), atol=1e-13)
+    rng = np.random.default_rng(p)
+    coef = rng.standard_normal(p + 1)
+    poly = np.polynomial.Polynomial(coef)
+    pts = np.linspace(-1.0, 1.0, 11)
+    Lp, dLp = oracle.lagrange_eval(xi, pts)
+    assert np.allclose(Lp @ poly(xi), poly(pts), atol=1e-12)
+    assert np.allclose(dLp @ poly(xi), poly.deriv()(pts), atol=1e-11)
+
+
+@pytest.mark.parametrize("p", [1, 4, 7])
+def test_collocated_mass_is_exact(p):
+    """The diagonal GL mass w_a h/2 equals the exact int l_a l_b (Gauss rule
+    with more points), so the Kronecker form uses the exact mass."""
+    xi, w = oracle.gauss_legendre(p + 1)
+    xq, wq = oracle.gauss_legendre(p + 4)
+    L, _ = oracle.lagrange_eval(xi, xq)
+    Mex = L.T @ (wq[:, None] * L)
+    assert np.allclose(Mex, np.diag(w), atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# SIPDG operator (Eq. 19, Sec. 3.4, Sec. 5.3)
+# ---------------------------------------------------------------------------
+TINY = [
+    ([-1.0, -2.0, -1.5], [1.0, 2.0, 2.0], (2, 2, 3), 2),
+    ([-3.0] * 3, [3.0] * 3, (3, 3, 3), 1),
+    ([-2.0, -1.0, 0.0], [2.0, 1.0, 1.5], (1, 2, 2), 3),
+]
+
+
+@pytest.mark.parametrize("lo,hi,n,p", TINY)
+@pytest.mark.parametrize("form", [0, 1])
+def test_dense_equals_kronecker_and_spd(lo, hi, n, p, form):
+    m = oracle.Mesh(lo, hi, n, p)
+    Ad = oracle.assemble_dense(m, penalty_form=form)
+    Ak = oracle.assemble_kron(m, penalty_form=form).toarray()
+    scale = np.abs(Ad).max()
+    assert np.abs(Ad - Ak).max() <= 1e-13 * scale
+    assert np.abs(Ad - Ad.T).max() <= 1e-13 * scale
+    assert np.linalg.eigvalsh(Ad).min() > 0.0
+
+
+def _poly_problem(m):
+    def u(P):
+        return P[..., 0] ** 2 * P[..., 1] - 3.0 * P[..., 2] + P[..., 0] * P[..., 1] * P[..., 2] ** 2 + 0.5
+
+    def lap(P):
+        return 2.0 * P[..., 1] + 2.0 * P[..., 0] * P[..., 1]
+
+    x = oracle.node_coords(m)
+    f = -lap(x) / (4.0 * math.pi)
+    g = [u(pts) for pts in oracle.boundary_face_nodes(m)]
+    return u(x), f, g
+
+
+@pytest.mark.parametrize("lo,hi,n,p", [TINY[0], ([-2.0, -1.0, 0.0], [2.0, 1.0, 1.5], (2, 1, 2), 3)])
+@pytest.mark.parametrize("form", [0, 1])
+def test_polynomial_reproduction(lo, hi, n, p, form):
+    """SIP + Nitsche is consistent: a global Q_p solution with f = -Lap u/(4 pi)
+    and g = u on the boundary is reproduced to round-off. This pins the sign
+    and weight of every face, boundary and load term."""
+    m = oracle.Mesh(lo, hi, n, p)
+    uex, f, g = _poly_problem(m)
+    b = oracle.rhs(m, f, g, penalty_form=form)
+    v = oracle.solve_dense(oracle.assemble_dense(m, penalty_form=form), b)
+    assert np.abs(v - uex).max() < 1e-11 * np.abs(uex).max()
+    v2 = oracle.solve_fdm(m, b, penalty_form=form)
+    assert np.abs(v2 - uex).max() < 1e-11 * np.abs(uex).max()
+
+
+def test_planted_mistake_is_caught(monkeypatch):
+    """Flip the sign of the endpoint derivatives (a wrong normal in the trace of
+    grad v): polynomial reproduction must fail."""
+    m = oracle.Mesh(*TINY[0])
+    real = O.lagrange_eval
+
+    def wrong(nodes, x):
+        L, dL = real(nodes, x)
+        x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+        ends = np.abs(np.abs(x) - 1.0) < 1e-15
+        dL[ends] *= -1.0
+        return L, dL
+
+    monkeypatch.setattr(O, "lagrange_eval", wrong)
+    uex, f, g = _poly_problem(m)
+    b = oracle.rhs(m, f, g)
+    v = oracle.solve_dense(oracle.assemble_dense(m), b)
+    assert np.abs(v - uex).max() > 1e-3 * np.abs(uex).max()
+
+
+@pytest.mark.parametrize("lo,hi,n,p", TINY)
+def test_fdm_equals_cholesky(lo, hi, n, p):
+    m = oracle.Mesh(lo, hi, n, p)
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal((2, m.Nq))
+    A = oracle.assemble_dense(m)
+    x1 = np.stack([oracle.solve_dense(A, bb) for bb in b])
+    x2 = oracle.solve_fdm(m, b)
+    assert np.abs(x1 - x2).max() <= 1e-10 * np.abs(x1).max()
+
+
+# ---------------------------------------------------------------------------
+# Boundary data and Gaussian potentials (Sec. 5.3, Eqs. 33-34)
+# ---------------------------------------------------------------------------
+A_EXP = 2.0
+CENTER = np.array([0.35, -0.2, 0.1])
+
+
+def _unit_gaussian(x):
+    r = np.linalg.norm(x - CENTER, axis=-1)
+    return (A_EXP / math.pi) ** 1.5 * np.exp(-A_EXP * r * r)
+
+
+def _erf_potential(x):
+    r = np.linalg.norm(x - CENTER, axis=-1)
+    return erf(math.sqrt(A_EXP) * r) / r
+
+
+def test_boundary_data_matches_erf_potential():
+    errs = []
+    for p in (4, 6, 8):
+        m = oracle.Mesh([-8.0] * 3, [8.0] * 3, 4, p)
+        g = oracle.boundary_data_direct(m, _unit_gaussian(oracle.node_coords(m)))
+        errs.append(max(np.abs(gf - _erf_potential(pts)).max() for gf, pts in zip(g, oracle.boundary_face_nodes(m))))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-5
+
+
+def test_boundary_data_direct_brute_force():
+    m = oracle.Mesh([-2.0, -1.0, -1.0], [2.0, 1.0, 1.5], (2, 1, 2), 2)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(m.Nq)
+    g = oracle.boundary_data_direct(m, f, chunk=7)
+    x = oracle.node_coords(m)
+    W = oracle.quad_weights(m)
+    for face, pts in enumerate(oracle.boundary_face_nodes(m)):
+        for (i, j) in [(0, 0), (pts.shape[0] - 1, pts.shape[1] - 1), (1, 2)]:
+            ref = sum(W[q] * f[q] / math.dist(pts[i, j], x[q]) for q in range(m.Nq))
+            assert abs(g[face][i, j] - ref) < 1e-12 * max(1.0, abs(ref))
+
+
+def test_gaussian_potential_converges_to_erf():
+    """A unit Gaussian charge has v = erf(sqrt(a) r)/r; the discrete solution
+    converges to it under p- and h-refinement."""
+    errs = {}
+    for (n, p) in [(4, 4), (4, 6), (4, 8), (8, 4)]:
+        m = oracle.Mesh([-8.0] * 3, [8.0] * 3, n, p)
+        x = oracle.node_coords(m)
+        v, _ = oracle.poisson(m, _unit_gaussian(x), method="fdm")
+        errs[(n, p)] = np.abs(v[0] - _erf_potential(x)).max()
+    assert errs[(4, 4)] > errs[(4, 6)] > errs[(4, 8)]
+    assert errs[(4, 4)] > 4 * errs[(8, 4)]
+    assert errs[(4, 8)] < 5e-3
+
+
+def test_hartree_self_energy_converges():
+    """(rho|rho) of a unit Gaussian of exponent a is sqrt(2a/pi)."""
+    ref = math.sqrt(2.0 * A_EXP / math.pi)
+    errs = []
+    for p in (4, 6, 8):
+        m = oracle.Mesh([-8.0] * 3, [8.0] * 3, 4, p)
+        x = oracle.node_coords(m)
+        f = _unit_gaussian(x)
+        v, _ = oracle.poisson(m, f, method="fdm")
+        errs.append(abs(np.sum(oracle.quad_weights(m) * f * v[0]) - ref))
+    assert errs[0] > 100 * errs[2]
+    assert errs[2] < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Exchange matrix and energies (Eq. 29, Sec. 2.3.1)
+# ---------------------------------------------------------------------------
+def _tiny_continuum():
+    """Free-space values for two normalised s-Gaussians (exponent 1) at
+    (+-0.7, 0, 0), from the Gaussian product theorem and the Coulomb energy of
+    two unit Gaussians, erf(sqrt(ab/(a+b)) R)/R."""
+    S = math.exp(-0.98)
+    i1111 = 2.0 / math.sqrt(math.pi)
+    i1212 = S * S * i1111
+    i1122 = math.erf(1.4) / 1.4
+    i1112 = S * math.erf(0.7) / 0.7
+    return {"K11": i1111 + i1212, "K12": 2.0 * i1112, "E_H": 0.5 * (2 * i1111 + 2 * i1122)}
+
+
+def test_tiny_system_converges_to_continuum():
+    ref = _tiny_continuum()
+    spec = inputs.tiny_system()
+    errs = []
+    for (n, p) in [(4, 4), (4, 6)]:
+        m = oracle.Mesh([-8.0] * 3, [8.0] * 3, n, p)
+        psi = inputs.orbitals(spec, oracle.node_coords(m))
+        r = oracle.exchange_build(m, psi, method="fdm")
+        errs.append(max(abs(r["K"][0, 0] - ref["K11"]), abs(r["K"][0, 1] - ref["K12"]), abs(r["E_H"] - ref["E_H"])))
+        assert abs(r["E_X"] + 0.5 * np.trace(r["K"])) < 1e-15
+    assert errs[0] > 10 * errs[1]
+    assert errs[1] < 5e-3
+
+
+def _small_system(seed=11, N=4):
+    m = oracle.Mesh([-6.0] * 3, [6.0] * 3, 2, 4)
+    atoms = np.array([[-1.0, 0.2, 0.0], [1.1, -0.3, 0.4], [0.0, 0.9, -0.8]])
+    spec = inputs.gto_system(inputs.MeshSpec(tuple(m.lo), tuple(m.hi), m.n, m.p), atoms, N, seed)
+    psi = inputs.orbitals(spec, oracle.node_coords(m), oracle.quad_weights(m))
+    return m, psi
+
+
+def test_exchange_matrix_symmetric_psd_and_rotation_invariant():
+    m, psi = _small_system()
+    r = oracle.exchange_build(m, psi, method="fdm")
+    K = r["K"]
+    nrm = np.abs(K).max()
+    # the Dirichlet lift makes K non-symmetric at discretisation level only
+    assert np.abs(K - K.T).max() < 1e-2 * nrm
+    assert np.linalg.eigvalsh(0.5 * (K + K.T)).min() > -1e-10 * nrm
+    # K_ii = sum_s (is|si) >= (ii|ii) > 0
+    Wq = oracle.quad_weights(m)
+    for i in range(psi.shape[0]):
+        v, _ = oracle.poisson(m, psi[i] * psi[i], method="fdm")
+        self_e = np.sum(Wq * psi[i] * psi[i] * v[0])
+        assert self_e > 0 and K[i, i] >= self_e - 1e-12
+    # orthogonal rotation of the orbitals: K -> Q K Q^T, energies unchanged
+    Q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((psi.shape[0],) * 2))
+    r2 = oracle.exchange_build(m, Q @ psi, method="fdm")
+    assert np.abs(r2["K"] - Q @ K @ Q.T).max() < 1e-11 * nrm
+    assert abs(r2["E_H"] - r["E_H"]) < 1e-11 * abs(r["E_H"])
+    assert abs(r2["E_X"] - r["E_X"]) < 1e-11 * abs(r["E_X"])
+
+
+def test_pair_list_order():
+    assert oracle.pair_list(3) == [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+    assert len(oracle.pair_list(64)) == 2080
