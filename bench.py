@@ -1,0 +1,419 @@
+"""Exchange-build benchmark: pair Poisson solves per second at a 1e-8 FP64
+true relative residual, the chosen form (mixed precision) against the plain
+FP64 form, on one synthetic Gaussian-orbital system per GPU.
+
+One step = one dg_exchange_build: the Hartree solve, the N(N+1)/2 pair solves
+(right-hand sides, Coulomb-quadrature Dirichlet data by the Gaussian-sum
+route, multigrid-preconditioned CG to 1e-8), the exchange accumulation, the K
+contraction and the energies. value = pair solves of all ranks / max-over-ranks
+time. Inputs (orbital values at the nodes) are resident in HBM for `value`;
+`e2e` copies them from pinned host memory every step and reads K back.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload chain10|mixed64|tiny] [--precision mixed|fp64]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "tiny": "tiny",
+    "chain10": "chain10",
+    "mixed64": "mixed64",
+}
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA throughput of a GB300 measured with the probe under
+# paper_2510_21213_gb300/csrc/peak_probe.cu (152 SMs, FP64 pipe)
+FP64_PEAK_TFLOPS = 1.20
+FP32_PEAK_TFLOPS = 73.3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chain10", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.samples.append([x.strip() for x in line.split(",")])
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[1]))
+                smax.append(float(s[2]))
+                for nm, v in zip(names, s[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(spec, xyz, w):
+    from paper_2510_21213_gb300 import inputs
+
+    return inputs.orbitals(spec, xyz, w)
+
+
+def system_for(workload, rank):
+    from paper_2510_21213_gb300 import inputs
+
+    if workload == "tiny":
+        return inputs.tiny_system()
+    if workload == "chain10":
+        return inputs.chain_system(seed=2 + 1000 * rank)
+    return inputs.random_system(seed=3 + 1000 * rank)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)
+
+
+def time_builds(solver, psi_dev, steps, warmup, torch, flush):
+    for _ in range(warmup):
+        solver.exchange_build(psi_dev)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush_l2(flush)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record()
+        K, eh, ex, stats = solver.exchange_build(psi_dev)
+        s1.record()
+        s1.synchronize()
+        times.append(s0.elapsed_time(s1))
+    return times, (K, eh, ex, stats)
+
+
+def kernel_roofline(solver, B, precision, torch, nrep=20):
+    """Average launch duration of the fine-level operator and smoother kernels
+    (CUDA events on the launching stream) and their algorithmic work."""
+    Nq = solver.Nq
+    n1 = solver.info.level_p[0] + 1
+    dt = torch.float32 if precision == "mixed" else torch.float64
+    u = torch.randn((B, Nq), dtype=dt, device="cuda")
+    out = torch.empty_like(u)
+    res = {}
+    for name, fn in (("apply", lambda: solver.apply(u)), ("smoother", lambda: solver.smoother(u))):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(nrep):
+            fn()
+        e1.record()
+        e1.synchronize()
+        res[name] = e0.elapsed_time(e1) / nrep
+    del out
+    E = Nq // n1 ** 3
+    # operator: 3 directions x (n1 diag-block MACs + 4 coupling MACs), 5 flops of
+    # mass scaling, traces 6 faces x n1^2 x 2 x n1 MACs per element
+    apply_flops = Nq * (3 * (2 * n1 + 8) + 5) + E * 6 * n1 * n1 * 2 * 2 * n1
+    m = n1 + 2
+    sm_flops = E * (6 * 2 * m ** 4 + m ** 3)
+    s = 4 if precision == "mixed" else 8
+    apply_bytes = 2 * Nq * s
+    sm_bytes = Nq * s + E * m ** 3 * s  # patch kernel: read r, write patch solution
+    return {
+        "apply_ms": res["apply"], "smoother_ms": res["smoother"], "B": B,
+        "apply_flops": apply_flops * B, "apply_bytes": apply_bytes * B,
+        "smoother_flops": sm_flops * B, "smoother_bytes": sm_bytes * B,
+    }
+
+
+def cpu_oracle_sample(spec, n_src=4, node_stride=8):
+    """The CPU oracle on a bounded sample of the same workload: the Coulomb
+    boundary sum of n_src pair sources over every node_stride-th boundary node
+    (extrapolated to all nodes), plus their exact FDM solves. Returns
+    (pairs_per_s, seconds, description)."""
+    import oracle
+
+    m = oracle.Mesh(spec.mesh.lo, spec.mesh.hi, spec.mesh.n, spec.mesh.p)
+    x = oracle.node_coords(m)
+    W = oracle.quad_weights(m)
+    psi = make_inputs(spec, x, W)
+    pairs = oracle.pair_list(psi.shape[0])[:n_src]
+    f = np.stack([psi[i] * psi[j] for i, j in pairs])
+    t0 = time.perf_counter()
+    oracle.boundary_data_direct(m, f, node_stride=node_stride)
+    t_bc = time.perf_counter() - t0
+    g0 = [np.zeros((len(pairs),) + pts.shape[:2]) for pts in oracle.boundary_face_nodes(m)]
+    t0 = time.perf_counter()
+    B = np.stack([oracle.rhs(m, f[k], [gg[k] for gg in g0]) for k in range(len(pairs))])
+    oracle.solve_fdm(m, B)
+    t_solve = time.perf_counter() - t0
+    total = t_bc * node_stride + t_solve
+    desc = (f"{len(pairs)} pair solves of the same workload: direct Coulomb boundary sum over 1/{node_stride} "
+            f"of the boundary nodes (time x{node_stride}) + exact fast-diagonalisation solves")
+    return len(pairs) / total, t_bc + t_solve, desc
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    spec = system_for(args.workload, 0)
+    P = spec.N * (spec.N + 1) // 2
+    times, rates = [], []
+    desc = ""
+    for it in range(args.warmup + args.steps):
+        rate, secs, desc = cpu_oracle_sample(spec)
+        if it >= args.warmup:
+            times.append(secs)
+            rates.append(rate)
+    value = float(np.mean(rates))
+    line = {
+        "impl": "reference", "metric": "exchange-build pair Poisson solves/s at 1e-8 residual",
+        "value": value, "unit": "pair_solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": P / value * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: n={spec.mesh.n[0]}^3 p={spec.mesh.p} N={spec.N} pairs={P}"},
+        "cpu_baseline": {"value": value, "unit": "pair_solves/s", "cores": cores(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "pair_solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2510_21213_gb300 import build, dgx
+
+    build.build()
+    spec = system_for(args.workload, rank)
+    m = spec.mesh
+    N = spec.N
+    P = N * (N + 1) // 2
+    prec = dgx.DG_PREC_MIXED if args.precision == "mixed" else dgx.DG_PREC_FP64
+    solver = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=prec, rtol=1e-8)
+    xyz, w = solver.node_coords()
+    psi_host = make_inputs(spec, xyz, w)
+    psi_dev = torch.tensor(psi_host, device="cuda")
+    flush = torch.empty(int(256 * 2 ** 20 / 4), dtype=torch.float32, device="cuda")  # 256 MB > L2 (126 MB)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # timed region (device-resident inputs)
+    for _ in range(args.warmup):
+        solver.exchange_build(psi_dev)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = dgx.dg_kernel_launch_count()
+    times = []
+    for _ in range(args.steps):
+        flush_l2(flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        K, eh, ex, stats = solver.exchange_build(psi_dev)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = (dgx.dg_kernel_launch_count() - l0) // args.steps
+    clocks = clk.stop()
+    barrier()
+    tot = sum(times) / 1e3
+    if ws > 1:
+        t = torch.tensor([tot], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot = float(t.item())
+    value = ws * P * args.steps / tot
+    iters = [s["iters"] for s in stats[1:]]
+    resid = max(s["rel_residual"] for s in stats)
+    status_ok = all(s["status"] == 0 for s in stats)
+
+    # end to end through the public API: pinned host inputs copied in every step, K read back
+    pin = torch.tensor(psi_host).pin_memory()
+    dev_buf = torch.empty_like(psi_dev)
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush_l2(flush)
+        t0.record()
+        dev_buf.copy_(pin, non_blocking=True)
+        solver.exchange_build(dev_buf)
+        t1.record()
+        t1.synchronize()
+        e2e_times.append(t0.elapsed_time(t1))
+    e2e_tot = sum(e2e_times) / 1e3
+    if ws > 1:
+        t = torch.tensor([e2e_tot], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = ws * P * args.steps / e2e_tot
+
+    # plain FP64 form on the same system (the metric's comparison)
+    plain = None
+    if not args.no_plain and prec != dgx.DG_PREC_FP64:
+        solver64 = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=dgx.DG_PREC_FP64, rtol=1e-8)
+        ptimes, (K64, eh64, ex64, st64) = time_builds(solver64, psi_dev, max(1, min(args.steps, 3)), 1, torch, flush)
+        ptot = sum(ptimes) / 1e3
+        if ws > 1:
+            t = torch.tensor([ptot], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ptot = float(t.item())
+        plain = {"value": ws * P * len(ptimes) / ptot, "ms_per_step": ptot / len(ptimes) * 1e3,
+                 "mean_iters": float(np.mean([s["iters"] for s in st64[1:]])),
+                 "K_rel_diff_vs_chosen": float(np.abs(K64 - K).max() / np.abs(K64).max()),
+                 "E_X_rel_diff_vs_chosen": abs(ex64 - ex) / abs(ex64)}
+        solver64.close()
+
+    # roofline of the dominant kernel (the smoother patch solve; see profiles/)
+    B = min(P + 1, 64)
+    rf = kernel_roofline(solver, B, args.precision, torch)
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    alu_peak = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
+    sm_tf = rf["smoother_flops"] / (rf["smoother_ms"] * 1e-3) / 1e12
+    sm_gbs = rf["smoother_bytes"] / (rf["smoother_ms"] * 1e-3) / 1e9
+    ap_tf = rf["apply_flops"] / (rf["apply_ms"] * 1e-3) / 1e12
+    ap_gbs = rf["apply_bytes"] / (rf["apply_ms"] * 1e-3) / 1e9
+    roofline = {
+        "kernel": "k_schwarz_patch (fine-level smoother patch solve) + k_schwarz_gather",
+        "bound": "alu", "achieved": sm_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": sm_tf / alu_peak,
+        "traffic": None,
+        "peak_source": ("FP32 FMA probe (paper_2510_21213_gb300/csrc/peak_probe.cu)" if args.precision == "mixed"
+                        else "FP64 FMA probe (paper_2510_21213_gb300/csrc/peak_probe.cu)"),
+        "launch_ms": rf["smoother_ms"], "B": B, "hbm_gbs": sm_gbs, "hbm_frac_of_measured": sm_gbs / hbm,
+        "operator": {"launch_ms": rf["apply_ms"], "tflops": ap_tf, "frac_alu": ap_tf / alu_peak,
+                     "gbs": ap_gbs, "frac_hbm_of_measured": ap_gbs / hbm},
+    }
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, secs, desc = cpu_oracle_sample(spec)
+        cpu = {"value": rate, "unit": "pair_solves/s", "cores": cores(), "kind": "oracle", "sample": desc,
+               "seconds": secs}
+
+    if rank == 0:
+        line = {
+            "metric": "exchange-build pair Poisson solves/s at 1e-8 residual",
+            "value": value, "unit": "pair_solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: box [-12,12]^3, n={m.n[0]}^3 elements, p={m.p}, "
+                                   f"N={N} orbitals, {P} pair solves + Hartree per step",
+                       "precision": args.precision, "rtol": 1e-8, "l2": "flushed (256 MB write) between steps",
+                       "parallelism": f"independent system per GPU x{ws}"},
+            "e2e": {"value": e2e_value, "unit": "pair_solves/s", "h2d_bytes_per_step": int(psi_host.nbytes),
+                    "d2h_bytes_per_step": int(N * N * 8 + 16)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "plain_fp64": plain,
+            "solver": {"mean_iters": float(np.mean(iters)), "max_iters": int(max(iters)),
+                       "max_rel_residual": resid, "all_converged": status_ok,
+                       "outer_refinements": int(max(s["outer_refinements"] for s in stats)),
+                       "E_H": eh, "E_X": ex},
+        }
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as fh:
+                fh.write(s + "\n")
+    solver.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

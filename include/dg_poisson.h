@@ -1,0 +1,218 @@
+/*
+ * dg_poisson.h -- C ABI of the GB300 library for the exchange-build hot path of
+ * the discontinuous-Galerkin Hartree-Fock method of arXiv 2510.21213
+ * ("Fast adaptive discontinuous basis sets for electronic structure").
+ *
+ * What the library computes (citations are to the paper):
+ *
+ *   For every source f given at the Gauss-Legendre nodes of a uniform box mesh
+ *   of degree-p nodal elements (Sec. 6.2, eq. density_approx; the nodes double
+ *   as the quadrature rule), the solution v of the SIPDG-discretised Poisson problem
+ *       -Lap v = 4 pi f  in Omega,
+ *        v(r)  = int_Omega f(r') / |r - r'| dr'   on the boundary of Omega
+ *   (Sec. 6.3; the boundary integral is the grid's Gauss quadrature), with the
+ *   SIPDG bilinear form of Sec. 3.4 (eq. sip_bilinear) and the penalty of
+ *   Sec. 3.5 (eqs. Cprop, Csquared, pen_poly), solved by conjugate gradients
+ *   preconditioned with hp-multigrid: polynomial coarsening to degree 1, then
+ *   geometric coarsening on the nested hierarchy (Sec. 6.4).
+ *
+ *   dg_exchange_build applies this to the Hartree density rho = sum_k psi_k^2
+ *   (Sec. 2.3.1 eq. HF; Sec. 6.1.1 eq. hartree_poisson) and to every occupied
+ *   pair density psi_i psi_j (Sec. 6.1.2 eq. fock_poisson), then contracts
+ *   K_ij = sum_q W_q psi_i(q) sum_s psi_s(q) v_sj(q) on the quadrature grid
+ *   (eq. fock_exchange with phi_i -> psi_i, u -> psi_j), and returns
+ *   E_H = 1/2 sum_q W_q rho v_H and E_X = -1/2 tr K (HF energy, Sec. 2.3.1).
+ *
+ * Readings of points the paper leaves open (same in every entry point):
+ *   - Dirichlet data are imposed weakly by symmetric Nitsche terms
+ *     -u d_n v - d_n u v + sigma u v on boundary faces (paper: "inhomogeneous
+ *     Dirichlet", weak form unstated).
+ *   - sigma = (p+1)^2 / (eps h) (penalty_form 0) or the literal
+ *     (p+1)^2 / (eps h^2) (penalty_form 1); eps = 1/8 by default (Sec. 3.5).
+ *   - Each distinct pair (i <= j) is solved once, v_ij = v_ji.
+ *
+ * Layouts. All node-valued arrays are element-blocked: element index
+ * e = ex + nx*(ey + ny*ez), and inside an element the (p+1)^3 nodes are
+ * lexicographic, x fastest: local = a + (p+1)*(b + (p+1)*c). A field occupies
+ * Nq = nx*ny*nz*(p+1)^3 contiguous doubles; a batch of fields is [B][Nq].
+ * Orbital pairs are ordered upper-triangular row-major: (0,0),(0,1),...,(0,N-1),
+ * (1,1),...
+ *
+ * Ownership. The caller owns every input and output buffer. "dev" pointers are
+ * CUDA device memory of the current device, "host" pointers are host memory.
+ * The handle owns all workspace; it is allocated in dg_poisson_setup and grown
+ * (never shrunk) the first time a larger batch is solved.
+ *
+ * Errors. Every int-returning call returns DG_OK (0) or a negative DG_ERR_*
+ * code; no exception crosses the ABI. dg_error_string maps a code to text.
+ * dg_last_error_detail(h) returns a message for the last failure on a handle.
+ *
+ * Concurrency. One handle per stream; calls on a handle are stream-ordered and
+ * synchronise that stream before returning (results that land in host memory
+ * are complete on return).
+ */
+#ifndef DG_POISSON_H
+#define DG_POISSON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_ERR_INVALID_ARG (-1)
+#define DG_ERR_CUDA (-2)
+#define DG_ERR_NOT_CONVERGED (-3)
+#define DG_ERR_BREAKDOWN (-4)
+#define DG_ERR_NONFINITE (-5)
+#define DG_ERR_TIMEOUT (-6)
+#define DG_ERR_NO_MEMORY (-7)
+#define DG_ERR_UNSUPPORTED (-8)
+
+/* precision modes */
+#define DG_PREC_FP64 0  /* every step in FP64 */
+#define DG_PREC_MIXED 1 /* FP32 inner multigrid-PCG, FP64 dots, residuals and refinement */
+#define DG_PREC_MIXED_LEARNED 2 /* as MIXED, initial guess and coarse correction from a network */
+
+/* boundary-data routes */
+#define DG_BC_DIRECT 0   /* direct Gauss-quadrature Coulomb sum (the definition, Sec. 6.3) */
+#define DG_BC_GAUSSSUM 1 /* separable sum-of-Gaussians 1/r (Sec. 5.2) evaluated on the faces */
+
+/* multigrid smoothers (the paper names none; Sec. 6.4 gives only the hierarchy) */
+#define DG_SMOOTH_JACOBI 0  /* point Jacobi */
+#define DG_SMOOTH_SCHWARZ 1 /* additive Schwarz on element patches with one node of overlap, exact
+                               patch solves by fast diagonalisation */
+
+/* Uniform hexahedral box mesh: box [lo, hi], n[d] elements along axis d,
+ * tensor Gauss-Legendre nodal elements of degree p (1 <= p <= 8). */
+typedef struct {
+  double lo[3];
+  double hi[3];
+  int32_t n[3];
+  int32_t p;
+} dg_mesh_desc;
+
+typedef struct {
+  int32_t precision;     /* DG_PREC_* */
+  double rtol;           /* target FP64 true relative residual ||b - A v||_2 / ||b||_2 */
+  int32_t max_iter;      /* PCG iteration cap (per source, summed over refinements) */
+  double penalty_eps;    /* eps of Sec. 3.5 (default 1/8) */
+  int32_t penalty_form;  /* 0: (p+1)^2/(eps h); 1: (p+1)^2/(eps h^2) */
+  int32_t bc_route;      /* DG_BC_* */
+  double bc_tol;         /* relative accuracy of the Gaussian-sum 1/r (0 = precision default) */
+  int32_t batch;         /* sources solved together (0 = library default) */
+  int32_t smoother;      /* DG_SMOOTH_*: preconditioner inside the Chebyshev smoother */
+  int32_t smoother_degree; /* Chebyshev degree of the multigrid smoother (default 3) */
+  double cheb_range;     /* smoothing range lambda_max / lambda_min of the Chebyshev interval (default 10) */
+  double inner_rtol;     /* MIXED: relative reduction of each FP32 inner solve (default 1e-4) */
+  const char* nn_weights_path; /* MIXED_LEARNED: network weights file (NULL = none) */
+  int32_t verbose;       /* 0 silent, 1 per-solve summary on stderr */
+} dg_solver_opts;
+
+typedef struct {
+  int32_t iters;             /* PCG iterations (inner iterations in MIXED modes) */
+  int32_t outer_refinements; /* FP64 refinement steps (0 in FP64 mode) */
+  int32_t status;            /* DG_OK, DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN or DG_ERR_NONFINITE */
+  int32_t used_fallback;     /* 1 if a learned guess was rejected and the plain solver used */
+  double rel_residual;       /* final FP64 true relative residual */
+} dg_solve_stats;
+
+typedef struct {
+  int64_t Nq;          /* nodes (= unknowns) of the fine level */
+  int32_t levels;      /* multigrid levels, fine to coarsest */
+  int32_t level_n[16]; /* elements per axis (x) of each level */
+  int32_t level_p[16]; /* degree of each level */
+  int32_t coarse_dofs; /* unknowns of the coarsest (directly solved) level */
+  int32_t n_gauss;     /* terms of the Gaussian-sum 1/r used for boundary data */
+  double gauss_rmin, gauss_rmax; /* distance range on which that sum is accurate */
+  double gauss_relerr; /* measured max relative error of the sum on that range */
+  double sigma[3];     /* fine-level penalty per axis */
+  int64_t workspace_bytes; /* device workspace currently held by the handle */
+} dg_info;
+
+typedef struct dg_ctx* dg_handle;
+
+/* Fills *opts with defaults: FP64, rtol 1e-8, max_iter 500, eps 1/8,
+ * penalty_form 0, Gaussian-sum boundary data, Schwarz smoother, Chebyshev
+ * degree 3 over a smoothing range of 10. */
+void dg_default_opts(dg_solver_opts* opts);
+
+/* Builds the level hierarchy, 1-D operator tables, Chebyshev bounds, the
+ * coarsest-level inverse and the boundary-data tables (step S0); copies them
+ * to the device. mesh, opts: host structs, read only. *out receives a handle
+ * to be released with dg_destroy. Errors: DG_ERR_INVALID_ARG for p outside
+ * 1..8, non-positive sizes or an empty box; DG_ERR_UNSUPPORTED if the coarsest
+ * level would exceed 4096 unknowns; DG_ERR_CUDA / DG_ERR_NO_MEMORY. */
+int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_handle* out);
+
+/* Properties of a handle. info: host. */
+int dg_get_info(dg_handle h, dg_info* info);
+
+/* Node coordinates [Nq][3] and quadrature weights W_q [Nq] of the fine level
+ * in the element-blocked order (host buffers, caller-allocated). Either
+ * pointer may be NULL. */
+int dg_node_coords(dg_handle h, double* xyz_host, double* w_host);
+
+/* Solves -Lap v_b = 4 pi f_b with Coulomb-quadrature Dirichlet data for B
+ * sources (steps S1-S4 and S10 for a batch). f_dev: [B][Nq] source values at
+ * the nodes (device, read only). v_dev: [B][Nq] solutions (device, written).
+ * stats_host: [B] per-source statistics (host, may be NULL). cuda_stream: a
+ * cudaStream_t (NULL = default stream). Returns DG_OK when every source
+ * reached rtol; otherwise the worst per-source status (a non-converged source
+ * still returns its best iterate). DG_ERR_NONFINITE if a source is not finite
+ * (its v is set to zero). */
+int dg_pair_solve_batch(dg_handle h, const double* f_dev, int64_t B, double* v_dev,
+                        dg_solve_stats* stats_host, void* cuda_stream);
+
+/* Exchange build for N orbitals psi_dev [N][Nq] (device, read only): the
+ * Hartree solve, the N(N+1)/2 pair solves, the accumulation
+ * W_j = sum_s psi_s v_sj, K = Psi^T diag(W_q) W and the energies.
+ * K_host: [N*N] row-major K_ij (host). E_H, E_X: host scalars (may be NULL).
+ * stats_host: [N(N+1)/2 + 1] (host, may be NULL): entry 0 is the Hartree
+ * solve, then the pairs in the documented order. */
+int dg_exchange_build(dg_handle h, const double* psi_dev, int32_t N, double* K_host, double* E_H,
+                      double* E_X, dg_solve_stats* stats_host, void* cuda_stream);
+
+/* Matrix-free SIPDG operator of multigrid level `level` (0 = fine) applied to
+ * B fields: out = A u. u_dev, out_dev: [B][Nq_level] device arrays of the
+ * handle's working precision for that call: FP64 when fp32 == 0, FP32 when
+ * fp32 == 1. Exposed for tests and for timing the operator kernel alone. */
+int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u_dev, void* out_dev,
+                      int64_t B, void* cuda_stream);
+
+/* Preconditioner of the multigrid smoother of level `level` applied to B
+ * fields: z = M r with M the additive Schwarz operator sum_P R_P^T A_P^-1 R_P
+ * (DG_SMOOTH_SCHWARZ) or D^-1 (DG_SMOOTH_JACOBI); on the coarsest level M is
+ * the exact inverse A_c^-1. r_dev, z_dev: [B][Nq_level] device arrays, FP64
+ * (fp32 == 0) or FP32 (fp32 == 1). Exposed for tests and kernel timing. */
+int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r_dev, void* z_dev, int64_t B,
+                      void* cuda_stream);
+
+/* Boundary data g of Sec. 6.3 for B sources f_dev [B][Nq] (device): g_dev
+ * [B][n_face_nodes] (device, FP64), faces in the order -x,+x,-y,+y,-z,+z, each
+ * face a 2-D grid of its two tangential global node indices with the lower
+ * axis fastest. route: DG_BC_*. Returns the total face-node count in
+ * *n_face_nodes when g_dev is NULL. */
+int dg_boundary_data(dg_handle h, int32_t route, const double* f_dev, int64_t B, double* g_dev,
+                     int64_t* n_face_nodes, void* cuda_stream);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * since it was loaded (all handles, all streams). For profiling and for
+ * benchmarks that report how many of the library's kernels ran. */
+int64_t dg_kernel_launch_count(void);
+
+/* Releases the handle and all device memory it owns. NULL is ignored. */
+void dg_destroy(dg_handle h);
+
+/* Static text for a DG_* code. */
+const char* dg_error_string(int status);
+
+/* Message describing the last failure on h (empty string if none). */
+const char* dg_last_error_detail(dg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_POISSON_H */

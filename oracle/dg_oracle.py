@@ -6,29 +6,29 @@ TEST INFRASTRUCTURE ONLY -- never imported by the product path.
 What is restated here, and from where (arXiv 2510.21213):
 
 * Degree-q nodal Lagrange basis on the tensor Gauss-Legendre points of each
-  element; the same points define the quadrature rule (Sec. 5.2, Eq. 32
-  "density_approx"; Sec. 5.3).
-* SIPDG bilinear form, Eq. 19 ("sip_bilinear"): element volume gradients plus,
+  element; the same points define the quadrature rule (Sec. 6.2, eq.
+  density_approx; Sec. 6.3).
+* SIPDG bilinear form, Sec. 3.4 eq. sip_bilinear: element volume gradients plus,
   on every interior face, -[[u]].{grad v} - {grad u}.[[v]] + sigma [[u]].[[v]],
   with the jump [[f]] = f^- n^- + f^+ n^+ and average {f} = (f^- + f^+)/2 of
   Sec. 3.1.
-* Penalty sigma from Sec. 3.4 (Eqs. 20-22, "pen_poly"). The paper's units are
+* Penalty sigma from Sec. 3.5 (eqs. Cprop, Csquared, pen_poly). The paper's units are
   inconsistent (sigma >= C^2/(eps h) with C^2 = (p+1)^2/h); form 0 reads it as
   sigma = (p+1)^2/(eps h), form 1 keeps the literal (p+1)^2/(eps h^2).
-  eps = 1/8 as in Sec. 3.4.
+  eps = 1/8 as in Sec. 3.5.
 * Poisson problem -Lap u = 4 pi f in Omega with the inhomogeneous Dirichlet
   data u(r) = int_Omega f(r')/|r - r'| dr' on the boundary, evaluated with the
-  grid's Gauss quadrature (Sec. 5.3, Eqs. 33-34). The paper does not state the
+  grid's Gauss quadrature (Sec. 6.3). The paper does not state the
   weak form of the Dirichlet condition; the symmetric Nitsche terms
   -u d_n v - d_n u v + sigma u v on boundary faces (and the matching load
   sigma g v - g d_n v) are used, i.e. the boundary face is treated as a face
   whose exterior trace is zero.
-* Right-hand sides evaluated pointwise at the quadrature nodes (Sec. 5.1.2):
-  f = psi_i psi_j for the exchange problems (Eq. 30 "fock_poisson"),
-  f = rho = sum_k psi_k^2 for the Hartree problem (Eq. 27 "hartree_poisson",
-  with rho from Eq. 2).
-* K_ij = sum_q W_q psi_i(q) sum_s psi_s(q) v_sj(q) from Eq. 29
-  ("fock_exchange") with phi_i -> psi_i and u -> psi_j, each distinct pair
+* Right-hand sides evaluated pointwise at the quadrature nodes (Sec. 6.1.2):
+  f = psi_i psi_j for the exchange problems (eq. fock_poisson),
+  f = rho = sum_k psi_k^2 for the Hartree problem (eq. hartree_poisson,
+  with rho from eq. HF in Sec. 2.3.1).
+* K_ij = sum_q W_q psi_i(q) sum_s psi_s(q) v_sj(q) from eq. fock_exchange
+  (Sec. 6.1.2) with phi_i -> psi_i and u -> psi_j, each distinct pair
   solved once (v_sj = v_js).
 * E_H = 1/2 sum_q W_q rho v_H and E_X = -1/2 tr K (HF energy, Sec. 2.3.1).
 
@@ -119,7 +119,7 @@ def lagrange_eval(nodes, x):
 
 
 def penalty(p, h, form=0, eps=0.125):
-    """Face penalty sigma (Sec. 3.4, Eq. 22). form 0: (p+1)^2/(eps h); 1: (p+1)^2/(eps h^2)."""
+    """Face penalty sigma (Sec. 3.5, eq. pen_poly). form 0: (p+1)^2/(eps h); 1: (p+1)^2/(eps h^2)."""
     if form == 0:
         return (p + 1) ** 2 / (eps * h)
     if form == 1:
@@ -229,7 +229,7 @@ def level_sigmas(mesh, penalty_form=0, eps=0.125):
 
 def assemble_kron(mesh, penalty_form=0, eps=0.125):
     """3-D SIPDG matrix as the Kronecker sum Ax(x)My(x)Mz + Mx(x)Ay(x)Mz + Mx(x)My(x)Az
-    (the tensor-product reduction of Sec. 3.4), returned in element-blocked order
+    (the tensor-product reduction of Sec. 3.5), returned in element-blocked order
     as a scipy CSR matrix."""
     sig = level_sigmas(mesh, penalty_form, eps)
     A1, M1 = [], []
@@ -249,7 +249,7 @@ def _basis_1d_tables(xi, pts):
 
 
 def assemble_dense(mesh, penalty_form=0, eps=0.125, nq_extra=2):
-    """3-D SIPDG matrix assembled directly from Eq. 19 with explicit 3-D
+    """3-D SIPDG matrix assembled directly from eq. sip_bilinear with explicit 3-D
     gradients, normals, jumps and averages, element by element and face by
     face, using Gauss rules of p+1+nq_extra points. Tiny meshes only."""
     n1, p = mesh.n1, mesh.p
@@ -362,11 +362,14 @@ def boundary_face_nodes(mesh):
     return out
 
 
-def boundary_data_direct(mesh, f, chunk=64):
-    """Dirichlet data of Sec. 5.3, Eq. 34: g(x_b) = sum_q W_q f(x_q)/|x_b - x_q|
+def boundary_data_direct(mesh, f, chunk=64, node_stride=1):
+    """Dirichlet data of Sec. 6.3: g(x_b) = sum_q W_q f(x_q)/|x_b - x_q|
     at every boundary face node, by direct Gauss quadrature.
 
     f: [Nq] or [nf, Nq]. Returns a list of 6 arrays [nf, T1, T2] (or [T1, T2]).
+    node_stride > 1 evaluates only every node_stride-th node of each face
+    (flattened order) and returns flat arrays [nf, n_eval]; used to time a
+    bounded sample of the full evaluation.
     """
     f = np.asarray(f, dtype=np.float64)
     single = f.ndim == 1
@@ -376,6 +379,9 @@ def boundary_data_direct(mesh, f, chunk=64):
     for pts in boundary_face_nodes(mesh):
         shp = pts.shape[:2]
         P = pts.reshape(-1, 3)
+        if node_stride > 1:
+            P = P[::node_stride]
+            shp = (P.shape[0],)
         g = np.zeros((P.shape[0], F.shape[1]))
         for s in range(0, P.shape[0], chunk):
             blk = P[s:s + chunk]

@@ -1,0 +1,209 @@
+// Dirichlet data of the auxiliary-grid Poisson problems (Sec. 6.3):
+//     g(x_b) = sum_q W_q f(x_q) / |x_b - x_q|
+// at every Gauss-Legendre node of the six boundary faces.
+//
+// Route DIRECT evaluates that sum as written (FP64, O(N_faces N_q) per source).
+// Route GAUSSSUM replaces 1/r by sum_k c_k exp(-alpha_k r^2) (the separable
+// Gaussian-sum approximation of Sec. 5.2), so that, on the tensor grid of
+// nodes, the sum for the faces normal to axis d factorises into three 1-D
+// contractions per term: along d with the face position, then along the two
+// tangential axes. Those contractions run as strided batched GEMMs (k_gemm).
+#include "dg_internal.h"
+
+namespace dg {
+
+// Flex[src][X + Lx (Y + Ly Z)] = W_q f_src(q): element-blocked -> global lexicographic.
+__global__ void k_weighted_lex(const LevelOp* __restrict__ op, const double* __restrict__ f,
+                               const double* __restrict__ W, double* __restrict__ flex) {
+  const long long Nq = op->Nq;
+  const int n1 = op->n1, npe = n1 * n1 * n1;
+  const int nx = op->n[0], ny = op->n[1];
+  const long long Lx = (long long)nx * n1, Ly = (long long)ny * n1;
+  const long long src = blockIdx.y;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Nq; q += (long long)gridDim.x * blockDim.x) {
+    const int e = (int)(q / npe), loc = (int)(q % npe);
+    const int a = loc % n1, b = (loc / n1) % n1, c = loc / (n1 * n1);
+    const long long X = (long long)(e % nx) * n1 + a;
+    const long long Y = (long long)((e / nx) % ny) * n1 + b;
+    const long long Z = (long long)(e / (nx * ny)) * n1 + c;
+    flex[src * Nq + X + Lx * (Y + Ly * Z)] = W[q] * f[src * Nq + q];
+  }
+}
+
+cudaError_t launch_weighted_lex(const LevelOp& hop, const LevelOp* dop, const double* f, const double* W,
+                                double* flex, int nsrc, cudaStream_t s) {
+  if (nsrc == 0) return cudaSuccess;
+  long long gx = (hop.Nq + 1023) / 1024;
+  if (gx > 4096) gx = 4096;
+  count_launch();
+  k_weighted_lex<<<dim3((unsigned)gx, nsrc), 256, 0, s>>>(dop, f, W, flex);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Strided batched GEMM: C[m,n] = alpha sum_k A[m,k] B[k,n] + beta C[m,n]
+// with arbitrary element strides and a two-level batch index.
+// 64 x 64 output tile, K step 16, 256 threads with 4 x 4 outputs each.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int batch_base) {
+  __shared__ T sA[16][64 + 1];
+  __shared__ T sB[16][64 + 1];
+  const int bz = batch_base + blockIdx.z;
+  const int b1 = bz / g.nb2, b2 = bz % g.nb2;
+  const T* A = (const T*)g.A + b1 * g.sA1 + b2 * g.sA2;
+  const T* B = (const T*)g.B + b1 * g.sB1 + b2 * g.sB2;
+  T* C = (T*)g.C + b1 * g.sC1 + b2 * g.sC2;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const bool a_k_fast = g.sAk == 1;
+  const bool b_n_fast = g.sBn == 1;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+  for (int k0 = 0; k0 < g.K; k0 += 16) {
+    for (int t = tid; t < 64 * 16; t += 256) {
+      int kk, mm;
+      if (a_k_fast) {
+        kk = t % 16;
+        mm = t / 16;
+      } else {
+        mm = t % 64;
+        kk = t / 64;
+      }
+      const int m = m0 + mm, k = k0 + kk;
+      sA[kk][mm] = (m < g.M && k < g.K) ? A[(long long)m * g.sAm + (long long)k * g.sAk] : (T)0;
+      int nn, kb;
+      if (b_n_fast) {
+        nn = t % 64;
+        kb = t / 64;
+      } else {
+        kb = t % 16;
+        nn = t / 16;
+      }
+      const int n = n0 + nn, kx = k0 + kb;
+      sB[kb][nn] = (n < g.N && kx < g.K) ? B[(long long)kx * g.sBk + (long long)n * g.sBn] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  const T alpha = (T)g.alpha, beta = (T)g.beta;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= g.N) continue;
+      T* cp = C + (long long)m * g.sCm + (long long)n * g.sCn;
+      *cp = g.beta != 0.0 ? alpha * acc[i][j] + beta * (*cp) : alpha * acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0 || g.nb1 * (long long)g.nb2 <= 0) return cudaSuccess;
+  const long long nb = (long long)g.nb1 * g.nb2;
+  const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, 1);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
+  for (long long base = 0; base < nb; base += 65535) {
+    const long long cnt = nb - base < 65535 ? nb - base : 65535;
+    count_launch();
+    k_gemm<T><<<dim3(grid.x, grid.y, (unsigned)cnt), 256, 0, s>>>(g, (int)base);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_gemm<double>(const GemmArgs&, cudaStream_t);
+template cudaError_t launch_gemm<float>(const GemmArgs&, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Direct quadrature: one thread per face node, all volume nodes in tiles.
+// ---------------------------------------------------------------------------
+static constexpr int BCT = 128;
+
+__global__ void __launch_bounds__(BCT) k_bc_direct(const LevelOp* __restrict__ op, const double* __restrict__ f,
+                                                   const double* __restrict__ W, const double* __restrict__ xq,
+                                                   const double* __restrict__ axn, int lmax,
+                                                   double* __restrict__ g, long long gstride, long long nface) {
+  __shared__ double sx[BCT], sy[BCT], sz[BCT], sf[BCT];
+  const long long src = blockIdx.y;
+  const long long Nq = op->Nq;
+  const int n1 = op->n1;
+  const long long t = (long long)blockIdx.x * BCT + threadIdx.x;
+  // locate the face node
+  double bx = 0, by = 0, bz = 0;
+  if (t < nface) {
+    long long rem = t;
+    for (int d = 0; d < 3; ++d) {
+      const int t1ax = d == 0 ? 1 : 0, t2ax = d == 2 ? 1 : 2;
+      const long long L1 = (long long)op->n[t1ax] * n1, L2 = (long long)op->n[t2ax] * n1;
+      for (int side = 0; side < 2; ++side) {
+        if (rem >= 0 && rem < L1 * L2) {
+          double c[3];
+          c[d] = side == 0 ? op->ax[d].lo : op->ax[d].hi;
+          c[t1ax] = axn[t1ax * lmax + (rem % L1)];
+          c[t2ax] = axn[t2ax * lmax + (rem / L1)];
+          bx = c[0];
+          by = c[1];
+          bz = c[2];
+        }
+        rem -= L1 * L2;
+      }
+    }
+  }
+  double acc = 0.0;
+  for (long long q0 = 0; q0 < Nq; q0 += BCT) {
+    const long long q = q0 + threadIdx.x;
+    __syncthreads();
+    if (q < Nq) {
+      sx[threadIdx.x] = xq[3 * q];
+      sy[threadIdx.x] = xq[3 * q + 1];
+      sz[threadIdx.x] = xq[3 * q + 2];
+      sf[threadIdx.x] = W[q] * f[src * Nq + q];
+    } else {
+      sx[threadIdx.x] = 1e300;
+      sy[threadIdx.x] = 0.0;
+      sz[threadIdx.x] = 0.0;
+      sf[threadIdx.x] = 0.0;
+    }
+    __syncthreads();
+    if (t < nface) {
+#pragma unroll 4
+      for (int j = 0; j < BCT; ++j) {
+        const double dx = bx - sx[j], dy = by - sy[j], dz = bz - sz[j];
+        acc += sf[j] / sqrt(dx * dx + dy * dy + dz * dz);
+      }
+    }
+  }
+  if (t < nface) g[src * gstride + t] = acc;
+}
+
+cudaError_t launch_bc_direct(const LevelOp& hop, const LevelOp* dop, const double* f, const double* W,
+                             const double* xq, const double* axis_nodes, int lmax, double* g, int nsrc,
+                             long long gstride, long long nface, cudaStream_t s) {
+  if (nsrc == 0) return cudaSuccess;
+  (void)hop;
+  count_launch();
+  k_bc_direct<<<dim3((unsigned)((nface + BCT - 1) / BCT), nsrc), BCT, 0, s>>>(dop, f, W, xq, axis_nodes, lmax, g,
+                                                                           gstride, nface);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -1,0 +1,1235 @@
+// Host driver and C ABI: hp-multigrid-preconditioned CG (Sec. 6.4) over a
+// batch of sources, Dirichlet data (Sec. 6.3), the exchange build
+// (Sec. 6.1.2, eq. fock_exchange) and the entry points of dg_poisson.h.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dg_setup.h"
+
+namespace dg {
+
+// ---------------------------------------------------------------------------
+// device buffer helper
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = b;
+    return cudaSuccess;
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+// per-level multigrid workspace of one precision
+struct LevelWork {
+  DevBuf x, b, res, d, invD, z, zp;
+};
+
+template <typename T>
+struct PrecWork {
+  std::vector<LevelWork> lev;            // per level (level 0: res, d, invD only)
+  DevBuf x, r, z, p, q;                  // CG vectors on the fine level
+  int cap = 0;
+};
+
+struct Level {
+  LevelOp op;
+  LevelOp* dop = nullptr;
+  TransferOp tr;                 // to the next coarser level
+  TransferOp* dtr = nullptr;
+  double lam_max = 0;            // lambda_max(D^-1 A) (point Jacobi)
+  double lam_sw = 0;             // lambda_max(M_S A) estimate (Schwarz)
+  DevBuf sw_tabs;                // Schwarz patch tables
+};
+
+struct BcAxisTables {
+  int L = 0;
+  DevBuf gn;   // [2][NG][L]       exp(-a_k (x_X - face_s)^2)
+  DevBuf G;    // [NG][L][L]       exp(-a_k (x_i - x_j)^2)
+  DevBuf Gs;   // [L][NG * L]      c_k exp(-a_k (x_i - x_j)^2)
+};
+
+}  // namespace dg
+
+struct dg_ctx {
+  dg_mesh_desc mesh;
+  dg_solver_opts opts;
+  std::vector<dg::Level> levels;
+  int nlev = 0;
+  // coarsest level
+  int Nc = 0;
+  dg::DevBuf coarse_inv;
+  // fine-level geometry
+  long long Nq = 0;
+  std::vector<double> axis_nodes[3];
+  dg::DevBuf d_W, d_xq, d_axn;
+  int lmax = 0;
+  long long nface = 0;
+  // boundary-data tables
+  dg::GaussSum gsum;
+  int NG = 0;
+  dg::BcAxisTables bct[3];
+  // workspaces
+  dg::PrecWork<double> w64;
+  dg::PrecWork<float> w32;
+  dg::DevBuf f64, b64, x64, r64;   // [cap][Nq]
+  dg::DevBuf flex, T1, T2, g;      // boundary data
+  dg::DevBuf part, scal, act, flags, pidx;
+  dg::DevBuf Wacc, kpart, Kdev;
+  int cap = 0;
+  std::string err;
+  long long ws_bytes = 0;
+};
+
+namespace dg {
+
+#define DG_CK(call)                                                                                    \
+  do {                                                                                                 \
+    cudaError_t e__ = (call);                                                                          \
+    if (e__ != cudaSuccess) {                                                                          \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e__);                                    \
+      return e__ == cudaErrorMemoryAllocation ? DG_ERR_NO_MEMORY : DG_ERR_CUDA;                        \
+    }                                                                                                  \
+  } while (0)
+
+#define DG_RET(call)                 \
+  do {                               \
+    int r__ = (call);                \
+    if (r__ != DG_OK) return r__;    \
+  } while (0)
+
+// scalar slots of h->scal, each [cap] doubles
+enum { S_BN = 0, S_RR, S_RZ, S_RZN, S_PQ, S_AL, S_BE, S_NSLOT };
+
+static double* scal(dg_ctx* h, int slot) { return h->scal.as<double>() + (size_t)slot * h->cap; }
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+template <typename T>
+static int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap) {
+  if (w.cap >= cap && !w.lev.empty()) return DG_OK;
+  w.lev.resize(h->nlev);
+  for (int l = 0; l < h->nlev; ++l) {
+    const long long N = h->levels[l].op.Nq;
+    LevelWork& L = w.lev[l];
+    if (l > 0) {
+      DG_CK(L.x.ensure(sizeof(T) * N * cap));
+      DG_CK(L.b.ensure(sizeof(T) * N * cap));
+    }
+    DG_CK(L.res.ensure(sizeof(T) * N * cap));
+    DG_CK(L.d.ensure(sizeof(T) * N * cap));
+    if (h->opts.smoother == DG_SMOOTH_SCHWARZ && l + 1 < h->nlev) {
+      const long long mp = h->levels[l].op.n1 + 2;
+      DG_CK(L.z.ensure(sizeof(T) * N * cap));
+      DG_CK(L.zp.ensure(sizeof(T) * (size_t)h->levels[l].op.E * mp * mp * mp * cap));
+    }
+    if (!L.invD.p) {
+      DG_CK(L.invD.ensure(sizeof(T) * N));
+      DG_CK(launch_inv_diag<T>(h->levels[l].op, h->levels[l].dop, L.invD.as<T>(), 0));
+    }
+  }
+  const long long N = h->Nq;
+  DG_CK(w.x.ensure(sizeof(T) * N * cap));
+  DG_CK(w.r.ensure(sizeof(T) * N * cap));
+  DG_CK(w.z.ensure(sizeof(T) * N * cap));
+  DG_CK(w.p.ensure(sizeof(T) * N * cap));
+  DG_CK(w.q.ensure(sizeof(T) * N * cap));
+  w.cap = cap;
+  DG_CK(cudaDeviceSynchronize());
+  return DG_OK;
+}
+
+static int ensure_common(dg_ctx* h, int cap) {
+  if (h->cap >= cap) return DG_OK;
+  const long long N = h->Nq;
+  DG_CK(h->f64.ensure(sizeof(double) * N * cap));
+  DG_CK(h->b64.ensure(sizeof(double) * N * cap));
+  DG_CK(h->x64.ensure(sizeof(double) * N * cap));
+  DG_CK(h->r64.ensure(sizeof(double) * N * cap));
+  DG_CK(h->part.ensure(sizeof(double) * 304 * cap));
+  DG_CK(h->scal.ensure(sizeof(double) * S_NSLOT * cap));
+  DG_CK(h->act.ensure(sizeof(int) * cap));
+  DG_CK(h->flags.ensure(sizeof(int) * cap));
+  DG_CK(h->pidx.ensure(sizeof(int) * 2 * cap));
+  DG_CK(h->g.ensure(sizeof(double) * h->nface * cap));
+  h->cap = cap;
+  return DG_OK;
+}
+
+static int ensure_bc_work(dg_ctx* h, int nsrc) {
+  const long long N = h->Nq;
+  DG_CK(h->flex.ensure(sizeof(double) * N * nsrc));
+  long long maxface = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    maxface = std::max(maxface, (long long)h->bct[t1].L * h->bct[t2].L);
+  }
+  const size_t tb = sizeof(double) * 2 * (size_t)h->NG * maxface * nsrc;
+  DG_CK(h->T1.ensure(tb));
+  DG_CK(h->T2.ensure(tb));
+  return DG_OK;
+}
+
+static void account(dg_ctx* h) {
+  long long b = 0;
+  auto add = [&](const DevBuf& x) { b += (long long)x.bytes; };
+  for (auto* w : {&h->f64, &h->b64, &h->x64, &h->r64, &h->flex, &h->T1, &h->T2, &h->g, &h->part, &h->scal,
+                  &h->act, &h->flags, &h->pidx, &h->Wacc, &h->kpart, &h->Kdev, &h->coarse_inv, &h->d_W, &h->d_xq,
+                  &h->d_axn})
+    add(*w);
+  for (auto& L : h->w64.lev) {
+    add(L.x); add(L.b); add(L.res); add(L.d); add(L.invD); add(L.z); add(L.zp);
+  }
+  for (auto& L : h->w32.lev) {
+    add(L.x); add(L.b); add(L.res); add(L.d); add(L.invD); add(L.z); add(L.zp);
+  }
+  for (auto& L : h->levels) add(L.sw_tabs);
+  for (auto* w : {&h->w64.x, &h->w64.r, &h->w64.z, &h->w64.p, &h->w64.q}) add(*w);
+  for (auto* w : {&h->w32.x, &h->w32.r, &h->w32.z, &h->w32.p, &h->w32.q}) add(*w);
+  for (int d = 0; d < 3; ++d) {
+    add(h->bct[d].gn); add(h->bct[d].G); add(h->bct[d].Gs);
+  }
+  h->ws_bytes = b;
+}
+
+// ---------------------------------------------------------------------------
+// multigrid V-cycle (Sec. 6.4: degree coarsening to 1, then geometric)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MG {
+  dg_ctx* h;
+  PrecWork<T>* w;
+  const int* act;
+  int nact;
+  cudaStream_t s;
+
+  // Chebyshev-Jacobi smoothing of A x = b on level l (degree k), Chebyshev
+  // semi-iteration on D^-1 A over [lam/range, lam]. On exit, if want_res,
+  // lev[l].res holds b - A x.
+  int cheb(int l, const T* b, T* x, bool zero_init, bool want_res) {
+    Level& L = h->levels[l];
+    LevelWork& W = w->lev[l];
+    T* res = W.res.as<T>();
+    T* d = W.d.as<T>();
+    const bool sw = h->opts.smoother == DG_SMOOTH_SCHWARZ;
+    // sw: the smoother preconditioner is M_S (z = M_S res), else D^-1 (fused)
+    const T* invD = sw ? nullptr : W.invD.as<T>();
+    T* z = sw ? W.z.as<T>() : nullptr;
+    const long long Nq = L.op.Nq;
+    const int k = std::max(1, h->opts.smoother_degree);
+    const double bmax = sw ? L.lam_sw : L.lam_max * (1.0 + 1e-6);
+    const double amin = bmax / std::max(1.5, h->opts.cheb_range);
+    const double theta = 0.5 * (bmax + amin), delta = 0.5 * (bmax - amin);
+    const double sig1 = theta / delta;
+    const T* r0 = b;
+    if (!zero_init) {
+      DG_CK(launch_apply<T>(L.op, L.dop, 1, x, res, b, act, nact, s));
+      r0 = res;
+    }
+    if (sw) {
+      DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r0, W.zp.as<T>(), z, act, nact, s));
+      r0 = z;
+    }
+    DG_CK(launch_cheb_first<T>(x, d, r0, invD, 1.0 / theta, zero_init ? 1 : 0, Nq, act, nact, s));
+    double rho_prev = 1.0 / sig1;
+    bool res_is_b = zero_init;  // the residual of the current x is b - A d when res_is_b
+    for (int j = 2; j <= k; ++j) {
+      if (res_is_b)
+        DG_CK(launch_apply<T>(L.op, L.dop, 1, d, res, b, act, nact, s));
+      else
+        DG_CK(launch_apply<T>(L.op, L.dop, 2, d, res, nullptr, act, nact, s));
+      res_is_b = false;
+      const double rho = 1.0 / (2.0 * sig1 - rho_prev);
+      const T* rr = res;
+      if (sw) {
+        DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), res, W.zp.as<T>(), z, act, nact, s));
+        rr = z;
+      }
+      DG_CK(launch_cheb_step<T>(x, d, rr, invD, rho * rho_prev, 2.0 * rho / delta, Nq, act, nact, s));
+      rho_prev = rho;
+    }
+    if (want_res) {
+      if (res_is_b)
+        DG_CK(launch_apply<T>(L.op, L.dop, 1, d, res, b, act, nact, s));
+      else
+        DG_CK(launch_apply<T>(L.op, L.dop, 2, d, res, nullptr, act, nact, s));
+    }
+    return DG_OK;
+  }
+
+  // x = V(b) on level l (x overwritten)
+  int vcycle(int l, const T* b, T* x) {
+    if (l == h->nlev - 1) {
+      DG_CK(launch_coarse_solve<T>(h->coarse_inv.as<double>(), h->Nc, b, x, act, nact, s));
+      return DG_OK;
+    }
+    Level& L = h->levels[l];
+    Level& C = h->levels[l + 1];
+    LevelWork& Wc = w->lev[l + 1];
+    DG_RET(cheb(l, b, x, true, true));
+    DG_CK(launch_restrict<T>(L.tr, L.dtr, L.op, C.op, w->lev[l].res.template as<T>(), Wc.b.as<T>(), act, nact, s));
+    DG_RET(vcycle(l + 1, Wc.b.as<T>(), Wc.x.as<T>()));
+    DG_CK(launch_prolong_add<T>(L.tr, L.dtr, L.op, C.op, Wc.x.as<T>(), x, act, nact, s));
+    DG_RET(cheb(l, b, x, false, false));
+    return DG_OK;
+  }
+};
+
+// device per-rhs scalar update: out = num / den (0 and a breakdown flag when den <= 0 or not finite)
+__global__ void k_ratio(const double* num, const double* den, double* out, const int* act, int nact, int* flags,
+                        int check) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nact) return;
+  const int r = act[k];
+  const double dn = den[r];
+  if (!(dn > 0.0) || !isfinite(dn) || !isfinite(num[r])) {
+    out[r] = 0.0;
+    if (check) flags[r] |= 2;
+  } else {
+    out[r] = num[r] / dn;
+  }
+}
+
+__global__ void k_copy_slot(const double* src, double* dst, const int* act, int nact) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nact) dst[act[k]] = src[act[k]];
+}
+
+static int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s) {
+  if (a.empty()) return DG_OK;
+  DG_CK(cudaMemcpyAsync(h->act.p, a.data(), sizeof(int) * a.size(), cudaMemcpyHostToDevice, s));
+  DG_CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+// Preconditioned CG in precision T on the fine level for the sources in
+// `act0`: solves A x = r (r overwritten by the residual) starting from x = 0
+// until ||r||_2 <= tol * ||r_0||_2 or maxit iterations. iters[k] receives the
+// iterations used by each source; flags (device) collect breakdowns.
+template <typename T>
+static int pcg(dg_ctx* h, PrecWork<T>& w, const std::vector<int>& act0, const std::vector<double>& tol, int maxit,
+               cudaStream_t s, std::vector<int>& iters, std::vector<double>& relres) {
+  const long long Nq = h->Nq;
+  T* x = w.x.template as<T>();
+  T* r = w.r.template as<T>();
+  T* z = w.z.template as<T>();
+  T* p = w.p.template as<T>();
+  T* q = w.q.template as<T>();
+  double* part = h->part.as<double>();
+  int* flags = h->flags.as<int>();
+  std::vector<int> act = act0;
+  int nact = (int)act.size();
+  if (nact == 0) return DG_OK;
+  DG_RET(upload_act(h, act, s));
+  const int* dact = h->act.as<int>();
+  MG<T> mg{h, &w, dact, nact, s};
+  DG_CK(launch_zero<T>(x, Nq, dact, nact, s));
+  DG_CK(launch_dot<T>(r, r, nullptr, scal(h, S_BN), part, Nq, dact, nact, s));
+  DG_RET(mg.vcycle(0, r, z));
+  DG_CK((launch_convert<T, T>(p, z, Nq, dact, nact, 1.0, 0, s)));
+  DG_CK(launch_dot<T>(r, z, nullptr, scal(h, S_RZ), part, Nq, dact, nact, s));
+  std::vector<double> bn(h->cap, 0.0), rr(h->cap, 0.0);
+  DG_CK(cudaMemcpyAsync(bn.data(), scal(h, S_BN), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  for (int k : act) {
+    iters[k] = 0;
+    relres[k] = bn[k] > 0 ? 1.0 : 0.0;
+  }
+  // sources with a zero right-hand side are done at x = 0
+  {
+    std::vector<int> a2;
+    for (int k : act)
+      if (bn[k] > 0.0) a2.push_back(k);
+    if (a2.size() != act.size()) {
+      act = a2;
+      nact = (int)act.size();
+      if (nact == 0) return DG_OK;
+      DG_RET(upload_act(h, act, s));
+      mg.nact = nact;
+    }
+  }
+  for (int it = 1; it <= maxit; ++it) {
+    DG_CK(launch_apply<T>(h->levels[0].op, h->levels[0].dop, 0, p, q, nullptr, dact, nact, s));
+    DG_CK(launch_dot<T>(p, q, nullptr, scal(h, S_PQ), part, Nq, dact, nact, s));
+    count_launch();
+    k_ratio<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZ), scal(h, S_PQ), scal(h, S_AL), dact, nact, flags, 1);
+    DG_CK(launch_cg_xr<T>(x, r, p, q, scal(h, S_AL), Nq, dact, nact, s));
+    DG_CK(launch_dot<T>(r, r, nullptr, scal(h, S_RR), part, Nq, dact, nact, s));
+    DG_CK(cudaMemcpyAsync(rr.data(), scal(h, S_RR), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+    DG_CK(cudaStreamSynchronize(s));
+    std::vector<int> a2;
+    for (int k : act) {
+      iters[k] = it;
+      relres[k] = std::sqrt(std::max(rr[k], 0.0) / bn[k]);
+      if (!(relres[k] <= tol[k]) && std::isfinite(relres[k])) a2.push_back(k);
+    }
+    if (a2.empty()) break;
+    if (a2.size() != act.size()) {
+      act = a2;
+      nact = (int)act.size();
+      DG_RET(upload_act(h, act, s));
+      mg.nact = nact;
+    }
+    if (it == maxit) break;
+    DG_RET(mg.vcycle(0, r, z));
+    DG_CK(launch_dot<T>(r, z, nullptr, scal(h, S_RZN), part, Nq, dact, nact, s));
+    count_launch();
+    k_ratio<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), scal(h, S_BE), dact, nact, flags, 0);
+    count_launch();
+    k_copy_slot<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), dact, nact);
+    DG_CK(launch_cg_p<T>(p, z, scal(h, S_BE), Nq, dact, nact, s));
+  }
+  return DG_OK;
+}
+
+// FP64 true residual r64 = b64 - A x64 and its relative norm per source.
+static int true_residual(dg_ctx* h, const std::vector<int>& act, const std::vector<double>& bnorm2,
+                         std::vector<double>& rel, cudaStream_t s) {
+  if (act.empty()) return DG_OK;
+  DG_RET(upload_act(h, act, s));
+  const int* dact = h->act.as<int>();
+  const int nact = (int)act.size();
+  DG_CK(launch_apply<double>(h->levels[0].op, h->levels[0].dop, 1, h->x64.as<double>(), h->r64.as<double>(),
+                             h->b64.as<double>(), dact, nact, s));
+  DG_CK(launch_dot<double>(h->r64.as<double>(), h->r64.as<double>(), nullptr, scal(h, S_RR), h->part.as<double>(),
+                           h->Nq, dact, nact, s));
+  std::vector<double> rr(h->cap);
+  DG_CK(cudaMemcpyAsync(rr.data(), scal(h, S_RR), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  for (int k : act) rel[k] = bnorm2[k] > 0 ? std::sqrt(std::max(rr[k], 0.0) / bnorm2[k]) : 0.0;
+  return DG_OK;
+}
+
+// Solves A x64 = b64 for sources 0..nsrc-1 of the current chunk (b64 filled).
+static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_solve_stats* st, cudaStream_t s) {
+  const long long Nq = h->Nq;
+  const double rtol = h->opts.rtol;
+  std::vector<int> act;
+  for (int k = 0; k < nsrc; ++k)
+    if (finite[k]) act.push_back(k);
+  std::vector<int> all(nsrc);
+  for (int k = 0; k < nsrc; ++k) all[k] = k;
+  DG_RET(upload_act(h, all, s));
+  DG_CK(launch_zero<double>(h->x64.as<double>(), Nq, h->act.as<int>(), nsrc, s));
+  DG_CK(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * h->cap, s));
+  std::vector<double> bnorm2(h->cap, 0.0), rel(h->cap, 1.0);
+  if (!act.empty()) {
+    DG_RET(upload_act(h, act, s));
+    DG_CK(launch_dot<double>(h->b64.as<double>(), h->b64.as<double>(), nullptr, scal(h, S_BN), h->part.as<double>(),
+                             Nq, h->act.as<int>(), (int)act.size(), s));
+    DG_CK(cudaMemcpyAsync(bnorm2.data(), scal(h, S_BN), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+    DG_CK(cudaStreamSynchronize(s));
+  }
+  std::vector<int> iters(h->cap, 0), it_inner(h->cap, 0), outer(h->cap, 0);
+  const int maxit = h->opts.max_iter;
+  const bool mixed = h->opts.precision != DG_PREC_FP64;
+  // r64 = b64 (x64 = 0)
+  if (!act.empty()) {
+    DG_RET(upload_act(h, act, s));
+    DG_CK((launch_convert<double, double>(h->r64.as<double>(), h->b64.as<double>(), Nq, h->act.as<int>(),
+                                          (int)act.size(), 1.0, 0, s)));
+  }
+  for (int k : act) rel[k] = bnorm2[k] > 0 ? 1.0 : 0.0;
+  std::vector<int> todo;
+  for (int k : act)
+    if (rel[k] > rtol) todo.push_back(k);
+  int round = 0;
+  while (!todo.empty() && round < 64) {
+    ++round;
+    DG_RET(upload_act(h, todo, s));
+    const int* dact = h->act.as<int>();
+    const int nt = (int)todo.size();
+    // relative reduction asked of this round, per source: enough for the
+    // true residual to reach rtol (FP64), at most inner_rtol (mixed)
+    std::vector<double> tolv(h->cap, 1.0), rl(h->cap, 1.0);
+    int remaining = 1;
+    for (int k : todo) {
+      const double need = 0.5 * rtol / std::max(rel[k], 1e-300);
+      tolv[k] = mixed ? std::max(need, h->opts.inner_rtol) : std::max(need, 1e-15);
+      remaining = std::max(remaining, maxit - iters[k]);
+    }
+    if (!mixed) {
+      DG_CK((launch_convert<double, double>(h->w64.r.as<double>(), h->r64.as<double>(), Nq, dact, nt, 1.0, 0, s)));
+      DG_RET(pcg<double>(h, h->w64, todo, tolv, remaining, s, it_inner, rl));
+      DG_RET(upload_act(h, todo, s));
+      DG_CK((launch_convert<double, double>(h->x64.as<double>(), h->w64.x.as<double>(), Nq, dact, nt, 1.0, 1, s)));
+    } else {
+      DG_CK((launch_convert<float, double>(h->w32.r.as<float>(), h->r64.as<double>(), Nq, dact, nt, 1.0, 0, s)));
+      DG_RET(pcg<float>(h, h->w32, todo, tolv, remaining, s, it_inner, rl));
+      DG_RET(upload_act(h, todo, s));
+      DG_CK((launch_convert<double, float>(h->x64.as<double>(), h->w32.x.as<float>(), Nq, dact, nt, 1.0, 1, s)));
+    }
+    for (int k : todo) {
+      iters[k] += it_inner[k];
+      outer[k] += 1;
+    }
+    DG_RET(true_residual(h, todo, bnorm2, rel, s));
+    std::vector<int> t2;
+    for (int k : todo)
+      if (rel[k] > rtol && std::isfinite(rel[k]) && iters[k] < maxit) t2.push_back(k);
+    todo = t2;
+  }
+  std::vector<int> fl(h->cap, 0);
+  DG_CK(cudaMemcpyAsync(fl.data(), h->flags.p, sizeof(int) * h->cap, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  int worst = DG_OK;
+  for (int k = 0; k < nsrc; ++k) {
+    dg_solve_stats S;
+    S.iters = iters[k];
+    S.outer_refinements = mixed ? outer[k] : 0;
+    S.used_fallback = 0;
+    S.rel_residual = finite[k] ? rel[k] : NAN;
+    if (!finite[k])
+      S.status = DG_ERR_NONFINITE;
+    else if (!(rel[k] <= rtol))
+      S.status = (fl[k] & 2) ? DG_ERR_BREAKDOWN : DG_ERR_NOT_CONVERGED;
+    else
+      S.status = DG_OK;
+    if (st) st[k] = S;
+    if (S.status != DG_OK && (worst == DG_OK || S.status < worst)) worst = S.status;
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
+// boundary data of the sources in f64[0..nsrc) into g[0..nsrc)
+// ---------------------------------------------------------------------------
+static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double* g, cudaStream_t s) {
+  const LevelOp& op = h->levels[0].op;
+  if (route == DG_BC_DIRECT) {
+    DG_CK(launch_bc_direct(op, h->levels[0].dop, f, h->d_W.as<double>(), h->d_xq.as<double>(),
+                           h->d_axn.as<double>(), h->lmax, g, nsrc, h->nface, h->nface, s));
+    return DG_OK;
+  }
+  DG_RET(ensure_bc_work(h, nsrc));
+  double* flex = h->flex.as<double>();
+  DG_CK(launch_weighted_lex(op, h->levels[0].dop, f, h->d_W.as<double>(), flex, nsrc, s));
+  const int NG = h->NG;
+  const long long Lx = h->bct[0].L, Ly = h->bct[1].L, Lz = h->bct[2].L;
+  const long long Nq = h->Nq;
+  long long face_off = 0;
+  double* T1 = h->T1.as<double>();
+  double* T2 = h->T2.as<double>();
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    const long long L1 = h->bct[t1].L, L2 = h->bct[t2].L, Ld = h->bct[d].L;
+    const long long tsz = 2LL * NG * L1 * L2;  // per source
+    // step 1: contraction along the normal axis with both face positions
+    GemmArgs a{};
+    a.M = 2 * NG;
+    a.K = (int)Ld;
+    a.A = h->bct[d].gn.p;
+    a.sAm = Ld;
+    a.sAk = 1;
+    a.C = T1;
+    a.sCm = L1 * L2;
+    a.sCn = 1;
+    a.alpha = 1.0;
+    a.beta = 0.0;
+    if (d == 0) {
+      a.N = (int)(Ly * Lz);
+      a.nb1 = nsrc;
+      a.nb2 = 1;
+      a.B = flex;
+      a.sBk = 1;
+      a.sBn = Lx;
+      a.sB1 = Nq;
+      a.sC1 = tsz;
+    } else if (d == 1) {
+      a.N = (int)Lx;
+      a.nb1 = nsrc;
+      a.nb2 = (int)Lz;
+      a.B = flex;
+      a.sBk = Lx;
+      a.sBn = 1;
+      a.sB1 = Nq;
+      a.sB2 = Lx * Ly;
+      a.sC1 = tsz;
+      a.sC2 = Lx;
+    } else {
+      a.N = (int)(Lx * Ly);
+      a.nb1 = nsrc;
+      a.nb2 = 1;
+      a.B = flex;
+      a.sBk = Lx * Ly;
+      a.sBn = 1;
+      a.sB1 = Nq;
+      a.sC1 = tsz;
+    }
+    DG_CK(launch_gemm<double>(a, s));
+    // step 2: along t1 (fastest index), per (source, side, term)
+    GemmArgs b{};
+    b.M = (int)L2;
+    b.N = (int)L1;
+    b.K = (int)L1;
+    b.nb1 = nsrc * 2;
+    b.nb2 = NG;
+    b.A = T1;
+    b.sAm = L1;
+    b.sAk = 1;
+    b.sA1 = (long long)NG * L1 * L2;
+    b.sA2 = L1 * L2;
+    b.B = h->bct[t1].G.p;
+    b.sBk = 1;
+    b.sBn = L1;
+    b.sB1 = 0;
+    b.sB2 = L1 * L1;
+    b.C = T2;
+    b.sCm = L1;
+    b.sCn = 1;
+    b.sC1 = (long long)NG * L1 * L2;
+    b.sC2 = L1 * L2;
+    b.alpha = 1.0;
+    b.beta = 0.0;
+    DG_CK(launch_gemm<double>(b, s));
+    // step 3: along t2 together with the weighted sum over terms
+    GemmArgs c{};
+    c.M = (int)L2;
+    c.N = (int)L1;
+    c.K = (int)(NG * L2);
+    c.nb1 = nsrc;
+    c.nb2 = 2;
+    c.A = h->bct[t2].Gs.p;
+    c.sAm = NG * L2;
+    c.sAk = 1;
+    c.B = T2;
+    c.sBk = L1;
+    c.sBn = 1;
+    c.sB1 = 2LL * NG * L1 * L2;
+    c.sB2 = (long long)NG * L1 * L2;
+    c.C = g + face_off;
+    c.sCm = L1;
+    c.sCn = 1;
+    c.sC1 = h->nface;
+    c.sC2 = L1 * L2;
+    c.alpha = 1.0;
+    c.beta = 0.0;
+    DG_CK(launch_gemm<double>(c, s));
+    face_off += 2 * L1 * L2;
+  }
+  (void)Lz;
+  return DG_OK;
+}
+
+// b64 = 4 pi W f + Nitsche lift of g(f) for f64[0..nsrc)
+static int form_rhs(dg_ctx* h, const double* f, int nsrc, cudaStream_t s) {
+  DG_CK(launch_rhs_volume(f, h->d_W.as<double>(), h->b64.as<double>(), h->Nq, nsrc, s));
+  DG_RET(boundary_data(h, h->opts.bc_route, f, nsrc, h->g.as<double>(), s));
+  DG_CK(launch_lift(h->levels[0].op, h->levels[0].dop, h->g.as<double>(), h->b64.as<double>(), nsrc, h->nface, s));
+  return DG_OK;
+}
+
+static int check_finite(dg_ctx* h, const double* f, int nsrc, std::vector<int>& finite, cudaStream_t s) {
+  DG_CK(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * nsrc, s));
+  DG_CK(launch_finite_flags(f, h->Nq, nsrc, h->flags.as<int>(), s));
+  std::vector<int> fl(nsrc);
+  DG_CK(cudaMemcpyAsync(fl.data(), h->flags.p, sizeof(int) * nsrc, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  finite.assign(nsrc, 1);
+  for (int k = 0; k < nsrc; ++k) finite[k] = fl[k] ? 0 : 1;
+  return DG_OK;
+}
+
+static int default_batch(dg_ctx* h) {
+  if (h->opts.batch > 0) return h->opts.batch;
+  // fill roughly 8 GB of FP64 fine-level vectors
+  long long per = h->Nq * 8LL * 12;
+  long long b = (8LL << 30) / std::max(per, 1LL);
+  return (int)std::max(1LL, std::min(b, 256LL));
+}
+
+static int prepare(dg_ctx* h, int cap) {
+  DG_RET(ensure_common(h, cap));
+  if (h->opts.precision == DG_PREC_FP64)
+    DG_RET(ensure_prec<double>(h, h->w64, cap));
+  else
+    DG_RET(ensure_prec<float>(h, h->w32, cap));
+  account(h);
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// lambda_max(M_S A) of a level by Lanczos from 24 preconditioned CG steps on a
+// seeded random right-hand side (FP64); returned with a 8 % safety margin
+// (Chebyshev smoothing must not see modes above its interval)
+// ---------------------------------------------------------------------------
+static int estimate_lambda_schwarz(dg_ctx* h, int l, double* out) {
+  Level& L = h->levels[l];
+  const long long N = L.op.Nq;
+  const long long mp = L.op.n1 + 2;
+  DevBuf r, z, p, q, x, zp, part, dsc, dact;
+  DG_CK(r.ensure(sizeof(double) * N));
+  DG_CK(z.ensure(sizeof(double) * N));
+  DG_CK(p.ensure(sizeof(double) * N));
+  DG_CK(q.ensure(sizeof(double) * N));
+  DG_CK(x.ensure(sizeof(double) * N));
+  DG_CK(zp.ensure(sizeof(double) * (size_t)L.op.E * mp * mp * mp));
+  DG_CK(part.ensure(sizeof(double) * 304));
+  DG_CK(dsc.ensure(sizeof(double) * 4));
+  DG_CK(dact.ensure(sizeof(int)));
+  DG_CK(cudaMemset(dact.p, 0, sizeof(int)));
+  std::vector<double> hr(N);
+  unsigned long long st = 0x9E3779B97F4A7C15ull + (unsigned long long)l;
+  for (long long i = 0; i < N; ++i) {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    hr[i] = ((double)(st >> 11) / 9007199254740992.0) - 0.5;
+  }
+  DG_CK(cudaMemcpy(r.p, hr.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+  const int* a = dact.as<int>();
+  double* sc = dsc.as<double>();
+  auto dot = [&](const double* u, const double* v, double* res) -> int {
+    DG_CK(launch_dot<double>(u, v, nullptr, sc + 3, part.as<double>(), N, a, 1, 0));
+    DG_CK(cudaMemcpy(res, sc + 3, sizeof(double), cudaMemcpyDeviceToHost));
+    return DG_OK;
+  };
+  DG_CK(launch_schwarz<double>(L.op, L.dop, L.sw_tabs.as<double>(), r.as<double>(), zp.as<double>(),
+                               z.as<double>(), a, 1, 0));
+  DG_CK(cudaMemcpy(p.p, z.p, sizeof(double) * N, cudaMemcpyDeviceToDevice));
+  double rz = 0.0;
+  DG_RET(dot(r.as<double>(), z.as<double>(), &rz));
+  std::vector<double> al, be;
+  const int K = (int)std::min<long long>(24, N);
+  for (int k = 0; k < K; ++k) {
+    DG_CK(launch_apply<double>(L.op, L.dop, 0, p.as<double>(), q.as<double>(), nullptr, a, 1, 0));
+    double pq = 0.0;
+    DG_RET(dot(p.as<double>(), q.as<double>(), &pq));
+    if (!(pq > 0.0) || !(rz > 0.0)) break;
+    const double alpha = rz / pq;
+    DG_CK(cudaMemcpy(sc, &alpha, sizeof(double), cudaMemcpyHostToDevice));
+    DG_CK(launch_cg_xr<double>(x.as<double>(), r.as<double>(), p.as<double>(), q.as<double>(), sc, N, a, 1, 0));
+    DG_CK(launch_schwarz<double>(L.op, L.dop, L.sw_tabs.as<double>(), r.as<double>(), zp.as<double>(),
+                                 z.as<double>(), a, 1, 0));
+    double rzn = 0.0;
+    DG_RET(dot(r.as<double>(), z.as<double>(), &rzn));
+    const double beta = rzn / rz;
+    rz = rzn;
+    al.push_back(alpha);
+    be.push_back(beta);
+    DG_CK(cudaMemcpy(sc + 1, &beta, sizeof(double), cudaMemcpyHostToDevice));
+    DG_CK(launch_cg_p<double>(p.as<double>(), z.as<double>(), sc + 1, N, a, 1, 0));
+    if (!(rz > 0.0)) break;
+  }
+  const int m = (int)al.size();
+  if (m == 0) {
+    h->err = "Lanczos estimate of the smoother spectrum failed";
+    return DG_ERR_INVALID_ARG;
+  }
+  std::vector<double> T((size_t)m * m, 0.0);
+  for (int k = 0; k < m; ++k) {
+    T[(size_t)k * m + k] = 1.0 / al[k] + (k > 0 ? be[k - 1] / al[k - 1] : 0.0);
+    if (k + 1 < m) {
+      const double o = std::sqrt(std::max(be[k], 0.0)) / al[k];
+      T[(size_t)k * m + k + 1] = o;
+      T[(size_t)(k + 1) * m + k] = o;
+    }
+  }
+  *out = 1.08 * sym_max_eig(T, m);
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+static int setup(dg_ctx* h) {
+  const dg_mesh_desc& m = h->mesh;
+  const dg_solver_opts& o = h->opts;
+  // level list: degree p -> floor(p/2) down to 1, then n -> n/2 while even
+  int n[3] = {m.n[0], m.n[1], m.n[2]};
+  int p = m.p;
+  std::vector<std::pair<std::array<int, 3>, int>> spec;
+  spec.push_back({{n[0], n[1], n[2]}, p});
+  while (p > 1) {
+    p = std::max(1, p / 2);
+    spec.push_back({{n[0], n[1], n[2]}, p});
+  }
+  while (n[0] % 2 == 0 && n[1] % 2 == 0 && n[2] % 2 == 0 && n[0] >= 2 && n[1] >= 2 && n[2] >= 2 &&
+         (int)spec.size() < MAXLEV) {
+    n[0] /= 2;
+    n[1] /= 2;
+    n[2] /= 2;
+    spec.push_back({{n[0], n[1], n[2]}, 1});
+  }
+  h->nlev = (int)spec.size();
+  h->levels.resize(h->nlev);
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& L = h->levels[l];
+    build_level(L.op, spec[l].first.data(), spec[l].second, m.lo, m.hi, o.penalty_form, o.penalty_eps);
+    L.lam_max = level_lambda_max(L.op);
+  }
+  for (int l = 0; l + 1 < h->nlev; ++l) build_transfer(h->levels[l].tr, h->levels[l].op, h->levels[l + 1].op);
+  const LevelOp& Lc = h->levels[h->nlev - 1].op;
+  if (Lc.Nq > 4096) {
+    h->err = "coarsest multigrid level has more than 4096 unknowns";
+    return DG_ERR_UNSUPPORTED;
+  }
+  h->Nc = (int)Lc.Nq;
+  {
+    std::vector<double> Ac = level_dense(Lc);
+    if (!spd_inverse(Ac, h->Nc)) {
+      h->err = "coarsest-level operator is not positive definite";
+      return DG_ERR_INVALID_ARG;
+    }
+    DG_CK(h->coarse_inv.ensure(sizeof(double) * Ac.size()));
+    DG_CK(cudaMemcpy(h->coarse_inv.p, Ac.data(), sizeof(double) * Ac.size(), cudaMemcpyHostToDevice));
+  }
+  for (int l = 0; l < h->nlev; ++l) {
+    Level& L = h->levels[l];
+    DG_CK(cudaMalloc(&L.dop, sizeof(LevelOp)));
+    DG_CK(cudaMemcpy(L.dop, &L.op, sizeof(LevelOp), cudaMemcpyHostToDevice));
+    DG_CK(cudaMalloc(&L.dtr, sizeof(TransferOp)));
+    DG_CK(cudaMemcpy(L.dtr, &L.tr, sizeof(TransferOp), cudaMemcpyHostToDevice));
+  }
+  if (o.smoother == DG_SMOOTH_SCHWARZ) {
+    for (int l = 0; l + 1 < h->nlev; ++l) {
+      Level& L = h->levels[l];
+      const std::vector<double> tb = schwarz_tables(L.op);
+      DG_CK(L.sw_tabs.ensure(sizeof(double) * tb.size()));
+      DG_CK(cudaMemcpy(L.sw_tabs.p, tb.data(), sizeof(double) * tb.size(), cudaMemcpyHostToDevice));
+      DG_RET(estimate_lambda_schwarz(h, l, &L.lam_sw));
+    }
+  }
+  // fine-level nodes, weights
+  const LevelOp& F = h->levels[0].op;
+  h->Nq = F.Nq;
+  const int n1 = F.n1;
+  double xi[MAXN1], w[MAXN1];
+  gauss_legendre(n1, xi, w);
+  h->lmax = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int Ld = F.n[d] * n1;
+    h->lmax = std::max(h->lmax, Ld);
+    h->axis_nodes[d].resize(Ld);
+    const double hd = F.ax[d].h;
+    for (int e = 0; e < F.n[d]; ++e)
+      for (int a = 0; a < n1; ++a) h->axis_nodes[d][e * n1 + a] = m.lo[d] + hd * (e + (xi[a] + 1.0) / 2.0);
+  }
+  {
+    std::vector<double> W(h->Nq), X(3 * h->Nq);
+    const int npe = n1 * n1 * n1;
+    for (long long q = 0; q < h->Nq; ++q) {
+      const int e = (int)(q / npe), loc = (int)(q % npe);
+      const int a = loc % n1, b = (loc / n1) % n1, c = loc / (n1 * n1);
+      const int ex = e % F.n[0], ey = (e / F.n[0]) % F.n[1], ez = e / (F.n[0] * F.n[1]);
+      W[q] = F.ax[0].m[a] * F.ax[1].m[b] * F.ax[2].m[c];
+      X[3 * q] = h->axis_nodes[0][ex * n1 + a];
+      X[3 * q + 1] = h->axis_nodes[1][ey * n1 + b];
+      X[3 * q + 2] = h->axis_nodes[2][ez * n1 + c];
+    }
+    DG_CK(h->d_W.ensure(sizeof(double) * h->Nq));
+    DG_CK(cudaMemcpy(h->d_W.p, W.data(), sizeof(double) * h->Nq, cudaMemcpyHostToDevice));
+    DG_CK(h->d_xq.ensure(sizeof(double) * 3 * h->Nq));
+    DG_CK(cudaMemcpy(h->d_xq.p, X.data(), sizeof(double) * 3 * h->Nq, cudaMemcpyHostToDevice));
+    std::vector<double> axn(3 * (size_t)h->lmax, 0.0);
+    for (int d = 0; d < 3; ++d)
+      for (size_t i = 0; i < h->axis_nodes[d].size(); ++i) axn[d * h->lmax + i] = h->axis_nodes[d][i];
+    DG_CK(h->d_axn.ensure(sizeof(double) * axn.size()));
+    DG_CK(cudaMemcpy(h->d_axn.p, axn.data(), sizeof(double) * axn.size(), cudaMemcpyHostToDevice));
+  }
+  h->nface = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    h->nface += 2LL * F.n[t1] * n1 * F.n[t2] * n1;
+  }
+  // Gaussian-sum tables: accurate on [rmin, rmax], rmin the smallest
+  // face-node to volume-node distance (the first interior node along the
+  // normal), rmax the box diagonal
+  {
+    double rmin = 1e300, diag2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      rmin = std::min(rmin, (1.0 - xi[n1 - 1]) * F.ax[d].h / 2.0);
+      diag2 += (m.hi[d] - m.lo[d]) * (m.hi[d] - m.lo[d]);
+    }
+    const double tol = o.bc_tol > 0 ? o.bc_tol : 1e-12;
+    h->gsum = make_gauss_sum(rmin * 0.999, std::sqrt(diag2) * 1.001, tol);
+    h->NG = (int)h->gsum.c.size();
+    if (h->NG == 0) {
+      h->err = "could not build the Gaussian-sum 1/r table";
+      return DG_ERR_INVALID_ARG;
+    }
+    const int NG = h->NG;
+    for (int d = 0; d < 3; ++d) {
+      const int L = (int)h->axis_nodes[d].size();
+      h->bct[d].L = L;
+      const std::vector<double>& x = h->axis_nodes[d];
+      std::vector<double> gn(2 * (size_t)NG * L), G((size_t)NG * L * L), Gs((size_t)L * NG * L);
+      for (int sd = 0; sd < 2; ++sd) {
+        const double xf = sd == 0 ? m.lo[d] : m.hi[d];
+        for (int k = 0; k < NG; ++k)
+          for (int i = 0; i < L; ++i) gn[((size_t)sd * NG + k) * L + i] = std::exp(-h->gsum.a[k] * (x[i] - xf) * (x[i] - xf));
+      }
+      for (int k = 0; k < NG; ++k)
+        for (int i = 0; i < L; ++i)
+          for (int j = 0; j < L; ++j) {
+            const double v = std::exp(-h->gsum.a[k] * (x[i] - x[j]) * (x[i] - x[j]));
+            G[((size_t)k * L + i) * L + j] = v;
+            Gs[(size_t)i * NG * L + (size_t)k * L + j] = h->gsum.c[k] * v;
+          }
+      DG_CK(h->bct[d].gn.ensure(sizeof(double) * gn.size()));
+      DG_CK(cudaMemcpy(h->bct[d].gn.p, gn.data(), sizeof(double) * gn.size(), cudaMemcpyHostToDevice));
+      DG_CK(h->bct[d].G.ensure(sizeof(double) * G.size()));
+      DG_CK(cudaMemcpy(h->bct[d].G.p, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice));
+      DG_CK(h->bct[d].Gs.ensure(sizeof(double) * Gs.size()));
+      DG_CK(cudaMemcpy(h->bct[d].Gs.p, Gs.data(), sizeof(double) * Gs.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  account(h);
+  return DG_OK;
+}
+
+}  // namespace dg
+
+namespace dg {
+std::atomic<long long> g_launch_count{0};
+
+template <typename T>
+static int apply_smoother_t(dg_ctx* h, PrecWork<T>& w, int level, const T* r, T* z, int nb, cudaStream_t s) {
+  const Level& L = h->levels[level];
+  const int* a = h->act.as<int>();
+  if (level == h->nlev - 1) {
+    DG_CK(launch_coarse_solve<T>(h->coarse_inv.as<double>(), h->Nc, r, z, a, nb, s));
+  } else if (h->opts.smoother == DG_SMOOTH_SCHWARZ) {
+    DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r, w.lev[level].zp.template as<T>(), z, a, nb, s));
+  } else {
+    DG_CK(launch_cheb_first<T>(z, z, r, w.lev[level].invD.template as<T>(), 1.0, 1, L.op.Nq, a, nb, s));
+  }
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void dg_default_opts(dg_solver_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = DG_PREC_FP64;
+  o->rtol = 1e-8;
+  o->max_iter = 500;
+  o->penalty_eps = 0.125;
+  o->penalty_form = 0;
+  o->bc_route = DG_BC_GAUSSSUM;
+  o->bc_tol = 0.0;
+  o->batch = 0;
+  o->smoother = DG_SMOOTH_SCHWARZ;
+  o->smoother_degree = 3;
+  o->cheb_range = 10.0;
+  o->inner_rtol = 1e-4;
+  o->nn_weights_path = nullptr;
+  o->verbose = 0;
+}
+
+const char* dg_error_string(int status) {
+  switch (status) {
+    case DG_OK: return "ok";
+    case DG_ERR_INVALID_ARG: return "invalid argument";
+    case DG_ERR_CUDA: return "CUDA error";
+    case DG_ERR_NOT_CONVERGED: return "not converged";
+    case DG_ERR_BREAKDOWN: return "CG breakdown";
+    case DG_ERR_NONFINITE: return "non-finite input";
+    case DG_ERR_TIMEOUT: return "timeout";
+    case DG_ERR_NO_MEMORY: return "out of device memory";
+    case DG_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char* dg_last_error_detail(dg_handle h) { return h ? h->err.c_str() : ""; }
+
+int64_t dg_kernel_launch_count(void) { return g_launch_count.load(); }
+
+int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_handle* out) {
+  if (!mesh || !out) return DG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (mesh->p < 1 || mesh->p > 8) return DG_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d) {
+    if (mesh->n[d] < 1 || mesh->n[d] > 4096) return DG_ERR_INVALID_ARG;
+    if (!(mesh->hi[d] > mesh->lo[d]) || !std::isfinite(mesh->lo[d]) || !std::isfinite(mesh->hi[d]))
+      return DG_ERR_INVALID_ARG;
+  }
+  dg_solver_opts o;
+  if (opts)
+    o = *opts;
+  else
+    dg_default_opts(&o);
+  if (!(o.rtol > 0) || o.max_iter < 1 || !(o.penalty_eps > 0) || (o.penalty_form != 0 && o.penalty_form != 1) ||
+      (o.bc_route != DG_BC_DIRECT && o.bc_route != DG_BC_GAUSSSUM) || o.precision < 0 || o.precision > 2 ||
+      o.smoother_degree < 1 || o.smoother_degree > 16 || o.batch < 0 ||
+      (o.smoother != DG_SMOOTH_JACOBI && o.smoother != DG_SMOOTH_SCHWARZ))
+    return DG_ERR_INVALID_ARG;
+  if (o.cheb_range <= 1.0) o.cheb_range = 10.0;
+  if (o.inner_rtol <= 0.0) o.inner_rtol = 1e-4;
+  if (o.precision == DG_PREC_MIXED_LEARNED && !o.nn_weights_path) return DG_ERR_INVALID_ARG;
+  dg_ctx* h = new (std::nothrow) dg_ctx();
+  if (!h) return DG_ERR_NO_MEMORY;
+  h->mesh = *mesh;
+  h->opts = o;
+  const int rc = setup(h);
+  if (rc != DG_OK) {
+    fprintf(stderr, "dg_poisson_setup: %s\n", h->err.c_str());
+    dg_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return DG_OK;
+}
+
+void dg_destroy(dg_handle h) {
+  if (!h) return;
+  for (auto& L : h->levels) {
+    if (L.dop) cudaFree(L.dop);
+    if (L.dtr) cudaFree(L.dtr);
+  }
+  delete h;
+}
+
+int dg_get_info(dg_handle h, dg_info* info) {
+  if (!h || !info) return DG_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->Nq = h->Nq;
+  info->levels = h->nlev;
+  for (int l = 0; l < h->nlev && l < 16; ++l) {
+    info->level_n[l] = h->levels[l].op.n[0];
+    info->level_p[l] = h->levels[l].op.p;
+  }
+  info->coarse_dofs = h->Nc;
+  info->n_gauss = h->NG;
+  info->gauss_rmin = h->gsum.rmin;
+  info->gauss_rmax = h->gsum.rmax;
+  info->gauss_relerr = h->gsum.relerr;
+  for (int d = 0; d < 3; ++d) info->sigma[d] = h->levels[0].op.ax[d].sigma;
+  account(h);
+  info->workspace_bytes = h->ws_bytes;
+  return DG_OK;
+}
+
+int dg_node_coords(dg_handle h, double* xyz, double* w) {
+  if (!h) return DG_ERR_INVALID_ARG;
+  const LevelOp& F = h->levels[0].op;
+  const int n1 = F.n1, npe = n1 * n1 * n1;
+  for (long long q = 0; q < h->Nq; ++q) {
+    const int e = (int)(q / npe), loc = (int)(q % npe);
+    const int a = loc % n1, b = (loc / n1) % n1, c = loc / (n1 * n1);
+    const int ex = e % F.n[0], ey = (e / F.n[0]) % F.n[1], ez = e / (F.n[0] * F.n[1]);
+    if (xyz) {
+      xyz[3 * q] = h->axis_nodes[0][ex * n1 + a];
+      xyz[3 * q + 1] = h->axis_nodes[1][ey * n1 + b];
+      xyz[3 * q + 2] = h->axis_nodes[2][ez * n1 + c];
+    }
+    if (w) w[q] = F.ax[0].m[a] * F.ax[1].m[b] * F.ax[2].m[c];
+  }
+  return DG_OK;
+}
+
+int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u, void* out, int64_t B, void* stream) {
+  if (!h || level < 0 || level >= h->nlev || B < 0 || (B > 0 && (!u || !out))) return DG_ERR_INVALID_ARG;
+  if (B == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cap = (int)std::min<int64_t>(B, 65535);
+  DG_RET(ensure_common(h, cap));
+  const Level& L = h->levels[level];
+  for (int64_t b0 = 0; b0 < B; b0 += cap) {
+    const int nb = (int)std::min<int64_t>(cap, B - b0);
+    std::vector<int> a(nb);
+    for (int k = 0; k < nb; ++k) a[k] = k;
+    DG_RET(upload_act(h, a, s));
+    if (fp32)
+      DG_CK(launch_apply<float>(L.op, L.dop, 0, (const float*)u + b0 * L.op.Nq, (float*)out + b0 * L.op.Nq, nullptr,
+                                h->act.as<int>(), nb, s));
+    else
+      DG_CK(launch_apply<double>(L.op, L.dop, 0, (const double*)u + b0 * L.op.Nq, (double*)out + b0 * L.op.Nq,
+                                 nullptr, h->act.as<int>(), nb, s));
+  }
+  DG_CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r, void* z, int64_t B, void* stream) {
+  if (!h || level < 0 || level >= h->nlev || B < 0 || (B > 0 && (!r || !z))) return DG_ERR_INVALID_ARG;
+  if (B == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cap = (int)std::min<int64_t>(B, 4096);
+  DG_RET(ensure_common(h, cap));
+  if (fp32)
+    DG_RET(ensure_prec<float>(h, h->w32, cap));
+  else
+    DG_RET(ensure_prec<double>(h, h->w64, cap));
+  const long long N = h->levels[level].op.Nq;
+  for (int64_t b0 = 0; b0 < B; b0 += cap) {
+    const int nb = (int)std::min<int64_t>(cap, B - b0);
+    std::vector<int> a(nb);
+    for (int k = 0; k < nb; ++k) a[k] = k;
+    DG_RET(upload_act(h, a, s));
+    if (fp32)
+      DG_RET(apply_smoother_t<float>(h, h->w32, level, (const float*)r + b0 * N, (float*)z + b0 * N, nb, s));
+    else
+      DG_RET(apply_smoother_t<double>(h, h->w64, level, (const double*)r + b0 * N, (double*)z + b0 * N, nb, s));
+  }
+  DG_CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+int dg_boundary_data(dg_handle h, int32_t route, const double* f, int64_t B, double* g, int64_t* nface,
+                     void* stream) {
+  if (!h || (route != DG_BC_DIRECT && route != DG_BC_GAUSSSUM) || B < 0) return DG_ERR_INVALID_ARG;
+  if (nface) *nface = h->nface;
+  if (!g || B == 0) return DG_OK;
+  if (!f) return DG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cap = std::max(1, std::min(default_batch(h), (int)B));
+  for (int64_t b0 = 0; b0 < B; b0 += cap) {
+    const int nb = (int)std::min<int64_t>(cap, B - b0);
+    DG_RET(boundary_data(h, route, f + b0 * h->Nq, nb, g + b0 * h->nface, s));
+  }
+  DG_CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_solve_stats* stats, void* stream) {
+  if (!h || B < 0 || (B > 0 && (!f || !v))) return DG_ERR_INVALID_ARG;
+  if (B == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cap = std::max(1, std::min(default_batch(h), (int)std::min<int64_t>(B, 65535)));
+  DG_RET(prepare(h, cap));
+  int worst = DG_OK;
+  for (int64_t b0 = 0; b0 < B; b0 += cap) {
+    const int nb = (int)std::min<int64_t>(cap, B - b0);
+    const double* fc = f + b0 * h->Nq;
+    std::vector<int> finite;
+    DG_RET(check_finite(h, fc, nb, finite, s));
+    DG_RET(form_rhs(h, fc, nb, s));
+    const int rc = solve_chunk(h, nb, finite, stats ? stats + b0 : nullptr, s);
+    if (rc == DG_ERR_CUDA || rc == DG_ERR_NO_MEMORY) return rc;
+    if (rc != DG_OK && (worst == DG_OK || rc < worst)) worst = rc;
+    DG_CK(cudaMemcpyAsync(v + b0 * h->Nq, h->x64.p, sizeof(double) * h->Nq * nb, cudaMemcpyDeviceToDevice, s));
+  }
+  DG_CK(cudaStreamSynchronize(s));
+  if (h->opts.verbose) fprintf(stderr, "dg_pair_solve_batch: %lld sources, status %d\n", (long long)B, worst);
+  return worst;
+}
+
+int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host, double* E_H, double* E_X,
+                      dg_solve_stats* stats, void* stream) {
+  if (!h || N < 1 || !psi || !K_host) return DG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long Nq = h->Nq;
+  const int P = N * (N + 1) / 2;
+  const int nsrc_total = P + 1;
+  const int cap = std::max(1, std::min(default_batch(h), nsrc_total));
+  DG_RET(prepare(h, cap));
+  DG_CK(h->Wacc.ensure(sizeof(double) * N * Nq));
+  const int nch = kmat_chunks(Nq);
+  DG_CK(h->kpart.ensure(sizeof(double) * (size_t)nch * N * N));
+  DG_CK(h->Kdev.ensure(sizeof(double) * ((size_t)N * N + 4)));
+  DG_CK(cudaMemsetAsync(h->Wacc.p, 0, sizeof(double) * N * Nq, s));
+  // source list: 0 = Hartree density, then pairs (i <= j) row-major
+  std::vector<int> si(nsrc_total), sj(nsrc_total);
+  si[0] = -1;
+  sj[0] = -1;
+  {
+    int k = 1;
+    for (int i = 0; i < N; ++i)
+      for (int j = i; j < N; ++j, ++k) {
+        si[k] = i;
+        sj[k] = j;
+      }
+  }
+  int worst = DG_OK;
+  double eh = 0.0;
+  DevBuf lists;
+  for (int b0 = 0; b0 < nsrc_total; b0 += cap) {
+    const int nb = std::min(cap, nsrc_total - b0);
+    DG_CK(cudaMemcpyAsync(h->pidx.p, si.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    DG_CK(cudaMemcpyAsync(h->pidx.as<int>() + cap, sj.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    DG_CK(launch_pair_sources(psi, N, h->pidx.as<int>(), h->pidx.as<int>() + cap, nb, Nq, h->f64.as<double>(), s));
+    std::vector<int> finite;
+    DG_RET(check_finite(h, h->f64.as<double>(), nb, finite, s));
+    DG_RET(form_rhs(h, h->f64.as<double>(), nb, s));
+    const int rc = solve_chunk(h, nb, finite, stats ? stats + b0 : nullptr, s);
+    if (rc == DG_ERR_CUDA || rc == DG_ERR_NO_MEMORY) return rc;
+    if (rc != DG_OK && (worst == DG_OK || rc < worst)) worst = rc;
+    const double* v = h->x64.as<double>();
+    if (b0 == 0) {
+      // E_H = 1/2 sum_q W_q rho v_H (source 0 holds rho)
+      std::vector<int> a0{0};
+      DG_RET(upload_act(h, a0, s));
+      DG_CK(launch_dot<double>(h->f64.as<double>(), v, h->d_W.as<double>(), scal(h, S_RR), h->part.as<double>(), Nq,
+                               h->act.as<int>(), 1, s));
+      double val = 0.0;
+      DG_CK(cudaMemcpyAsync(&val, scal(h, S_RR), sizeof(double), cudaMemcpyDeviceToHost, s));
+      DG_CK(cudaStreamSynchronize(s));
+      eh = 0.5 * val;
+    }
+    // W_j += psi_s v_sj and W_s += psi_j v_sj (s != j), per orbital in fixed order
+    std::vector<std::vector<std::pair<int, int>>> per(N);
+    for (int k = 0; k < nb; ++k) {
+      const int g = b0 + k;
+      if (si[g] < 0) continue;
+      per[sj[g]].push_back({k, si[g]});
+      if (si[g] != sj[g]) per[si[g]].push_back({k, sj[g]});
+    }
+    std::vector<int> ptr(N + 1, 0), eb, es;
+    for (int m = 0; m < N; ++m) {
+      for (auto& e : per[m]) {
+        eb.push_back(e.first);
+        es.push_back(e.second);
+      }
+      ptr[m + 1] = (int)eb.size();
+    }
+    if (!eb.empty()) {
+      std::vector<int> pack;
+      pack.insert(pack.end(), ptr.begin(), ptr.end());
+      pack.insert(pack.end(), eb.begin(), eb.end());
+      pack.insert(pack.end(), es.begin(), es.end());
+      DG_CK(lists.ensure(sizeof(int) * pack.size()));
+      DG_CK(cudaMemcpyAsync(lists.p, pack.data(), sizeof(int) * pack.size(), cudaMemcpyHostToDevice, s));
+      const int* dl = lists.as<int>();
+      DG_CK(launch_exch_accum(psi, v, h->Wacc.as<double>(), dl, dl + N + 1, dl + N + 1 + eb.size(), N, Nq, s));
+      DG_CK(cudaStreamSynchronize(s));  // pack is a host temporary
+    }
+  }
+  DG_CK(launch_kmat(psi, h->d_W.as<double>(), h->Wacc.as<double>(), N, Nq, h->kpart.as<double>(), nch,
+                    h->Kdev.as<double>(), s));
+  DG_CK(cudaMemcpyAsync(K_host, h->Kdev.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  if (E_H) *E_H = eh;
+  if (E_X) {
+    double tr = 0.0;
+    for (int i = 0; i < N; ++i) tr += K_host[(size_t)i * N + i];
+    *E_X = -0.5 * tr;
+  }
+  account(h);
+  return worst;
+}
+
+}  // extern "C"

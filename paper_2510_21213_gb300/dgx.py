@@ -1,0 +1,320 @@
+"""Thin Python binding of the C ABI in include/dg_poisson.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libdgx.so. Device arrays are torch CUDA tensors (contiguous,
+float64 unless stated); the binding passes their data pointers and the
+current torch stream. There is no CPU fallback: importing this module fails
+loudly if the library has not been built.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libdgx.so")
+
+DG_OK = 0
+DG_ERR_INVALID_ARG = -1
+DG_ERR_CUDA = -2
+DG_ERR_NOT_CONVERGED = -3
+DG_ERR_BREAKDOWN = -4
+DG_ERR_NONFINITE = -5
+DG_ERR_TIMEOUT = -6
+DG_ERR_NO_MEMORY = -7
+DG_ERR_UNSUPPORTED = -8
+
+DG_PREC_FP64 = 0
+DG_PREC_MIXED = 1
+DG_PREC_MIXED_LEARNED = 2
+DG_BC_DIRECT = 0
+DG_BC_GAUSSSUM = 1
+DG_SMOOTH_JACOBI = 0
+DG_SMOOTH_SCHWARZ = 1
+
+
+class dg_mesh_desc(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("n", C.c_int32 * 3), ("p", C.c_int32)]
+
+
+class dg_solver_opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int32),
+        ("rtol", C.c_double),
+        ("max_iter", C.c_int32),
+        ("penalty_eps", C.c_double),
+        ("penalty_form", C.c_int32),
+        ("bc_route", C.c_int32),
+        ("bc_tol", C.c_double),
+        ("batch", C.c_int32),
+        ("smoother", C.c_int32),
+        ("smoother_degree", C.c_int32),
+        ("cheb_range", C.c_double),
+        ("inner_rtol", C.c_double),
+        ("nn_weights_path", C.c_char_p),
+        ("verbose", C.c_int32),
+    ]
+
+
+class dg_solve_stats(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32),
+        ("outer_refinements", C.c_int32),
+        ("status", C.c_int32),
+        ("used_fallback", C.c_int32),
+        ("rel_residual", C.c_double),
+    ]
+
+
+class dg_info(C.Structure):
+    _fields_ = [
+        ("Nq", C.c_int64),
+        ("levels", C.c_int32),
+        ("level_n", C.c_int32 * 16),
+        ("level_p", C.c_int32 * 16),
+        ("coarse_dofs", C.c_int32),
+        ("n_gauss", C.c_int32),
+        ("gauss_rmin", C.c_double),
+        ("gauss_rmax", C.c_double),
+        ("gauss_relerr", C.c_double),
+        ("sigma", C.c_double * 3),
+        ("workspace_bytes", C.c_int64),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libdgx.so (built by paper_2510_21213_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2510_21213_gb300.build.build() first")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    lib.dg_default_opts.argtypes = [C.POINTER(dg_solver_opts)]
+    lib.dg_default_opts.restype = None
+    lib.dg_poisson_setup.argtypes = [C.POINTER(dg_mesh_desc), C.POINTER(dg_solver_opts), C.POINTER(vp)]
+    lib.dg_get_info.argtypes = [vp, C.POINTER(dg_info)]
+    lib.dg_node_coords.argtypes = [vp, vp, vp]
+    lib.dg_pair_solve_batch.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+    lib.dg_exchange_build.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp]
+    lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
+    lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
+    lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
+    lib.dg_kernel_launch_count.argtypes = []
+    lib.dg_kernel_launch_count.restype = C.c_int64
+    lib.dg_destroy.argtypes = [vp]
+    lib.dg_destroy.restype = None
+    lib.dg_error_string.argtypes = [C.c_int]
+    lib.dg_error_string.restype = C.c_char_p
+    lib.dg_last_error_detail.argtypes = [vp]
+    lib.dg_last_error_detail.restype = C.c_char_p
+    for name in ("dg_poisson_setup", "dg_get_info", "dg_node_coords", "dg_pair_solve_batch", "dg_exchange_build",
+                 "dg_apply_operator", "dg_boundary_data", "dg_apply_smoother"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        msg = load().dg_error_string(code).decode()
+        super().__init__(f"{where}: {msg} ({code}) {detail}".strip())
+
+
+def _check(code, where, handle=None, allow=()):
+    if code != DG_OK and code not in allow:
+        detail = load().dg_last_error_detail(handle).decode() if handle else ""
+        raise DGError(code, where, detail)
+    return code
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def dg_default_opts(**overrides):
+    o = dg_solver_opts()
+    load().dg_default_opts(C.byref(o))
+    for k, v in overrides.items():
+        if k == "nn_weights_path" and v is not None:
+            v = str(v).encode()
+        setattr(o, k, v)
+    return o
+
+
+def dg_poisson_setup(lo, hi, n, p, opts=None):
+    """Returns a handle (c_void_p). lo, hi: 3 floats; n: int or 3 ints; p: degree."""
+    if np.isscalar(n):
+        n = (n, n, n)
+    m = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
+    if opts is None:
+        opts = dg_default_opts()
+    h = C.c_void_p()
+    _check(load().dg_poisson_setup(C.byref(m), C.byref(opts), C.byref(h)), "dg_poisson_setup")
+    return h
+
+
+def dg_get_info(h):
+    info = dg_info()
+    _check(load().dg_get_info(h, C.byref(info)), "dg_get_info", h)
+    return info
+
+
+def dg_node_coords(h):
+    """(xyz [Nq, 3], W [Nq]) numpy arrays, element-blocked order."""
+    Nq = dg_get_info(h).Nq
+    xyz = np.empty((Nq, 3), dtype=np.float64)
+    w = np.empty(Nq, dtype=np.float64)
+    _check(load().dg_node_coords(h, xyz.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)), "dg_node_coords", h)
+    return xyz, w
+
+
+def _stats_list(arr):
+    return [{"iters": s.iters, "outer_refinements": s.outer_refinements, "status": s.status,
+             "used_fallback": s.used_fallback, "rel_residual": s.rel_residual} for s in arr]
+
+
+def dg_pair_solve_batch(h, f, v=None, stream=None, allow_unconverged=False):
+    """f: CUDA float64 [B, Nq]. Returns (v, stats)."""
+    import torch
+
+    B = f.shape[0]
+    if v is None:
+        v = torch.empty_like(f)
+    st = (dg_solve_stats * max(B, 1))()
+    allow = (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_NONFINITE) if allow_unconverged else ()
+    code = load().dg_pair_solve_batch(h, _dev_ptr(f, torch.float64), B, _dev_ptr(v, torch.float64),
+                                      C.cast(st, C.c_void_p), _stream_ptr(stream))
+    _check(code, "dg_pair_solve_batch", h, allow)
+    return v, _stats_list(st[:B])
+
+
+def dg_exchange_build(h, psi, stream=None, allow_unconverged=False):
+    """psi: CUDA float64 [N, Nq]. Returns (K [N, N] numpy, E_H, E_X, stats)."""
+    import torch
+
+    N = psi.shape[0]
+    K = np.empty((N, N), dtype=np.float64)
+    eh = C.c_double()
+    ex = C.c_double()
+    P = N * (N + 1) // 2 + 1
+    st = (dg_solve_stats * P)()
+    allow = (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_NONFINITE) if allow_unconverged else ()
+    code = load().dg_exchange_build(h, _dev_ptr(psi, torch.float64), N, K.ctypes.data_as(C.c_void_p), C.byref(eh),
+                                    C.byref(ex), C.cast(st, C.c_void_p), _stream_ptr(stream))
+    _check(code, "dg_exchange_build", h, allow)
+    return K, eh.value, ex.value, _stats_list(st[:P])
+
+
+def dg_apply_operator(h, u, level=0, out=None, stream=None):
+    """u: CUDA [B, Nq_level] float64 or float32; returns A u."""
+    import torch
+
+    if out is None:
+        out = torch.empty_like(u)
+    fp32 = 1 if u.dtype == torch.float32 else 0
+    code = load().dg_apply_operator(h, level, fp32, _dev_ptr(u), _dev_ptr(out, u.dtype), u.shape[0],
+                                    _stream_ptr(stream))
+    _check(code, "dg_apply_operator", h)
+    return out
+
+
+def dg_apply_smoother(h, r, level=0, out=None, stream=None):
+    """r: CUDA [B, Nq_level] float64 or float32; returns M r (smoother preconditioner)."""
+    import torch
+
+    if out is None:
+        out = torch.empty_like(r)
+    fp32 = 1 if r.dtype == torch.float32 else 0
+    code = load().dg_apply_smoother(h, level, fp32, _dev_ptr(r), _dev_ptr(out, r.dtype), r.shape[0],
+                                    _stream_ptr(stream))
+    _check(code, "dg_apply_smoother", h)
+    return out
+
+
+def dg_boundary_data(h, f, route=DG_BC_GAUSSSUM, stream=None):
+    """f: CUDA float64 [B, Nq]. Returns g [B, n_face_nodes] (faces -x,+x,-y,+y,-z,+z)."""
+    import torch
+
+    nf = C.c_int64()
+    lib = load()
+    _check(lib.dg_boundary_data(h, route, None, 0, None, C.byref(nf), None), "dg_boundary_data", h)
+    g = torch.empty((f.shape[0], nf.value), dtype=torch.float64, device=f.device)
+    _check(lib.dg_boundary_data(h, route, _dev_ptr(f, torch.float64), f.shape[0], _dev_ptr(g), C.byref(nf),
+                                _stream_ptr(stream)), "dg_boundary_data", h)
+    return g
+
+
+def dg_kernel_launch_count():
+    return int(load().dg_kernel_launch_count())
+
+
+def dg_destroy(h):
+    if h:
+        load().dg_destroy(h)
+
+
+class PoissonSolver:
+    """Owns one handle: a uniform box mesh and its solver settings."""
+
+    def __init__(self, lo, hi, n, p, **opts):
+        self.opts = dg_default_opts(**opts)
+        self.h = dg_poisson_setup(lo, hi, n, p, self.opts)
+        self.info = dg_get_info(self.h)
+
+    @property
+    def Nq(self):
+        return self.info.Nq
+
+    def node_coords(self):
+        return dg_node_coords(self.h)
+
+    def solve(self, f, **kw):
+        return dg_pair_solve_batch(self.h, f, **kw)
+
+    def exchange_build(self, psi, **kw):
+        return dg_exchange_build(self.h, psi, **kw)
+
+    def apply(self, u, level=0):
+        return dg_apply_operator(self.h, u, level)
+
+    def smoother(self, r, level=0):
+        return dg_apply_smoother(self.h, r, level)
+
+    def boundary_data(self, f, route=DG_BC_GAUSSSUM):
+        return dg_boundary_data(self.h, f, route)
+
+    def close(self):
+        if self.h:
+            dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,7 +7,7 @@ passes in (optionally Loewdin-orthonormalised in the discrete inner product
 given by the caller's quadrature weights). Both the CUDA path and the CPU
 oracle are fed from here, so they see identical inputs.
 
-Recipes (the paper uses Gaussian-type orbitals on molecules, Sec. 4.2; the
+Recipes (the paper uses Gaussian-type orbitals on molecules, Sec. 4.1.2; the
 systems below are synthetic stand-ins with the same structure):
 
 * "tiny":    box [-8, 8]^3, 4^3 elements, p = 4; two normalised s-Gaussians of

@@ -18,7 +18,7 @@ from paper_2510_21213_gb300 import inputs
 
 
 # ---------------------------------------------------------------------------
-# Quadrature and the nodal basis (Sec. 5.2: degree-q nodal GL elements whose
+# Quadrature and the nodal basis (Sec. 6.2: degree-q nodal GL elements whose
 # nodes double as the quadrature rule)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("p", [1, 2, 4, 7])
@@ -71,7 +71,7 @@ def test_collocated_mass_is_exact(p):
 
 
 # ---------------------------------------------------------------------------
-# SIPDG operator (Eq. 19, Sec. 3.4, Sec. 5.3)
+# SIPDG operator (Sec. 3.4 eq. sip_bilinear, Sec. 3.5, Sec. 6.3)
 # ---------------------------------------------------------------------------
 TINY = [
     ([-1.0, -2.0, -1.5], [1.0, 2.0, 2.0], (2, 2, 3), 2),
@@ -152,7 +152,7 @@ def test_fdm_equals_cholesky(lo, hi, n, p):
 
 
 # ---------------------------------------------------------------------------
-# Boundary data and Gaussian potentials (Sec. 5.3, Eqs. 33-34)
+# Boundary data and Gaussian potentials (Sec. 6.3)
 # ---------------------------------------------------------------------------
 A_EXP = 2.0
 CENTER = np.array([0.35, -0.2, 0.1])
@@ -220,7 +220,7 @@ def test_hartree_self_energy_converges():
 
 
 # ---------------------------------------------------------------------------
-# Exchange matrix and energies (Eq. 29, Sec. 2.3.1)
+# Exchange matrix and energies (Sec. 6.1.2 eq. fock_exchange, Sec. 2.3.1)
 # ---------------------------------------------------------------------------
 def _tiny_continuum():
     """Free-space values for two normalised s-Gaussians (exponent 1) at
