@@ -129,6 +129,8 @@ typedef struct {
   double gauss_relerr; /* measured max relative error of the sum on that range */
   double sigma[3];     /* fine-level penalty per axis */
   int64_t workspace_bytes; /* device workspace currently held by the handle */
+  int32_t n_gauss_fp32; /* terms of the FP32 Gaussian sum of the mixed modes (0 in FP64 mode) */
+  double gauss_relerr_fp32; /* its measured max relative error */
 } dg_info;
 
 typedef struct dg_ctx* dg_handle;
@@ -177,7 +179,8 @@ int dg_exchange_build(dg_handle h, const double* psi_dev, int32_t N, double* K_h
 /* Matrix-free SIPDG operator of multigrid level `level` (0 = fine) applied to
  * B fields: out = A u. u_dev, out_dev: [B][Nq_level] device arrays of the
  * handle's working precision for that call: FP64 when fp32 == 0, FP32 when
- * fp32 == 1. Exposed for tests and for timing the operator kernel alone. */
+ * fp32 == 1. Exposed for tests and for timing the operator kernel alone: the
+ * call is stream-ordered and returns without synchronising the stream. */
 int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u_dev, void* out_dev,
                       int64_t B, void* cuda_stream);
 
@@ -185,12 +188,14 @@ int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u_de
  * fields: z = M r with M the additive Schwarz operator sum_P R_P^T A_P^-1 R_P
  * (DG_SMOOTH_SCHWARZ) or D^-1 (DG_SMOOTH_JACOBI); on the coarsest level M is
  * the exact inverse A_c^-1. r_dev, z_dev: [B][Nq_level] device arrays, FP64
- * (fp32 == 0) or FP32 (fp32 == 1). Exposed for tests and kernel timing. */
+ * (fp32 == 0) or FP32 (fp32 == 1). Exposed for tests and kernel timing; the
+ * call is stream-ordered and returns without synchronising the stream. */
 int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r_dev, void* z_dev, int64_t B,
                       void* cuda_stream);
 
 /* Boundary data g of Sec. 6.3 for B sources f_dev [B][Nq] (device): g_dev
- * [B][n_face_nodes] (device, FP64), faces in the order -x,+x,-y,+y,-z,+z, each
+ * [B][n_face_nodes] (device, FP64; the Gaussian-sum route is evaluated in FP32
+ * with a 1e-7 table when the handle is in a mixed mode, as in the solves), faces in the order -x,+x,-y,+y,-z,+z, each
  * face a 2-D grid of its two tangential global node indices with the lower
  * axis fastest. route: DG_BC_*. Returns the total face-node count in
  * *n_face_nodes when g_dev is NULL. */

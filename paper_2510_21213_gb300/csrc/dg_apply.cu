@@ -14,26 +14,90 @@
 
 namespace dg {
 
-template <int N1>
+// Launch layout: EPB elements per block; in the three 1-D passes each thread
+// owns LPT lines of one element (line values in registers, the 1-D block rows
+// streamed from shared memory and reused across the lines). Loads of the
+// element, the neighbour traces and the final store are spread over all
+// threads of the block and coalesced.
+template <typename T, int N1>
 struct ApplyCfg {
   static constexpr int NPE = N1 * N1 * N1;
   static constexpr int NF = N1 * N1;
-  static constexpr int EPB = (NPE >= 128) ? 1 : (256 / NPE);
-  static constexpr int THREADS = EPB * NPE;
+  static constexpr int LPT = sizeof(T) == 4 ? 3 : 1;
+  static constexpr int TPE = (NF + LPT - 1) / LPT;
+  static constexpr int PER_ELEM = (2 * NPE + 12 * NF + 3) * (int)sizeof(T);
+  static constexpr int EPB_T = 256 / TPE < 1 ? 1 : 256 / TPE;
+  static constexpr int EPB_S = 36864 / PER_ELEM < 1 ? 1 : 36864 / PER_ELEM;
+  static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;
+  static constexpr int THREADS = EPB * TPE < 32 ? 32 : EPB * TPE;
 };
 
+// one direction of the operator for LPT lines of one element:
+// sacc[line] (+)= m1 * m2 * (K_ty v + cLv tv- + cLd td- + cRv tv+ + cRd td+)
+template <typename T, int N1, int LPT, int TPE, int DIR, bool ACCUM>
+__device__ __forceinline__ void ap_pass(const T* __restrict__ su, T* __restrict__ sacc, const T* __restrict__ K,
+                                        const T* __restrict__ cc, const T* __restrict__ tr,
+                                        const T* __restrict__ mA, const T* __restrict__ mB, int lt) {
+  constexpr int NF = N1 * N1;
+  constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N1 : NF);
+  T v[LPT][N1];
+  int base[LPT], tt[LPT];
+  bool ok[LPT];
+  T scale[LPT], tvm[LPT], tdm[LPT], tvp[LPT], tdp[LPT];
+#pragma unroll
+  for (int s = 0; s < LPT; ++s) {
+    const int l = lt + TPE * s;
+    ok[s] = l < NF;
+    const int l1 = ok[s] ? l % N1 : 0, l2 = ok[s] ? l / N1 : 0;
+    // line (l1, l2) = (b, c) for x, (a, c) for y, (a, b) for z
+    base[s] = DIR == 0 ? N1 * l1 + NF * l2 : (DIR == 1 ? l1 + NF * l2 : l1 + N1 * l2);
+    tt[s] = l1 + N1 * l2;
+    scale[s] = mA[l1] * mB[l2];
+    tvm[s] = tr[(0 * 2 + 0) * NF + tt[s]];
+    tdm[s] = tr[(0 * 2 + 1) * NF + tt[s]];
+    tvp[s] = tr[(1 * 2 + 0) * NF + tt[s]];
+    tdp[s] = tr[(1 * 2 + 1) * NF + tt[s]];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) v[s][i] = su[base[s] + i * stride];
+  }
+#pragma unroll 1
+  for (int a = 0; a < N1; ++a) {
+    T acc[LPT];
+    const T c0 = cc[0 * N1 + a], c1 = cc[1 * N1 + a], c2 = cc[2 * N1 + a], c3 = cc[3 * N1 + a];
+#pragma unroll
+    for (int s = 0; s < LPT; ++s) acc[s] = c0 * tvm[s] + c1 * tdm[s] + c2 * tvp[s] + c3 * tdp[s];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      const T kv = K[a * N1 + i];
+#pragma unroll
+      for (int s = 0; s < LPT; ++s) acc[s] += kv * v[s][i];
+    }
+#pragma unroll
+    for (int s = 0; s < LPT; ++s)
+      if (ok[s]) {
+        T* dst = sacc + base[s] + a * stride;
+        if (ACCUM)
+          *dst += scale[s] * acc[s];
+        else
+          *dst = scale[s] * acc[s];
+      }
+  }
+}
+
 template <typename T, int N1, int MODE>
-__global__ void __launch_bounds__(ApplyCfg<N1>::THREADS)
+__global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS)
     k_apply(const LevelOp* __restrict__ op, const T* __restrict__ u, T* __restrict__ out,
             const T* __restrict__ rin, const int* __restrict__ act, int nact) {
-  using C = ApplyCfg<N1>;
-  constexpr int NPE = C::NPE, NF = C::NF, EPB = C::EPB, NT = C::THREADS;
+  using C = ApplyCfg<T, N1>;
+  constexpr int NPE = C::NPE, NF = C::NF, EPB = C::EPB, NT = C::THREADS, TPE = C::TPE, LPT = C::LPT;
   __shared__ T sK[3][4][NF];
   __shared__ T sC[3][4][N1];
   __shared__ T sM[3][N1];
   __shared__ T sTr[4][N1];
   __shared__ T su[EPB][NPE];
+  __shared__ T sacc[EPB][NPE];
   __shared__ T st[EPB][6][2][NF];
+  __shared__ int sty[EPB][3];
 
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * 4 * NF; i += NT) {
@@ -57,99 +121,105 @@ __global__ void __launch_bounds__(ApplyCfg<N1>::THREADS)
   const int nx = op->n[0], ny = op->n[1], nz = op->n[2];
   const int E = op->E;
   const long long Nq = op->Nq;
-  const int slot = tid / NPE, loc = tid % NPE;
-  const long long item = (long long)blockIdx.x * EPB + slot;
-  const bool valid = item < (long long)nact * E;
-  const int k = valid ? (int)(item / E) : 0;
-  const int e = valid ? (int)(item % E) : 0;
-  const long long rhs = valid ? (long long)act[k] : 0;
-  const T* ub = u + rhs * Nq;
-  if (valid) su[slot][loc] = ub[(long long)e * NPE + loc];
-  const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
-  __syncthreads();
-
-  // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d)
-  for (int t = loc; t < 6 * NF; t += NPE) {
-    const int f = t / NF, tt = t % NF;
-    const int d = f >> 1, side = f & 1;
-    const int coord = d == 0 ? ex : (d == 1 ? ey : ez);
-    const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
-    T val = 0, der = 0;
-    const bool has = valid && (side == 0 ? coord > 0 : coord < nd - 1);
-    if (has) {
-      const int se = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
-      const int en = e + (side == 0 ? -se : se);
-      const T* un = ub + (long long)en * NPE;
-      const int t1 = tt % N1, t2 = tt / N1;
-      int base, sd;
-      if (d == 0) {
-        base = N1 * t1 + NF * t2;
-        sd = 1;
-      } else if (d == 1) {
-        base = t1 + NF * t2;
-        sd = N1;
-      } else {
-        base = t1 + N1 * t2;
-        sd = NF;
+  const int slot = tid / TPE, lt = tid % TPE;
+  const long long items = (long long)nact * E;
+  const long long groups = (items + EPB - 1) / EPB;
+  for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
+    __syncthreads();  // tables ready / previous group done with the shared buffers
+    // own elements (coalesced over consecutive items)
+    for (int t = tid; t < EPB * NPE; t += NT) {
+      const int sl = t / NPE, loc = t % NPE;
+      const long long it = grp * EPB + sl;
+      T v = 0;
+      if (it < items) {
+        const int e = (int)(it % E);
+        v = u[(long long)act[it / E] * Nq + (long long)e * NPE + loc];
       }
-      // the -d neighbour meets us at its right end, the +d neighbour at its left end
-      const T* tv = side == 0 ? sTr[1] : sTr[0];
-      const T* td = side == 0 ? sTr[3] : sTr[2];
+      su[sl][loc] = v;
+    }
+    for (int t = tid; t < EPB * 3; t += NT) {
+      const int sl = t / 3, d = t % 3;
+      const long long it = grp * EPB + sl;
+      const int e = it < items ? (int)(it % E) : 0;
+      const int cd = d == 0 ? e % nx : (d == 1 ? (e / nx) % ny : e / (nx * ny));
+      const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
+      sty[sl][d] = (cd == 0 ? 1 : 0) | (cd == nd - 1 ? 2 : 0);
+    }
+    // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d)
+    for (int t = tid; t < EPB * 6 * NF; t += NT) {
+      const int sl = t / (6 * NF), rem = t % (6 * NF);
+      const int f = rem / NF, tt = rem % NF;
+      const int d = f >> 1, side = f & 1;
+      const long long it = grp * EPB + sl;
+      T val = 0, der = 0;
+      if (it < items) {
+        const int e = (int)(it % E);
+        const int coord = d == 0 ? e % nx : (d == 1 ? (e / nx) % ny : e / (nx * ny));
+        const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
+        if (side == 0 ? coord > 0 : coord < nd - 1) {
+          const int se = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
+          const T* un = u + (long long)act[it / E] * Nq + (long long)(e + (side == 0 ? -se : se)) * NPE;
+          const int t1 = tt % N1, t2 = tt / N1;
+          const int base = d == 0 ? N1 * t1 + NF * t2 : (d == 1 ? t1 + NF * t2 : t1 + N1 * t2);
+          const int sd = d == 0 ? 1 : (d == 1 ? N1 : NF);
+          // the -d neighbour meets us at its right end, the +d neighbour at its left end
+          const T* tv = side == 0 ? sTr[1] : sTr[0];
+          const T* td = side == 0 ? sTr[3] : sTr[2];
 #pragma unroll
-      for (int i = 0; i < N1; ++i) {
-        const T x = un[base + i * sd];
-        val += tv[i] * x;
-        der += td[i] * x;
+          for (int i = 0; i < N1; ++i) {
+            const T xv = un[base + i * sd];
+            val += tv[i] * xv;
+            der += td[i] * xv;
+          }
+        }
+      }
+      st[sl][f][0][tt] = val;
+      st[sl][f][1][tt] = der;
+    }
+    __syncthreads();
+    if (slot < EPB) {
+      ap_pass<T, N1, LPT, TPE, 0, false>(su[slot], sacc[slot], sK[0][sty[slot][0]], sC[0][0], &st[slot][0][0][0],
+                                         sM[1], sM[2], lt);
+    }
+    __syncthreads();
+    if (slot < EPB) {
+      ap_pass<T, N1, LPT, TPE, 1, true>(su[slot], sacc[slot], sK[1][sty[slot][1]], sC[1][0], &st[slot][2][0][0],
+                                        sM[0], sM[2], lt);
+    }
+    __syncthreads();
+    if (slot < EPB) {
+      ap_pass<T, N1, LPT, TPE, 2, true>(su[slot], sacc[slot], sK[2][sty[slot][2]], sC[2][0], &st[slot][4][0][0],
+                                        sM[0], sM[1], lt);
+    }
+    __syncthreads();
+    for (int t = tid; t < EPB * NPE; t += NT) {
+      const int sl = t / NPE, loc = t % NPE;
+      const long long it = grp * EPB + sl;
+      if (it < items) {
+        const long long gi = (long long)act[it / E] * Nq + (long long)(it % E) * NPE + loc;
+        const T Au = sacc[sl][loc];
+        if (MODE == 0) {
+          out[gi] = Au;
+        } else if (MODE == 1) {
+          out[gi] = rin[gi] - Au;
+        } else {
+          out[gi] = out[gi] - Au;
+        }
       }
     }
-    st[slot][f][0][tt] = val;
-    st[slot][f][1][tt] = der;
-  }
-  __syncthreads();
-  if (!valid) return;
-
-  const int a = loc % N1, b = (loc / N1) % N1, c = loc / NF;
-  const int tyx = (ex == 0 ? 1 : 0) | (ex == nx - 1 ? 2 : 0);
-  const int tyy = (ey == 0 ? 1 : 0) | (ey == ny - 1 ? 2 : 0);
-  const int tyz = (ez == 0 ? 1 : 0) | (ez == nz - 1 ? 2 : 0);
-  const T* us = su[slot];
-
-  T sx = 0, sy = 0, sz = 0;
-#pragma unroll
-  for (int i = 0; i < N1; ++i) {
-    sx += sK[0][tyx][a * N1 + i] * us[i + N1 * b + NF * c];
-    sy += sK[1][tyy][b * N1 + i] * us[a + N1 * i + NF * c];
-    sz += sK[2][tyz][c * N1 + i] * us[a + N1 * b + NF * i];
-  }
-  {
-    const int tx = b + N1 * c;
-    sx += sC[0][0][a] * st[slot][0][0][tx] + sC[0][1][a] * st[slot][0][1][tx] + sC[0][2][a] * st[slot][1][0][tx] +
-          sC[0][3][a] * st[slot][1][1][tx];
-    const int ty = a + N1 * c;
-    sy += sC[1][0][b] * st[slot][2][0][ty] + sC[1][1][b] * st[slot][2][1][ty] + sC[1][2][b] * st[slot][3][0][ty] +
-          sC[1][3][b] * st[slot][3][1][ty];
-    const int tz = a + N1 * b;
-    sz += sC[2][0][c] * st[slot][4][0][tz] + sC[2][1][c] * st[slot][4][1][tz] + sC[2][2][c] * st[slot][5][0][tz] +
-          sC[2][3][c] * st[slot][5][1][tz];
-  }
-  const T Au = sM[1][b] * sM[2][c] * sx + sM[0][a] * sM[2][c] * sy + sM[0][a] * sM[1][b] * sz;
-  const long long gi = rhs * Nq + (long long)e * NPE + loc;
-  if (MODE == 0) {
-    out[gi] = Au;
-  } else if (MODE == 1) {
-    out[gi] = rin[gi] - Au;
-  } else {
-    out[gi] = out[gi] - Au;
   }
 }
 
 template <typename T, int N1>
 static cudaError_t apply_n1(const LevelOp& hop, const LevelOp* dop, int mode, const T* u, T* out, const T* rin,
                             const int* act, int nact, cudaStream_t s) {
-  using C = ApplyCfg<N1>;
+  using C = ApplyCfg<T, N1>;
   const long long items = (long long)nact * hop.E;
-  const long long blocks = (items + C::EPB - 1) / C::EPB;
+  long long blocks = (items + C::EPB - 1) / C::EPB;
   if (blocks == 0) return cudaSuccess;
+  // persistent-style grid: a few resident blocks per SM loop over element groups
+  const long long cap = 152LL * (2048 / C::THREADS) * 2;
+  if (blocks > cap) blocks = cap;
   count_launch();
   if (mode == 0)
     k_apply<T, N1, 0><<<(unsigned)blocks, C::THREADS, 0, s>>>(dop, u, out, rin, act, nact);

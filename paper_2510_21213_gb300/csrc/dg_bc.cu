@@ -13,8 +13,9 @@
 namespace dg {
 
 // Flex[src][X + Lx (Y + Ly Z)] = W_q f_src(q): element-blocked -> global lexicographic.
+template <typename T>
 __global__ void k_weighted_lex(const LevelOp* __restrict__ op, const double* __restrict__ f,
-                               const double* __restrict__ W, double* __restrict__ flex) {
+                               const double* __restrict__ W, T* __restrict__ flex) {
   const long long Nq = op->Nq;
   const int n1 = op->n1, npe = n1 * n1 * n1;
   const int nx = op->n[0], ny = op->n[1];
@@ -26,19 +27,24 @@ __global__ void k_weighted_lex(const LevelOp* __restrict__ op, const double* __r
     const long long X = (long long)(e % nx) * n1 + a;
     const long long Y = (long long)((e / nx) % ny) * n1 + b;
     const long long Z = (long long)(e / (nx * ny)) * n1 + c;
-    flex[src * Nq + X + Lx * (Y + Ly * Z)] = W[q] * f[src * Nq + q];
+    flex[src * Nq + X + Lx * (Y + Ly * Z)] = (T)(W[q] * f[src * Nq + q]);
   }
 }
 
-cudaError_t launch_weighted_lex(const LevelOp& hop, const LevelOp* dop, const double* f, const double* W,
-                                double* flex, int nsrc, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_weighted_lex(const LevelOp& hop, const LevelOp* dop, const double* f, const double* W, T* flex,
+                                int nsrc, cudaStream_t s) {
   if (nsrc == 0) return cudaSuccess;
   long long gx = (hop.Nq + 1023) / 1024;
   if (gx > 4096) gx = 4096;
   count_launch();
-  k_weighted_lex<<<dim3((unsigned)gx, nsrc), 256, 0, s>>>(dop, f, W, flex);
+  k_weighted_lex<T><<<dim3((unsigned)gx, nsrc), 256, 0, s>>>(dop, f, W, flex);
   return cudaGetLastError();
 }
+template cudaError_t launch_weighted_lex<double>(const LevelOp&, const LevelOp*, const double*, const double*,
+                                                 double*, int, cudaStream_t);
+template cudaError_t launch_weighted_lex<float>(const LevelOp&, const LevelOp*, const double*, const double*, float*,
+                                                int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Strided batched GEMM: C[m,n] = alpha sum_k A[m,k] B[k,n] + beta C[m,n]

@@ -90,10 +90,12 @@ struct dg_ctx {
   dg::DevBuf d_W, d_xq, d_axn;
   int lmax = 0;
   long long nface = 0;
-  // boundary-data tables
-  dg::GaussSum gsum;
-  int NG = 0;
-  dg::BcAxisTables bct[3];
+  // boundary-data tables: FP64 (1e-12 Gaussian sum) and, in the mixed modes,
+  // FP32 (1e-7 Gaussian sum)
+  dg::GaussSum gsum, gsum32;
+  int NG = 0, NG32 = 0;
+  dg::BcAxisTables bct[3], bct32[3];
+  dg::DevBuf flex32, T1_32, T2_32, g32;
   // workspaces
   dg::PrecWork<double> w64;
   dg::PrecWork<float> w32;
@@ -102,6 +104,7 @@ struct dg_ctx {
   dg::DevBuf part, scal, act, flags, pidx;
   dg::DevBuf Wacc, kpart, Kdev;
   int cap = 0;
+  std::vector<int> act_host;  // contents of act (device) as last uploaded
   std::string err;
   long long ws_bytes = 0;
 };
@@ -146,7 +149,6 @@ static int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap) {
     DG_CK(L.d.ensure(sizeof(T) * N * cap));
     if (h->opts.smoother == DG_SMOOTH_SCHWARZ && l + 1 < h->nlev) {
       const long long mp = h->levels[l].op.n1 + 2;
-      DG_CK(L.z.ensure(sizeof(T) * N * cap));
       DG_CK(L.zp.ensure(sizeof(T) * (size_t)h->levels[l].op.E * mp * mp * mp * cap));
     }
     if (!L.invD.p) {
@@ -175,6 +177,7 @@ static int ensure_common(dg_ctx* h, int cap) {
   DG_CK(h->part.ensure(sizeof(double) * 304 * cap));
   DG_CK(h->scal.ensure(sizeof(double) * S_NSLOT * cap));
   DG_CK(h->act.ensure(sizeof(int) * cap));
+  h->act_host.clear();
   DG_CK(h->flags.ensure(sizeof(int) * cap));
   DG_CK(h->pidx.ensure(sizeof(int) * 2 * cap));
   DG_CK(h->g.ensure(sizeof(double) * h->nface * cap));
@@ -182,17 +185,18 @@ static int ensure_common(dg_ctx* h, int cap) {
   return DG_OK;
 }
 
-static int ensure_bc_work(dg_ctx* h, int nsrc) {
+template <typename T>
+static int ensure_bc_work(dg_ctx* h, int nsrc, int NG, BcAxisTables* bct, DevBuf& flex, DevBuf& T1, DevBuf& T2) {
   const long long N = h->Nq;
-  DG_CK(h->flex.ensure(sizeof(double) * N * nsrc));
+  DG_CK(flex.ensure(sizeof(T) * N * nsrc));
   long long maxface = 0;
   for (int d = 0; d < 3; ++d) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    maxface = std::max(maxface, (long long)h->bct[t1].L * h->bct[t2].L);
+    maxface = std::max(maxface, (long long)bct[t1].L * bct[t2].L);
   }
-  const size_t tb = sizeof(double) * 2 * (size_t)h->NG * maxface * nsrc;
-  DG_CK(h->T1.ensure(tb));
-  DG_CK(h->T2.ensure(tb));
+  const size_t tb = sizeof(T) * 2 * (size_t)NG * maxface * nsrc;
+  DG_CK(T1.ensure(tb));
+  DG_CK(T2.ensure(tb));
   return DG_OK;
 }
 
@@ -200,6 +204,7 @@ static void account(dg_ctx* h) {
   long long b = 0;
   auto add = [&](const DevBuf& x) { b += (long long)x.bytes; };
   for (auto* w : {&h->f64, &h->b64, &h->x64, &h->r64, &h->flex, &h->T1, &h->T2, &h->g, &h->part, &h->scal,
+                  &h->flex32, &h->T1_32, &h->T2_32, &h->g32,
                   &h->act, &h->flags, &h->pidx, &h->Wacc, &h->kpart, &h->Kdev, &h->coarse_inv, &h->d_W, &h->d_xq,
                   &h->d_axn})
     add(*w);
@@ -214,6 +219,7 @@ static void account(dg_ctx* h) {
   for (auto* w : {&h->w32.x, &h->w32.r, &h->w32.z, &h->w32.p, &h->w32.q}) add(*w);
   for (int d = 0; d < 3; ++d) {
     add(h->bct[d].gn); add(h->bct[d].G); add(h->bct[d].Gs);
+    add(h->bct32[d].gn); add(h->bct32[d].G); add(h->bct32[d].Gs);
   }
   h->ws_bytes = b;
 }
@@ -240,7 +246,6 @@ struct MG {
     const bool sw = h->opts.smoother == DG_SMOOTH_SCHWARZ;
     // sw: the smoother preconditioner is M_S (z = M_S res), else D^-1 (fused)
     const T* invD = sw ? nullptr : W.invD.as<T>();
-    T* z = sw ? W.z.as<T>() : nullptr;
     const long long Nq = L.op.Nq;
     const int k = std::max(1, h->opts.smoother_degree);
     const double bmax = sw ? L.lam_sw : L.lam_max * (1.0 + 1e-6);
@@ -252,11 +257,11 @@ struct MG {
       DG_CK(launch_apply<T>(L.op, L.dop, 1, x, res, b, act, nact, s));
       r0 = res;
     }
-    if (sw) {
-      DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r0, W.zp.as<T>(), z, act, nact, s));
-      r0 = z;
-    }
-    DG_CK(launch_cheb_first<T>(x, d, r0, invD, 1.0 / theta, zero_init ? 1 : 0, Nq, act, nact, s));
+    if (sw)
+      DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r0, W.zp.as<T>(), d, x, zero_init ? 1 : 2,
+                              1.0 / theta, 0.0, act, nact, s));
+    else
+      DG_CK(launch_cheb_first<T>(x, d, r0, invD, 1.0 / theta, zero_init ? 1 : 0, Nq, act, nact, s));
     double rho_prev = 1.0 / sig1;
     bool res_is_b = zero_init;  // the residual of the current x is b - A d when res_is_b
     for (int j = 2; j <= k; ++j) {
@@ -266,12 +271,11 @@ struct MG {
         DG_CK(launch_apply<T>(L.op, L.dop, 2, d, res, nullptr, act, nact, s));
       res_is_b = false;
       const double rho = 1.0 / (2.0 * sig1 - rho_prev);
-      const T* rr = res;
-      if (sw) {
-        DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), res, W.zp.as<T>(), z, act, nact, s));
-        rr = z;
-      }
-      DG_CK(launch_cheb_step<T>(x, d, rr, invD, rho * rho_prev, 2.0 * rho / delta, Nq, act, nact, s));
+      if (sw)
+        DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), res, W.zp.as<T>(), d, x, 3, rho * rho_prev,
+                                2.0 * rho / delta, act, nact, s));
+      else
+        DG_CK(launch_cheb_step<T>(x, d, res, invD, rho * rho_prev, 2.0 * rho / delta, Nq, act, nact, s));
       rho_prev = rho;
     }
     if (want_res) {
@@ -321,10 +325,13 @@ __global__ void k_copy_slot(const double* src, double* dst, const int* act, int 
   if (k < nact) dst[act[k]] = src[act[k]];
 }
 
+// Active source list on the device; re-uploaded only when it changes.
 static int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s) {
   if (a.empty()) return DG_OK;
+  if (h->act_host == a) return DG_OK;
   DG_CK(cudaMemcpyAsync(h->act.p, a.data(), sizeof(int) * a.size(), cudaMemcpyHostToDevice, s));
   DG_CK(cudaStreamSynchronize(s));
+  h->act_host = a;
   return DG_OK;
 }
 
@@ -520,31 +527,28 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
 // ---------------------------------------------------------------------------
 // boundary data of the sources in f64[0..nsrc) into g[0..nsrc)
 // ---------------------------------------------------------------------------
-static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double* g, cudaStream_t s) {
+// Gaussian-sum route in precision T (tables bct, NG terms)
+template <typename T>
+static int boundary_gausssum(dg_ctx* h, const double* f, int nsrc, T* g, BcAxisTables* bct, int NG, DevBuf& flexb,
+                             DevBuf& T1b, DevBuf& T2b, cudaStream_t s) {
   const LevelOp& op = h->levels[0].op;
-  if (route == DG_BC_DIRECT) {
-    DG_CK(launch_bc_direct(op, h->levels[0].dop, f, h->d_W.as<double>(), h->d_xq.as<double>(),
-                           h->d_axn.as<double>(), h->lmax, g, nsrc, h->nface, h->nface, s));
-    return DG_OK;
-  }
-  DG_RET(ensure_bc_work(h, nsrc));
-  double* flex = h->flex.as<double>();
-  DG_CK(launch_weighted_lex(op, h->levels[0].dop, f, h->d_W.as<double>(), flex, nsrc, s));
-  const int NG = h->NG;
-  const long long Lx = h->bct[0].L, Ly = h->bct[1].L, Lz = h->bct[2].L;
+  DG_RET(ensure_bc_work<T>(h, nsrc, NG, bct, flexb, T1b, T2b));
+  T* flex = flexb.as<T>();
+  DG_CK(launch_weighted_lex<T>(op, h->levels[0].dop, f, h->d_W.as<double>(), flex, nsrc, s));
+  const long long Lx = bct[0].L, Ly = bct[1].L, Lz = bct[2].L;
   const long long Nq = h->Nq;
   long long face_off = 0;
-  double* T1 = h->T1.as<double>();
-  double* T2 = h->T2.as<double>();
+  T* T1 = T1b.as<T>();
+  T* T2 = T2b.as<T>();
   for (int d = 0; d < 3; ++d) {
     const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    const long long L1 = h->bct[t1].L, L2 = h->bct[t2].L, Ld = h->bct[d].L;
+    const long long L1 = bct[t1].L, L2 = bct[t2].L, Ld = bct[d].L;
     const long long tsz = 2LL * NG * L1 * L2;  // per source
     // step 1: contraction along the normal axis with both face positions
     GemmArgs a{};
     a.M = 2 * NG;
     a.K = (int)Ld;
-    a.A = h->bct[d].gn.p;
+    a.A = bct[d].gn.p;
     a.sAm = Ld;
     a.sAk = 1;
     a.C = T1;
@@ -552,37 +556,29 @@ static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double
     a.sCn = 1;
     a.alpha = 1.0;
     a.beta = 0.0;
+    a.B = flex;
+    a.nb1 = nsrc;
+    a.sB1 = Nq;
+    a.sC1 = tsz;
     if (d == 0) {
       a.N = (int)(Ly * Lz);
-      a.nb1 = nsrc;
       a.nb2 = 1;
-      a.B = flex;
       a.sBk = 1;
       a.sBn = Lx;
-      a.sB1 = Nq;
-      a.sC1 = tsz;
     } else if (d == 1) {
       a.N = (int)Lx;
-      a.nb1 = nsrc;
       a.nb2 = (int)Lz;
-      a.B = flex;
       a.sBk = Lx;
       a.sBn = 1;
-      a.sB1 = Nq;
       a.sB2 = Lx * Ly;
-      a.sC1 = tsz;
       a.sC2 = Lx;
     } else {
       a.N = (int)(Lx * Ly);
-      a.nb1 = nsrc;
       a.nb2 = 1;
-      a.B = flex;
       a.sBk = Lx * Ly;
       a.sBn = 1;
-      a.sB1 = Nq;
-      a.sC1 = tsz;
     }
-    DG_CK(launch_gemm<double>(a, s));
+    DG_CK(launch_gemm<T>(a, s));
     // step 2: along t1 (fastest index), per (source, side, term)
     GemmArgs b{};
     b.M = (int)L2;
@@ -595,7 +591,7 @@ static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double
     b.sAk = 1;
     b.sA1 = (long long)NG * L1 * L2;
     b.sA2 = L1 * L2;
-    b.B = h->bct[t1].G.p;
+    b.B = bct[t1].G.p;
     b.sBk = 1;
     b.sBn = L1;
     b.sB1 = 0;
@@ -607,7 +603,7 @@ static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double
     b.sC2 = L1 * L2;
     b.alpha = 1.0;
     b.beta = 0.0;
-    DG_CK(launch_gemm<double>(b, s));
+    DG_CK(launch_gemm<T>(b, s));
     // step 3: along t2 together with the weighted sum over terms
     GemmArgs c{};
     c.M = (int)L2;
@@ -615,7 +611,7 @@ static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double
     c.K = (int)(NG * L2);
     c.nb1 = nsrc;
     c.nb2 = 2;
-    c.A = h->bct[t2].Gs.p;
+    c.A = bct[t2].Gs.p;
     c.sAm = NG * L2;
     c.sAk = 1;
     c.B = T2;
@@ -630,18 +626,42 @@ static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double
     c.sC2 = L1 * L2;
     c.alpha = 1.0;
     c.beta = 0.0;
-    DG_CK(launch_gemm<double>(c, s));
+    DG_CK(launch_gemm<T>(c, s));
     face_off += 2 * L1 * L2;
   }
-  (void)Lz;
   return DG_OK;
 }
 
-// b64 = 4 pi W f + Nitsche lift of g(f) for f64[0..nsrc)
+// boundary data of the sources f[0..nsrc) into g[0..nsrc) (FP64)
+static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double* g, cudaStream_t s) {
+  const LevelOp& op = h->levels[0].op;
+  if (route == DG_BC_DIRECT) {
+    DG_CK(launch_bc_direct(op, h->levels[0].dop, f, h->d_W.as<double>(), h->d_xq.as<double>(),
+                           h->d_axn.as<double>(), h->lmax, g, nsrc, h->nface, h->nface, s));
+    return DG_OK;
+  }
+  return boundary_gausssum<double>(h, f, nsrc, g, h->bct, h->NG, h->flex, h->T1, h->T2, s);
+}
+
+// b64 = 4 pi W f + Nitsche lift of g(f) for f[0..nsrc). The mixed modes
+// evaluate the Gaussian-sum route in FP32 with their own (1e-7) table.
+static bool bc_fp32(const dg_ctx* h) {
+  return h->opts.precision != DG_PREC_FP64 && h->opts.bc_route == DG_BC_GAUSSSUM;
+}
+
 static int form_rhs(dg_ctx* h, const double* f, int nsrc, cudaStream_t s) {
   DG_CK(launch_rhs_volume(f, h->d_W.as<double>(), h->b64.as<double>(), h->Nq, nsrc, s));
-  DG_RET(boundary_data(h, h->opts.bc_route, f, nsrc, h->g.as<double>(), s));
-  DG_CK(launch_lift(h->levels[0].op, h->levels[0].dop, h->g.as<double>(), h->b64.as<double>(), nsrc, h->nface, s));
+  if (bc_fp32(h)) {
+    DG_CK(h->g32.ensure(sizeof(float) * h->nface * nsrc));
+    DG_RET(boundary_gausssum<float>(h, f, nsrc, h->g32.as<float>(), h->bct32, h->NG32, h->flex32, h->T1_32,
+                                    h->T2_32, s));
+    DG_CK(launch_lift<float>(h->levels[0].op, h->levels[0].dop, h->g32.as<float>(), h->b64.as<double>(), nsrc,
+                             h->nface, s));
+  } else {
+    DG_RET(boundary_data(h, h->opts.bc_route, f, nsrc, h->g.as<double>(), s));
+    DG_CK(launch_lift<double>(h->levels[0].op, h->levels[0].dop, h->g.as<double>(), h->b64.as<double>(), nsrc,
+                              h->nface, s));
+  }
   return DG_OK;
 }
 
@@ -709,7 +729,7 @@ static int estimate_lambda_schwarz(dg_ctx* h, int l, double* out) {
     return DG_OK;
   };
   DG_CK(launch_schwarz<double>(L.op, L.dop, L.sw_tabs.as<double>(), r.as<double>(), zp.as<double>(),
-                               z.as<double>(), a, 1, 0));
+                               z.as<double>(), nullptr, 0, 0.0, 0.0, a, 1, 0));
   DG_CK(cudaMemcpy(p.p, z.p, sizeof(double) * N, cudaMemcpyDeviceToDevice));
   double rz = 0.0;
   DG_RET(dot(r.as<double>(), z.as<double>(), &rz));
@@ -724,7 +744,7 @@ static int estimate_lambda_schwarz(dg_ctx* h, int l, double* out) {
     DG_CK(cudaMemcpy(sc, &alpha, sizeof(double), cudaMemcpyHostToDevice));
     DG_CK(launch_cg_xr<double>(x.as<double>(), r.as<double>(), p.as<double>(), q.as<double>(), sc, N, a, 1, 0));
     DG_CK(launch_schwarz<double>(L.op, L.dop, L.sw_tabs.as<double>(), r.as<double>(), zp.as<double>(),
-                                 z.as<double>(), a, 1, 0));
+                                 z.as<double>(), nullptr, 0, 0.0, 0.0, a, 1, 0));
     double rzn = 0.0;
     DG_RET(dot(r.as<double>(), z.as<double>(), &rzn));
     const double beta = rzn / rz;
@@ -865,38 +885,50 @@ static int setup(dg_ctx* h) {
       rmin = std::min(rmin, (1.0 - xi[n1 - 1]) * F.ax[d].h / 2.0);
       diag2 += (m.hi[d] - m.lo[d]) * (m.hi[d] - m.lo[d]);
     }
-    const double tol = o.bc_tol > 0 ? o.bc_tol : 1e-12;
-    h->gsum = make_gauss_sum(rmin * 0.999, std::sqrt(diag2) * 1.001, tol);
-    h->NG = (int)h->gsum.c.size();
-    if (h->NG == 0) {
-      h->err = "could not build the Gaussian-sum 1/r table";
-      return DG_ERR_INVALID_ARG;
-    }
-    const int NG = h->NG;
-    for (int d = 0; d < 3; ++d) {
-      const int L = (int)h->axis_nodes[d].size();
-      h->bct[d].L = L;
-      const std::vector<double>& x = h->axis_nodes[d];
-      std::vector<double> gn(2 * (size_t)NG * L), G((size_t)NG * L * L), Gs((size_t)L * NG * L);
-      for (int sd = 0; sd < 2; ++sd) {
-        const double xf = sd == 0 ? m.lo[d] : m.hi[d];
-        for (int k = 0; k < NG; ++k)
-          for (int i = 0; i < L; ++i) gn[((size_t)sd * NG + k) * L + i] = std::exp(-h->gsum.a[k] * (x[i] - xf) * (x[i] - xf));
+    auto build_tables = [&](double tol, GaussSum& gs, int& NG, BcAxisTables* bct, bool fp32) -> int {
+      gs = make_gauss_sum(rmin * 0.999, std::sqrt(diag2) * 1.001, tol);
+      NG = (int)gs.c.size();
+      if (NG == 0) {
+        h->err = "could not build the Gaussian-sum 1/r table";
+        return DG_ERR_INVALID_ARG;
       }
-      for (int k = 0; k < NG; ++k)
-        for (int i = 0; i < L; ++i)
-          for (int j = 0; j < L; ++j) {
-            const double v = std::exp(-h->gsum.a[k] * (x[i] - x[j]) * (x[i] - x[j]));
-            G[((size_t)k * L + i) * L + j] = v;
-            Gs[(size_t)i * NG * L + (size_t)k * L + j] = h->gsum.c[k] * v;
+      for (int d = 0; d < 3; ++d) {
+        const int L = (int)h->axis_nodes[d].size();
+        bct[d].L = L;
+        const std::vector<double>& x = h->axis_nodes[d];
+        std::vector<double> gn(2 * (size_t)NG * L), G((size_t)NG * L * L), Gs((size_t)L * NG * L);
+        for (int sd = 0; sd < 2; ++sd) {
+          const double xf = sd == 0 ? m.lo[d] : m.hi[d];
+          for (int k = 0; k < NG; ++k)
+            for (int i = 0; i < L; ++i) gn[((size_t)sd * NG + k) * L + i] = std::exp(-gs.a[k] * (x[i] - xf) * (x[i] - xf));
+        }
+        for (int k = 0; k < NG; ++k)
+          for (int i = 0; i < L; ++i)
+            for (int j = 0; j < L; ++j) {
+              const double v = std::exp(-gs.a[k] * (x[i] - x[j]) * (x[i] - x[j]));
+              G[((size_t)k * L + i) * L + j] = v;
+              Gs[(size_t)i * NG * L + (size_t)k * L + j] = gs.c[k] * v;
+            }
+        auto up = [&](DevBuf& dst, const std::vector<double>& src) -> int {
+          if (fp32) {
+            std::vector<float> t(src.begin(), src.end());
+            DG_CK(dst.ensure(sizeof(float) * t.size()));
+            DG_CK(cudaMemcpy(dst.p, t.data(), sizeof(float) * t.size(), cudaMemcpyHostToDevice));
+          } else {
+            DG_CK(dst.ensure(sizeof(double) * src.size()));
+            DG_CK(cudaMemcpy(dst.p, src.data(), sizeof(double) * src.size(), cudaMemcpyHostToDevice));
           }
-      DG_CK(h->bct[d].gn.ensure(sizeof(double) * gn.size()));
-      DG_CK(cudaMemcpy(h->bct[d].gn.p, gn.data(), sizeof(double) * gn.size(), cudaMemcpyHostToDevice));
-      DG_CK(h->bct[d].G.ensure(sizeof(double) * G.size()));
-      DG_CK(cudaMemcpy(h->bct[d].G.p, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice));
-      DG_CK(h->bct[d].Gs.ensure(sizeof(double) * Gs.size()));
-      DG_CK(cudaMemcpy(h->bct[d].Gs.p, Gs.data(), sizeof(double) * Gs.size(), cudaMemcpyHostToDevice));
-    }
+          return DG_OK;
+        };
+        DG_RET(up(bct[d].gn, gn));
+        DG_RET(up(bct[d].G, G));
+        DG_RET(up(bct[d].Gs, Gs));
+      }
+      return DG_OK;
+    };
+    const double tol = o.bc_tol > 0 ? o.bc_tol : 1e-12;
+    DG_RET(build_tables(tol, h->gsum, h->NG, h->bct, false));
+    if (o.precision != DG_PREC_FP64) DG_RET(build_tables(1e-7, h->gsum32, h->NG32, h->bct32, true));
   }
   account(h);
   return DG_OK;
@@ -914,7 +946,8 @@ static int apply_smoother_t(dg_ctx* h, PrecWork<T>& w, int level, const T* r, T*
   if (level == h->nlev - 1) {
     DG_CK(launch_coarse_solve<T>(h->coarse_inv.as<double>(), h->Nc, r, z, a, nb, s));
   } else if (h->opts.smoother == DG_SMOOTH_SCHWARZ) {
-    DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r, w.lev[level].zp.template as<T>(), z, a, nb, s));
+    DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r, w.lev[level].zp.template as<T>(), z, nullptr, 0,
+                            0.0, 0.0, a, nb, s));
   } else {
     DG_CK(launch_cheb_first<T>(z, z, r, w.lev[level].invD.template as<T>(), 1.0, 1, L.op.Nq, a, nb, s));
   }
@@ -1027,6 +1060,8 @@ int dg_get_info(dg_handle h, dg_info* info) {
   info->gauss_rmin = h->gsum.rmin;
   info->gauss_rmax = h->gsum.rmax;
   info->gauss_relerr = h->gsum.relerr;
+  info->n_gauss_fp32 = h->NG32;
+  info->gauss_relerr_fp32 = h->gsum32.relerr;
   for (int d = 0; d < 3; ++d) info->sigma[d] = h->levels[0].op.ax[d].sigma;
   account(h);
   info->workspace_bytes = h->ws_bytes;
@@ -1070,7 +1105,6 @@ int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u, v
       DG_CK(launch_apply<double>(L.op, L.dop, 0, (const double*)u + b0 * L.op.Nq, (double*)out + b0 * L.op.Nq,
                                  nullptr, h->act.as<int>(), nb, s));
   }
-  DG_CK(cudaStreamSynchronize(s));
   return DG_OK;
 }
 
@@ -1095,7 +1129,6 @@ int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r, v
     else
       DG_RET(apply_smoother_t<double>(h, h->w64, level, (const double*)r + b0 * N, (double*)z + b0 * N, nb, s));
   }
-  DG_CK(cudaStreamSynchronize(s));
   return DG_OK;
 }
 
@@ -1107,9 +1140,21 @@ int dg_boundary_data(dg_handle h, int32_t route, const double* f, int64_t B, dou
   if (!f) return DG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int cap = std::max(1, std::min(default_batch(h), (int)B));
+  DG_RET(ensure_common(h, cap));
   for (int64_t b0 = 0; b0 < B; b0 += cap) {
     const int nb = (int)std::min<int64_t>(cap, B - b0);
-    DG_RET(boundary_data(h, route, f + b0 * h->Nq, nb, g + b0 * h->nface, s));
+    if (route == DG_BC_GAUSSSUM && bc_fp32(h)) {
+      DG_CK(h->g32.ensure(sizeof(float) * h->nface * nb));
+      DG_RET(boundary_gausssum<float>(h, f + b0 * h->Nq, nb, h->g32.as<float>(), h->bct32, h->NG32, h->flex32,
+                                      h->T1_32, h->T2_32, s));
+      std::vector<int> a(nb);
+      for (int k = 0; k < nb; ++k) a[k] = k;
+      DG_RET(upload_act(h, a, s));
+      DG_CK((launch_convert<double, float>(g + b0 * h->nface, h->g32.as<float>(), h->nface, h->act.as<int>(), nb,
+                                           1.0, 0, s)));
+    } else {
+      DG_RET(boundary_data(h, route, f + b0 * h->Nq, nb, g + b0 * h->nface, s));
+    }
   }
   DG_CK(cudaStreamSynchronize(s));
   return DG_OK;

@@ -126,10 +126,11 @@ template <typename T>
 cudaError_t launch_coarse_solve(const double* Ainv, int Nc, const T* r, T* x, const int* act, int nact,
                                 cudaStream_t s);
 
-// Schwarz smoother: zp[rhs][e][MP^3] = A_P^-1 R_P r, then z = sum_P R_P^T zp
+// Schwarz smoother: zp[rhs][e][MP^3] = A_P^-1 R_P r, then with y = sum_P R_P^T zp:
+// mode 0: z = y; 1: z = c1 y, x = z; 2: z = c1 y, x += z; 3: z = c1 z + c2 y, x += z
 template <typename T>
 cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
-                           const int* act, int nact, cudaStream_t s);
+                           T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s);
 
 // sources and right-hand sides
 cudaError_t launch_pair_sources(const double* psi, int N, const int* pi, const int* pj, int nsrc, long long Nq,
@@ -137,12 +138,14 @@ cudaError_t launch_pair_sources(const double* psi, int N, const int* pi, const i
 cudaError_t launch_rhs_volume(const double* f, const double* W, double* b, long long Nq, int nsrc,
                               cudaStream_t s);
 cudaError_t launch_finite_flags(const double* f, long long Nq, int nsrc, int* flags, cudaStream_t s);
-cudaError_t launch_lift(const LevelOp& hop, const LevelOp* dop, const double* g, double* b, int nsrc,
+template <typename Tg>
+cudaError_t launch_lift(const LevelOp& hop, const LevelOp* dop, const Tg* g, double* b, int nsrc,
                         long long gstride, cudaStream_t s);
 
 // boundary data
-cudaError_t launch_weighted_lex(const LevelOp& hop, const LevelOp* dop, const double* f, const double* W,
-                                double* flex, int nsrc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_weighted_lex(const LevelOp& hop, const LevelOp* dop, const double* f, const double* W, T* flex,
+                                int nsrc, cudaStream_t s);
 template <typename T>
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s);
 cudaError_t launch_bc_direct(const LevelOp& hop, const LevelOp* dop, const double* f, const double* W,

@@ -7,9 +7,11 @@
 // overlap, accelerated by Chebyshev iteration. Each patch problem is solved
 // exactly by fast diagonalisation (the patch operator is a Kronecker sum of
 // restricted 1-D matrices; tables built at setup):
-//   k_schwarz_patch:  zp_e = A_P(e)^-1 R_P(e) r        (one block per element)
-//   k_schwarz_gather: z    = sum_e R_P(e)^T zp_e       (each node gathers the
-//                            at most 8 patches covering it; no atomics)
+//   k_schwarz_patch:  zp_e = A_P(e)^-1 R_P(e) r        (EPB elements per block,
+//                     one thread per patch line in each of the six 1-D passes)
+//   k_schwarz_gather: z = sum_e R_P(e)^T zp_e          (each node gathers the
+//                     at most 8 patches covering it; no atomics), fused with
+//                     the Chebyshev update d = c1 d + c2 z, x += d
 #include "dg_internal.h"
 
 namespace dg {
@@ -18,164 +20,288 @@ __host__ __device__ inline int sw_axis_off(const LevelOp* op, int d, int stride)
   return d == 0 ? 0 : (d == 1 ? op->n[0] * stride : (op->n[0] + op->n[1]) * stride);
 }
 
+// Patch kernel layout: each thread owns LPT = 3 lines of the patch in every
+// 1-D pass (line values and outputs in registers, the 1-D matrix streamed from
+// shared memory and reused across the three lines).
 template <typename T, int N1>
-__global__ void __launch_bounds__(256)
-    k_schwarz_patch(const LevelOp* __restrict__ op, const double* __restrict__ tabs, const T* __restrict__ r,
-                    T* __restrict__ zp, const int* __restrict__ act) {
-  constexpr int MP = N1 + 2, MP3 = MP * MP * MP, NPE = N1 * N1 * N1, STR = 2 + MP * MP + MP;
-  __shared__ T sS[3][MP * MP];
-  __shared__ T sL[3][MP];
-  __shared__ T b0[MP3];
-  __shared__ T b1[MP3];
-  const int e = blockIdx.x;
-  const long long rhs = act[blockIdx.y];
-  const int nx = op->n[0], ny = op->n[1];
-  const int E = op->E;
-  const long long Nq = op->Nq;
-  const int pos[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
-  int m[3], oL[3];
+struct SwCfg {
+  static constexpr int MP = N1 + 2;
+  static constexpr int LINES = MP * MP;
+  // FP32: three lines per thread (shared-memory traffic per FMA / 3); FP64 is
+  // bound by the FP64 pipe, one line per thread keeps registers in check
+  static constexpr int LPT = sizeof(T) == 4 ? 3 : 1;
+  static constexpr int TPE = (LINES + LPT - 1) / LPT;  // threads per element
+  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;  // resident blocks per SM asked of ptxas
+  static constexpr int PER_ELEM = (MP * MP * MP + 3 * MP * MP + 3 * MP) * (int)sizeof(T);
+  static constexpr int EPB_T = 256 / TPE < 1 ? 1 : 256 / TPE;
+  static constexpr int EPB_S = 40960 / PER_ELEM < 1 ? 1 : 40960 / PER_ELEM;
+  static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;
+  static constexpr int THREADS = EPB * TPE;
+};
+
+// One 1-D pass over up to three lines l = lt + TPE s of one patch.
+// dir 0: x lines (j, k) stride 1; dir 1: y lines (i, k) stride MP; dir 2: z
+// lines (i, j) stride MP^2. Forward: v[q] <- sum_i S[i][q] v[i]; backward:
+// v[i] <- sum_q S[i][q] v[q].
+template <typename T, int MP, int TPE, int LPT, int DIR, bool BACKWARD>
+__device__ __forceinline__ void sw_pass3(T* __restrict__ buf, const T* __restrict__ S, int lt) {
+  constexpr int MP2 = MP * MP;
+  constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? MP : MP2);
+  int base[LPT];
+  bool ok[LPT];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double* tb = tabs + sw_axis_off(op, d, STR) + (long long)pos[d] * STR;
-    m[d] = (int)tb[0];
-    oL[d] = (int)tb[1];
-    for (int i = threadIdx.x; i < MP * MP; i += blockDim.x) sS[d][i] = (T)tb[2 + i];
-    for (int i = threadIdx.x; i < MP; i += blockDim.x) sL[d][i] = (T)tb[2 + MP * MP + i];
+  for (int s = 0; s < LPT; ++s) {
+    const int l = lt + TPE * s;
+    ok[s] = l < MP2;
+    const int l1 = l % MP, l2 = l / MP;
+    base[s] = ok[s] ? (DIR == 0 ? (l1 + MP * l2) * MP : (DIR == 1 ? l1 + MP2 * l2 : l1 + MP * l2)) : 0;
   }
-  // gather the patch residual (own element plus one node layer of the neighbours)
-  for (int t = threadIdx.x; t < MP3; t += blockDim.x) {
-    const int i = t % MP, j = (t / MP) % MP, k = t / (MP * MP);
-    T v = 0;
-    if (i < m[0] && j < m[1] && k < m[2]) {
-      const int X = pos[0] * N1 - oL[0] + i, Y = pos[1] * N1 - oL[1] + j, Z = pos[2] * N1 - oL[2] + k;
-      const long long en = (long long)(X / N1) + (long long)nx * ((Y / N1) + (long long)ny * (Z / N1));
-      const int loc = (X % N1) + N1 * ((Y % N1) + N1 * (Z % N1));
-      v = r[rhs * Nq + en * NPE + loc];
+  if (!BACKWARD) {
+    // o[q] = sum_i S[i][q] v[i]: inputs streamed row by row, outputs in registers
+    T o[LPT][MP];
+#pragma unroll
+    for (int s = 0; s < LPT; ++s)
+#pragma unroll
+      for (int q = 0; q < MP; ++q) o[s][q] = (T)0;
+#pragma unroll 1
+    for (int i = 0; i < MP; ++i) {
+      T vi[LPT];
+#pragma unroll
+      for (int s = 0; s < LPT; ++s) vi[s] = buf[base[s] + i * stride];
+#pragma unroll
+      for (int q = 0; q < MP; ++q) {
+        const T sv = S[i * MP + q];
+#pragma unroll
+        for (int s = 0; s < LPT; ++s) o[s][q] += sv * vi[s];
+      }
     }
-    b0[t] = v;
-  }
-  __syncthreads();
-  // forward transforms: b <- (Sx (x) Sy (x) Sz)^T b
-  for (int t = threadIdx.x; t < MP3; t += blockDim.x) {
-    const int q = t % MP, jk = t / MP;
-    T acc = 0;
-    for (int i = 0; i < m[0]; ++i) acc += sS[0][i * MP + q] * b0[jk * MP + i];
-    b1[t] = acc;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < MP3; t += blockDim.x) {
-    const int i = t % MP, q = (t / MP) % MP, k = t / (MP * MP);
-    T acc = 0;
-    for (int j = 0; j < m[1]; ++j) acc += sS[1][j * MP + q] * b1[(k * MP + j) * MP + i];
-    b0[t] = acc;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < MP3; t += blockDim.x) {
-    const int i = t % MP, j = (t / MP) % MP, q = t / (MP * MP);
-    T acc = 0;
-    for (int k = 0; k < m[2]; ++k) acc += sS[2][k * MP + q] * b0[(k * MP + j) * MP + i];
-    const bool in = i < m[0] && j < m[1] && q < m[2];
-    b1[t] = in ? acc / (sL[0][i] + sL[1][j] + sL[2][q]) : (T)0;
-  }
-  __syncthreads();
-  // backward transforms: b <- (Sx (x) Sy (x) Sz) b
-  for (int t = threadIdx.x; t < MP3; t += blockDim.x) {
-    const int i = t % MP, jk = t / MP;
-    T acc = 0;
-    for (int q = 0; q < m[0]; ++q) acc += sS[0][i * MP + q] * b1[jk * MP + q];
-    b0[t] = acc;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < MP3; t += blockDim.x) {
-    const int i = t % MP, j = (t / MP) % MP, k = t / (MP * MP);
-    T acc = 0;
-    for (int q = 0; q < m[1]; ++q) acc += sS[1][j * MP + q] * b0[(k * MP + q) * MP + i];
-    b1[t] = acc;
-  }
-  __syncthreads();
-  T* out = zp + ((long long)rhs * E + e) * MP3;
-  for (int t = threadIdx.x; t < MP3; t += blockDim.x) {
-    const int ij = t % (MP * MP), k = t / (MP * MP);
-    T acc = 0;
-    for (int q = 0; q < m[2]; ++q) acc += sS[2][k * MP + q] * b1[q * MP * MP + ij];
-    out[t] = acc;
+#pragma unroll
+    for (int s = 0; s < LPT; ++s)
+      if (ok[s]) {
+#pragma unroll
+        for (int q = 0; q < MP; ++q) buf[base[s] + q * stride] = o[s][q];
+      }
+  } else {
+    // o[i] = sum_q S[i][q] v[q]: inputs in registers, each output written when done
+    T v[LPT][MP];
+#pragma unroll
+    for (int s = 0; s < LPT; ++s)
+#pragma unroll
+      for (int q = 0; q < MP; ++q) v[s][q] = buf[base[s] + q * stride];
+#pragma unroll 1
+    for (int i = 0; i < MP; ++i) {
+      T acc[LPT];
+#pragma unroll
+      for (int s = 0; s < LPT; ++s) acc[s] = (T)0;
+#pragma unroll
+      for (int q = 0; q < MP; ++q) {
+        const T sv = S[i * MP + q];
+#pragma unroll
+        for (int s = 0; s < LPT; ++s) acc[s] += sv * v[s][q];
+      }
+#pragma unroll
+      for (int s = 0; s < LPT; ++s)
+        if (ok[s]) buf[base[s] + i * stride] = acc[s];
+    }
   }
 }
 
 template <typename T, int N1>
-__global__ void k_schwarz_gather(const LevelOp* __restrict__ op, const T* __restrict__ zp, T* __restrict__ z,
-                                 const int* __restrict__ act) {
+__global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
+    k_schwarz_patch(const LevelOp* __restrict__ op, const double* __restrict__ tabs, const T* __restrict__ r,
+                    T* __restrict__ zp, const int* __restrict__ act, int nact) {
+  using C = SwCfg<T, N1>;
+  constexpr int MP = C::MP, MP2 = MP * MP, MP3 = MP * MP * MP, NPE = N1 * N1 * N1, STR = 2 + MP2 + MP;
+  constexpr int EPB = C::EPB, NT = C::THREADS, TPE = C::TPE, LPT = C::LPT;
+  __shared__ T sS[EPB][3][MP2];
+  __shared__ T sL[EPB][3][MP];
+  __shared__ T buf[EPB][MP3];
+  __shared__ int sm[EPB][3], soL[EPB][3];
+  const int nx = op->n[0], ny = op->n[1];
+  const int E = op->E;
+  const long long Nq = op->Nq;
+  const int slot = threadIdx.x / TPE, lt = threadIdx.x % TPE;
+  const long long items = (long long)nact * E;
+  const long long item = (long long)blockIdx.x * EPB + slot;
+  const bool valid = item < items;
+  const int e = valid ? (int)(item % E) : 0;
+  const long long rhs = valid ? act[item / E] : 0;
+  const int pos[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
+  // patch tables of the EPB elements
+  for (int t = threadIdx.x; t < EPB * 3 * STR; t += NT) {
+    const int sl = t / (3 * STR), rem = t % (3 * STR);
+    const int d = rem / STR, k = rem % STR;
+    const long long it = (long long)blockIdx.x * EPB + sl;
+    const int ee = it < items ? (int)(it % E) : 0;
+    const int pd = d == 0 ? ee % nx : (d == 1 ? (ee / nx) % ny : ee / (nx * ny));
+    const double* tb = tabs + sw_axis_off(op, d, STR) + (long long)pd * STR;
+    if (k < 2) {
+      if (k == 0)
+        sm[sl][d] = (int)tb[0];
+      else
+        soL[sl][d] = (int)tb[1];
+    } else if (k < 2 + MP2) {
+      sS[sl][d][k - 2] = (T)tb[k];
+    } else {
+      sL[sl][d][k - 2 - MP2] = (T)tb[k];
+    }
+  }
+  __syncthreads();
+  const int mx = sm[slot][0], my = sm[slot][1], mz = sm[slot][2];
+  const int oLx = soL[slot][0], oLy = soL[slot][1], oLz = soL[slot][2];
+  T* b = buf[slot];
+  // gather the patch residual (own element plus one node layer of each neighbour)
+  const T* rr = r + rhs * Nq;
+  for (int t = lt; t < MP3; t += TPE) {
+    const int i = t % MP, j = (t / MP) % MP, k = t / MP2;
+    T v = 0;
+    if (valid && i < mx && j < my && k < mz) {
+      const int X = pos[0] * N1 - oLx + i, Y = pos[1] * N1 - oLy + j, Z = pos[2] * N1 - oLz + k;
+      const int ex = X / N1, ey = Y / N1, ez = Z / N1;
+      const long long en = ex + (long long)nx * (ey + (long long)ny * ez);
+      v = rr[en * NPE + (X - ex * N1) + N1 * ((Y - ey * N1) + N1 * (Z - ez * N1))];
+    }
+    b[t] = v;
+  }
+  __syncthreads();
+  sw_pass3<T, MP, TPE, LPT, 0, false>(b, sS[slot][0], lt);
+  __syncthreads();
+  sw_pass3<T, MP, TPE, LPT, 1, false>(b, sS[slot][1], lt);
+  __syncthreads();
+  sw_pass3<T, MP, TPE, LPT, 2, false>(b, sS[slot][2], lt);
+  // scale by 1 / (lx + ly + lz) along this thread's z lines (i, j)
+#pragma unroll
+  for (int s = 0; s < LPT; ++s) {
+    const int l = lt + TPE * s;
+    if (l < MP2) {
+      const int l1 = l % MP, l2 = l / MP;
+#pragma unroll
+      for (int k = 0; k < MP; ++k) {
+        const int t = l + MP2 * k;
+        const bool in = l1 < mx && l2 < my && k < mz;
+        b[t] = in ? b[t] / (sL[slot][0][l1] + sL[slot][1][l2] + sL[slot][2][k]) : (T)0;
+      }
+    }
+  }
+  sw_pass3<T, MP, TPE, LPT, 2, true>(b, sS[slot][2], lt);
+  __syncthreads();
+  sw_pass3<T, MP, TPE, LPT, 1, true>(b, sS[slot][1], lt);
+  __syncthreads();
+  sw_pass3<T, MP, TPE, LPT, 0, true>(b, sS[slot][0], lt);
+  __syncthreads();
+  if (!valid) return;
+  T* out = zp + (rhs * E + e) * (long long)MP3;
+  for (int t = lt; t < MP3; t += TPE) out[t] = b[t];
+}
+
+// mode 0: z = M r; 1: d = c1 M r, x = d; 2: d = c1 M r, x += d; 3: d = c1 d + c2 M r, x += d
+// (d is passed in z). One block per element (grid-stride), one thread per node.
+template <typename T, int N1, int MODE>
+__global__ void __launch_bounds__(N1 * N1 * N1 < 64 ? 64 : N1 * N1 * N1)
+    k_schwarz_gather(const LevelOp* __restrict__ op, const T* __restrict__ zp, T* __restrict__ z, T* __restrict__ x,
+                     T c1, T c2, const int* __restrict__ act) {
   constexpr int MP = N1 + 2, MP3 = MP * MP * MP, NPE = N1 * N1 * N1;
-  const long long rhs = act[blockIdx.y];
   const int nx = op->n[0], ny = op->n[1], nz = op->n[2];
   const int E = op->E;
   const long long Nq = op->Nq;
+  const long long rhs = act[blockIdx.y];
   const T* zr = zp + rhs * E * (long long)MP3;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Nq; q += (long long)gridDim.x * blockDim.x) {
-    const int e = (int)(q / NPE), loc = (int)(q % NPE);
-    const int lc[3] = {loc % N1, (loc / N1) % N1, loc / (N1 * N1)};
-    const int ec[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
-    const int nn[3] = {nx, ny, nz};
-    // per axis: up to two (patch position, coordinate inside that patch)
-    int cp[3][2], cc[3][2], cn[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      cn[d] = 1;
-      cp[d][0] = ec[d];
-      cc[d][0] = lc[d] + (ec[d] > 0 ? 1 : 0);
-      if (lc[d] == 0 && ec[d] > 0) {
-        cp[d][1] = ec[d] - 1;
-        cc[d][1] = N1 + (ec[d] - 1 > 0 ? 1 : 0);
-        cn[d] = 2;
-      } else if (lc[d] == N1 - 1 && ec[d] < nn[d] - 1) {
-        cp[d][1] = ec[d] + 1;
-        cc[d][1] = 0;
-        cn[d] = 2;
-      }
+  const int loc = threadIdx.x;
+  if (loc >= NPE) return;
+  const int a = loc % N1, bb = (loc / N1) % N1, c = loc / (N1 * N1);
+  for (int e = blockIdx.x; e < E; e += gridDim.x) {
+    const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+    const int ix = a + (ex > 0), iy = bb + (ey > 0), iz = c + (ez > 0);
+    // neighbour along each axis whose patch also covers this node, if any
+    int dx = 0, jx = 0, dy = 0, jy = 0, dz = 0, jz = 0;
+    if (a == 0 && ex > 0) {
+      dx = -1;
+      jx = N1 + (ex > 1);
+    } else if (a == N1 - 1 && ex < nx - 1) {
+      dx = 1;
     }
-    T acc = 0;
-    for (int u = 0; u < cn[2]; ++u)
-      for (int v = 0; v < cn[1]; ++v)
-        for (int w = 0; w < cn[0]; ++w) {
-          const long long pe = cp[0][w] + (long long)nx * (cp[1][v] + (long long)ny * cp[2][u]);
-          acc += zr[pe * MP3 + cc[0][w] + MP * (cc[1][v] + MP * cc[2][u])];
-        }
-    z[rhs * Nq + q] = acc;
+    if (bb == 0 && ey > 0) {
+      dy = -nx;
+      jy = N1 + (ey > 1);
+    } else if (bb == N1 - 1 && ey < ny - 1) {
+      dy = nx;
+    }
+    if (c == 0 && ez > 0) {
+      dz = -nx * ny;
+      jz = N1 + (ez > 1);
+    } else if (c == N1 - 1 && ez < nz - 1) {
+      dz = nx * ny;
+    }
+    T acc = zr[(long long)e * MP3 + ix + MP * (iy + MP * iz)];
+    if (dx) acc += zr[(long long)(e + dx) * MP3 + jx + MP * (iy + MP * iz)];
+    if (dy) acc += zr[(long long)(e + dy) * MP3 + ix + MP * (jy + MP * iz)];
+    if (dz) acc += zr[(long long)(e + dz) * MP3 + ix + MP * (iy + MP * jz)];
+    if (dx && dy) acc += zr[(long long)(e + dx + dy) * MP3 + jx + MP * (jy + MP * iz)];
+    if (dx && dz) acc += zr[(long long)(e + dx + dz) * MP3 + jx + MP * (iy + MP * jz)];
+    if (dy && dz) acc += zr[(long long)(e + dy + dz) * MP3 + ix + MP * (jy + MP * jz)];
+    if (dx && dy && dz) acc += zr[(long long)(e + dx + dy + dz) * MP3 + jx + MP * (jy + MP * jz)];
+    const long long gi = rhs * Nq + (long long)e * NPE + loc;
+    if (MODE == 0) {
+      z[gi] = acc;
+    } else if (MODE == 1) {
+      const T v = c1 * acc;
+      z[gi] = v;
+      x[gi] = v;
+    } else if (MODE == 2) {
+      const T v = c1 * acc;
+      z[gi] = v;
+      x[gi] += v;
+    } else {
+      const T v = c1 * z[gi] + c2 * acc;
+      z[gi] = v;
+      x[gi] += v;
+    }
   }
 }
 
 template <typename T, int N1>
 static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
-                              const int* act, int nact, cudaStream_t s) {
+                              T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s) {
+  using C = SwCfg<T, N1>;
+  const long long items = (long long)nact * hop.E;
   count_launch();
-  k_schwarz_patch<T, N1><<<dim3(hop.E, nact), 256, 0, s>>>(dop, tabs, r, zp, act);
-  long long gx = (hop.Nq + 1023) / 1024;
-  if (gx > 4096) gx = 4096;
+  k_schwarz_patch<T, N1><<<(unsigned)((items + C::EPB - 1) / C::EPB), C::THREADS, 0, s>>>(dop, tabs, r, zp, act, nact);
+  constexpr int NPE = N1 * N1 * N1;
+  constexpr int GT = NPE < 64 ? 64 : NPE;
+  long long gx = hop.E;
+  const long long cap = 152LL * 8 / (nact > 0 ? nact : 1) + 1;
+  if (gx > cap) gx = cap;
+  const dim3 grid((unsigned)gx, (unsigned)nact);
   count_launch();
-  k_schwarz_gather<T, N1><<<dim3((unsigned)gx, nact), 256, 0, s>>>(dop, zp, z, act);
+  switch (mode) {
+    case 0: k_schwarz_gather<T, N1, 0><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
+    case 1: k_schwarz_gather<T, N1, 1><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
+    case 2: k_schwarz_gather<T, N1, 2><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
+    default: k_schwarz_gather<T, N1, 3><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
-                           const int* act, int nact, cudaStream_t s) {
+                           T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s) {
   if (nact == 0) return cudaSuccess;
   switch (hop.n1) {
-    case 2: return schwarz_n1<T, 2>(hop, dop, tabs, r, zp, z, act, nact, s);
-    case 3: return schwarz_n1<T, 3>(hop, dop, tabs, r, zp, z, act, nact, s);
-    case 4: return schwarz_n1<T, 4>(hop, dop, tabs, r, zp, z, act, nact, s);
-    case 5: return schwarz_n1<T, 5>(hop, dop, tabs, r, zp, z, act, nact, s);
-    case 6: return schwarz_n1<T, 6>(hop, dop, tabs, r, zp, z, act, nact, s);
-    case 7: return schwarz_n1<T, 7>(hop, dop, tabs, r, zp, z, act, nact, s);
-    case 8: return schwarz_n1<T, 8>(hop, dop, tabs, r, zp, z, act, nact, s);
-    case 9: return schwarz_n1<T, 9>(hop, dop, tabs, r, zp, z, act, nact, s);
+    case 2: return schwarz_n1<T, 2>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 3: return schwarz_n1<T, 3>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 4: return schwarz_n1<T, 4>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 5: return schwarz_n1<T, 5>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 6: return schwarz_n1<T, 6>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 7: return schwarz_n1<T, 7>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 8: return schwarz_n1<T, 8>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 9: return schwarz_n1<T, 9>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_schwarz<double>(const LevelOp&, const LevelOp*, const double*, const double*, double*,
-                                            double*, const int*, int, cudaStream_t);
+                                            double*, double*, int, double, double, const int*, int, cudaStream_t);
 template cudaError_t launch_schwarz<float>(const LevelOp&, const LevelOp*, const double*, const float*, float*,
-                                           float*, const int*, int, cudaStream_t);
+                                           float*, float*, int, double, double, const int*, int, cudaStream_t);
 
 }  // namespace dg

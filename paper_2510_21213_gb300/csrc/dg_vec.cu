@@ -421,7 +421,8 @@ cudaError_t launch_finite_flags(const double* f, long long Nq, int nsrc, int* fl
 
 // Nitsche load on one face: b[node] += lift_d[side][a_d] * M_t1 * M_t2 * g(t1, t2).
 // g layout per source: faces -x,+x,-y,+y,-z,+z, each [L_t2][L_t1] (t1 fastest).
-__global__ void k_lift(const LevelOp* __restrict__ op, const double* __restrict__ g, double* __restrict__ b, int d,
+template <typename Tg>
+__global__ void k_lift(const LevelOp* __restrict__ op, const Tg* __restrict__ g, double* __restrict__ b, int d,
                        int side, long long face_off, long long gstride) {
   const int n1 = op->n1, npe = n1 * n1 * n1;
   const int t1ax = d == 0 ? 1 : 0, t2ax = d == 2 ? 1 : 2;
@@ -444,12 +445,13 @@ __global__ void k_lift(const LevelOp* __restrict__ op, const double* __restrict_
     const long long e = ec[0] + (long long)op->n[0] * (ec[1] + (long long)op->n[1] * ec[2]);
     const int loc = lc[0] + n1 * (lc[1] + n1 * lc[2]);
     const double coef = op->ax[d].lift[side][ad] * op->ax[t1ax].m[a1] * op->ax[t2ax].m[a2];
-    const double gv = g[src * gstride + face_off + T1 + (long long)L1 * T2];
+    const double gv = (double)g[src * gstride + face_off + T1 + (long long)L1 * T2];
     b[src * op->Nq + e * npe + loc] += coef * gv;
   }
 }
 
-cudaError_t launch_lift(const LevelOp& hop, const LevelOp* dop, const double* g, double* b, int nsrc,
+template <typename Tg>
+cudaError_t launch_lift(const LevelOp& hop, const LevelOp* dop, const Tg* g, double* b, int nsrc,
                         long long gstride, cudaStream_t s) {
   if (nsrc == 0) return cudaSuccess;
   long long off = 0;
@@ -460,7 +462,7 @@ cudaError_t launch_lift(const LevelOp& hop, const LevelOp* dop, const double* g,
       // faces are launched one after another: nodes of edges and corners get
       // one contribution per face without races
       count_launch();
-      k_lift<<<vgrid(L1 * L2 * hop.n1, nsrc), VT, 0, s>>>(dop, g, b, d, side, off, gstride);
+      k_lift<Tg><<<vgrid(L1 * L2 * hop.n1, nsrc), VT, 0, s>>>(dop, g, b, d, side, off, gstride);
       off += L1 * L2;
     }
   }
@@ -580,6 +582,10 @@ template cudaError_t launch_convert<float, double>(float*, const double*, long l
                                                    cudaStream_t);
 template cudaError_t launch_convert<double, double>(double*, const double*, long long, const int*, int, double, int,
                                                     cudaStream_t);
+template cudaError_t launch_lift<double>(const LevelOp&, const LevelOp*, const double*, double*, int, long long,
+                                         cudaStream_t);
+template cudaError_t launch_lift<float>(const LevelOp&, const LevelOp*, const float*, double*, int, long long,
+                                        cudaStream_t);
 template cudaError_t launch_convert<float, float>(float*, const float*, long long, const int*, int, double, int,
                                                   cudaStream_t);
 

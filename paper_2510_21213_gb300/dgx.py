@@ -82,6 +82,8 @@ class dg_info(C.Structure):
         ("gauss_relerr", C.c_double),
         ("sigma", C.c_double * 3),
         ("workspace_bytes", C.c_int64),
+        ("n_gauss_fp32", C.c_int32),
+        ("gauss_relerr_fp32", C.c_double),
     ]
 
 

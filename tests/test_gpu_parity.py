@@ -238,3 +238,42 @@ def test_iteration_counts_are_small(dgx):
         assert st[0]["status"] == 0
         s.close()
     assert max(out.values()) <= 15, out
+
+
+def test_boundary_data_fp32_route_bound(dgx):
+    """Mixed modes evaluate the Gaussian-sum boundary data in FP32 with a 1e-7
+    table; the error relative to sum_q |W_q f_q| / r stays below 1e-5."""
+    lo, hi, n, p = [-6.0] * 3, [6.0] * 3, (3, 3, 3), 5
+    m = oracle.Mesh(lo, hi, n, p)
+    rng = np.random.default_rng(17)
+    f = np.concatenate([_gauss_sources(m, [[0.3, -0.2, 0.1]], [1.5]), rng.standard_normal((1, m.Nq))])
+    s = dgx.PoissonSolver(lo, hi, n, p, precision=dgx.DG_PREC_MIXED)
+    assert s.info.n_gauss_fp32 > 0 and s.info.gauss_relerr_fp32 <= 1e-7
+    g = s.boundary_data(torch.tensor(f, device="cuda"), route=1).cpu().numpy()
+    ref = oracle.boundary_data_direct(m, f)
+    bound = oracle.boundary_data_direct(m, np.abs(f))
+    for k in range(f.shape[0]):
+        faces = _face_arrays(g[k], m)
+        for fi in range(6):
+            err = np.abs(faces[fi] - ref[fi][k]).max() / bound[fi][k].max()
+            assert err < 1e-5, (k, fi, err)
+    s.close()
+
+
+def test_mixed_precision_exchange_build_error_bounds(dgx):
+    """Mixed mode (FP32 multigrid-PCG and boundary data, FP64 residuals and
+    refinement) reaches the same 1e-8 FP64 residual; K, E_H, E_X and the
+    potentials stay within the stated bounds of the FP64 oracle."""
+    m = oracle.Mesh([-8.0] * 3, [8.0] * 3, 4, 5)
+    atoms = np.array([[-1.0, 0.2, 0.0], [1.1, -0.3, 0.4], [0.0, 0.9, -0.8]])
+    spec = inputs.gto_system(inputs.MeshSpec(tuple(m.lo), tuple(m.hi), m.n, m.p), atoms, 4, 5)
+    psi = inputs.orbitals(spec, oracle.node_coords(m), oracle.quad_weights(m))
+    ref = oracle.exchange_build(m, psi, method="fdm")
+    s = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=dgx.DG_PREC_MIXED, rtol=1e-8)
+    K, eh, ex, stats = s.exchange_build(torch.tensor(psi, device="cuda"))
+    assert all(st["status"] == 0 and st["rel_residual"] <= 1e-8 for st in stats)
+    assert all(st["outer_refinements"] >= 1 for st in stats)
+    assert np.abs(K - ref["K"]).max() <= 1e-6 * np.abs(ref["K"]).max()
+    assert abs(eh - ref["E_H"]) <= 1e-6 * abs(ref["E_H"])
+    assert abs(ex - ref["E_X"]) <= 1e-6 * abs(ref["E_X"])
+    s.close()
