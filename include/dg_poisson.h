@@ -16,6 +16,10 @@
  *   preconditioned with hp-multigrid: polynomial coarsening to degree 1, then
  *   geometric coarsening on the nested hierarchy (Sec. 6.4).
  *
+ *   Level hierarchy: degree p -> floor(p/2) down to 1 on the fine mesh, then
+ *   n -> n/2 (all axes) while every n is even and the level has more than 512
+ *   unknowns; the last level is solved exactly (dense inverse).
+ *
  *   dg_exchange_build applies this to the Hartree density rho = sum_k psi_k^2
  *   (Sec. 2.3.1 eq. HF; Sec. 6.1.1 eq. hartree_poisson) and to every occupied
  *   pair density psi_i psi_j (Sec. 6.1.2 eq. fock_poisson), then contracts

@@ -29,7 +29,9 @@ struct ApplyCfg {
   static constexpr int EPB_T = 256 / TPE < 1 ? 1 : 256 / TPE;
   static constexpr int EPB_S = 36864 / PER_ELEM < 1 ? 1 : 36864 / PER_ELEM;
   static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;
-  static constexpr int THREADS = EPB * TPE < 32 ? 32 : EPB * TPE;
+  // the load and trace phases use every thread of the block; the line passes
+  // use the first EPB * TPE
+  static constexpr int THREADS = EPB * TPE < 256 ? 256 : EPB * TPE;
 };
 
 // one direction of the operator for LPT lines of one element:
@@ -145,36 +147,57 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS)
       const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
       sty[sl][d] = (cd == 0 ? 1 : 0) | (cd == nd - 1 ? 2 : 0);
     }
-    // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d)
-    for (int t = tid; t < EPB * 6 * NF; t += NT) {
-      const int sl = t / (6 * NF), rem = t % (6 * NF);
-      const int f = rem / NF, tt = rem % NF;
-      const int d = f >> 1, side = f & 1;
-      const long long it = grp * EPB + sl;
-      T val = 0, der = 0;
-      if (it < items) {
-        const int e = (int)(it % E);
-        const int coord = d == 0 ? e % nx : (d == 1 ? (e / nx) % ny : e / (nx * ny));
-        const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
-        if (side == 0 ? coord > 0 : coord < nd - 1) {
-          const int se = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
-          const T* un = u + (long long)act[it / E] * Nq + (long long)(e + (side == 0 ? -se : se)) * NPE;
-          const int t1 = tt % N1, t2 = tt / N1;
-          const int base = d == 0 ? N1 * t1 + NF * t2 : (d == 1 ? t1 + NF * t2 : t1 + N1 * t2);
-          const int sd = d == 0 ? 1 : (d == 1 ? N1 : NF);
+    // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d);
+    // two traces per thread and iteration so that 2 N1 loads are in flight
+    for (int t0 = tid; t0 < EPB * 6 * NF; t0 += 2 * NT) {
+      T vals[2][N1];
+      int tts[2], fs[2], sls[2];
+      bool has[2];
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const int t = t0 + w * NT;
+        const int sl = t / (6 * NF), rem = t % (6 * NF);
+        const int f = rem / NF, tt = rem % NF;
+        const int d = f >> 1, side = f & 1;
+        const long long it = grp * EPB + sl;
+        sls[w] = sl;
+        fs[w] = f;
+        tts[w] = tt;
+        has[w] = false;
+        if (t < EPB * 6 * NF && it < items) {
+          const int e = (int)(it % E);
+          const int coord = d == 0 ? e % nx : (d == 1 ? (e / nx) % ny : e / (nx * ny));
+          const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
+          has[w] = side == 0 ? coord > 0 : coord < nd - 1;
+          if (has[w]) {
+            const int se = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
+            const T* un = u + (long long)act[it / E] * Nq + (long long)(e + (side == 0 ? -se : se)) * NPE;
+            const int t1 = tt % N1, t2 = tt / N1;
+            const int base = d == 0 ? N1 * t1 + NF * t2 : (d == 1 ? t1 + NF * t2 : t1 + N1 * t2);
+            const int sd = d == 0 ? 1 : (d == 1 ? N1 : NF);
+#pragma unroll
+            for (int i = 0; i < N1; ++i) vals[w][i] = un[base + i * sd];
+          }
+        }
+      }
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        if (t0 + w * NT >= EPB * 6 * NF) continue;
+        T val = 0, der = 0;
+        if (has[w]) {
           // the -d neighbour meets us at its right end, the +d neighbour at its left end
+          const int side = fs[w] & 1;
           const T* tv = side == 0 ? sTr[1] : sTr[0];
           const T* td = side == 0 ? sTr[3] : sTr[2];
 #pragma unroll
           for (int i = 0; i < N1; ++i) {
-            const T xv = un[base + i * sd];
-            val += tv[i] * xv;
-            der += td[i] * xv;
+            val += tv[i] * vals[w][i];
+            der += td[i] * vals[w][i];
           }
         }
+        st[sls[w]][fs[w]][0][tts[w]] = val;
+        st[sls[w]][fs[w]][1][tts[w]] = der;
       }
-      st[sl][f][0][tt] = val;
-      st[sl][f][1][tt] = der;
     }
     __syncthreads();
     if (slot < EPB) {

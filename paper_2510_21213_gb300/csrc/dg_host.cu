@@ -12,119 +12,9 @@
 #include <string>
 #include <vector>
 
-#include "dg_setup.h"
+#include "dg_ctx.h"
 
 namespace dg {
-
-// ---------------------------------------------------------------------------
-// device buffer helper
-// ---------------------------------------------------------------------------
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  ~DevBuf() { release(); }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  cudaError_t ensure(size_t b) {
-    if (b <= bytes) return cudaSuccess;
-    release();
-    cudaError_t e = cudaMalloc(&p, b);
-    if (e != cudaSuccess) {
-      p = nullptr;
-      return e;
-    }
-    bytes = b;
-    return cudaSuccess;
-  }
-  template <typename T>
-  T* as() const {
-    return (T*)p;
-  }
-};
-
-// per-level multigrid workspace of one precision
-struct LevelWork {
-  DevBuf x, b, res, d, invD, z, zp;
-};
-
-template <typename T>
-struct PrecWork {
-  std::vector<LevelWork> lev;            // per level (level 0: res, d, invD only)
-  DevBuf x, r, z, p, q;                  // CG vectors on the fine level
-  int cap = 0;
-};
-
-struct Level {
-  LevelOp op;
-  LevelOp* dop = nullptr;
-  TransferOp tr;                 // to the next coarser level
-  TransferOp* dtr = nullptr;
-  double lam_max = 0;            // lambda_max(D^-1 A) (point Jacobi)
-  double lam_sw = 0;             // lambda_max(M_S A) estimate (Schwarz)
-  DevBuf sw_tabs;                // Schwarz patch tables
-};
-
-struct BcAxisTables {
-  int L = 0;
-  DevBuf gn;   // [2][NG][L]       exp(-a_k (x_X - face_s)^2)
-  DevBuf G;    // [NG][L][L]       exp(-a_k (x_i - x_j)^2)
-  DevBuf Gs;   // [L][NG * L]      c_k exp(-a_k (x_i - x_j)^2)
-};
-
-}  // namespace dg
-
-struct dg_ctx {
-  dg_mesh_desc mesh;
-  dg_solver_opts opts;
-  std::vector<dg::Level> levels;
-  int nlev = 0;
-  // coarsest level
-  int Nc = 0;
-  dg::DevBuf coarse_inv;
-  // fine-level geometry
-  long long Nq = 0;
-  std::vector<double> axis_nodes[3];
-  dg::DevBuf d_W, d_xq, d_axn;
-  int lmax = 0;
-  long long nface = 0;
-  // boundary-data tables: FP64 (1e-12 Gaussian sum) and, in the mixed modes,
-  // FP32 (1e-7 Gaussian sum)
-  dg::GaussSum gsum, gsum32;
-  int NG = 0, NG32 = 0;
-  dg::BcAxisTables bct[3], bct32[3];
-  dg::DevBuf flex32, T1_32, T2_32, g32;
-  // workspaces
-  dg::PrecWork<double> w64;
-  dg::PrecWork<float> w32;
-  dg::DevBuf f64, b64, x64, r64;   // [cap][Nq]
-  dg::DevBuf flex, T1, T2, g;      // boundary data
-  dg::DevBuf part, scal, act, flags, pidx;
-  dg::DevBuf Wacc, kpart, Kdev;
-  int cap = 0;
-  std::vector<int> act_host;  // contents of act (device) as last uploaded
-  std::string err;
-  long long ws_bytes = 0;
-};
-
-namespace dg {
-
-#define DG_CK(call)                                                                                    \
-  do {                                                                                                 \
-    cudaError_t e__ = (call);                                                                          \
-    if (e__ != cudaSuccess) {                                                                          \
-      h->err = std::string(#call) + ": " + cudaGetErrorString(e__);                                    \
-      return e__ == cudaErrorMemoryAllocation ? DG_ERR_NO_MEMORY : DG_ERR_CUDA;                        \
-    }                                                                                                  \
-  } while (0)
-
-#define DG_RET(call)                 \
-  do {                               \
-    int r__ = (call);                \
-    if (r__ != DG_OK) return r__;    \
-  } while (0)
 
 // scalar slots of h->scal, each [cap] doubles
 enum { S_BN = 0, S_RR, S_RZ, S_RZN, S_PQ, S_AL, S_BE, S_NSLOT };
@@ -788,8 +678,10 @@ static int setup(dg_ctx* h) {
     p = std::max(1, p / 2);
     spec.push_back({{n[0], n[1], n[2]}, p});
   }
+  // geometric coarsening while every n is even, until a level small enough for
+  // the dense coarsest solve (<= 512 unknowns at degree 1) is reached
   while (n[0] % 2 == 0 && n[1] % 2 == 0 && n[2] % 2 == 0 && n[0] >= 2 && n[1] >= 2 && n[2] >= 2 &&
-         (int)spec.size() < MAXLEV) {
+         8LL * n[0] * n[1] * n[2] > 512 && (int)spec.size() < MAXLEV) {
     n[0] /= 2;
     n[1] /= 2;
     n[2] /= 2;
@@ -953,6 +845,7 @@ static int apply_smoother_t(dg_ctx* h, PrecWork<T>& w, int level, const T* r, T*
   }
   return DG_OK;
 }
+
 
 }  // namespace dg
 

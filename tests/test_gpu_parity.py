@@ -32,7 +32,7 @@ def level_meshes(lo, hi, n, p):
     while p > 1:
         p = max(1, p // 2)
         out.append((tuple(n), p))
-    while all(v % 2 == 0 and v >= 2 for v in n):
+    while all(v % 2 == 0 and v >= 2 for v in n) and 8 * n[0] * n[1] * n[2] > 512:
         n = [v // 2 for v in n]
         out.append((tuple(n), 1))
     return [oracle.Mesh(lo, hi, nn, pp) for nn, pp in out]
