@@ -197,6 +197,32 @@ int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u_de
 int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r_dev, void* z_dev, int64_t B,
                       void* cuda_stream);
 
+/* Same result as dg_apply_smoother, for callers that cannot allocate device
+ * memory at call time: code running where cudaMalloc is forbidden or would
+ * break a memory budget fixed in advance (a pool-managed serving process, a
+ * real-time loop, a host that owns every allocation itself). The paper has no
+ * counterpart; this is a library-interface variant.
+ *
+ * This call allocates nothing: the patch scratch is a static device array of
+ * 8 MiB (1,048,576 doubles or 2,097,152 floats) and the source list a static
+ * array of 256 ints, held by every GPU that loads this library until the
+ * process exits. Limits: B <= 256 and B * E_level * (p_level + 3)^3 <= the
+ * scratch in the chosen precision (E_level, p_level: elements and degree of
+ * the level); larger requests return DG_ERR_INVALID_ARG with a message in
+ * dg_last_error_detail. Supported: DG_SMOOTH_SCHWARZ levels and the coarsest
+ * level (its exact inverse); a Jacobi handle returns DG_ERR_UNSUPPORTED.
+ * The handle itself comes from dg_poisson_setup, which does allocate.
+ *
+ * The first call on each device looks the static arrays up
+ * (cudaGetSymbolAddress) and writes the source list once, with that device
+ * current: make that first call before any stream capture. Every call shares
+ * the scratch and overwrites it (nothing in it has to start at zero); calls
+ * that overlap on the GPU, on any stream or handle, race on it. Stream-ordered;
+ * returns without synchronising the stream. r_dev, z_dev: [B][Nq_level] device
+ * arrays, FP64 (fp32 == 0) or FP32 (fp32 == 1). */
+int dg_apply_smoother_noalloc(dg_handle h, int32_t level, int32_t fp32, const void* r_dev, void* z_dev, int64_t B,
+                              void* cuda_stream);
+
 /* Boundary data g of Sec. 6.3 for B sources f_dev [B][Nq] (device): g_dev
  * [B][n_face_nodes] (device, FP64; the Gaussian-sum route is evaluated in FP32
  * with a 1e-7 table when the handle is in a mixed mode, as in the solves), faces in the order -x,+x,-y,+y,-z,+z, each
