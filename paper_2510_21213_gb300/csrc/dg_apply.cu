@@ -32,6 +32,7 @@ struct ApplyCfg {
   // the load and trace phases use every thread of the block; the line passes
   // use the first EPB * TPE
   static constexpr int THREADS = EPB * TPE < 256 ? 256 : EPB * TPE;
+  static constexpr int MINB = sizeof(T) == 4 ? 3 : 2;  // resident blocks per SM asked of ptxas
 };
 
 // one direction of the operator for LPT lines of one element:
@@ -87,7 +88,7 @@ __device__ __forceinline__ void ap_pass(const T* __restrict__ su, T* __restrict_
 }
 
 template <typename T, int N1, int MODE>
-__global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS)
+__global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS, ApplyCfg<T, N1>::MINB)
     k_apply(const LevelOp* __restrict__ op, const T* __restrict__ u, T* __restrict__ out,
             const T* __restrict__ rin, const int* __restrict__ act, int nact) {
   using C = ApplyCfg<T, N1>;
@@ -99,6 +100,8 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS)
   __shared__ T su[EPB][NPE];
   __shared__ T sacc[EPB][NPE];
   __shared__ T st[EPB][6][2][NF];
+  __shared__ long long sbase[EPB];  // rhs * Nq + e * NPE of the slot, or -1
+  __shared__ int snb[EPB][6];       // neighbour element offset (elements) per face, 0 = none
   __shared__ int sty[EPB][3];
 
   const int tid = threadIdx.x;
@@ -128,24 +131,33 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS)
   const long long groups = (items + EPB - 1) / EPB;
   for (long long grp = blockIdx.x; grp < groups; grp += gridDim.x) {
     __syncthreads();  // tables ready / previous group done with the shared buffers
+    for (int sl = tid; sl < EPB; sl += NT) {
+      const long long it = grp * EPB + sl;
+      if (it < items) {
+        const int k = (int)(it / E), e = (int)(it - (long long)k * E);
+        sbase[sl] = (long long)act[k] * Nq + (long long)e * NPE;
+        const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+        snb[sl][0] = ex > 0 ? -1 : 0;
+        snb[sl][1] = ex < nx - 1 ? 1 : 0;
+        snb[sl][2] = ey > 0 ? -nx : 0;
+        snb[sl][3] = ey < ny - 1 ? nx : 0;
+        snb[sl][4] = ez > 0 ? -nx * ny : 0;
+        snb[sl][5] = ez < nz - 1 ? nx * ny : 0;
+        sty[sl][0] = (ex == 0 ? 1 : 0) | (ex == nx - 1 ? 2 : 0);
+        sty[sl][1] = (ey == 0 ? 1 : 0) | (ey == ny - 1 ? 2 : 0);
+        sty[sl][2] = (ez == 0 ? 1 : 0) | (ez == nz - 1 ? 2 : 0);
+      } else {
+        sbase[sl] = -1;
+        for (int f = 0; f < 6; ++f) snb[sl][f] = 0;
+        sty[sl][0] = sty[sl][1] = sty[sl][2] = 0;
+      }
+    }
+    __syncthreads();
     // own elements (coalesced over consecutive items)
     for (int t = tid; t < EPB * NPE; t += NT) {
-      const int sl = t / NPE, loc = t % NPE;
-      const long long it = grp * EPB + sl;
-      T v = 0;
-      if (it < items) {
-        const int e = (int)(it % E);
-        v = u[(long long)act[it / E] * Nq + (long long)e * NPE + loc];
-      }
-      su[sl][loc] = v;
-    }
-    for (int t = tid; t < EPB * 3; t += NT) {
-      const int sl = t / 3, d = t % 3;
-      const long long it = grp * EPB + sl;
-      const int e = it < items ? (int)(it % E) : 0;
-      const int cd = d == 0 ? e % nx : (d == 1 ? (e / nx) % ny : e / (nx * ny));
-      const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
-      sty[sl][d] = (cd == 0 ? 1 : 0) | (cd == nd - 1 ? 2 : 0);
+      const int sl = t / NPE, loc = t - sl * NPE;
+      const long long b0 = sbase[sl];
+      su[sl][loc] = b0 >= 0 ? u[b0 + loc] : (T)0;
     }
     // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d);
     // two traces per thread and iteration so that 2 N1 loads are in flight
@@ -156,22 +168,19 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS)
 #pragma unroll
       for (int w = 0; w < 2; ++w) {
         const int t = t0 + w * NT;
-        const int sl = t / (6 * NF), rem = t % (6 * NF);
-        const int f = rem / NF, tt = rem % NF;
-        const int d = f >> 1, side = f & 1;
-        const long long it = grp * EPB + sl;
+        const int sl = t / (6 * NF), rem = t - sl * (6 * NF);
+        const int f = rem / NF, tt = rem - f * NF;
         sls[w] = sl;
         fs[w] = f;
         tts[w] = tt;
         has[w] = false;
-        if (t < EPB * 6 * NF && it < items) {
-          const int e = (int)(it % E);
-          const int coord = d == 0 ? e % nx : (d == 1 ? (e / nx) % ny : e / (nx * ny));
-          const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
-          has[w] = side == 0 ? coord > 0 : coord < nd - 1;
+        if (t < EPB * 6 * NF) {
+          const long long b0 = sbase[sl];
+          const int nb = snb[sl][f];
+          has[w] = b0 >= 0 && nb != 0;
           if (has[w]) {
-            const int se = d == 0 ? 1 : (d == 1 ? nx : nx * ny);
-            const T* un = u + (long long)act[it / E] * Nq + (long long)(e + (side == 0 ? -se : se)) * NPE;
+            const int d = f >> 1;
+            const T* un = u + b0 + (long long)nb * NPE;
             const int t1 = tt % N1, t2 = tt / N1;
             const int base = d == 0 ? N1 * t1 + NF * t2 : (d == 1 ? t1 + NF * t2 : t1 + N1 * t2);
             const int sd = d == 0 ? 1 : (d == 1 ? N1 : NF);
@@ -216,10 +225,10 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS)
     }
     __syncthreads();
     for (int t = tid; t < EPB * NPE; t += NT) {
-      const int sl = t / NPE, loc = t % NPE;
-      const long long it = grp * EPB + sl;
-      if (it < items) {
-        const long long gi = (long long)act[it / E] * Nq + (long long)(it % E) * NPE + loc;
+      const int sl = t / NPE, loc = t - sl * NPE;
+      const long long b0 = sbase[sl];
+      if (b0 >= 0) {
+        const long long gi = b0 + loc;
         const T Au = sacc[sl][loc];
         if (MODE == 0) {
           out[gi] = Au;

@@ -150,18 +150,35 @@ __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
   const int mx = sm[slot][0], my = sm[slot][1], mz = sm[slot][2];
   const int oLx = soL[slot][0], oLy = soL[slot][1], oLz = soL[slot][2];
   T* b = buf[slot];
-  // gather the patch residual (own element plus one node layer of each neighbour)
-  const T* rr = r + rhs * Nq;
-  for (int t = lt; t < MP3; t += TPE) {
-    const int i = t % MP, j = (t / MP) % MP, k = t / MP2;
-    T v = 0;
-    if (valid && i < mx && j < my && k < mz) {
-      const int X = pos[0] * N1 - oLx + i, Y = pos[1] * N1 - oLy + j, Z = pos[2] * N1 - oLz + k;
-      const int ex = X / N1, ey = Y / N1, ez = Z / N1;
-      const long long en = ex + (long long)nx * (ey + (long long)ny * ez);
-      v = rr[en * NPE + (X - ex * N1) + N1 * ((Y - ey * N1) + N1 * (Z - ez * N1))];
+  // gather the patch residual (own element plus one node layer of each
+  // neighbour), one patch row (j, k) at a time: the row's element offsets are
+  // computed once, the row's MP entries are three segments (left neighbour,
+  // own element, right neighbour)
+  if (valid) {
+    const T* rr = r + rhs * Nq;
+    for (int row = lt; row < MP2; row += TPE) {
+      const int j = row % MP, k = row / MP;
+      T* brow = b + row * MP;
+      if (j >= my || k >= mz) {
+#pragma unroll
+        for (int i = 0; i < MP; ++i) brow[i] = (T)0;
+        continue;
+      }
+      const int Y = pos[1] * N1 - oLy + j, Z = pos[2] * N1 - oLz + k;
+      const int ey = Y / N1, ez = Z / N1;
+      const long long rowe = (long long)nx * (ey + (long long)ny * ez);  // element index without x
+      const int lyz = N1 * ((Y - ey * N1) + N1 * (Z - ez * N1));
+      const T* own = rr + (rowe + pos[0]) * NPE + lyz;
+      int i = 0;
+      if (oLx) brow[i++] = rr[(rowe + pos[0] - 1) * NPE + lyz + (N1 - 1)];
+#pragma unroll
+      for (int a = 0; a < N1; ++a) brow[i + a] = own[a];
+      i += N1;
+      if (i < mx) brow[i++] = rr[(rowe + pos[0] + 1) * NPE + lyz];
+      for (; i < MP; ++i) brow[i] = (T)0;
     }
-    b[t] = v;
+  } else {
+    for (int t = lt; t < MP3; t += TPE) b[t] = (T)0;
   }
   __syncthreads();
   sw_pass3<T, MP, TPE, LPT, 0, false>(b, sS[slot][0], lt);
@@ -210,7 +227,7 @@ __global__ void __launch_bounds__(N1 * N1 * N1 < 64 ? 64 : N1 * N1 * N1)
   if (loc >= NPE) return;
   const int a = loc % N1, bb = (loc / N1) % N1, c = loc / (N1 * N1);
   for (int e = blockIdx.x; e < E; e += gridDim.x) {
-    const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+    const int ex = e % nx, exy = e / nx, ey = exy % ny, ez = exy / ny;
     const int ix = a + (ex > 0), iy = bb + (ey > 0), iz = c + (ez > 0);
     // neighbour along each axis whose patch also covers this node, if any
     int dx = 0, jx = 0, dy = 0, jy = 0, dz = 0, jz = 0;

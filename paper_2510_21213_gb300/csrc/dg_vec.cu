@@ -335,12 +335,14 @@ cudaError_t launch_restrict(const TransferOp& htr, const TransferOp* dtr, const 
 template <typename T>
 __global__ void k_coarse_solve(const double* __restrict__ Ainv, int Nc, const T* __restrict__ r, T* __restrict__ x,
                                const int* __restrict__ act) {
+  // grid (row blocks of 32 rows, active sources); one warp per row
   extern __shared__ double sr[];
-  const long long off = (long long)act[blockIdx.x] * Nc;
+  const long long off = (long long)act[blockIdx.y] * Nc;
   for (int i = threadIdx.x; i < Nc; i += blockDim.x) sr[i] = (double)r[off + i];
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int row = warp; row < Nc; row += nw) {
+  const int r0 = blockIdx.x * 32, r1 = min(Nc, r0 + 32);
+  for (int row = r0 + warp; row < r1; row += nw) {
     double acc = 0.0;
     for (int j = lane; j < Nc; j += 32) acc += Ainv[(long long)row * Nc + j] * sr[j];
     acc = warp_sum(acc);
@@ -353,7 +355,7 @@ cudaError_t launch_coarse_solve(const double* Ainv, int Nc, const T* r, T* x, co
                                 cudaStream_t s) {
   if (nact == 0) return cudaSuccess;
   count_launch();
-  k_coarse_solve<T><<<nact, 256, Nc * sizeof(double), s>>>(Ainv, Nc, r, x, act);
+  k_coarse_solve<T><<<dim3((Nc + 31) / 32, nact), 256, Nc * sizeof(double), s>>>(Ainv, Nc, r, x, act);
   return cudaGetLastError();
 }
 
@@ -500,8 +502,8 @@ static constexpr int KT = 32;   // output tile (KT x KT), 256 threads x 4 output
 static constexpr int KQ = 64;   // nodes per shared-memory stage
 
 int kmat_chunks(long long Nq) {
-  long long c = (Nq + 8191) / 8192;
-  if (c > 1024) c = 1024;
+  long long c = (Nq + 1023) / 1024;
+  if (c > 2048) c = 2048;
   return (int)(c < 1 ? 1 : c);
 }
 
