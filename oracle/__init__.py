@@ -24,6 +24,8 @@ from .dg_oracle import (  # noqa: F401
     assemble_dense,
     boundary_face_nodes,
     boundary_data_direct,
+    boundary_data_gausssum,
+    gauss_sum_1_over_r,
     rhs,
     solve_dense,
     solve_fdm,

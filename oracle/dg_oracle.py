@@ -395,6 +395,72 @@ def boundary_data_direct(mesh, f, chunk=64, node_stride=1):
     return out
 
 
+def gauss_sum_1_over_r(rmin, rmax, tol):
+    """Coefficients of 1/r ~ sum_k c_k exp(-a_k r^2) on [rmin, rmax] (Sec. 5.2).
+
+    Trapezoidal rule in t for 1/r = (2/sqrt(pi)) int exp(-r^2 e^(2t) + t) dt:
+    c_k = (2/sqrt(pi)) h e^(t_k), a_k = e^(2 t_k). The t-range drops tails
+    below tol at both ends; the step h is halved from 1 until the maximum
+    relative error on 4000 log-spaced radii is below tol."""
+    from scipy.special import erfc
+    t_lo = math.log(tol * math.sqrt(math.pi) / (2.0 * rmax))
+    x = 0.5
+    while erfc(x) > 0.5 * tol:
+        x += 0.01
+    t_hi = math.log(x / rmin)
+    r = np.exp(np.linspace(math.log(rmin), math.log(rmax), 4000))
+    h = 1.0
+    while h > 1e-3:
+        t = np.arange(t_lo, t_hi + h, h)
+        c = 2.0 / math.sqrt(math.pi) * h * np.exp(t)
+        a = np.exp(2.0 * t)
+        err = np.abs((np.exp(-np.outer(r * r, a)) @ c) * r - 1.0).max()
+        if err <= tol:
+            return c, a, err
+        h *= 0.5
+    raise RuntimeError("Gaussian-sum step search failed")
+
+
+def boundary_data_gausssum(mesh, f, tol=1e-12):
+    """Dirichlet data of Sec. 6.3 with 1/r replaced by the Gaussian sum of
+    Sec. 5.2, evaluated on the tensor grid as three 1-D contractions per term
+    and face. f: [nf, Nq]. Returns the same layout as boundary_data_direct."""
+    f = np.atleast_2d(np.asarray(f, dtype=np.float64))
+    xq = [axis_nodes(mesh, d) for d in range(3)]
+    xi, _ = gauss_legendre(mesh.n1)
+    rmin = min((1.0 - xi[-1]) * mesh.h[d] / 2.0 for d in range(3))
+    rmax = float(np.linalg.norm(mesh.hi - mesh.lo))
+    c, a, _ = gauss_sum_1_over_r(0.999 * rmin, 1.001 * rmax, tol)
+    perm = lex_of_eb(mesh)
+    Lx, Ly, Lz = mesh.L
+    out = [np.zeros((f.shape[0], mesh.L[[ax for ax in range(3) if ax != d][0]],
+                     mesh.L[[ax for ax in range(3) if ax != d][1]])) for d in range(3) for _ in range(2)]
+    W = quad_weights(mesh)
+    for r_ in range(f.shape[0]):
+        F = np.empty(mesh.Nq)
+        F[perm] = W * f[r_]
+        F = F.reshape(Lz, Ly, Lx)  # [Z, Y, X]
+        for d in range(3):
+            t = [ax for ax in range(3) if ax != d]
+            for side in range(2):
+                face = mesh.lo[d] if side == 0 else mesh.hi[d]
+                GN = np.exp(-np.outer(a, (xq[d] - face) ** 2))  # [k, L_d]
+                # contraction along the normal axis for all terms k at once
+                if d == 0:
+                    T = np.tensordot(F, GN, axes=([2], [1])).transpose(2, 1, 0)  # [k, y, z]
+                elif d == 1:
+                    T = np.tensordot(F, GN, axes=([1], [1])).transpose(2, 1, 0)  # [k, x, z]
+                else:
+                    T = np.tensordot(F, GN, axes=([0], [1])).transpose(2, 1, 0)  # [k, x, y]
+                acc = np.zeros((mesh.L[t[0]], mesh.L[t[1]]))
+                for k in range(len(c)):
+                    G1 = np.exp(-a[k] * (xq[t[0]][:, None] - xq[t[0]][None, :]) ** 2)
+                    G2 = np.exp(-a[k] * (xq[t[1]][:, None] - xq[t[1]][None, :]) ** 2)
+                    acc += c[k] * (G1 @ T[k] @ G2.T)
+                out[2 * d + side][r_] = acc
+    return out
+
+
 def rhs(mesh, f, g, penalty_form=0, eps=0.125):
     """Load vector of the Nitsche-SIPDG Poisson problem.
 
@@ -469,14 +535,15 @@ def solve_fdm(mesh, b, penalty_form=0, eps=0.125, factors=None):
         blex = np.empty(mesh.Nq)
         blex[perm] = B[r]
         t = blex.reshape(Lz, Ly, Lx)
-        t = np.einsum("zyx,xi->zyi", t, Sx)
-        t = np.einsum("zyi,yj->zji", t, Sy)
-        t = np.einsum("zji,zk->kji", t, Sz)
-        t = t / denom
-        t = np.einsum("kji,xi->kjx", t, Sx)
-        t = np.einsum("kjx,yj->kyx", t, Sy)
-        t = np.einsum("kyx,zk->zyx", t, Sz)
-        out[r] = t.ravel()[perm]
+        # (Sz (x) Sy (x) Sx)^T b, one axis at a time: t[k, j, i] = sum S_z[z,k] S_y[y,j] S_x[x,i] b[z,y,x]
+        t = np.tensordot(t, Sx, axes=([2], [0]))            # [z, y, i]
+        t = np.tensordot(t, Sy, axes=([1], [0]))            # [z, i, j]
+        t = np.tensordot(t, Sz, axes=([0], [0]))            # [i, j, k]
+        t = t.transpose(2, 1, 0) / denom                    # [k, j, i]
+        t = np.tensordot(t, Sx, axes=([2], [1]))            # [k, j, x]
+        t = np.tensordot(t, Sy, axes=([1], [1]))            # [k, x, y]
+        t = np.tensordot(t, Sz, axes=([0], [1]))            # [x, y, z]
+        out[r] = t.transpose(2, 1, 0).ravel()[perm]
     return out[0] if single else out
 
 

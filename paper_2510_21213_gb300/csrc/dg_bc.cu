@@ -51,8 +51,21 @@ template cudaError_t launch_weighted_lex<float>(const LevelOp&, const LevelOp*, 
 // with arbitrary element strides and a two-level batch index.
 // 64 x 64 output tile, K step 16, 256 threads with 4 x 4 outputs each.
 // ---------------------------------------------------------------------------
+// FP32 instances keep a compensated running sum across K tiles: each 16-term
+// tile is accumulated in registers and then added to (sum, carry) with
+// Knuth's TwoSum, so the error does not grow with K (K reaches N_G L ~ 10^4 in
+// the boundary-data contractions).
+template <typename T>
+__device__ __forceinline__ void two_sum_add(T& s, T& c, T a) {
+  const T t = s + a;
+  const T bp = t - s;
+  c += (s - (t - bp)) + (a - bp);
+  s = t;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int batch_base) {
+  constexpr bool COMP = sizeof(T) == 4;
   __shared__ T sA[16][64 + 1];
   __shared__ T sB[16][64 + 1];
   const int bz = batch_base + blockIdx.z;
@@ -64,11 +77,15 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int batch_base) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const bool a_k_fast = g.sAk == 1;
   const bool b_n_fast = g.sBn == 1;
-  T acc[4][4];
+  T acc[4][4], sum[4][4], car[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j] = (T)0;
+      sum[i][j] = (T)0;
+      car[i][j] = (T)0;
+    }
   for (int k0 = 0; k0 < g.K; k0 += 16) {
     for (int t = tid; t < 64 * 16; t += 256) {
       int kk, mm;
@@ -105,6 +122,15 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int batch_base) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
     }
+    if (COMP) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          two_sum_add(sum[i][j], car[i][j], acc[i][j]);
+          acc[i][j] = (T)0;
+        }
+    }
     __syncthreads();
   }
   const T alpha = (T)g.alpha, beta = (T)g.beta;
@@ -116,8 +142,9 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int batch_base) {
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx + 16 * j;
       if (n >= g.N) continue;
+      const T v = COMP ? sum[i][j] + car[i][j] : acc[i][j];
       T* cp = C + (long long)m * g.sCm + (long long)n * g.sCn;
-      *cp = g.beta != 0.0 ? alpha * acc[i][j] + beta * (*cp) : alpha * acc[i][j];
+      *cp = g.beta != 0.0 ? alpha * v + beta * (*cp) : alpha * v;
     }
   }
 }

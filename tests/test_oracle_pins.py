@@ -281,3 +281,19 @@ def test_exchange_matrix_symmetric_psd_and_rotation_invariant():
 def test_pair_list_order():
     assert oracle.pair_list(3) == [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
     assert len(oracle.pair_list(64)) == 2080
+
+
+def test_gaussian_sum_route_matches_direct_quadrature():
+    """The separable Gaussian-sum evaluation of the Dirichlet data (Sec. 5.2
+    applied to Sec. 6.3) agrees with the direct quadrature within its bound."""
+    m = oracle.Mesh([-4.0, -3.0, -3.5], [4.0, 3.5, 3.0], (3, 2, 3), 4)
+    rng = np.random.default_rng(7)
+    f = np.concatenate([rng.standard_normal((1, m.Nq)), _unit_gaussian(oracle.node_coords(m))[None, :]])
+    g1 = oracle.boundary_data_direct(m, f)
+    g2 = oracle.boundary_data_gausssum(m, f, tol=1e-12)
+    bound = oracle.boundary_data_direct(m, np.abs(f))
+    for a, b, c in zip(g1, g2, bound):
+        assert np.abs(a - b).max() <= 2e-12 * c.max()
+    c, a, err = oracle.gauss_sum_1_over_r(0.03, 42.0, 1e-10)
+    r = np.exp(np.linspace(math.log(0.03), math.log(42.0), 777))
+    assert np.abs((np.exp(-np.outer(r * r, a)) @ c) * r - 1.0).max() <= 1e-10 and err <= 1e-10
