@@ -180,6 +180,31 @@ int dg_pair_solve_batch(dg_handle h, const double* f_dev, int64_t B, double* v_d
 int dg_exchange_build(dg_handle h, const double* psi_dev, int32_t N, double* K_host, double* E_H,
                       double* E_X, dg_solve_stats* stats_host, void* cuda_stream);
 
+/* Exchange builds of nsys independent systems with their own meshes and
+ * orbital counts (uneven sizes), as one call. meshes [nsys] (host), psi_devs
+ * [nsys] device pointers to [Ns[i]][Nq_i], K_hosts [nsys] host pointers to
+ * [Ns[i]^2], E_H / E_X [nsys] (host, may be NULL), stats_hosts [nsys] host
+ * pointers to [Ns[i](Ns[i]+1)/2 + 1] stats each (array or entries may be
+ * NULL). Systems are ordered by cost and spread over `lanes` concurrent host
+ * threads (<= 0: 4), each lane with its own handle per mesh and its own stream;
+ * handles are cached across calls (released by dg_release_cached_handles) and
+ * their source-batch size is chosen by the autotuner unless opts->batch > 0.
+ * Returns the worst status over the systems. */
+int dg_exchange_build_multi(const dg_mesh_desc* meshes, const double* const* psi_devs, const int32_t* Ns,
+                            int32_t nsys, const dg_solver_opts* opts, double* const* K_hosts, double* E_H,
+                            double* E_X, dg_solve_stats* const* stats_hosts, int32_t lanes, void* cuda_stream);
+
+/* Frees the handles cached by dg_exchange_build_multi. */
+void dg_release_cached_handles(void);
+
+/* Autotuner: times the fine-level operator and smoother for source-batch
+ * sizes 8..512 (within ~2 GB of vectors) and sets the handle's batch to the
+ * smallest size within 10 % of the best time per source (at most
+ * max_sources). Results are cached per GPU name, mesh and precision in
+ * $DG_AUTOTUNE_CACHE (default ~/.cache/dgx_autotune.jsonl). *batch receives
+ * the choice. */
+int dg_autotune_batch(dg_handle h, int32_t max_sources, int32_t* batch);
+
 /* Matrix-free SIPDG operator of multigrid level `level` (0 = fine) applied to
  * B fields: out = A u. u_dev, out_dev: [B][Nq_level] device arrays of the
  * handle's working precision for that call: FP64 when fp32 == 0, FP32 when

@@ -43,11 +43,24 @@ struct LevelWork {
   DevBuf x, b, res, d, invD, z, zp;
 };
 
+// One captured phase of a PCG iteration (CUDA graph), valid for one active
+// source count and one generation of the workspace buffers.
+struct PhaseGraph {
+  cudaGraphExec_t exec = nullptr;
+  int nact = -1;
+  long long gen = -1;
+  long long nkernels = 0;
+  ~PhaseGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 template <typename T>
 struct PrecWork {
   std::vector<LevelWork> lev;            // per level (level 0: res, d, invD only)
   DevBuf x, r, z, p, q;                  // CG vectors on the fine level
   int cap = 0;
+  PhaseGraph gA, gB;                     // captured PCG phases (operator / preconditioner)
 };
 
 struct Level {
@@ -100,6 +113,15 @@ struct dg_ctx {
   std::vector<int> act_host;  // contents of act (device) as last uploaded
   std::string err;
   long long ws_bytes = 0;
+  long long buf_gen = 0;      // bumped whenever a workspace buffer is (re)allocated
+  bool use_graphs = true;     // capture the PCG phases as CUDA graphs
+  cudaStream_t ws = nullptr;  // the handle's own stream (graph capture needs a non-default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  ~dg_ctx() {
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (ws) cudaStreamDestroy(ws);
+  }
 };
 
 namespace dg {
@@ -112,6 +134,13 @@ namespace dg {
       return e__ == cudaErrorMemoryAllocation ? DG_ERR_NO_MEMORY : DG_ERR_CUDA;                        \
     }                                                                                                  \
   } while (0)
+
+// workspace helpers shared by the translation units of the library
+template <typename T>
+int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap);
+int ensure_common(dg_ctx* h, int cap);
+int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s);
+int autotune_batch(dg_ctx* h, int max_sources, cudaStream_t s);
 
 #define DG_RET(call)                 \
   do {                               \

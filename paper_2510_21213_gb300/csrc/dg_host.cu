@@ -25,8 +25,9 @@ static double* scal(dg_ctx* h, int slot) { return h->scal.as<double>() + (size_t
 // workspace
 // ---------------------------------------------------------------------------
 template <typename T>
-static int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap) {
+int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap) {
   if (w.cap >= cap && !w.lev.empty()) return DG_OK;
+  ++h->buf_gen;
   w.lev.resize(h->nlev);
   for (int l = 0; l < h->nlev; ++l) {
     const long long N = h->levels[l].op.Nq;
@@ -57,8 +58,12 @@ static int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap) {
   return DG_OK;
 }
 
-static int ensure_common(dg_ctx* h, int cap) {
+template int ensure_prec<double>(dg_ctx*, PrecWork<double>&, int);
+template int ensure_prec<float>(dg_ctx*, PrecWork<float>&, int);
+
+int ensure_common(dg_ctx* h, int cap) {
   if (h->cap >= cap) return DG_OK;
+  ++h->buf_gen;
   const long long N = h->Nq;
   DG_CK(h->f64.ensure(sizeof(double) * N * cap));
   DG_CK(h->b64.ensure(sizeof(double) * N * cap));
@@ -216,7 +221,7 @@ __global__ void k_copy_slot(const double* src, double* dst, const int* act, int 
 }
 
 // Active source list on the device; re-uploaded only when it changes.
-static int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s) {
+int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s) {
   if (a.empty()) return DG_OK;
   if (h->act_host == a) return DG_OK;
   DG_CK(cudaMemcpyAsync(h->act.p, a.data(), sizeof(int) * a.size(), cudaMemcpyHostToDevice, s));
@@ -225,10 +230,51 @@ static int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s) {
   return DG_OK;
 }
 
+// Runs `body` (kernel launches only) on stream s, through a CUDA graph captured
+// on first use and replayed while the active source count and the workspace
+// buffers stay the same.
+template <typename F>
+static int run_phase(dg_ctx* h, PhaseGraph& g, int nact, cudaStream_t s, F&& body) {
+  if (!h->use_graphs || s == nullptr) return body();
+  if (g.exec && g.nact == nact && g.gen == h->buf_gen) {
+    DG_CK(cudaGraphLaunch(g.exec, s));
+    count_launch((int)g.nkernels);
+    return DG_OK;
+  }
+  if (g.exec) {
+    cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
+  const long long l0 = g_launch_count.load();
+  DG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  const int rc = body();
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  // kernels counted while capturing did not run; they are counted at replay
+  const long long nk = g_launch_count.load() - l0;
+  g_launch_count.fetch_sub(nk);
+  if (rc != DG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  DG_CK(e);
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  DG_CK(ei);
+  g.nact = nact;
+  g.gen = h->buf_gen;
+  g.nkernels = nk;
+  DG_CK(cudaGraphLaunch(g.exec, s));
+  count_launch((int)nk);
+  return DG_OK;
+}
+
 // Preconditioned CG in precision T on the fine level for the sources in
 // `act0`: solves A x = r (r overwritten by the residual) starting from x = 0
 // until ||r||_2 <= tol * ||r_0||_2 or maxit iterations. iters[k] receives the
-// iterations used by each source; flags (device) collect breakdowns.
+// iterations used by each source; flags (device) collect breakdowns. Each
+// iteration is two device-only phases (operator + updates; preconditioner +
+// direction update), replayed as CUDA graphs, and one host read of ||r||^2.
 template <typename T>
 static int pcg(dg_ctx* h, PrecWork<T>& w, const std::vector<int>& act0, const std::vector<double>& tol, int maxit,
                cudaStream_t s, std::vector<int>& iters, std::vector<double>& relres) {
@@ -271,13 +317,27 @@ static int pcg(dg_ctx* h, PrecWork<T>& w, const std::vector<int>& act0, const st
       mg.nact = nact;
     }
   }
-  for (int it = 1; it <= maxit; ++it) {
+  auto phaseA = [&]() -> int {
     DG_CK(launch_apply<T>(h->levels[0].op, h->levels[0].dop, 0, p, q, nullptr, dact, nact, s));
     DG_CK(launch_dot<T>(p, q, nullptr, scal(h, S_PQ), part, Nq, dact, nact, s));
     count_launch();
     k_ratio<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZ), scal(h, S_PQ), scal(h, S_AL), dact, nact, flags, 1);
     DG_CK(launch_cg_xr<T>(x, r, p, q, scal(h, S_AL), Nq, dact, nact, s));
     DG_CK(launch_dot<T>(r, r, nullptr, scal(h, S_RR), part, Nq, dact, nact, s));
+    return DG_OK;
+  };
+  auto phaseB = [&]() -> int {
+    DG_RET(mg.vcycle(0, r, z));
+    DG_CK(launch_dot<T>(r, z, nullptr, scal(h, S_RZN), part, Nq, dact, nact, s));
+    count_launch();
+    k_ratio<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), scal(h, S_BE), dact, nact, flags, 0);
+    count_launch();
+    k_copy_slot<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), dact, nact);
+    DG_CK(launch_cg_p<T>(p, z, scal(h, S_BE), Nq, dact, nact, s));
+    return DG_OK;
+  };
+  for (int it = 1; it <= maxit; ++it) {
+    DG_RET(run_phase(h, w.gA, nact, s, phaseA));
     DG_CK(cudaMemcpyAsync(rr.data(), scal(h, S_RR), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
     DG_CK(cudaStreamSynchronize(s));
     std::vector<int> a2;
@@ -294,13 +354,7 @@ static int pcg(dg_ctx* h, PrecWork<T>& w, const std::vector<int>& act0, const st
       mg.nact = nact;
     }
     if (it == maxit) break;
-    DG_RET(mg.vcycle(0, r, z));
-    DG_CK(launch_dot<T>(r, z, nullptr, scal(h, S_RZN), part, Nq, dact, nact, s));
-    count_launch();
-    k_ratio<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), scal(h, S_BE), dact, nact, flags, 0);
-    count_launch();
-    k_copy_slot<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), dact, nact);
-    DG_CK(launch_cg_p<T>(p, z, scal(h, S_BE), Nq, dact, nact, s));
+    DG_RET(run_phase(h, w.gB, nact, s, phaseB));
   }
   return DG_OK;
 }
@@ -695,6 +749,9 @@ static int setup(dg_ctx* h) {
     L.lam_max = level_lambda_max(L.op);
   }
   for (int l = 0; l + 1 < h->nlev; ++l) build_transfer(h->levels[l].tr, h->levels[l].op, h->levels[l + 1].op);
+  DG_CK(cudaStreamCreateWithFlags(&h->ws, cudaStreamNonBlocking));
+  DG_CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+  DG_CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
   const LevelOp& Lc = h->levels[h->nlev - 1].op;
   if (Lc.Nq > 4096) {
     h->err = "coarsest multigrid level has more than 4096 unknowns";
@@ -1056,7 +1113,11 @@ int dg_boundary_data(dg_handle h, int32_t route, const double* f, int64_t B, dou
 int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_solve_stats* stats, void* stream) {
   if (!h || B < 0 || (B > 0 && (!f || !v))) return DG_ERR_INVALID_ARG;
   if (B == 0) return DG_OK;
-  cudaStream_t s = (cudaStream_t)stream;
+  // work runs on the handle's stream, ordered after the caller's stream
+  cudaStream_t us = (cudaStream_t)stream;
+  DG_CK(cudaEventRecord(h->ev_in, us));
+  DG_CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
+  cudaStream_t s = h->ws;
   const int cap = std::max(1, std::min(default_batch(h), (int)std::min<int64_t>(B, 65535)));
   DG_RET(prepare(h, cap));
   int worst = DG_OK;
@@ -1072,6 +1133,8 @@ int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_s
     DG_CK(cudaMemcpyAsync(v + b0 * h->Nq, h->x64.p, sizeof(double) * h->Nq * nb, cudaMemcpyDeviceToDevice, s));
   }
   DG_CK(cudaStreamSynchronize(s));
+  DG_CK(cudaEventRecord(h->ev_out, s));
+  DG_CK(cudaStreamWaitEvent(us, h->ev_out, 0));
   if (h->opts.verbose) fprintf(stderr, "dg_pair_solve_batch: %lld sources, status %d\n", (long long)B, worst);
   return worst;
 }
@@ -1079,7 +1142,10 @@ int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_s
 int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host, double* E_H, double* E_X,
                       dg_solve_stats* stats, void* stream) {
   if (!h || N < 1 || !psi || !K_host) return DG_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t us = (cudaStream_t)stream;
+  DG_CK(cudaEventRecord(h->ev_in, us));
+  DG_CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
+  cudaStream_t s = h->ws;
   const long long Nq = h->Nq;
   const int P = N * (N + 1) / 2;
   const int nsrc_total = P + 1;
@@ -1160,6 +1226,8 @@ int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host,
                     h->Kdev.as<double>(), s));
   DG_CK(cudaMemcpyAsync(K_host, h->Kdev.p, sizeof(double) * N * N, cudaMemcpyDeviceToHost, s));
   DG_CK(cudaStreamSynchronize(s));
+  DG_CK(cudaEventRecord(h->ev_out, s));
+  DG_CK(cudaStreamWaitEvent(us, h->ev_out, 0));
   if (E_H) *E_H = eh;
   if (E_X) {
     double tr = 0.0;

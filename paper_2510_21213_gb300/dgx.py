@@ -109,6 +109,12 @@ def load():
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
+    lib.dg_exchange_build_multi.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp, vp, vp, C.c_int32, vp]
+    lib.dg_exchange_build_multi.restype = C.c_int
+    lib.dg_release_cached_handles.argtypes = []
+    lib.dg_release_cached_handles.restype = None
+    lib.dg_autotune_batch.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+    lib.dg_autotune_batch.restype = C.c_int
     lib.dg_kernel_launch_count.argtypes = []
     lib.dg_kernel_launch_count.restype = C.c_int64
     lib.dg_destroy.argtypes = [vp]
@@ -269,6 +275,51 @@ def dg_boundary_data(h, f, route=DG_BC_GAUSSSUM, stream=None):
     _check(lib.dg_boundary_data(h, route, _dev_ptr(f, torch.float64), f.shape[0], _dev_ptr(g), C.byref(nf),
                                 _stream_ptr(stream)), "dg_boundary_data", h)
     return g
+
+
+def dg_exchange_build_multi(systems, opts=None, lanes=4, stream=None, allow_unconverged=False):
+    """systems: list of (lo, hi, n, p, psi) with psi a CUDA float64 [N, Nq] tensor.
+    Returns lists (K, E_H, E_X, stats) per system."""
+    import torch
+
+    nsys = len(systems)
+    meshes = (dg_mesh_desc * nsys)()
+    psis = (C.c_void_p * nsys)()
+    Ns = (C.c_int32 * nsys)()
+    Ks, Kp, sts, stp = [], (C.c_void_p * nsys)(), [], (C.c_void_p * nsys)()
+    for i, (lo, hi, n, p, psi) in enumerate(systems):
+        if np.isscalar(n):
+            n = (n, n, n)
+        meshes[i] = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
+        psis[i] = _dev_ptr(psi, torch.float64)
+        N = psi.shape[0]
+        Ns[i] = N
+        K = np.empty((N, N), dtype=np.float64)
+        Ks.append(K)
+        Kp[i] = K.ctypes.data_as(C.c_void_p)
+        st = (dg_solve_stats * (N * (N + 1) // 2 + 1))()
+        sts.append(st)
+        stp[i] = C.cast(st, C.c_void_p)
+    eh = (C.c_double * nsys)()
+    ex = (C.c_double * nsys)()
+    if opts is None:
+        opts = dg_default_opts()
+    allow = (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_NONFINITE) if allow_unconverged else ()
+    code = load().dg_exchange_build_multi(C.cast(meshes, C.c_void_p), C.cast(psis, C.c_void_p), C.cast(Ns, C.c_void_p),
+                                          nsys, C.byref(opts), C.cast(Kp, C.c_void_p), C.cast(eh, C.c_void_p),
+                                          C.cast(ex, C.c_void_p), C.cast(stp, C.c_void_p), lanes, _stream_ptr(stream))
+    _check(code, "dg_exchange_build_multi", None, allow)
+    return Ks, list(eh), list(ex), [_stats_list(st) for st in sts]
+
+
+def dg_release_cached_handles():
+    load().dg_release_cached_handles()
+
+
+def dg_autotune_batch(h, max_sources=0):
+    b = C.c_int32()
+    _check(load().dg_autotune_batch(h, max_sources, C.byref(b)), "dg_autotune_batch", h)
+    return b.value
 
 
 def dg_kernel_launch_count():
