@@ -160,6 +160,10 @@ int dg_get_info(dg_handle h, dg_info* info);
  * pointer may be NULL. */
 int dg_node_coords(dg_handle h, double* xyz_host, double* w_host);
 
+/* As dg_node_coords, from a mesh description alone (host computation, no
+ * handle, no GPU). */
+int dg_mesh_node_coords(const dg_mesh_desc* mesh, double* xyz_host, double* w_host);
+
 /* Solves -Lap v_b = 4 pi f_b with Coulomb-quadrature Dirichlet data for B
  * sources (steps S1-S4 and S10 for a batch). f_dev: [B][Nq] source values at
  * the nodes (device, read only). v_dev: [B][Nq] solutions (device, written).

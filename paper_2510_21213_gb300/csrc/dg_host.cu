@@ -1018,6 +1018,30 @@ int dg_get_info(dg_handle h, dg_info* info) {
   return DG_OK;
 }
 
+int dg_mesh_node_coords(const dg_mesh_desc* m, double* xyz, double* w) {
+  if (!m || m->p < 1 || m->p > 8) return DG_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (m->n[d] < 1 || !(m->hi[d] > m->lo[d])) return DG_ERR_INVALID_ARG;
+  const int n1 = m->p + 1, npe = n1 * n1 * n1;
+  double xi[MAXN1], wg[MAXN1];
+  gauss_legendre(n1, xi, wg);
+  double hd[3];
+  for (int d = 0; d < 3; ++d) hd[d] = (m->hi[d] - m->lo[d]) / m->n[d];
+  const long long Nq = (long long)m->n[0] * m->n[1] * m->n[2] * npe;
+  for (long long q = 0; q < Nq; ++q) {
+    const int e = (int)(q / npe), loc = (int)(q % npe);
+    const int a[3] = {loc % n1, (loc / n1) % n1, loc / (n1 * n1)};
+    const int ec[3] = {e % m->n[0], (e / m->n[0]) % m->n[1], e / (m->n[0] * m->n[1])};
+    double wq = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      if (xyz) xyz[3 * q + d] = m->lo[d] + hd[d] * (ec[d] + (xi[a[d]] + 1.0) / 2.0);
+      wq *= wg[a[d]] * hd[d] / 2.0;
+    }
+    if (w) w[q] = wq;
+  }
+  return DG_OK;
+}
+
 int dg_node_coords(dg_handle h, double* xyz, double* w) {
   if (!h) return DG_ERR_INVALID_ARG;
   const LevelOp& F = h->levels[0].op;

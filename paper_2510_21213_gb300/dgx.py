@@ -104,6 +104,8 @@ def load():
     lib.dg_poisson_setup.argtypes = [C.POINTER(dg_mesh_desc), C.POINTER(dg_solver_opts), C.POINTER(vp)]
     lib.dg_get_info.argtypes = [vp, C.POINTER(dg_info)]
     lib.dg_node_coords.argtypes = [vp, vp, vp]
+    lib.dg_mesh_node_coords.argtypes = [C.POINTER(dg_mesh_desc), vp, vp]
+    lib.dg_mesh_node_coords.restype = C.c_int
     lib.dg_pair_solve_batch.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     lib.dg_exchange_build.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp]
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -198,6 +200,19 @@ def dg_node_coords(h):
     xyz = np.empty((Nq, 3), dtype=np.float64)
     w = np.empty(Nq, dtype=np.float64)
     _check(load().dg_node_coords(h, xyz.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)), "dg_node_coords", h)
+    return xyz, w
+
+
+def dg_mesh_node_coords(lo, hi, n, p):
+    """(xyz [Nq, 3], W [Nq]) of a mesh without a handle (host computation)."""
+    if np.isscalar(n):
+        n = (n, n, n)
+    m = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
+    Nq = int(n[0] * n[1] * n[2] * (p + 1) ** 3)
+    xyz = np.empty((Nq, 3), dtype=np.float64)
+    w = np.empty(Nq, dtype=np.float64)
+    _check(load().dg_mesh_node_coords(C.byref(m), xyz.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)),
+           "dg_mesh_node_coords")
     return xyz, w
 
 
