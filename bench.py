@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chain10", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "learned"])
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
+    ap.add_argument("--no-learned", action="store_true", help="skip timing the learned form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
@@ -158,7 +159,7 @@ def kernel_roofline(solver, B, precision, torch, nrep=20):
     (CUDA events on the launching stream) and their algorithmic work."""
     Nq = solver.Nq
     n1 = solver.info.level_p[0] + 1
-    dt = torch.float32 if precision == "mixed" else torch.float64
+    dt = torch.float64 if precision == "fp64" else torch.float32
     u = torch.randn((B, Nq), dtype=dt, device="cuda")
     out = torch.empty_like(u)
     res = {}
@@ -180,7 +181,7 @@ def kernel_roofline(solver, B, precision, torch, nrep=20):
     apply_flops = Nq * (3 * (2 * n1 + 8) + 5) + E * 6 * n1 * n1 * 2 * 2 * n1
     m = n1 + 2
     sm_flops = E * (6 * 2 * m ** 4 + m ** 3)
-    s = 4 if precision == "mixed" else 8
+    s = 8 if precision == "fp64" else 4
     apply_bytes = 2 * Nq * s
     sm_bytes = Nq * s + E * m ** 3 * s  # patch kernel: read r, write patch solution
     return {
@@ -326,8 +327,12 @@ def run_ours(args):
     m = spec.mesh
     N = spec.N
     P = N * (N + 1) // 2
-    prec = dgx.DG_PREC_MIXED if args.precision == "mixed" else dgx.DG_PREC_FP64
-    solver = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=prec, rtol=1e-8)
+    prec = {"mixed": dgx.DG_PREC_MIXED, "fp64": dgx.DG_PREC_FP64, "learned": dgx.DG_PREC_MIXED_LEARNED}[args.precision]
+    weights = dgx.default_nn_weights(m.p)
+    if prec == dgx.DG_PREC_MIXED_LEARNED and weights is None:
+        raise SystemExit(f"no trained network weights for p = {m.p}")
+    solver = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=prec, rtol=1e-8,
+                               nn_weights_path=weights if prec == dgx.DG_PREC_MIXED_LEARNED else None)
     xyz, w = solver.node_coords()
     psi_host = make_inputs(spec, xyz, w)
     psi_dev = torch.tensor(psi_host, device="cuda")
@@ -406,12 +411,31 @@ def run_ours(args):
                  "E_X_rel_diff_vs_chosen": abs(ex64 - ex) / abs(ex64)}
         solver64.close()
 
+    # learned form (network initial guess) on the same system, where weights for this degree exist
+    learned = None
+    if not args.no_learned and prec == dgx.DG_PREC_MIXED and weights is not None:
+        solver_l = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=dgx.DG_PREC_MIXED_LEARNED, rtol=1e-8,
+                                     nn_weights_path=weights)
+        ltimes, (Kl, ehl, exl, stl) = time_builds(solver_l, psi_dev, max(1, min(args.steps, 3)), 1, torch, flush)
+        ltot = sum(ltimes) / 1e3
+        if ws > 1:
+            t = torch.tensor([ltot], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ltot = float(t.item())
+        learned = {"value": ws * P * len(ltimes) / ltot, "ms_per_step": ltot / len(ltimes) * 1e3,
+                   "mean_iters": float(np.mean([s["iters"] for s in stl[1:]])),
+                   "fallbacks": int(sum(s["used_fallback"] for s in stl)),
+                   "mean_guess_rel_residual": float(np.mean([s["guess_rel_residual"] for s in stl[1:]])),
+                   "K_rel_diff_vs_chosen": float(np.abs(Kl - K).max() / np.abs(K).max()),
+                   "weights": os.path.relpath(weights, ROOT)}
+        solver_l.close()
+
     # roofline of the dominant kernel (the smoother patch solve; see profiles/)
     B = min(P + 1, 64)
     rf = kernel_roofline(solver, B, args.precision, torch)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    alu_peak = FP32_PEAK_TFLOPS if args.precision == "mixed" else FP64_PEAK_TFLOPS
+    alu_peak = FP32_PEAK_TFLOPS if args.precision != "fp64" else FP64_PEAK_TFLOPS
     sm_tf = rf["smoother_flops"] / (rf["smoother_ms"] * 1e-3) / 1e12
     sm_gbs = rf["smoother_bytes"] / (rf["smoother_ms"] * 1e-3) / 1e9
     ap_tf = rf["apply_flops"] / (rf["apply_ms"] * 1e-3) / 1e12
@@ -420,7 +444,7 @@ def run_ours(args):
         "kernel": "k_schwarz_patch (fine-level smoother patch solve) + k_schwarz_gather",
         "bound": "alu", "achieved": sm_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": sm_tf / alu_peak,
         "traffic": None,
-        "peak_source": ("FP32 FMA probe (paper_2510_21213_gb300/csrc/peak_probe.cu)" if args.precision == "mixed"
+        "peak_source": ("FP32 FMA probe (paper_2510_21213_gb300/csrc/peak_probe.cu)" if args.precision != "fp64"
                         else "FP64 FMA probe (paper_2510_21213_gb300/csrc/peak_probe.cu)"),
         "launch_ms": rf["smoother_ms"], "B": B, "hbm_gbs": sm_gbs, "hbm_frac_of_measured": sm_gbs / hbm,
         "operator": {"launch_ms": rf["apply_ms"], "tflops": ap_tf, "frac_alu": ap_tf / alu_peak,
@@ -439,7 +463,8 @@ def run_ours(args):
             "value": value, "unit": "pair_solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "dtype": {"mixed": "f32+f64", "fp64": "f64", "learned": "bf16+f32+f64"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: box [-12,12]^3, n={m.n[0]}^3 elements, p={m.p}, "
                                    f"N={N} orbitals, {P} pair solves + Hartree per step",
                        "precision": args.precision, "rtol": 1e-8, "l2": "flushed (256 MB write) between steps",
@@ -451,6 +476,7 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "plain_fp64": plain,
+            "learned": learned,
             "solver": {"mean_iters": float(np.mean(iters)), "max_iters": int(max(iters)),
                        "max_rel_residual": resid, "all_converged": status_ok,
                        "outer_refinements": int(max(s["outer_refinements"] for s in stats)),

@@ -110,8 +110,10 @@ typedef struct {
   int32_t smoother_degree; /* Chebyshev degree of the multigrid smoother (default 3) */
   double cheb_range;     /* smoothing range lambda_max / lambda_min of the Chebyshev interval (default 10) */
   double inner_rtol;     /* MIXED: relative reduction of each FP32 inner solve (default 1e-4) */
-  const char* nn_weights_path; /* MIXED_LEARNED: network weights file (NULL = none) */
-  int32_t verbose;       /* 0 silent, 1 per-solve summary on stderr */
+  const char* nn_weights_path; /* MIXED_LEARNED: network weights file (NULL: set by dg_nn_set_params) */
+  int32_t verbose;       /* 0 silent, 1 per-solve summary, 2 also per refinement round (stderr) */
+  int32_t coarse_penalty; /* 0: each multigrid level uses the penalty of its own p and h;
+                             1: every level uses the fine level's penalty (Galerkin-consistent hierarchy) */
 } dg_solver_opts;
 
 typedef struct {
@@ -120,6 +122,7 @@ typedef struct {
   int32_t status;            /* DG_OK, DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN or DG_ERR_NONFINITE */
   int32_t used_fallback;     /* 1 if a learned guess was rejected and the plain solver used */
   double rel_residual;       /* final FP64 true relative residual */
+  double guess_rel_residual; /* FP64 relative residual of the initial guess (1 for the zero guess) */
 } dg_solve_stats;
 
 typedef struct {

@@ -80,6 +80,16 @@ struct BcAxisTables {
   DevBuf Gs;   // [L][NG * L]      c_k exp(-a_k (x_i - x_j)^2)
 };
 
+// network of the learned initial guess: parameters, Adam state, batch buffers
+struct NNState {
+  bool have = false;     // parameters set
+  bool bf16_ok = false;  // BF16 copies of W2 match prm
+  int step = 0;          // Adam steps taken
+  DevBuf prm, W2t, W2o, m, v, grad, part;
+  DevBuf in, out, a1, a2;
+  long long save_ne = -1;  // elements whose activations a1 / a2 hold (-1: none)
+};
+
 }  // namespace dg
 
 struct dg_ctx {
@@ -117,6 +127,7 @@ struct dg_ctx {
   bool use_graphs = true;     // capture the PCG phases as CUDA graphs
   cudaStream_t ws = nullptr;  // the handle's own stream (graph capture needs a non-default stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  dg::NNState nn;             // learned initial guess (DG_PREC_MIXED_LEARNED)
   ~dg_ctx() {
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -141,6 +152,20 @@ int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap);
 int ensure_common(dg_ctx* h, int cap);
 int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s);
 int autotune_batch(dg_ctx* h, int max_sources, cudaStream_t s);
+int prepare(dg_ctx* h, int cap);
+int form_rhs(dg_ctx* h, const double* f, int nsrc, cudaStream_t s);
+int check_finite(dg_ctx* h, const double* f, int nsrc, std::vector<int>& finite, cudaStream_t s);
+
+// learned initial guess (dg_learned.cu): for the sources in act, sets x64 and
+// r64 = b64 - A x64 (b64 formed), rel[k] = ||r64|| / ||b64||, fb[k] = 1 where
+// the guess was rejected (x64 = 0, r64 = b64)
+int learned_guess(dg_ctx* h, const std::vector<int>& act, const std::vector<double>& bnorm2, bool use_net,
+                  std::vector<double>& rel, std::vector<int>& fb, cudaStream_t s);
+int nn_load_file(dg_ctx* h, const char* path);
+
+// scalar slots of h->scal, each [cap] doubles
+enum { S_BN = 0, S_RR, S_RZ, S_RZN, S_PQ, S_AL, S_BE, S_G1, S_G2, S_G3, S_NSLOT };
+inline double* scal(dg_ctx* h, int slot) { return h->scal.as<double>() + (size_t)slot * h->cap; }
 
 #define DG_RET(call)                 \
   do {                               \

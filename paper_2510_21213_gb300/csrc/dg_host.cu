@@ -13,13 +13,10 @@
 #include <vector>
 
 #include "dg_ctx.h"
+#include "dg_mg.h"
 
 namespace dg {
 
-// scalar slots of h->scal, each [cap] doubles
-enum { S_BN = 0, S_RR, S_RZ, S_RZN, S_PQ, S_AL, S_BE, S_NSLOT };
-
-static double* scal(dg_ctx* h, int slot) { return h->scal.as<double>() + (size_t)slot * h->cap; }
 
 // ---------------------------------------------------------------------------
 // workspace
@@ -118,87 +115,6 @@ static void account(dg_ctx* h) {
   }
   h->ws_bytes = b;
 }
-
-// ---------------------------------------------------------------------------
-// multigrid V-cycle (Sec. 6.4: degree coarsening to 1, then geometric)
-// ---------------------------------------------------------------------------
-template <typename T>
-struct MG {
-  dg_ctx* h;
-  PrecWork<T>* w;
-  const int* act;
-  int nact;
-  cudaStream_t s;
-
-  // Chebyshev-Jacobi smoothing of A x = b on level l (degree k), Chebyshev
-  // semi-iteration on D^-1 A over [lam/range, lam]. On exit, if want_res,
-  // lev[l].res holds b - A x.
-  int cheb(int l, const T* b, T* x, bool zero_init, bool want_res) {
-    Level& L = h->levels[l];
-    LevelWork& W = w->lev[l];
-    T* res = W.res.as<T>();
-    T* d = W.d.as<T>();
-    const bool sw = h->opts.smoother == DG_SMOOTH_SCHWARZ;
-    // sw: the smoother preconditioner is M_S (z = M_S res), else D^-1 (fused)
-    const T* invD = sw ? nullptr : W.invD.as<T>();
-    const long long Nq = L.op.Nq;
-    const int k = std::max(1, h->opts.smoother_degree);
-    const double bmax = sw ? L.lam_sw : L.lam_max * (1.0 + 1e-6);
-    const double amin = bmax / std::max(1.5, h->opts.cheb_range);
-    const double theta = 0.5 * (bmax + amin), delta = 0.5 * (bmax - amin);
-    const double sig1 = theta / delta;
-    const T* r0 = b;
-    if (!zero_init) {
-      DG_CK(launch_apply<T>(L.op, L.dop, 1, x, res, b, act, nact, s));
-      r0 = res;
-    }
-    if (sw)
-      DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r0, W.zp.as<T>(), d, x, zero_init ? 1 : 2,
-                              1.0 / theta, 0.0, act, nact, s));
-    else
-      DG_CK(launch_cheb_first<T>(x, d, r0, invD, 1.0 / theta, zero_init ? 1 : 0, Nq, act, nact, s));
-    double rho_prev = 1.0 / sig1;
-    bool res_is_b = zero_init;  // the residual of the current x is b - A d when res_is_b
-    for (int j = 2; j <= k; ++j) {
-      if (res_is_b)
-        DG_CK(launch_apply<T>(L.op, L.dop, 1, d, res, b, act, nact, s));
-      else
-        DG_CK(launch_apply<T>(L.op, L.dop, 2, d, res, nullptr, act, nact, s));
-      res_is_b = false;
-      const double rho = 1.0 / (2.0 * sig1 - rho_prev);
-      if (sw)
-        DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), res, W.zp.as<T>(), d, x, 3, rho * rho_prev,
-                                2.0 * rho / delta, act, nact, s));
-      else
-        DG_CK(launch_cheb_step<T>(x, d, res, invD, rho * rho_prev, 2.0 * rho / delta, Nq, act, nact, s));
-      rho_prev = rho;
-    }
-    if (want_res) {
-      if (res_is_b)
-        DG_CK(launch_apply<T>(L.op, L.dop, 1, d, res, b, act, nact, s));
-      else
-        DG_CK(launch_apply<T>(L.op, L.dop, 2, d, res, nullptr, act, nact, s));
-    }
-    return DG_OK;
-  }
-
-  // x = V(b) on level l (x overwritten)
-  int vcycle(int l, const T* b, T* x) {
-    if (l == h->nlev - 1) {
-      DG_CK(launch_coarse_solve<T>(h->coarse_inv.as<double>(), h->Nc, b, x, act, nact, s));
-      return DG_OK;
-    }
-    Level& L = h->levels[l];
-    Level& C = h->levels[l + 1];
-    LevelWork& Wc = w->lev[l + 1];
-    DG_RET(cheb(l, b, x, true, true));
-    DG_CK(launch_restrict<T>(L.tr, L.dtr, L.op, C.op, w->lev[l].res.template as<T>(), Wc.b.as<T>(), act, nact, s));
-    DG_RET(vcycle(l + 1, Wc.b.as<T>(), Wc.x.as<T>()));
-    DG_CK(launch_prolong_add<T>(L.tr, L.dtr, L.op, C.op, Wc.x.as<T>(), x, act, nact, s));
-    DG_RET(cheb(l, b, x, false, false));
-    return DG_OK;
-  }
-};
 
 // device per-rhs scalar update: out = num / den (0 and a breakdown flag when den <= 0 or not finite)
 __global__ void k_ratio(const double* num, const double* den, double* out, const int* act, int nact, int* flags,
@@ -407,6 +323,16 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
                                           (int)act.size(), 1.0, 0, s)));
   }
   for (int k : act) rel[k] = bnorm2[k] > 0 ? 1.0 : 0.0;
+  // learned form: start from the network's guess (x64, r64, rel set; rejected
+  // guesses fall back to x64 = 0)
+  std::vector<int> fbk(h->cap, 0);
+  if (h->opts.precision == DG_PREC_MIXED_LEARNED) {
+    std::vector<int> nz;
+    for (int k : act)
+      if (bnorm2[k] > 0) nz.push_back(k);
+    DG_RET(learned_guess(h, nz, bnorm2, true, rel, fbk, s));
+  }
+  std::vector<double> grel = rel;
   std::vector<int> todo;
   for (int k : act)
     if (rel[k] > rtol) todo.push_back(k);
@@ -441,6 +367,10 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
       outer[k] += 1;
     }
     DG_RET(true_residual(h, todo, bnorm2, rel, s));
+    if (h->opts.verbose >= 2)
+      for (int k : todo)
+        std::fprintf(stderr, "  source %d round %d: inner iterations %d (asked %.2e), true residual %.3e\n", k, round,
+                     it_inner[k], tolv[k], rel[k]);
     std::vector<int> t2;
     for (int k : todo)
       if (rel[k] > rtol && std::isfinite(rel[k]) && iters[k] < maxit) t2.push_back(k);
@@ -454,8 +384,9 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
     dg_solve_stats S;
     S.iters = iters[k];
     S.outer_refinements = mixed ? outer[k] : 0;
-    S.used_fallback = 0;
+    S.used_fallback = fbk[k];
     S.rel_residual = finite[k] ? rel[k] : NAN;
+    S.guess_rel_residual = finite[k] ? grel[k] : NAN;
     if (!finite[k])
       S.status = DG_ERR_NONFINITE;
     else if (!(rel[k] <= rtol))
@@ -593,7 +524,7 @@ static bool bc_fp32(const dg_ctx* h) {
   return h->opts.precision != DG_PREC_FP64 && h->opts.bc_route == DG_BC_GAUSSSUM;
 }
 
-static int form_rhs(dg_ctx* h, const double* f, int nsrc, cudaStream_t s) {
+int form_rhs(dg_ctx* h, const double* f, int nsrc, cudaStream_t s) {
   DG_CK(launch_rhs_volume(f, h->d_W.as<double>(), h->b64.as<double>(), h->Nq, nsrc, s));
   if (bc_fp32(h)) {
     DG_CK(h->g32.ensure(sizeof(float) * h->nface * nsrc));
@@ -609,7 +540,7 @@ static int form_rhs(dg_ctx* h, const double* f, int nsrc, cudaStream_t s) {
   return DG_OK;
 }
 
-static int check_finite(dg_ctx* h, const double* f, int nsrc, std::vector<int>& finite, cudaStream_t s) {
+int check_finite(dg_ctx* h, const double* f, int nsrc, std::vector<int>& finite, cudaStream_t s) {
   DG_CK(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * nsrc, s));
   DG_CK(launch_finite_flags(f, h->Nq, nsrc, h->flags.as<int>(), s));
   std::vector<int> fl(nsrc);
@@ -628,7 +559,7 @@ static int default_batch(dg_ctx* h) {
   return (int)std::max(1LL, std::min(b, 256LL));
 }
 
-static int prepare(dg_ctx* h, int cap) {
+int prepare(dg_ctx* h, int cap) {
   DG_RET(ensure_common(h, cap));
   if (h->opts.precision == DG_PREC_FP64)
     DG_RET(ensure_prec<double>(h, h->w64, cap));
@@ -745,7 +676,10 @@ static int setup(dg_ctx* h) {
   h->levels.resize(h->nlev);
   for (int l = 0; l < h->nlev; ++l) {
     Level& L = h->levels[l];
-    build_level(L.op, spec[l].first.data(), spec[l].second, m.lo, m.hi, o.penalty_form, o.penalty_eps);
+    double sig0[3];
+    for (int d = 0; d < 3; ++d) sig0[d] = h->levels[0].op.ax[d].sigma;
+    build_level(L.op, spec[l].first.data(), spec[l].second, m.lo, m.hi, o.penalty_form, o.penalty_eps,
+                (l > 0 && o.coarse_penalty == 1) ? sig0 : nullptr);
     L.lam_max = level_lambda_max(L.op);
   }
   for (int l = 0; l + 1 < h->nlev; ++l) build_transfer(h->levels[l].tr, h->levels[l].op, h->levels[l + 1].op);
@@ -930,6 +864,7 @@ void dg_default_opts(dg_solver_opts* o) {
   o->inner_rtol = 1e-4;
   o->nn_weights_path = nullptr;
   o->verbose = 0;
+  o->coarse_penalty = 0;
 }
 
 const char* dg_error_string(int status) {
@@ -968,16 +903,19 @@ int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_ha
   if (!(o.rtol > 0) || o.max_iter < 1 || !(o.penalty_eps > 0) || (o.penalty_form != 0 && o.penalty_form != 1) ||
       (o.bc_route != DG_BC_DIRECT && o.bc_route != DG_BC_GAUSSSUM) || o.precision < 0 || o.precision > 2 ||
       o.smoother_degree < 1 || o.smoother_degree > 16 || o.batch < 0 ||
-      (o.smoother != DG_SMOOTH_JACOBI && o.smoother != DG_SMOOTH_SCHWARZ))
+      (o.smoother != DG_SMOOTH_JACOBI && o.smoother != DG_SMOOTH_SCHWARZ) ||
+      (o.coarse_penalty != 0 && o.coarse_penalty != 1))
     return DG_ERR_INVALID_ARG;
   if (o.cheb_range <= 1.0) o.cheb_range = 10.0;
   if (o.inner_rtol <= 0.0) o.inner_rtol = 1e-4;
-  if (o.precision == DG_PREC_MIXED_LEARNED && !o.nn_weights_path) return DG_ERR_INVALID_ARG;
+  if (o.precision == DG_PREC_MIXED_LEARNED && mesh->p > NN_MAXN1 - 1) return DG_ERR_UNSUPPORTED;
   dg_ctx* h = new (std::nothrow) dg_ctx();
   if (!h) return DG_ERR_NO_MEMORY;
   h->mesh = *mesh;
   h->opts = o;
-  const int rc = setup(h);
+  int rc = setup(h);
+  if (rc == DG_OK && o.precision == DG_PREC_MIXED_LEARNED && o.nn_weights_path) rc = nn_load_file(h, o.nn_weights_path);
+  h->opts.nn_weights_path = nullptr;  // the caller's string is not kept
   if (rc != DG_OK) {
     fprintf(stderr, "dg_poisson_setup: %s\n", h->err.c_str());
     dg_destroy(h);

@@ -160,4 +160,17 @@ cudaError_t launch_kmat(const double* psi, const double* W, const double* Wacc, 
 
 int kmat_chunks(long long Nq);
 
+// per-element convolutional network of the learned initial guess (dg_nn.cu);
+// parameters FP32 [NN_NPARAM], W2 also as BF16 [27][co][ci] (W2t) and [27][ci][co] (W2o)
+constexpr int NN_NPARAM = 31170;
+constexpr int NN_MAXN1 = 8;
+cudaError_t nn_prep(const float* prm, void* W2t, void* W2o, cudaStream_t s);
+cudaError_t nn_forward(int n1, const float* prm, const void* W2t, const float* in, float* out, void* a1, void* a2,
+                       long long ne, cudaStream_t s);
+int nn_backward_blocks(int n1, long long ne);
+cudaError_t nn_backward(int n1, const float* prm, const void* W2o, const float* in, const void* a1, const void* a2,
+                        const float* gout, float* part, float* grad, long long ne, cudaStream_t s);
+cudaError_t nn_adam(float* prm, const float* grad, float* m, float* v, float lr, float b1, float b2, float eps,
+                    int step, cudaStream_t s);
+
 }  // namespace dg

@@ -126,7 +126,8 @@ void build_axis(AxisOp& A, int n, int p, double lo, double hi, double sigma) {
   }
 }
 
-void build_level(LevelOp& L, const int n[3], int p, const double lo[3], const double hi[3], int pform, double eps) {
+void build_level(LevelOp& L, const int n[3], int p, const double lo[3], const double hi[3], int pform, double eps,
+                 const double* sigma) {
   std::memset(&L, 0, sizeof(L));
   const int n1 = p + 1;
   for (int d = 0; d < 3; ++d) L.n[d] = n[d];
@@ -140,7 +141,7 @@ void build_level(LevelOp& L, const int n[3], int p, const double lo[3], const do
   lagrange(xi, n1, 1.0, L.tr, L.dr);
   for (int d = 0; d < 3; ++d) {
     const double h = (hi[d] - lo[d]) / n[d];
-    build_axis(L.ax[d], n[d], p, lo[d], hi[d], penalty(p, h, pform, eps));
+    build_axis(L.ax[d], n[d], p, lo[d], hi[d], sigma ? sigma[d] : penalty(p, h, pform, eps));
   }
 }
 

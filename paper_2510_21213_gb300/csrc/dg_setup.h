@@ -18,7 +18,9 @@ void gauss_legendre(int n, double* x, double* w);
 void lagrange(const double* nodes, int m, double x, double* L, double* dL);
 double penalty(int p, double h, int form, double eps);
 void build_axis(AxisOp& A, int n, int p, double lo, double hi, double sigma);
-void build_level(LevelOp& L, const int n[3], int p, const double lo[3], const double hi[3], int pform, double eps);
+// sigma (per axis) overrides the penalty of (p, h) when not null
+void build_level(LevelOp& L, const int n[3], int p, const double lo[3], const double hi[3], int pform, double eps,
+                 const double* sigma = nullptr);
 std::vector<double> axis_matrix(const AxisOp& A, const LevelOp& L);
 double sym_max_eig(std::vector<double> S, int n);
 double level_lambda_max(const LevelOp& L);

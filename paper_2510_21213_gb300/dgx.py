@@ -56,6 +56,7 @@ class dg_solver_opts(C.Structure):
         ("inner_rtol", C.c_double),
         ("nn_weights_path", C.c_char_p),
         ("verbose", C.c_int32),
+        ("coarse_penalty", C.c_int32),
     ]
 
 
@@ -66,6 +67,7 @@ class dg_solve_stats(C.Structure):
         ("status", C.c_int32),
         ("used_fallback", C.c_int32),
         ("rel_residual", C.c_double),
+        ("guess_rel_residual", C.c_double),
     ]
 
 
@@ -125,8 +127,16 @@ def load():
     lib.dg_error_string.restype = C.c_char_p
     lib.dg_last_error_detail.argtypes = [vp]
     lib.dg_last_error_detail.restype = C.c_char_p
+    lib.dg_nn_set_params.argtypes = [vp, vp]
+    lib.dg_nn_get_params.argtypes = [vp, vp]
+    lib.dg_nn_forward.argtypes = [vp, vp, vp, C.c_int64, C.c_int32, vp]
+    lib.dg_nn_backward.argtypes = [vp, vp, vp, vp, C.c_int64, vp]
+    lib.dg_nn_adam.argtypes = [vp, vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]
+    lib.dg_nn_train_step.argtypes = [vp, vp, vp, C.c_int64, C.c_float, vp, vp]
+    lib.dg_nn_guess.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, vp, vp]
     for name in ("dg_poisson_setup", "dg_get_info", "dg_node_coords", "dg_pair_solve_batch", "dg_exchange_build",
-                 "dg_apply_operator", "dg_boundary_data", "dg_apply_smoother"):
+                 "dg_apply_operator", "dg_boundary_data", "dg_apply_smoother", "dg_nn_set_params", "dg_nn_get_params",
+                 "dg_nn_forward", "dg_nn_backward", "dg_nn_adam", "dg_nn_train_step", "dg_nn_guess"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -218,7 +228,8 @@ def dg_mesh_node_coords(lo, hi, n, p):
 
 def _stats_list(arr):
     return [{"iters": s.iters, "outer_refinements": s.outer_refinements, "status": s.status,
-             "used_fallback": s.used_fallback, "rel_residual": s.rel_residual} for s in arr]
+             "used_fallback": s.used_fallback, "rel_residual": s.rel_residual,
+             "guess_rel_residual": s.guess_rel_residual} for s in arr]
 
 
 def dg_pair_solve_batch(h, f, v=None, stream=None, allow_unconverged=False):
@@ -335,6 +346,130 @@ def dg_autotune_batch(h, max_sources=0):
     b = C.c_int32()
     _check(load().dg_autotune_batch(h, max_sources, C.byref(b)), "dg_autotune_batch", h)
     return b.value
+
+
+# ---------------------------------------------------------------------------
+# learned initial guess (include/dg_nn.h)
+# ---------------------------------------------------------------------------
+DG_NN_NPARAM = 31170
+DG_NN_HIDDEN = 32
+# parameter layout: (name, shape) in order; W[t][ci][co] with t = 9 (dz+1) + 3 (dy+1) + (dx+1)
+NN_LAYOUT = (("W1", (3, 3, 3, 2, 32)), ("b1", (32,)), ("W2", (3, 3, 3, 32, 32)), ("b2", (32,)),
+             ("W3", (3, 3, 3, 32, 2)), ("b3", (2,)))
+WEIGHTS_DIR = os.path.join(_PKG, "weights")
+
+
+def nn_pack(params):
+    """dict of arrays (shapes of NN_LAYOUT) -> flat float32 [DG_NN_NPARAM]."""
+    flat = np.concatenate([np.asarray(params[k], dtype=np.float64).reshape(-1) for k, _ in NN_LAYOUT])
+    assert flat.size == DG_NN_NPARAM
+    return flat.astype(np.float32)
+
+
+def nn_unpack(flat):
+    """flat [DG_NN_NPARAM] -> dict of float64 arrays with the shapes of NN_LAYOUT."""
+    flat = np.asarray(flat, dtype=np.float64).reshape(-1)
+    out, o = {}, 0
+    for k, shp in NN_LAYOUT:
+        n = int(np.prod(shp))
+        out[k] = flat[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+def save_nn_weights(path, flat, p):
+    """Writes the weights file read by dg_poisson_setup (header "DGNN", 1, nparam, p)."""
+    flat = np.asarray(flat, dtype="<f4").reshape(-1)
+    if flat.size != DG_NN_NPARAM:
+        raise ValueError("wrong parameter count")
+    with open(path, "wb") as fh:
+        fh.write(b"DGNN")
+        fh.write(np.array([1, DG_NN_NPARAM, int(p)], dtype="<i4").tobytes())
+        fh.write(flat.tobytes())
+
+
+def load_nn_weights(path):
+    """(flat float32 params, p) of a weights file."""
+    with open(path, "rb") as fh:
+        raw = fh.read()
+    if raw[:4] != b"DGNN":
+        raise ValueError("not a DGNN weights file")
+    ver, n, p = np.frombuffer(raw[4:16], dtype="<i4")
+    if ver != 1 or n != DG_NN_NPARAM:
+        raise ValueError("unsupported weights file")
+    return np.frombuffer(raw[16:16 + 4 * n], dtype="<f4").copy(), int(p)
+
+
+def default_nn_weights(p):
+    """Path of the packaged weights for degree p, or None."""
+    path = os.path.join(WEIGHTS_DIR, f"dgnn_p{int(p)}.bin")
+    return path if os.path.exists(path) else None
+
+
+def dg_nn_set_params(h, flat):
+    flat = np.ascontiguousarray(np.asarray(flat, dtype=np.float32).reshape(-1))
+    if flat.size != DG_NN_NPARAM:
+        raise ValueError("wrong parameter count")
+    _check(load().dg_nn_set_params(h, flat.ctypes.data_as(C.c_void_p)), "dg_nn_set_params", h)
+
+
+def dg_nn_get_params(h):
+    flat = np.empty(DG_NN_NPARAM, dtype=np.float32)
+    _check(load().dg_nn_get_params(h, flat.ctypes.data_as(C.c_void_p)), "dg_nn_get_params", h)
+    return flat
+
+
+def dg_nn_forward(h, x, save_act=False, stream=None):
+    """x: CUDA float32 [n_elem, (p+1)^3, 2]. Returns the network output, same shape."""
+    import torch
+
+    out = torch.empty_like(x)
+    _check(load().dg_nn_forward(h, _dev_ptr(x, torch.float32), _dev_ptr(out, torch.float32), x.shape[0],
+                                int(bool(save_act)), _stream_ptr(stream)), "dg_nn_forward", h)
+    return out
+
+
+def dg_nn_backward(h, x, gout, stream=None):
+    """Gradient [DG_NN_NPARAM] (CUDA float32) of sum(gout * net(x)); needs dg_nn_forward(x, save_act=True)."""
+    import torch
+
+    grad = torch.empty(DG_NN_NPARAM, dtype=torch.float32, device=x.device)
+    _check(load().dg_nn_backward(h, _dev_ptr(x, torch.float32), _dev_ptr(gout, torch.float32),
+                                 _dev_ptr(grad, torch.float32), x.shape[0], _stream_ptr(stream)), "dg_nn_backward", h)
+    return grad
+
+
+def dg_nn_adam(h, grad, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    import torch
+
+    _check(load().dg_nn_adam(h, _dev_ptr(grad, torch.float32), lr, beta1, beta2, eps, _stream_ptr(stream)),
+           "dg_nn_adam", h)
+
+
+def dg_nn_train_step(h, f, v, lr, stream=None):
+    """One training step on sources f with target potentials v (CUDA float64 [B, Nq]).
+    Returns (loss, per-source losses)."""
+    import torch
+
+    B = f.shape[0]
+    if v.shape != f.shape:
+        raise ValueError("f and v must have the same shape")
+    loss = np.zeros(B + 1, dtype=np.float64)
+    _check(load().dg_nn_train_step(h, _dev_ptr(f, torch.float64), _dev_ptr(v, torch.float64), B, lr,
+                                   loss.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), "dg_nn_train_step", h)
+    return float(loss[0]), loss[1:].copy()
+
+
+def dg_nn_guess(h, f, use_net=True, stream=None):
+    """Initial guess of the solver for sources f (CUDA float64 [B, Nq]): (x0 [B, Nq], rel residuals [B])."""
+    import torch
+
+    B = f.shape[0]
+    x0 = torch.empty_like(f)
+    rel = np.zeros(max(B, 1), dtype=np.float64)
+    _check(load().dg_nn_guess(h, _dev_ptr(f, torch.float64), B, int(bool(use_net)), _dev_ptr(x0, torch.float64),
+                              rel.ctypes.data_as(C.c_void_p), _stream_ptr(stream)), "dg_nn_guess", h)
+    return x0, rel[:B].copy()
 
 
 def dg_kernel_launch_count():

@@ -171,3 +171,32 @@ def orbitals(spec, coords, weights=None):
             raise ValueError("orthonormalisation needs the quadrature weights")
         psi = lowdin(psi, np.asarray(weights, dtype=np.float64))
     return psi
+
+
+def orbitals_torch(spec, coords, weights=None):
+    """orbitals() evaluated with torch on the device of `coords` (float64
+    [Nq, 3] tensor; `weights` [Nq] tensor), for generating many large systems
+    quickly (network training). Same recipe as orbitals()."""
+    import torch
+
+    if spec.kind != "gto":
+        raise ValueError("only Gaussian-orbital systems")
+    dev = coords.device
+    atoms = torch.tensor(spec.atoms, dtype=torch.float64, device=dev)
+    exps = torch.tensor(spec.exponents, dtype=torch.float64, device=dev)
+    C = torch.tensor(spec.coeffs, dtype=torch.float64, device=dev)
+    psi = torch.zeros((C.shape[0], coords.shape[0]), dtype=torch.float64, device=dev)
+    for a in range(atoms.shape[0]):
+        d = coords - atoms[a]
+        g = torch.exp(-exps[a] * (d * d).sum(dim=1))
+        prim = torch.stack([g, d[:, 0] * g, d[:, 1] * g, d[:, 2] * g])
+        psi += C[:, 4 * a:4 * a + 4] @ prim
+    if spec.orthonormalise:
+        if weights is None:
+            raise ValueError("orthonormalisation needs the quadrature weights")
+        S = (psi * weights[None, :]) @ psi.T
+        lam, U = torch.linalg.eigh(S)
+        if lam.min() <= 0:
+            raise RuntimeError("orbital overlap is not positive definite")
+        psi = (U @ torch.diag(lam ** -0.5) @ U.T) @ psi
+    return psi

@@ -1,0 +1,223 @@
+"""GPU parity of the learned-guess network: forward, backward and Adam kernels
+through the C ABI against the float64 conv-net oracle, and the learned form of
+the solver (same converged result, fallback on a broken network)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import nn_oracle as nno
+from paper_2510_21213_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dgx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_21213_gb300 import build, dgx
+
+    build.build()
+    dgx.load()
+    return dgx
+
+
+def bf16(a):
+    """Round to bfloat16 (nearest, ties to even) through float32."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def random_case(n1, ne, seed):
+    rng = np.random.default_rng(seed)
+    params = nno.init_params(seed)
+    params = {k: f32(v) for k, v in params.items()}
+    for k in ("b1", "b2", "b3"):
+        params[k] = f32(0.1 * rng.standard_normal(params[k].shape))
+    x = f32(rng.standard_normal((ne, n1, n1, n1, 2)))
+    g = f32(rng.standard_normal((ne, n1, n1, n1, 2)))
+    return params, x, g
+
+
+def emulated_forward(params, x):
+    """The kernels' arithmetic: W1, W3 in FP32, W2 and the stored activations in BF16."""
+    a1 = bf16(np.maximum(nno.conv3(x, params["W1"], params["b1"]), 0.0))
+    a2 = bf16(np.maximum(nno.conv3(a1, bf16(params["W2"]), params["b2"]), 0.0))
+    return nno.conv3(a2, params["W3"], params["b3"]), (a1, a2)
+
+
+def emulated_backward(params, x, acts, g):
+    a1, a2 = acts
+    out = {"W3": nno.conv3_weight_grad(a2, g), "b3": g.sum(axis=(0, 1, 2, 3))}
+    g2 = bf16(nno.conv3_transpose(g, params["W3"]) * (a2 > 0))
+    out["W2"] = nno.conv3_weight_grad(a1, g2)
+    out["b2"] = g2.sum(axis=(0, 1, 2, 3))
+    g1 = bf16(nno.conv3_transpose(g2, bf16(params["W2"])) * (a1 > 0))
+    out["W1"] = nno.conv3_weight_grad(x, g1)
+    out["b1"] = g1.sum(axis=(0, 1, 2, 3))
+    return out
+
+
+def to_dev(a, n1):
+    ne = a.shape[0]
+    return torch.tensor(a.reshape(ne, n1 ** 3, 2), dtype=torch.float32, device="cuda").contiguous()
+
+
+# degrees 1..7: one, two and several 16-node tiles, ragged tails; 37 elements
+# is not a multiple of any grid
+@pytest.mark.parametrize("p,ne", [(1, 37), (2, 37), (4, 37), (6, 37), (7, 37), (7, 1)])
+def test_forward_backward_vs_oracle(dgx, p, ne):
+    n1 = p + 1
+    s = dgx.PoissonSolver([-1.0] * 3, [1.0] * 3, (1, 1, 1), p)
+    params, x, g = random_case(n1, ne, seed=10 + p)
+    dgx.dg_nn_set_params(s.h, dgx.nn_pack(params))
+    got = dgx.dg_nn_forward(s.h, to_dev(x, n1), save_act=True).cpu().double().numpy().reshape(x.shape)
+    ref_plain, cache = nno.forward(params, x)
+    ref_emul, acts = emulated_forward(params, x)
+    scale = np.abs(ref_plain).max()
+    # kernels' own arithmetic (BF16 storage emulated): FP32 accumulation order only
+    assert np.abs(got - ref_emul).max() <= 2e-3 * scale
+    # float64 network: the stated BF16 bound
+    assert np.abs(got - ref_plain).max() <= 1e-2 * scale
+
+    grad = dgx.dg_nn_backward(s.h, to_dev(x, n1), to_dev(g, n1)).cpu().double().numpy()
+    got_g = dgx.nn_unpack(grad)
+    ref_g = nno.backward(params, cache, g)
+    emu_g = emulated_backward(params, x, acts, g)
+    for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        nrm = np.linalg.norm(ref_g[k])
+        # the kernels' arithmetic: BF16 activations, gradients and W2 emulated
+        assert np.linalg.norm(got_g[k] - emu_g[k]) <= 2e-3 * nrm + 1e-6, k
+        # against the float64 network the gap is set by ReLU masks that flip
+        # where BF16 rounding moves a pre-activation across zero: each flip
+        # changes one gradient entry by its full size, so the norm error goes
+        # like the square root of the flipped fraction (a few per cent here)
+        assert np.linalg.norm(got_g[k] - ref_g[k]) <= 1e-1 * nrm + 1e-6, k
+    # fixed summation order: a second backward is bit-identical
+    grad2 = dgx.dg_nn_backward(s.h, to_dev(x, n1), to_dev(g, n1)).cpu().double().numpy()
+    assert np.array_equal(grad, grad2)
+    s.close()
+
+
+def test_backward_needs_saved_activations(dgx):
+    s = dgx.PoissonSolver([-1.0] * 3, [1.0] * 3, (1, 1, 1), 3)
+    params, x, g = random_case(4, 5, seed=3)
+    dgx.dg_nn_set_params(s.h, dgx.nn_pack(params))
+    dgx.dg_nn_forward(s.h, to_dev(x, 4), save_act=False)
+    with pytest.raises(dgx.DGError):
+        dgx.dg_nn_backward(s.h, to_dev(x, 4), to_dev(g, 4))
+    s.close()
+
+
+def test_no_params_and_bad_params_rejected(dgx):
+    s = dgx.PoissonSolver([-1.0] * 3, [1.0] * 3, (1, 1, 1), 3)
+    x = torch.zeros(2, 64, 2, dtype=torch.float32, device="cuda")
+    with pytest.raises(dgx.DGError):
+        dgx.dg_nn_forward(s.h, x)
+    bad = np.zeros(dgx.DG_NN_NPARAM, dtype=np.float32)
+    bad[7] = np.nan
+    with pytest.raises(dgx.DGError):
+        dgx.dg_nn_set_params(s.h, bad)
+    s.close()
+    with pytest.raises(dgx.DGError):  # p = 8 has no network
+        dgx.PoissonSolver([-1.0] * 3, [1.0] * 3, (1, 1, 1), 8, precision=dgx.DG_PREC_MIXED_LEARNED)
+
+
+def test_adam_step(dgx):
+    s = dgx.PoissonSolver([-1.0] * 3, [1.0] * 3, (1, 1, 1), 2)
+    rng = np.random.default_rng(5)
+    p0 = rng.standard_normal(dgx.DG_NN_NPARAM).astype(np.float32)
+    dgx.dg_nn_set_params(s.h, p0)
+    p = p0.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    lr, b1, b2, eps = 1e-2, 0.9, 0.999, 1e-8
+    for t in (1, 2, 3):
+        g = rng.standard_normal(dgx.DG_NN_NPARAM).astype(np.float32)
+        dgx.dg_nn_adam(s.h, torch.tensor(g, device="cuda"), lr, b1, b2, eps)
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g.astype(np.float64) ** 2
+        p = p - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+    got = dgx.dg_nn_get_params(s.h).astype(np.float64)
+    assert np.abs(got - p).max() <= 1e-5 * (1 + np.abs(p).max())
+    s.close()
+
+
+def tiny_sources(dgx, s, pairs):
+    spec = inputs.tiny_system()
+    xyz, w = s.node_coords()
+    psi = inputs.orbitals(spec, xyz, w)
+    f = np.stack([psi[i] * psi[j] for i, j in pairs])
+    return torch.tensor(f, device="cuda")
+
+
+def test_training_lowers_the_loss(dgx):
+    spec = inputs.tiny_system().mesh
+    s = dgx.PoissonSolver(spec.lo, spec.hi, spec.n, spec.p, precision=dgx.DG_PREC_MIXED_LEARNED,
+                          bc_route=dgx.DG_BC_GAUSSSUM)
+    params = nno.init_params(0)
+    dgx.dg_nn_set_params(s.h, dgx.nn_pack(params))
+    f = tiny_sources(dgx, s, [(0, 0), (0, 1), (1, 1)])
+    sm = dgx.PoissonSolver(spec.lo, spec.hi, spec.n, spec.p, precision=dgx.DG_PREC_MIXED,
+                           bc_route=dgx.DG_BC_GAUSSSUM)
+    v, _ = sm.solve(f)
+    sm.close()
+    losses = [dgx.dg_nn_train_step(s.h, f, v, 2e-3)[0] for _ in range(60)]
+    assert all(np.isfinite(losses))
+    assert np.mean(losses[-5:]) < losses[0]
+    # the guesses: coarse alone and network, both better than x = 0 (rel < 1)
+    x0c, rc = dgx.dg_nn_guess(s.h, f, use_net=False)
+    x0n, rn = dgx.dg_nn_guess(s.h, f, use_net=True)
+    assert np.all(rc < 1.0) and np.all(rn <= 1.0)
+    s.close()
+
+
+def test_learned_solver_matches_plain(dgx):
+    spec = inputs.tiny_system().mesh
+    kw = dict(bc_route=dgx.DG_BC_GAUSSSUM, rtol=1e-10)
+    sm = dgx.PoissonSolver(spec.lo, spec.hi, spec.n, spec.p, precision=dgx.DG_PREC_MIXED, **kw)
+    sl = dgx.PoissonSolver(spec.lo, spec.hi, spec.n, spec.p, precision=dgx.DG_PREC_MIXED_LEARNED, **kw)
+    f = tiny_sources(dgx, sm, [(0, 0), (0, 1), (1, 1)])
+    with pytest.raises(dgx.DGError):  # no parameters yet
+        sl.solve(f)
+    dgx.dg_nn_set_params(sl.h, dgx.nn_pack(nno.init_params(1)))
+    vm, stm = sm.solve(f)
+    vl, stl = sl.solve(f)
+    for a, b in zip(stm, stl):
+        assert a["status"] == 0 and b["status"] == 0
+        assert b["rel_residual"] <= 1e-10
+        assert 0.0 <= b["guess_rel_residual"] <= 1.0
+        assert a["guess_rel_residual"] == 1.0
+    err = (vl - vm).abs().max().item() / vm.abs().max().item()
+    assert err < 1e-7
+    # a network whose output overflows: every guess rejected, plain result
+    broken = nno.init_params(1)
+    broken["W3"] = np.full_like(broken["W3"], 1e38)
+    dgx.dg_nn_set_params(sl.h, dgx.nn_pack(broken))
+    vb, stb = sl.solve(f)
+    assert all(st["used_fallback"] == 1 and st["status"] == 0 for st in stb)
+    assert all(st["guess_rel_residual"] == 1.0 for st in stb)
+    assert (vb - vm).abs().max().item() / vm.abs().max().item() < 1e-7
+    sm.close()
+    sl.close()
+
+
+def test_weights_file_roundtrip(dgx, tmp_path):
+    spec = inputs.tiny_system().mesh
+    flat = dgx.nn_pack(nno.init_params(2))
+    path = tmp_path / "w.bin"
+    dgx.save_nn_weights(str(path), flat, spec.p)
+    s = dgx.PoissonSolver(spec.lo, spec.hi, spec.n, spec.p, precision=dgx.DG_PREC_MIXED_LEARNED,
+                          nn_weights_path=str(path))
+    assert np.array_equal(dgx.dg_nn_get_params(s.h), flat)
+    s.close()
+    with pytest.raises(dgx.DGError):  # weights of another degree
+        dgx.PoissonSolver(spec.lo, spec.hi, spec.n, spec.p + 1, precision=dgx.DG_PREC_MIXED_LEARNED,
+                          nn_weights_path=str(path))
