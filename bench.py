@@ -58,10 +58,9 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2510_21213_gb300 import dist as pd
+
+    return pd.env()
 
 
 class ClockSampler:
@@ -128,9 +127,11 @@ def system_for(workload, rank):
 
     if workload == "tiny":
         return inputs.tiny_system()
+    from paper_2510_21213_gb300 import dist as pd
+
     if workload == "chain10":
-        return inputs.chain_system(seed=2 + 1000 * rank)
-    return inputs.random_system(seed=3 + 1000 * rank)
+        return inputs.chain_system(seed=pd.rank_seed(2, rank))
+    return inputs.random_system(seed=pd.rank_seed(3, rank))
 
 
 def flush_l2(buf):
@@ -259,10 +260,13 @@ def run_batched(args):
 
     from paper_2510_21213_gb300 import build, dgx, inputs
 
+    from paper_2510_21213_gb300 import dist as pd
+
     build.build()
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    specs = [inputs.batched_system(4000 + k + 1000 * rank) for k in range(32)]
+    pd.init("nccl")
+    specs = [inputs.batched_system(sd) for sd in pd.rank_seeds(4000, 32, rank)]
     prec = dgx.DG_PREC_MIXED if args.precision == "mixed" else dgx.DG_PREC_FP64
     systems, host = [], []
     total_pairs = 0
@@ -277,7 +281,7 @@ def run_batched(args):
     flush = torch.empty(int(256 * 2 ** 20 / 4), dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         dgx.dg_exchange_build_multi(systems, opts=opts, lanes=4)
-    torch.cuda.synchronize()
+    pd.barrier()
     clk = ClockSampler(local)
     clk.start()
     l0 = dgx.dg_kernel_launch_count()
@@ -291,15 +295,21 @@ def run_batched(args):
         times.append(time.perf_counter() - t0)
     launches = (dgx.dg_kernel_launch_count() - l0) // args.steps
     clocks = clk.stop()
-    tot = sum(times)
-    value = total_pairs * args.steps / tot
+    pd.barrier()
+    tot = pd.max_over_ranks(sum(times), device="cuda")
+    value = pd.aggregate_rate(total_pairs, args.steps, tot, ws)
     iters = [x["iters"] for st in sts for x in st[1:]]
+    if rank != 0:
+        dgx.dg_release_cached_handles()
+        pd.finish()
+        return
     line = {
         "metric": "exchange-build pair Poisson solves/s at 1e-8 residual", "value": value, "unit": "pair_solves/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"batched32: 32 systems, seeds 4000-4031, {total_pairs} pair solves + 32 Hartree",
+        "config": {"workload": f"batched32: 32 systems per GPU, seeds 4000-4031 (+1000 per rank), "
+                               f"{total_pairs} pair solves + 32 Hartree on rank 0",
                    "sizes": [[sp.mesh.n[0], sp.mesh.p, sp.N] for sp in specs], "lanes": 4,
                    "timing": "host wall clock around each multi-system call (several streams)"},
         "gpu_launches": int(launches), "clocks": clocks,
@@ -308,18 +318,17 @@ def run_batched(args):
     }
     print(json.dumps(line), flush=True)
     dgx.dg_release_cached_handles()
+    pd.finish()
 
 
 def run_ours(args):
     import torch
 
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
+    from paper_2510_21213_gb300 import dist as pd
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    pd.init("nccl")
     from paper_2510_21213_gb300 import build, dgx
 
     build.build()
@@ -339,9 +348,7 @@ def run_ours(args):
     flush = torch.empty(int(256 * 2 ** 20 / 4), dtype=torch.float32, device="cuda")  # 256 MB > L2 (126 MB)
 
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+        pd.barrier()
 
     # timed region (device-resident inputs)
     for _ in range(args.warmup):
@@ -363,12 +370,8 @@ def run_ours(args):
     launches = (dgx.dg_kernel_launch_count() - l0) // args.steps
     clocks = clk.stop()
     barrier()
-    tot = sum(times) / 1e3
-    if ws > 1:
-        t = torch.tensor([tot], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = float(t.item())
-    value = ws * P * args.steps / tot
+    tot = pd.max_over_ranks(sum(times) / 1e3, device="cuda")
+    value = pd.aggregate_rate(P, args.steps, tot, ws)
     iters = [s["iters"] for s in stats[1:]]
     resid = max(s["rel_residual"] for s in stats)
     status_ok = all(s["status"] == 0 for s in stats)
@@ -388,24 +391,16 @@ def run_ours(args):
         t1.record()
         t1.synchronize()
         e2e_times.append(t0.elapsed_time(t1))
-    e2e_tot = sum(e2e_times) / 1e3
-    if ws > 1:
-        t = torch.tensor([e2e_tot], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = ws * P * args.steps / e2e_tot
+    e2e_tot = pd.max_over_ranks(sum(e2e_times) / 1e3, device="cuda")
+    e2e_value = pd.aggregate_rate(P, args.steps, e2e_tot, ws)
 
     # plain FP64 form on the same system (the metric's comparison)
     plain = None
     if not args.no_plain and prec != dgx.DG_PREC_FP64:
         solver64 = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=dgx.DG_PREC_FP64, rtol=1e-8)
         ptimes, (K64, eh64, ex64, st64) = time_builds(solver64, psi_dev, max(1, min(args.steps, 3)), 1, torch, flush)
-        ptot = sum(ptimes) / 1e3
-        if ws > 1:
-            t = torch.tensor([ptot], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ptot = float(t.item())
-        plain = {"value": ws * P * len(ptimes) / ptot, "ms_per_step": ptot / len(ptimes) * 1e3,
+        ptot = pd.max_over_ranks(sum(ptimes) / 1e3, device="cuda")
+        plain = {"value": pd.aggregate_rate(P, len(ptimes), ptot, ws), "ms_per_step": ptot / len(ptimes) * 1e3,
                  "mean_iters": float(np.mean([s["iters"] for s in st64[1:]])),
                  "K_rel_diff_vs_chosen": float(np.abs(K64 - K).max() / np.abs(K64).max()),
                  "E_X_rel_diff_vs_chosen": abs(ex64 - ex) / abs(ex64)}
@@ -417,12 +412,8 @@ def run_ours(args):
         solver_l = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=dgx.DG_PREC_MIXED_LEARNED, rtol=1e-8,
                                      nn_weights_path=weights)
         ltimes, (Kl, ehl, exl, stl) = time_builds(solver_l, psi_dev, max(1, min(args.steps, 3)), 1, torch, flush)
-        ltot = sum(ltimes) / 1e3
-        if ws > 1:
-            t = torch.tensor([ltot], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ltot = float(t.item())
-        learned = {"value": ws * P * len(ltimes) / ltot, "ms_per_step": ltot / len(ltimes) * 1e3,
+        ltot = pd.max_over_ranks(sum(ltimes) / 1e3, device="cuda")
+        learned = {"value": pd.aggregate_rate(P, len(ltimes), ltot, ws), "ms_per_step": ltot / len(ltimes) * 1e3,
                    "mean_iters": float(np.mean([s["iters"] for s in stl[1:]])),
                    "fallbacks": int(sum(s["used_fallback"] for s in stl)),
                    "mean_guess_rel_residual": float(np.mean([s["guess_rel_residual"] for s in stl[1:]])),
@@ -488,8 +479,7 @@ def run_ours(args):
             with open(args.json_out, "w") as fh:
                 fh.write(s + "\n")
     solver.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
+    pd.finish()
 
 
 def main():

@@ -107,7 +107,7 @@ typedef struct {
   double bc_tol;         /* relative accuracy of the Gaussian-sum 1/r (0 = precision default) */
   int32_t batch;         /* sources solved together (0 = library default) */
   int32_t smoother;      /* DG_SMOOTH_*: preconditioner inside the Chebyshev smoother */
-  int32_t smoother_degree; /* Chebyshev degree of the multigrid smoother (default 3) */
+  int32_t smoother_degree; /* Chebyshev degree of the multigrid smoother (default 4) */
   double cheb_range;     /* smoothing range lambda_max / lambda_min of the Chebyshev interval (default 10) */
   double inner_rtol;     /* MIXED: relative reduction of each FP32 inner solve (default 1e-4) */
   const char* nn_weights_path; /* MIXED_LEARNED: network weights file (NULL: set by dg_nn_set_params) */
@@ -144,7 +144,7 @@ typedef struct dg_ctx* dg_handle;
 
 /* Fills *opts with defaults: FP64, rtol 1e-8, max_iter 500, eps 1/8,
  * penalty_form 0, Gaussian-sum boundary data, Schwarz smoother, Chebyshev
- * degree 3 over a smoothing range of 10. */
+ * degree 4 over a smoothing range of 10, inner_rtol 1e-4, coarse_penalty 0. */
 void dg_default_opts(dg_solver_opts* opts);
 
 /* Builds the level hierarchy, 1-D operator tables, Chebyshev bounds, the

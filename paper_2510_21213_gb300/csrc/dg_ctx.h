@@ -128,6 +128,7 @@ struct dg_ctx {
   cudaStream_t ws = nullptr;  // the handle's own stream (graph capture needs a non-default stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   dg::NNState nn;             // learned initial guess (DG_PREC_MIXED_LEARNED)
+  dg::DevBuf dlift_op;        // fine-level LevelOp whose lift tables carry (sigma_c - sigma) (coarse guess)
   ~dg_ctx() {
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -159,8 +160,11 @@ int check_finite(dg_ctx* h, const double* f, int nsrc, std::vector<int>& finite,
 // learned initial guess (dg_learned.cu): for the sources in act, sets x64 and
 // r64 = b64 - A x64 (b64 formed), rel[k] = ||r64|| / ||b64||, fb[k] = 1 where
 // the guess was rejected (x64 = 0, r64 = b64)
-int learned_guess(dg_ctx* h, const std::vector<int>& act, const std::vector<double>& bnorm2, bool use_net,
+// nsrc: sources 0..nsrc-1 of the current chunk (b64 and the boundary data formed)
+int learned_guess(dg_ctx* h, int nsrc, const std::vector<int>& act, const std::vector<double>& bnorm2, bool use_net,
                   std::vector<double>& rel, std::vector<int>& fb, cudaStream_t s);
+// boundary data of the chunk are held in FP32 (g32) rather than FP64 (g)
+bool bc_fp32(const dg_ctx* h);
 int nn_load_file(dg_ctx* h, const char* path);
 
 // scalar slots of h->scal, each [cap] doubles

@@ -330,7 +330,7 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
     std::vector<int> nz;
     for (int k : act)
       if (bnorm2[k] > 0) nz.push_back(k);
-    DG_RET(learned_guess(h, nz, bnorm2, true, rel, fbk, s));
+    DG_RET(learned_guess(h, nsrc, nz, bnorm2, true, rel, fbk, s));
   }
   std::vector<double> grel = rel;
   std::vector<int> todo;
@@ -520,7 +520,7 @@ static int boundary_data(dg_ctx* h, int route, const double* f, int nsrc, double
 
 // b64 = 4 pi W f + Nitsche lift of g(f) for f[0..nsrc). The mixed modes
 // evaluate the Gaussian-sum route in FP32 with their own (1e-7) table.
-static bool bc_fp32(const dg_ctx* h) {
+bool bc_fp32(const dg_ctx* h) {
   return h->opts.precision != DG_PREC_FP64 && h->opts.bc_route == DG_BC_GAUSSSUM;
 }
 
@@ -859,7 +859,7 @@ void dg_default_opts(dg_solver_opts* o) {
   o->bc_tol = 0.0;
   o->batch = 0;
   o->smoother = DG_SMOOTH_SCHWARZ;
-  o->smoother_degree = 3;
+  o->smoother_degree = 4;
   o->cheb_range = 10.0;
   o->inner_rtol = 1e-4;
   o->nn_weights_path = nullptr;

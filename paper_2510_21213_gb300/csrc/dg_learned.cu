@@ -241,17 +241,44 @@ static int nn_ensure_io(dg_ctx* h, long long ne, bool io, bool save) {
 }
 
 // x_c (FP32, w32.x) of the active sources: two V-cycles on the first degree-1
-// level, applied to the restricted right-hand side (w32.r = (float) b64), then
-// prolongated level by level to the fine level. Uses w32.p and w32.q as
-// temporaries.
-static int coarse_guess(dg_ctx* h, const int* dact, int nact, cudaStream_t s) {
+// level l1, applied to the restricted right-hand side, then prolongated level
+// by level to the fine level. The restricted right-hand side carries the
+// boundary data with the penalty of level l1 (the Nitsche lift in b has the
+// fine penalty, 16x that of degree 1 when p = 7; restricted as it is, it would
+// impose about 16 g on the coarse boundary): b_c = b + lift_{sigma_l1 - sigma}(g),
+// formed in r64 (sources 0..nsrc-1). Sets w32.r = (float) b; uses w32.z, w32.p
+// and w32.q as temporaries.
+static int coarse_guess(dg_ctx* h, int nsrc, const int* dact, int nact, cudaStream_t s) {
   PrecWork<float>& w = h->w32;
   int l1 = 0;
   while (l1 < h->nlev - 1 && h->levels[l1].op.p > 1) ++l1;
   const long long Nq = h->Nq;
   DG_CK((launch_convert<float, double>(w.r.as<float>(), h->b64.as<double>(), Nq, dact, nact, 1.0, 0, s)));
+  const float* src0 = w.r.as<float>();
+  if (l1 > 0) {
+    if (!h->dlift_op.p) {
+      LevelOp D = h->levels[0].op;
+      for (int d = 0; d < 3; ++d) {
+        const double ds = h->levels[l1].op.ax[d].sigma - D.ax[d].sigma;
+        for (int a = 0; a < D.n1; ++a) {
+          D.ax[d].lift[0][a] = ds * D.tl[a];
+          D.ax[d].lift[1][a] = ds * D.tr[a];
+        }
+      }
+      DG_CK(h->dlift_op.ensure(sizeof(LevelOp)));
+      DG_CK(cudaMemcpy(h->dlift_op.p, &D, sizeof(LevelOp), cudaMemcpyHostToDevice));
+    }
+    double* bc = h->r64.as<double>();
+    DG_CK((launch_convert<double, double>(bc, h->b64.as<double>(), Nq, dact, nact, 1.0, 0, s)));
+    if (bc_fp32(h))
+      DG_CK(launch_lift<float>(h->levels[0].op, h->dlift_op.as<LevelOp>(), h->g32.as<float>(), bc, nsrc, h->nface, s));
+    else
+      DG_CK(launch_lift<double>(h->levels[0].op, h->dlift_op.as<LevelOp>(), h->g.as<double>(), bc, nsrc, h->nface, s));
+    DG_CK((launch_convert<float, double>(w.z.as<float>(), bc, Nq, dact, nact, 1.0, 0, s)));
+    src0 = w.z.as<float>();
+  }
   for (int l = 0; l < l1; ++l) {
-    const float* src = l == 0 ? w.r.as<float>() : w.lev[l].b.as<float>();
+    const float* src = l == 0 ? src0 : w.lev[l].b.as<float>();
     DG_CK(launch_restrict<float>(h->levels[l].tr, h->levels[l].dtr, h->levels[l].op, h->levels[l + 1].op, src,
                                  w.lev[l + 1].b.as<float>(), dact, nact, s));
   }
@@ -310,12 +337,13 @@ static int smooth_guess(dg_ctx* h, float* x, const int* dact, int nact, cudaStre
 // correction y (if use_net), then (if smooth) the fine-level Chebyshev
 // smoother; the guess in w32.q, w32.z and w32.p are scratch. With save, all
 // sources form one network batch and the activations are kept.
-static int guess_fp32(dg_ctx* h, const int* dact, int nact, bool use_net, bool save, bool smooth, cudaStream_t s) {
+static int guess_fp32(dg_ctx* h, int nsrc, const int* dact, int nact, bool use_net, bool save, bool smooth,
+                      cudaStream_t s) {
   PrecWork<float>& w = h->w32;
   const long long Nq = h->Nq;
   const LevelOp& F = h->levels[0].op;
   double* part = h->part.as<double>();
-  DG_RET(coarse_guess(h, dact, nact, s));
+  DG_RET(coarse_guess(h, nsrc, dact, nact, s));
   DG_CK(launch_apply<float>(F, h->levels[0].dop, 0, w.x.as<float>(), w.z.as<float>(), nullptr, dact, nact, s));
   DG_CK(launch_dot<float>(w.x.as<float>(), w.r.as<float>(), nullptr, scal(h, S_G1), part, Nq, dact, nact, s));
   DG_CK(launch_dot<float>(w.x.as<float>(), w.z.as<float>(), nullptr, scal(h, S_G2), part, Nq, dact, nact, s));
@@ -344,7 +372,7 @@ static int guess_fp32(dg_ctx* h, const int* dact, int nact, bool use_net, bool s
   return DG_OK;
 }
 
-int learned_guess(dg_ctx* h, const std::vector<int>& act, const std::vector<double>& bnorm2, bool use_net,
+int learned_guess(dg_ctx* h, int nsrc, const std::vector<int>& act, const std::vector<double>& bnorm2, bool use_net,
                   std::vector<double>& rel, std::vector<int>& fb, cudaStream_t s) {
   if (act.empty()) return DG_OK;
   if (use_net) DG_RET(nn_require(h));
@@ -356,7 +384,7 @@ int learned_guess(dg_ctx* h, const std::vector<int>& act, const std::vector<doub
   double* r64 = h->r64.as<double>();
   const double* b64 = h->b64.as<double>();
   double* part = h->part.as<double>();
-  DG_RET(guess_fp32(h, dact, nact, use_net, false, true, s));
+  DG_RET(guess_fp32(h, nsrc, dact, nact, use_net, false, true, s));
   DG_CK((launch_convert<double, float>(x64, h->w32.q.as<float>(), Nq, dact, nact, 1.0, 0, s)));
   // energy-optimal scaling alpha = b^T x0 / x0^T A x0, residual r = b - alpha A x0 (FP64)
   DG_CK(launch_apply<double>(h->levels[0].op, h->levels[0].dop, 0, x64, r64, nullptr, dact, nact, s));
@@ -491,7 +519,7 @@ int dg_nn_train_step(dg_handle h, const double* f_dev, const double* v_dev, int6
   PrecWork<float>& w = h->w32;
   const long long ne = (long long)nb * F.E;
   // network guess before smoothing (activations kept): y (w.q), x_c (w.x)
-  DG_RET(guess_fp32(h, dact, nb, true, true, false, s));
+  DG_RET(guess_fp32(h, nb, dact, nb, true, true, false, s));
   h->nn.save_ne = -1;  // the buffers now hold this step's activations, not a dg_nn_forward call's
   DG_CK(launch_dot<double>(v_dev, v_dev, h->d_W.as<double>(), scal(h, S_G2), part, Nq, dact, nb, s));
   count_launch();
@@ -555,7 +583,7 @@ int dg_nn_guess(dg_handle h, const double* f_dev, int64_t B, int32_t use_net, do
   std::vector<int> fb(h->cap, 0);
   DG_CK(cudaMemcpyAsync(bn.data(), scal(h, S_BN), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
   DG_CK(cudaStreamSynchronize(s));
-  DG_RET(learned_guess(h, all, bn, use_net != 0, rel, fb, s));
+  DG_RET(learned_guess(h, nb, all, bn, use_net != 0, rel, fb, s));
   DG_CK(cudaMemcpyAsync(x0_dev, h->x64.p, sizeof(double) * Nq * nb, cudaMemcpyDeviceToDevice, s));
   DG_CK(cudaStreamSynchronize(s));
   DG_CK(cudaEventRecord(h->ev_out, s));

@@ -194,9 +194,11 @@ def orbitals_torch(spec, coords, weights=None):
     if spec.orthonormalise:
         if weights is None:
             raise ValueError("orthonormalisation needs the quadrature weights")
-        S = (psi * weights[None, :]) @ psi.T
-        lam, U = torch.linalg.eigh(S)
+        # the N x N overlap is decomposed on the host (no device linear-algebra library needed)
+        S = ((psi * weights[None, :]) @ psi.T).cpu().numpy()
+        lam, U = np.linalg.eigh(S)
         if lam.min() <= 0:
             raise RuntimeError("orbital overlap is not positive definite")
-        psi = (U @ torch.diag(lam ** -0.5) @ U.T) @ psi
+        T = torch.tensor((U * lam ** -0.5) @ U.T, dtype=torch.float64, device=dev)
+        psi = T @ psi
     return psi

@@ -43,4 +43,4 @@ def test_binding_loads_and_error_strings():
     assert lib.dg_error_string(0) == b"ok"
     assert lib.dg_error_string(-3) == b"not converged"
     o = dgx.dg_default_opts()
-    assert o.rtol == pytest.approx(1e-8) and o.penalty_eps == pytest.approx(0.125) and o.smoother_degree == 3 and o.smoother == 1
+    assert o.rtol == pytest.approx(1e-8) and o.penalty_eps == pytest.approx(0.125) and o.smoother_degree == 4 and o.smoother == 1
