@@ -21,33 +21,34 @@ static_assert(DG_NN_NPARAM == NN_NPARAM, "parameter count");
 // kernels
 // ---------------------------------------------------------------------------
 // out[src] = max_q |u[src][q]| (divided by the nodal mass if by_mass); out
-// must be zero on entry. Non-negative doubles order like their bit patterns,
-// so the integer atomic max is exact and order-independent.
+// must be zero on entry. Grid (x: node blocks, y: active source); each block
+// reduces its nodes (warp shuffles, then shared memory) and issues one atomic
+// max. Non-negative doubles order like their bit patterns, so the integer
+// atomic max is exact and order-independent.
 __global__ void k_maxabs(const float* __restrict__ u, const LevelOp* __restrict__ op, int by_mass,
-                         const int* __restrict__ act, int nact, long long Nq, double* __restrict__ out) {
+                         const int* __restrict__ act, long long Nq, double* __restrict__ out) {
+  __shared__ double red[32];
   const int n1 = op->n1, npe = n1 * n1 * n1;
-  const long long total = (long long)nact * Nq;
+  const int src = act[blockIdx.y];
+  const float* us = u + (long long)src * Nq;
   double best = 0.0;
-  int cur = -1;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int kk = (int)(i / Nq);
-    if (kk != cur) {
-      if (cur >= 0 && best > 0.0)
-        atomicMax((unsigned long long*)&out[act[cur]], (unsigned long long)__double_as_longlong(best));
-      cur = kk;
-      best = 0.0;
-    }
-    const long long q = i - (long long)kk * Nq;
-    double v = fabs((double)u[(long long)act[kk] * Nq + q]);
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Nq; q += (long long)gridDim.x * blockDim.x) {
+    double v = fabs((double)us[q]);
     if (by_mass) {
       const int loc = (int)(q % npe);
       v /= op->ax[0].m[loc % n1] * op->ax[1].m[(loc / n1) % n1] * op->ax[2].m[loc / (n1 * n1)];
     }
-    if (v > best) best = v;  // NaN never enters: the fallback test catches it later
+    best = fmax(best, v);  // a NaN is dropped here; the fallback test catches it later
   }
-  if (cur >= 0 && best > 0.0)
-    atomicMax((unsigned long long*)&out[act[cur]], (unsigned long long)__double_as_longlong(best));
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    best = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (threadIdx.x == 0 && best > 0.0)
+      atomicMax((unsigned long long*)&out[src], (unsigned long long)__double_as_longlong(best));
+  }
 }
 
 // network input of nc sources act[0..nc): c0 = (b / m) / sb (right-hand side
@@ -356,8 +357,9 @@ static int guess_fp32(dg_ctx* h, int nsrc, const int* dact, int nact, bool use_n
     DG_CK(cudaMemsetAsync(scal(h, S_G1), 0, sizeof(double) * h->cap, s));
     DG_CK(cudaMemsetAsync(scal(h, S_G3), 0, sizeof(double) * h->cap, s));
     count_launch(2);
-    k_maxabs<<<flat_grid(nact * Nq), 256, 0, s>>>(w.r.as<float>(), h->levels[0].dop, 1, dact, nact, Nq, scal(h, S_G1));
-    k_maxabs<<<flat_grid(nact * Nq), 256, 0, s>>>(w.x.as<float>(), h->levels[0].dop, 0, dact, nact, Nq, scal(h, S_G3));
+    const dim3 mgrid((unsigned)std::max(1LL, std::min((Nq + 255) / 256, 152LL * 8 / nact + 1)), (unsigned)nact);
+    k_maxabs<<<mgrid, 256, 0, s>>>(w.r.as<float>(), h->levels[0].dop, 1, dact, Nq, scal(h, S_G1));
+    k_maxabs<<<mgrid, 256, 0, s>>>(w.x.as<float>(), h->levels[0].dop, 0, dact, Nq, scal(h, S_G3));
     DG_CK(cudaGetLastError());
     // network batches of at most ~512 MB of input + output (one batch when saving)
     const int chunk =

@@ -73,37 +73,54 @@ __device__ __forceinline__ int tap_offset(int t) {
 // ---------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------
+// Shared-memory activations: row p (padded node) holds 32 BF16 channels as four
+// 16-byte chunks; chunk c of row p is stored at position c ^ ((p >> 1) & 3), so
+// the eight consecutive rows an ldmatrix phase reads fall into distinct banks.
+__device__ __forceinline__ int swz(int p, int ch) {
+  return p * NN_H + ((((ch >> 3) ^ ((p >> 1) & 3)) << 3) | (ch & 7));
+}
+
+constexpr int NN_FWD_THREADS = 512;
+constexpr int NN_W2LD = 40;  // padded row of the staged W2 (bank-conflict-free B fragment loads)
+
 template <int N1>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(NN_FWD_THREADS, 1)
     k_nn_forward(const float* __restrict__ prm, const __nv_bfloat16* __restrict__ W2t, const float* __restrict__ in,
                  float* __restrict__ out, __nv_bfloat16* __restrict__ a1_out, __nv_bfloat16* __restrict__ a2_out,
                  long long ne) {
   using C = NNCfg<N1>;
   constexpr int P3 = C::P3, NPE = C::NPE, MT = C::MT;
+  constexpr int NT = NN_FWD_THREADS, NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  // the BF16 activations come first: ldmatrix rows must be 16-byte aligned
-  __nv_bfloat16* sA1 = (__nv_bfloat16*)smem;                           // [P3][32]
-  __nv_bfloat16* sA2 = sA1 + P3 * NN_H;                                 // [P3][32]
-  float* sIn = (float*)(sA2 + P3 * NN_H);                              // [P3][2]
+  __nv_bfloat16* sA1 = (__nv_bfloat16*)smem;                           // [P3][32] swizzled
+  __nv_bfloat16* sA2 = sA1 + P3 * NN_H;                                 // [P3][32] swizzled
+  __nv_bfloat16* sW2 = sA2 + P3 * NN_H;                                 // [27][32 co][NN_W2LD] (ci)
+  float* sIn = (float*)(sW2 + 27 * 32 * NN_W2LD);                      // [P3][2]
   float* sW1 = sIn + 2 * P3;                                           // [27][2][32] + b1
   float* sW3 = sW1 + 1728 + 32;                                        // [27][32][2] + b3
   float* sb2 = sW3 + 1728 + 2;                                         // [32]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < 2 * P3; i += 256) sIn[i] = 0.f;
-  for (int i = tid; i < 2 * P3 * NN_H; i += 256) sA1[i] = __float2bfloat16(0.f);
-  for (int i = tid; i < 1760; i += 256) sW1[i] = prm[NN_OW1 + i];
-  for (int i = tid; i < 1730; i += 256) sW3[i] = prm[NN_OW3 + i];
-  for (int i = tid; i < 32; i += 256) sb2[i] = prm[NN_OB2 + i];
+  for (int i = tid; i < 2 * P3; i += NT) sIn[i] = 0.f;
+  for (int i = tid; i < P3 * NN_H; i += NT) ((unsigned*)sA1)[i] = 0u;  // sA1 and sA2
+  for (int i = tid; i < 27 * 32 * 16; i += NT) {
+    const int row = i >> 4, c2 = i & 15;
+    ((unsigned*)(sW2 + row * NN_W2LD))[c2] = ((const unsigned*)(W2t + row * 32))[c2];
+  }
+  for (int i = tid; i < 1760; i += NT) sW1[i] = prm[NN_OW1 + i];
+  for (int i = tid; i < 1730; i += NT) sW3[i] = prm[NN_OW3 + i];
+  for (int i = tid; i < 32; i += NT) sb2[i] = prm[NN_OB2 + i];
   __syncthreads();
+  const int g = lane >> 2, c4 = lane & 3;
   for (long long e = blockIdx.x; e < ne; e += gridDim.x) {
-    for (int i = tid; i < NPE; i += 256) {
+    for (int i = tid; i < NPE; i += NT) {
       const int p = pad_index<N1>(i);
-      sIn[2 * p] = in[(e * NPE + i) * 2];
-      sIn[2 * p + 1] = in[(e * NPE + i) * 2 + 1];
+      const float2 v = ((const float2*)in)[e * NPE + i];
+      sIn[2 * p] = v.x;
+      sIn[2 * p + 1] = v.y;
     }
     __syncthreads();
-    // layer 1 (2 -> 32), SIMT: thread = (node, group of 8 output channels)
-    for (int w = tid; w < NPE * 4; w += 256) {
+    // layer 1 (2 -> 32), SIMT: thread = (node, group of 8 output channels = one chunk)
+    for (int w = tid; w < NPE * 4; w += NT) {
       const int n = w >> 2, cg = (w & 3) * 8;
       const int p = pad_index<N1>(n);
       float acc[8];
@@ -117,14 +134,20 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] += i0 * wt[c] + i1 * wt[32 + c];
       }
-      __nv_bfloat162* dst = (__nv_bfloat162*)(sA1 + p * NN_H + cg);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) dst[c] = __floats2bfloat162_rn(fmaxf(acc[2 * c], 0.f), fmaxf(acc[2 * c + 1], 0.f));
+      uint4 pk;
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(acc[0], 0.f), fmaxf(acc[1], 0.f));
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(acc[2], 0.f), fmaxf(acc[3], 0.f));
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(acc[4], 0.f), fmaxf(acc[5], 0.f));
+      __nv_bfloat162 h3 = __floats2bfloat162_rn(fmaxf(acc[6], 0.f), fmaxf(acc[7], 0.f));
+      pk.x = *(unsigned*)&h0;
+      pk.y = *(unsigned*)&h1;
+      pk.z = *(unsigned*)&h2;
+      pk.w = *(unsigned*)&h3;
+      *(uint4*)(sA1 + swz(p, cg)) = pk;
     }
     __syncthreads();
-    // layer 2 (32 -> 32) on the tensor cores: warp owns node tiles warp, warp+8, ...
-    for (int mt0 = warp; mt0 < MT; mt0 += 8 * 2) {
-      // two node tiles per pass (mt0, mt0 + 8)
+    // layer 2 (32 -> 32) on the tensor cores: warp owns node tiles warp, warp + NW, ...
+    for (int mt0 = warp; mt0 < MT; mt0 += 2 * NW) {
       float acc[2][4][4];
 #pragma unroll
       for (int a = 0; a < 2; ++a)
@@ -136,24 +159,22 @@ __global__ void __launch_bounds__(256, 1)
       bool tile_ok[2];
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        const int mt = mt0 + 8 * a;
+        const int mt = mt0 + NW * a;
         tile_ok[a] = mt < MT;
-        const int j = lane >> 3, r = lane & 7;
-        const int node = mt * 16 + r + 8 * (j & 1);
+        const int node = mt * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
         rowp[a] = (tile_ok[a] && node < NPE) ? pad_index<N1>(node) : 0;  // padded row 0 is all zero
       }
-      const int kh_sel = (lane >> 4) * 8;  // ldmatrix k-half of this lane's row address
+      const int khalf = lane >> 4;  // which 8 channels of the 16-channel k step this lane's row address serves
 #pragma unroll 1
       for (int t = 0; t < 27; ++t) {
         const int off = tap_offset<N1>(t);
 #pragma unroll
         for (int kh = 0; kh < 2; ++kh) {
-          // B fragments (k = ci, n = co) from W2t[t][co][ci]
+          // B fragments (k = ci, n = co) from the staged W2[t][co][ci]
           unsigned b[4][2];
-          const int g = lane >> 2, c4 = lane & 3;
 #pragma unroll
           for (int nt = 0; nt < 4; ++nt) {
-            const __nv_bfloat16* wp = W2t + ((long long)t * 32 + nt * 8 + g) * 32 + kh * 16 + 2 * c4;
+            const __nv_bfloat16* wp = sW2 + (t * 32 + nt * 8 + g) * NN_W2LD + kh * 16 + 2 * c4;
             b[nt][0] = *(const unsigned*)wp;
             b[nt][1] = *(const unsigned*)(wp + 8);
           }
@@ -162,18 +183,17 @@ __global__ void __launch_bounds__(256, 1)
             if (!tile_ok[a]) continue;
             const int qq = rowp[a] == 0 ? 0 : rowp[a] + off;  // rows past the element read the zero corner
             unsigned a0, a1, a2, a3;
-            ldsm_x4(smem_u32(sA1 + qq * NN_H + kh * 16 + kh_sel), a0, a1, a2, a3);
+            ldsm_x4(smem_u32(sA1 + swz(qq, kh * 16 + khalf * 8)), a0, a1, a2, a3);
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt) mma16816(acc[a][nt], a0, a1, a2, a3, b[nt][0], b[nt][1]);
           }
         }
       }
-      // epilogue: bias, ReLU, BF16 into sA2 (rows g and g+8, columns 2c, 2c+1)
-      const int g = lane >> 2, c4 = lane & 3;
+      // epilogue: bias, ReLU, BF16 into sA2 (rows g and g+8, columns 2c4, 2c4+1 of each n tile)
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         if (!tile_ok[a]) continue;
-        const int mt = mt0 + 8 * a;
+        const int mt = mt0 + NW * a;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int node = mt * 16 + g + 8 * h;
@@ -184,36 +204,41 @@ __global__ void __launch_bounds__(256, 1)
             const int co = nt * 8 + 2 * c4;
             const float v0 = fmaxf(acc[a][nt][2 * h] + sb2[co], 0.f);
             const float v1 = fmaxf(acc[a][nt][2 * h + 1] + sb2[co + 1], 0.f);
-            *(__nv_bfloat162*)(sA2 + p * NN_H + co) = __floats2bfloat162_rn(v0, v1);
+            *(__nv_bfloat162*)(sA2 + swz(p, co)) = __floats2bfloat162_rn(v0, v1);
           }
         }
       }
     }
     __syncthreads();
     // layer 3 (32 -> 2), SIMT; optional copies of the activations for training
-    for (int n = tid; n < NPE; n += 256) {
+    for (int n = tid; n < NPE; n += NT) {
       const int p = pad_index<N1>(n);
       float o0 = sW3[1728], o1 = sW3[1729];
 #pragma unroll 1
       for (int t = 0; t < 27; ++t) {
-        const __nv_bfloat162* row = (const __nv_bfloat162*)(sA2 + (p + tap_offset<N1>(t)) * NN_H);
+        const int q = p + tap_offset<N1>(t);
         const float* wt = sW3 + t * 64;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float2 v = __bfloat1622float2(row[c]);
-          o0 += v.x * wt[4 * c] + v.y * wt[4 * c + 2];
-          o1 += v.x * wt[4 * c + 1] + v.y * wt[4 * c + 3];
+        for (int c = 0; c < 4; ++c) {
+          const uint4 raw = *(const uint4*)(sA2 + swz(q, 8 * c));
+          const __nv_bfloat162* hv = (const __nv_bfloat162*)&raw;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float2 v = __bfloat1622float2(hv[k]);
+            const int ci = 8 * c + 2 * k;
+            o0 += v.x * wt[2 * ci] + v.y * wt[2 * ci + 2];
+            o1 += v.x * wt[2 * ci + 1] + v.y * wt[2 * ci + 3];
+          }
         }
       }
-      out[(e * NPE + n) * 2] = o0;
-      out[(e * NPE + n) * 2 + 1] = o1;
+      ((float2*)out)[e * NPE + n] = make_float2(o0, o1);
     }
     if (a1_out) {
-      for (int i = tid; i < NPE * 16; i += 256) {
-        const int n = i >> 4, c = i & 15;
+      for (int i = tid; i < NPE * 4; i += NT) {
+        const int n = i >> 2, c = i & 3;
         const int p = pad_index<N1>(n);
-        ((__nv_bfloat162*)(a1_out + (e * NPE + n) * NN_H))[c] = ((const __nv_bfloat162*)(sA1 + p * NN_H))[c];
-        ((__nv_bfloat162*)(a2_out + (e * NPE + n) * NN_H))[c] = ((const __nv_bfloat162*)(sA2 + p * NN_H))[c];
+        ((uint4*)(a1_out + (e * NPE + n) * NN_H))[c] = *(const uint4*)(sA1 + swz(p, 8 * c));
+        ((uint4*)(a2_out + (e * NPE + n) * NN_H))[c] = *(const uint4*)(sA2 + swz(p, 8 * c));
       }
     }
     __syncthreads();
@@ -464,7 +489,8 @@ __global__ void k_nn_adam(float* __restrict__ prm, const float* __restrict__ gra
 
 static size_t fwd_smem(int n1) {
   const int P3 = (n1 + 2) * (n1 + 2) * (n1 + 2);
-  return sizeof(float) * 2 * P3 + 2 * sizeof(__nv_bfloat16) * P3 * NN_H + sizeof(float) * (1760 + 1730 + 32);
+  return 2 * sizeof(__nv_bfloat16) * P3 * NN_H + sizeof(__nv_bfloat16) * 27 * 32 * NN_W2LD + sizeof(float) * 2 * P3 +
+         sizeof(float) * (1760 + 1730 + 32);
 }
 static size_t bwd_smem(int n1) {
   const int P3 = (n1 + 2) * (n1 + 2) * (n1 + 2), NPE = n1 * n1 * n1;
@@ -485,9 +511,9 @@ static int sm_count() {
 
 // resident blocks of a kernel per SM at its dynamic shared memory (at least 1)
 template <typename K>
-static int blocks_per_sm(K kern, size_t smem) {
+static int blocks_per_sm(K kern, size_t smem, int threads = 256) {
   int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, smem) != cudaSuccess || b < 1) b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, threads, smem) != cudaSuccess || b < 1) b = 1;
   return b;
 }
 
@@ -499,13 +525,13 @@ static cudaError_t nn_fwd_n1(const float* prm, const __nv_bfloat16* W2t, const f
   if (!bps) {
     cudaError_t e = cudaFuncSetAttribute(k_nn_forward<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    bps = blocks_per_sm(k_nn_forward<N1>, sm);
+    bps = blocks_per_sm(k_nn_forward<N1>, sm, NN_FWD_THREADS);
   }
   const long long cap = (long long)sm_count() * bps;
   const long long grid = ne < cap ? ne : cap;
   if (grid < 1) return cudaSuccess;
   count_launch();
-  k_nn_forward<N1><<<(unsigned)grid, 256, sm, s>>>(prm, W2t, in, out, a1, a2, ne);
+  k_nn_forward<N1><<<(unsigned)grid, NN_FWD_THREADS, sm, s>>>(prm, W2t, in, out, a1, a2, ne);
   return cudaGetLastError();
 }
 

@@ -71,8 +71,9 @@ def to_dev(a, n1):
 
 
 # degrees 1..7: one, two and several 16-node tiles, ragged tails; 37 elements
-# is not a multiple of any grid
-@pytest.mark.parametrize("p,ne", [(1, 37), (2, 37), (4, 37), (6, 37), (7, 37), (7, 1)])
+# is not a multiple of any grid; 700 elements at p = 4 make every block of the
+# persistent forward and backward grids loop over several elements
+@pytest.mark.parametrize("p,ne", [(1, 37), (2, 37), (4, 37), (6, 37), (7, 37), (7, 1), (4, 700)])
 def test_forward_backward_vs_oracle(dgx, p, ne):
     n1 = p + 1
     s = dgx.PoissonSolver([-1.0] * 3, [1.0] * 3, (1, 1, 1), p)
