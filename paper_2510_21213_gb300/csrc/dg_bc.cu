@@ -51,6 +51,7 @@ template cudaError_t launch_weighted_lex<float>(const LevelOp&, const LevelOp*, 
 // with arbitrary element strides and a two-level batch index.
 // 64 x 64 output tile, K step 16, 256 threads with 4 x 4 outputs each.
 // ---------------------------------------------------------------------------
+// (FP64 instances; FP32 runs on the tensor cores in k_gemm_tc below.)
 // FP32 instances keep a compensated running sum across K tiles: each 16-term
 // tile is accumulated in registers and then added to (sum, carry) with
 // Knuth's TwoSum, so the error does not grow with K (K reaches N_G L ~ 10^4 in
@@ -149,6 +150,142 @@ __global__ void __launch_bounds__(256) k_gemm(GemmArgs g, int batch_base) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 strided batched GEMM on the tensor cores: mma.sync m16n8k8 TF32 with
+// the 3xTF32 split (a = a_hi + a_lo, both TF32; a b ~ a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, error ~ 2^-22 of |a b|) and the same compensated accumulation
+// across 16-term K tiles as k_gemm. 64 x 64 output tile, 4 warps of 32 x 32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+constexpr int TCA = 20;  // padded row of the A tile (conflict-free fragment loads)
+constexpr int TCB = 72;  // padded row of the B tile
+
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base) {
+  __shared__ unsigned sAh[64][TCA], sAl[64][TCA];
+  __shared__ unsigned sBh[16][TCB], sBl[16][TCB];
+  const int bz = batch_base + blockIdx.z;
+  const int b1 = bz / g.nb2, b2 = bz % g.nb2;
+  const float* A = (const float*)g.A + b1 * g.sA1 + b2 * g.sA2;
+  const float* B = (const float*)g.B + b1 * g.sB1 + b2 * g.sB2;
+  float* C = (float*)g.C + b1 * g.sC1 + b2 * g.sC2;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gq = lane >> 2, c4 = lane & 3;
+  const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
+  const bool a_k_fast = g.sAk == 1;
+  const bool b_n_fast = g.sBn == 1;
+  float acc[2][4][4], sum[2][4][4], car[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        acc[i][j][e] = 0.f;
+        sum[i][j][e] = 0.f;
+        car[i][j][e] = 0.f;
+      }
+  for (int k0 = 0; k0 < g.K; k0 += 16) {
+    for (int t = tid; t < 64 * 16; t += 128) {
+      int kk, mm;
+      if (a_k_fast) {
+        kk = t % 16;
+        mm = t / 16;
+      } else {
+        mm = t % 64;
+        kk = t / 64;
+      }
+      const int m = m0 + mm, k = k0 + kk;
+      const float av = (m < g.M && k < g.K) ? A[(long long)m * g.sAm + (long long)k * g.sAk] : 0.f;
+      const unsigned ah = to_tf32(av);
+      sAh[mm][kk] = ah;
+      sAl[mm][kk] = to_tf32(av - __uint_as_float(ah));
+      int nn, kb;
+      if (b_n_fast) {
+        nn = t % 64;
+        kb = t / 64;
+      } else {
+        kb = t % 16;
+        nn = t / 16;
+      }
+      const int n = n0 + nn, kx = k0 + kb;
+      const float bv = (n < g.N && kx < g.K) ? B[(long long)kx * g.sBk + (long long)n * g.sBn] : 0.f;
+      const unsigned bh = to_tf32(bv);
+      sBh[kb][nn] = bh;
+      sBl[kb][nn] = to_tf32(bv - __uint_as_float(bh));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < 16; ks += 8) {
+      unsigned ah[2][4], al[2][4], bh[4][2], bl[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + gq;
+        ah[i][0] = sAh[r][ks + c4];
+        ah[i][1] = sAh[r + 8][ks + c4];
+        ah[i][2] = sAh[r][ks + c4 + 4];
+        ah[i][3] = sAh[r + 8][ks + c4 + 4];
+        al[i][0] = sAl[r][ks + c4];
+        al[i][1] = sAl[r + 8][ks + c4];
+        al[i][2] = sAl[r][ks + c4 + 4];
+        al[i][3] = sAl[r + 8][ks + c4 + 4];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + j * 8 + gq;
+        bh[j][0] = sBh[ks + c4][c];
+        bh[j][1] = sBh[ks + c4 + 4][c];
+        bl[j][0] = sBl[ks + c4][c];
+        bl[j][1] = sBl[ks + c4 + 4][c];
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          mma_tf32(acc[i][j], al[i], bh[j]);
+          mma_tf32(acc[i][j], ah[i], bl[j]);
+          mma_tf32(acc[i][j], ah[i], bh[j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          two_sum_add(sum[i][j][e], car[i][j][e], acc[i][j][e]);
+          acc[i][j][e] = 0.f;
+        }
+    __syncthreads();
+  }
+  const float alpha = (float)g.alpha, beta = (float)g.beta;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int m = m0 + wm + i * 16 + gq + (e >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + 2 * c4 + (e & 1);
+        if (m >= g.M || n >= g.N) continue;
+        const float v = sum[i][j][e] + car[i][j][e];
+        float* cp = C + (long long)m * g.sCm + (long long)n * g.sCn;
+        *cp = g.beta != 0.0 ? alpha * v + beta * (*cp) : alpha * v;
+      }
+}
+
 template <typename T>
 cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 * (long long)g.nb2 <= 0) return cudaSuccess;
@@ -158,7 +295,10 @@ cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
   for (long long base = 0; base < nb; base += 65535) {
     const long long cnt = nb - base < 65535 ? nb - base : 65535;
     count_launch();
-    k_gemm<T><<<dim3(grid.x, grid.y, (unsigned)cnt), 256, 0, s>>>(g, (int)base);
+    if constexpr (sizeof(T) == 4)
+      k_gemm_tc<<<dim3(grid.x, grid.y, (unsigned)cnt), 128, 0, s>>>(g, (int)base);
+    else
+      k_gemm<T><<<dim3(grid.x, grid.y, (unsigned)cnt), 256, 0, s>>>(g, (int)base);
   }
   return cudaGetLastError();
 }

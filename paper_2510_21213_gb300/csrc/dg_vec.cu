@@ -6,6 +6,8 @@
 // Batched fields are [B][Nq]; kernels work on the active right-hand sides
 // listed in act[0..nact), so converged sources cost nothing. All reductions
 // are deterministic: fixed grids, fixed summation order, FP64 accumulation.
+#include <algorithm>
+
 #include "dg_internal.h"
 
 namespace dg {
@@ -178,10 +180,13 @@ template <typename T>
 cudaError_t launch_dot(const T* u, const T* v, const double* w, double* out, double* part, long long Nq,
                        const int* act, int nact, cudaStream_t s) {
   if (nact == 0) return cudaSuccess;
+  // blocks per source from Nq alone (about 4096 nodes each, at most DOT_BLOCKS),
+  // so a source's summation order never depends on how many sources share the launch
+  const int nblk = (int)std::max(1LL, std::min((long long)DOT_BLOCKS, (Nq + 4095) / 4096));
   count_launch();
-  k_dot_partial<T><<<dim3(DOT_BLOCKS, nact), VT, 0, s>>>(u, v, w, part, Nq, act);
+  k_dot_partial<T><<<dim3(nblk, nact), VT, 0, s>>>(u, v, w, part, Nq, act);
   count_launch();
-  k_dot_final<<<nact, 32, 0, s>>>(part, out, DOT_BLOCKS, act);
+  k_dot_final<<<nact, 32, 0, s>>>(part, out, nblk, act);
   return cudaGetLastError();
 }
 

@@ -50,11 +50,13 @@ def test_fullsize_sampled_sources_fp64(setup):
 def test_fullsize_sampled_sources_mixed(setup):
     """Mixed mode at the metric's 1e-8 FP64 residual keeps smooth-mode error
     that a residual stop does not see (stated bound 2e-5, measured ~5e-6 for
-    the Hartree density); at a 1e-10 residual it matches to 1e-7, so the FP32
-    contractions and boundary data are not the limit."""
+    the Hartree density). At a 1e-10 residual the floor is the FP32 boundary
+    data: their contractions run on the tensor cores as 3xTF32 (about 22-bit
+    products), measured 1.4e-7 for the Hartree density (3e-8 with FP32 SIMT
+    contractions); stated bound 3e-7."""
     dgx, spec, m, psi, f, ref = setup
     mm = spec.mesh
-    for rtol, bound in ((1e-8, 2e-5), (1e-10, 1e-7)):
+    for rtol, bound in ((1e-8, 2e-5), (1e-10, 3e-7)):
         s = dgx.PoissonSolver(mm.lo, mm.hi, mm.n, mm.p, rtol=rtol, precision=dgx.DG_PREC_MIXED)
         v, st = s.solve(torch.tensor(f, device="cuda"))
         v = v.cpu().numpy()
