@@ -36,6 +36,21 @@ WORKLOADS = {
     "batched32": "batched32",
 }
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def measured_traffic(key):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json),
+    or None when the kernel source changed after the capture."""
+    import hashlib
+
+    try:
+        rec = json.load(open(TRAFFIC_FILE))[key]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            digest = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None
+    return rec["dram_bytes_per_launch"] if digest == rec["source_sha256"] else None
 # FP64 FMA throughput of a GB300 measured with the probe under
 # paper_2510_21213_gb300/csrc/peak_probe.cu (152 SMs, FP64 pipe)
 FP64_PEAK_TFLOPS = 1.20
@@ -434,7 +449,9 @@ def run_ours(args):
     roofline = {
         "kernel": "k_schwarz_patch (fine-level smoother patch solve) + k_schwarz_gather",
         "bound": "alu", "achieved": sm_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": sm_tf / alu_peak,
-        "traffic": None,
+        "traffic": (measured_traffic("smoother_chain10")
+                    if args.workload == "chain10" and args.precision != "fp64" and B == 56 else None),
+        "algorithmic_bytes": rf["smoother_bytes"],
         "peak_source": ("FP32 FMA probe (paper_2510_21213_gb300/csrc/peak_probe.cu)" if args.precision != "fp64"
                         else "FP64 FMA probe (paper_2510_21213_gb300/csrc/peak_probe.cu)"),
         "launch_ms": rf["smoother_ms"], "B": B, "hbm_gbs": sm_gbs, "hbm_frac_of_measured": sm_gbs / hbm,
