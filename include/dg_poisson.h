@@ -114,6 +114,7 @@ typedef struct {
   int32_t verbose;       /* 0 silent, 1 per-solve summary, 2 also per refinement round (stderr) */
   int32_t coarse_penalty; /* 0: each multigrid level uses the penalty of its own p and h;
                              1: every level uses the fine level's penalty (Galerkin-consistent hierarchy) */
+  int32_t coarse_smoother_degree; /* Chebyshev degree on the levels below the finest (0 = smoother_degree) */
 } dg_solver_opts;
 
 typedef struct {

@@ -19,20 +19,33 @@ namespace dg {
 // streamed from shared memory and reused across the lines). Loads of the
 // element, the neighbour traces and the final store are spread over all
 // threads of the block and coalesced.
+// Tuning constants (compile-time; the defaults were chosen by timing on a GB300)
+#ifndef DG_APPLY_LPT32
+#define DG_APPLY_LPT32 2      // lines per thread, FP32
+#endif
+#ifndef DG_APPLY_THREADS
+#define DG_APPLY_THREADS 256  // threads per block (at least)
+#endif
+#ifndef DG_APPLY_SMEM
+#define DG_APPLY_SMEM 36864   // shared-memory budget of the element slots (bytes)
+#endif
+#ifndef DG_APPLY_MINB32
+#define DG_APPLY_MINB32 3     // resident blocks per SM asked of ptxas, FP32
+#endif
 template <typename T, int N1>
 struct ApplyCfg {
   static constexpr int NPE = N1 * N1 * N1;
   static constexpr int NF = N1 * N1;
-  static constexpr int LPT = sizeof(T) == 4 ? 3 : 1;
+  static constexpr int LPT = sizeof(T) == 4 ? DG_APPLY_LPT32 : 1;
   static constexpr int TPE = (NF + LPT - 1) / LPT;
   static constexpr int PER_ELEM = (2 * NPE + 12 * NF + 3) * (int)sizeof(T);
-  static constexpr int EPB_T = 256 / TPE < 1 ? 1 : 256 / TPE;
-  static constexpr int EPB_S = 36864 / PER_ELEM < 1 ? 1 : 36864 / PER_ELEM;
+  static constexpr int EPB_T = DG_APPLY_THREADS / TPE < 1 ? 1 : DG_APPLY_THREADS / TPE;
+  static constexpr int EPB_S = DG_APPLY_SMEM / PER_ELEM < 1 ? 1 : DG_APPLY_SMEM / PER_ELEM;
   static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;
   // the load and trace phases use every thread of the block; the line passes
   // use the first EPB * TPE
-  static constexpr int THREADS = EPB * TPE < 256 ? 256 : EPB * TPE;
-  static constexpr int MINB = sizeof(T) == 4 ? 3 : 2;  // resident blocks per SM asked of ptxas
+  static constexpr int THREADS = EPB * TPE < DG_APPLY_THREADS ? DG_APPLY_THREADS : EPB * TPE;
+  static constexpr int MINB = sizeof(T) == 4 ? DG_APPLY_MINB32 : 2;  // resident blocks per SM asked of ptxas
 };
 
 // one direction of the operator for LPT lines of one element:

@@ -28,7 +28,9 @@ struct MG {
     // sw: the smoother preconditioner is M_S (z = M_S res), else D^-1 (fused)
     const T* invD = sw ? nullptr : W.invD.as<T>();
     const long long Nq = L.op.Nq;
-    const int k = std::max(1, h->opts.smoother_degree);
+    const int deg = (l > 0 && h->opts.coarse_smoother_degree > 0) ? h->opts.coarse_smoother_degree
+                                                                  : h->opts.smoother_degree;
+    const int k = std::max(1, deg);
     const double bmax = sw ? L.lam_sw : L.lam_max * (1.0 + 1e-6);
     const double amin = bmax / std::max(1.5, h->opts.cheb_range);
     const double theta = 0.5 * (bmax + amin), delta = 0.5 * (bmax - amin);

@@ -23,18 +23,31 @@ __host__ __device__ inline int sw_axis_off(const LevelOp* op, int d, int stride)
 // Patch kernel layout: each thread owns LPT = 3 lines of the patch in every
 // 1-D pass (line values and outputs in registers, the 1-D matrix streamed from
 // shared memory and reused across the three lines).
+// Tuning constants (compile-time; the defaults were chosen by timing on a GB300)
+// patch lines per thread, FP32: 2 for p = 1 and p >= 7, 3 otherwise (timed per degree)
+#ifdef DG_SW_LPT32
+#define DG_SW_LPT_OF(N1) DG_SW_LPT32
+#else
+#define DG_SW_LPT_OF(N1) ((N1) == 2 || (N1) >= 8 ? 2 : 3)
+#endif
+#ifndef DG_SW_THREADS
+#define DG_SW_THREADS 256  // thread budget per block
+#endif
+#ifndef DG_SW_SMEM
+#define DG_SW_SMEM 40960   // shared-memory budget of the patch slots (bytes)
+#endif
 template <typename T, int N1>
 struct SwCfg {
   static constexpr int MP = N1 + 2;
   static constexpr int LINES = MP * MP;
-  // FP32: three lines per thread (shared-memory traffic per FMA / 3); FP64 is
-  // bound by the FP64 pipe, one line per thread keeps registers in check
-  static constexpr int LPT = sizeof(T) == 4 ? 3 : 1;
+  // FP32: two or three lines per thread (shared-memory traffic per FMA / LPT);
+  // FP64 is bound by the FP64 pipe, one line per thread keeps registers in check
+  static constexpr int LPT = sizeof(T) == 4 ? DG_SW_LPT_OF(N1) : 1;
   static constexpr int TPE = (LINES + LPT - 1) / LPT;  // threads per element
   static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;  // resident blocks per SM asked of ptxas
   static constexpr int PER_ELEM = (MP * MP * MP + 3 * MP * MP + 3 * MP) * (int)sizeof(T);
-  static constexpr int EPB_T = 256 / TPE < 1 ? 1 : 256 / TPE;
-  static constexpr int EPB_S = 40960 / PER_ELEM < 1 ? 1 : 40960 / PER_ELEM;
+  static constexpr int EPB_T = DG_SW_THREADS / TPE < 1 ? 1 : DG_SW_THREADS / TPE;
+  static constexpr int EPB_S = DG_SW_SMEM / PER_ELEM < 1 ? 1 : DG_SW_SMEM / PER_ELEM;
   static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;
   static constexpr int THREADS = EPB * TPE;
 };

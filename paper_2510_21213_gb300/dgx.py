@@ -57,6 +57,7 @@ class dg_solver_opts(C.Structure):
         ("nn_weights_path", C.c_char_p),
         ("verbose", C.c_int32),
         ("coarse_penalty", C.c_int32),
+        ("coarse_smoother_degree", C.c_int32),
     ]
 
 
