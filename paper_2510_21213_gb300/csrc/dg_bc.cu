@@ -8,6 +8,8 @@
 // nodes, the sum for the faces normal to axis d factorises into three 1-D
 // contractions per term: along d with the face position, then along the two
 // tangential axes. Those contractions run as strided batched GEMMs (k_gemm).
+#include <algorithm>
+
 #include "dg_internal.h"
 
 namespace dg {
@@ -172,10 +174,15 @@ __device__ __forceinline__ void mma_tf32(float* d, const unsigned* a, const unsi
 constexpr int TCA = 20;  // padded row of the A tile (conflict-free fragment loads)
 constexpr int TCB = 72;  // padded row of the B tile
 
-__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base) {
+// With nsplit > 1, block z covers batch (batch_base + z / nsplit) and the K
+// range [kc (z % nsplit), kc (z % nsplit + 1)); its compensated partial sum goes
+// to work[split][batch][m][n] and k_gemm_splitk_reduce finishes C.
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base, int nsplit, int kc) {
   __shared__ unsigned sAh[64][TCA], sAl[64][TCA];
   __shared__ unsigned sBh[16][TCB], sBl[16][TCB];
-  const int bz = batch_base + blockIdx.z;
+  const int bz = batch_base + (int)blockIdx.z / nsplit;
+  const int split = (int)blockIdx.z % nsplit;
+  const int kbeg = split * kc, kend = min(g.K, kbeg + kc);
   const int b1 = bz / g.nb2, b2 = bz % g.nb2;
   const float* A = (const float*)g.A + b1 * g.sA1 + b2 * g.sA2;
   const float* B = (const float*)g.B + b1 * g.sB1 + b2 * g.sB2;
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base) {
         sum[i][j][e] = 0.f;
         car[i][j][e] = 0.f;
       }
-  for (int k0 = 0; k0 < g.K; k0 += 16) {
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     for (int t = tid; t < 64 * 16; t += 128) {
       int kk, mm;
       if (a_k_fast) {
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base) {
         kk = t / 64;
       }
       const int m = m0 + mm, k = k0 + kk;
-      const float av = (m < g.M && k < g.K) ? A[(long long)m * g.sAm + (long long)k * g.sAk] : 0.f;
+      const float av = (m < g.M && k < kend) ? A[(long long)m * g.sAm + (long long)k * g.sAk] : 0.f;
       const unsigned ah = to_tf32(av);
       sAh[mm][kk] = ah;
       sAl[mm][kk] = to_tf32(av - __uint_as_float(ah));
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base) {
         nn = t / 16;
       }
       const int n = n0 + nn, kx = k0 + kb;
-      const float bv = (n < g.N && kx < g.K) ? B[(long long)kx * g.sBk + (long long)n * g.sBn] : 0.f;
+      const float bv = (n < g.N && kx < kend) ? B[(long long)kx * g.sBk + (long long)n * g.sBn] : 0.f;
       const unsigned bh = to_tf32(bv);
       sBh[kb][nn] = bh;
       sBl[kb][nn] = to_tf32(bv - __uint_as_float(bh));
@@ -281,9 +288,32 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base) {
         const int n = n0 + wn + j * 8 + 2 * c4 + (e & 1);
         if (m >= g.M || n >= g.N) continue;
         const float v = sum[i][j][e] + car[i][j][e];
+        if (nsplit > 1) {
+          const long long nb = (long long)g.nb1 * g.nb2;
+          ((float*)g.work)[(((long long)split * nb + bz) * g.M + m) * g.N + n] = v;
+          continue;
+        }
         float* cp = C + (long long)m * g.sCm + (long long)n * g.sCn;
         *cp = g.beta != 0.0 ? alpha * v + beta * (*cp) : alpha * v;
       }
+}
+
+// C = alpha sum_split work[split] (+ beta C), splits added in order with TwoSum
+__global__ void k_gemm_splitk_reduce(GemmArgs g, int nsplit) {
+  const long long nb = (long long)g.nb1 * g.nb2;
+  const long long mn = (long long)g.M * g.N, total = nb * mn;
+  const float* w = (const float*)g.work;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    float sum = 0.f, car = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) two_sum_add(sum, car, w[(long long)sp * total + i]);
+    const long long bz = i / mn, r = i - bz * mn;
+    const int m = (int)(r / g.N), n = (int)(r - (long long)m * g.N);
+    const int b1 = (int)(bz / g.nb2), b2 = (int)(bz % g.nb2);
+    float* cp = (float*)g.C + b1 * g.sC1 + b2 * g.sC2 + (long long)m * g.sCm + (long long)n * g.sCn;
+    const float v = sum + car;
+    *cp = g.beta != 0.0 ? (float)g.alpha * v + (float)g.beta * (*cp) : (float)g.alpha * v;
+  }
 }
 
 template <typename T>
@@ -292,13 +322,33 @@ cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
   const long long nb = (long long)g.nb1 * g.nb2;
   const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, 1);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  for (long long base = 0; base < nb; base += 65535) {
-    const long long cnt = nb - base < 65535 ? nb - base : 65535;
-    count_launch();
-    if constexpr (sizeof(T) == 4)
-      k_gemm_tc<<<dim3(grid.x, grid.y, (unsigned)cnt), 128, 0, s>>>(g, (int)base);
-    else
+  if constexpr (sizeof(T) == 4) {
+    // split a long K over blocks when the output tiles cannot fill the GPU
+    const long long tiles = (long long)grid.x * grid.y * nb;
+    int nsplit = 1;
+    if (g.work && g.K >= 1024 && tiles < 2 * 152) {
+      nsplit = (int)std::min<long long>(32, std::min<long long>((g.K + 255) / 256, (4 * 152 + tiles - 1) / tiles));
+      while (nsplit > 1 && (long long)nsplit * nb * g.M * g.N > g.work_elems) --nsplit;
+    }
+    const int kc = nsplit > 1 ? ((g.K + nsplit - 1) / nsplit + 15) / 16 * 16 : g.K;
+    if (nsplit > 1) nsplit = (g.K + kc - 1) / kc;  // no empty split
+    const long long per = 65535 / nsplit;
+    for (long long base = 0; base < nb; base += per) {
+      const long long cnt = nb - base < per ? nb - base : per;
+      count_launch();
+      k_gemm_tc<<<dim3(grid.x, grid.y, (unsigned)(cnt * nsplit)), 128, 0, s>>>(g, (int)base, nsplit, kc);
+    }
+    if (nsplit > 1) {
+      count_launch();
+      const long long total = nb * g.M * g.N;
+      k_gemm_splitk_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 152LL * 16), 256, 0, s>>>(g, nsplit);
+    }
+  } else {
+    for (long long base = 0; base < nb; base += 65535) {
+      const long long cnt = nb - base < 65535 ? nb - base : 65535;
+      count_launch();
       k_gemm<T><<<dim3(grid.x, grid.y, (unsigned)cnt), 256, 0, s>>>(g, (int)base);
+    }
   }
   return cudaGetLastError();
 }

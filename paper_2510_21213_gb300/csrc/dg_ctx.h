@@ -10,6 +10,32 @@
 namespace dg {
 
 // ---------------------------------------------------------------------------
+// Device-wide operations (allocation and freeing, synchronous copies,
+// device synchronisation, launches on the legacy stream) must not run in one
+// host thread while another thread captures a CUDA graph: a device-wide
+// synchronisation invalidates the capture. Captures hold a process-wide lock
+// shared (CaptureGuard), device-wide sections hold it exclusively
+// (DeviceWideGuard); nested exclusive sections of one thread are counted.
+// ---------------------------------------------------------------------------
+class DeviceWideGuard {
+ public:
+  DeviceWideGuard();
+  ~DeviceWideGuard();
+  DeviceWideGuard(const DeviceWideGuard&) = delete;
+  DeviceWideGuard& operator=(const DeviceWideGuard&) = delete;
+};
+class CaptureGuard {
+ public:
+  CaptureGuard();
+  ~CaptureGuard();
+  CaptureGuard(const CaptureGuard&) = delete;
+  CaptureGuard& operator=(const CaptureGuard&) = delete;
+
+ private:
+  bool shared_;
+};
+
+// ---------------------------------------------------------------------------
 // device buffer helper
 // ---------------------------------------------------------------------------
 struct DevBuf {
@@ -17,13 +43,17 @@ struct DevBuf {
   size_t bytes = 0;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      DeviceWideGuard guard;
+      cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
   }
   cudaError_t ensure(size_t b) {
     if (b <= bytes) return cudaSuccess;
     release();
+    DeviceWideGuard guard;
     cudaError_t e = cudaMalloc(&p, b);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -112,6 +142,7 @@ struct dg_ctx {
   int NG = 0, NG32 = 0;
   dg::BcAxisTables bct[3], bct32[3];
   dg::DevBuf flex32, T1_32, T2_32, g32;
+  dg::DevBuf gemm_ws;              // split-K partials of the FP32 boundary-data GEMMs
   // workspaces
   dg::PrecWork<double> w64;
   dg::PrecWork<float> w32;

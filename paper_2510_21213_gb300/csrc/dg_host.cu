@@ -10,6 +10,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <shared_mutex>
 #include <vector>
 
 #include "dg_ctx.h"
@@ -17,6 +18,21 @@
 
 namespace dg {
 
+static std::shared_mutex g_capture_mu;
+static thread_local int t_device_wide = 0;
+
+DeviceWideGuard::DeviceWideGuard() {
+  if (t_device_wide++ == 0) g_capture_mu.lock();
+}
+DeviceWideGuard::~DeviceWideGuard() {
+  if (--t_device_wide == 0) g_capture_mu.unlock();
+}
+CaptureGuard::CaptureGuard() : shared_(t_device_wide == 0) {
+  if (shared_) g_capture_mu.lock_shared();
+}
+CaptureGuard::~CaptureGuard() {
+  if (shared_) g_capture_mu.unlock_shared();
+}
 
 // ---------------------------------------------------------------------------
 // workspace
@@ -24,6 +40,7 @@ namespace dg {
 template <typename T>
 int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap) {
   if (w.cap >= cap && !w.lev.empty()) return DG_OK;
+  DeviceWideGuard guard;
   ++h->buf_gen;
   w.lev.resize(h->nlev);
   for (int l = 0; l < h->nlev; ++l) {
@@ -60,6 +77,7 @@ template int ensure_prec<float>(dg_ctx*, PrecWork<float>&, int);
 
 int ensure_common(dg_ctx* h, int cap) {
   if (h->cap >= cap) return DG_OK;
+  DeviceWideGuard guard;
   ++h->buf_gen;
   const long long N = h->Nq;
   DG_CK(h->f64.ensure(sizeof(double) * N * cap));
@@ -89,6 +107,7 @@ static int ensure_bc_work(dg_ctx* h, int nsrc, int NG, BcAxisTables* bct, DevBuf
   const size_t tb = sizeof(T) * 2 * (size_t)NG * maxface * nsrc;
   DG_CK(T1.ensure(tb));
   DG_CK(T2.ensure(tb));
+  if (sizeof(T) == 4) DG_CK(h->gemm_ws.ensure(sizeof(float) * (16LL << 20)));  // 64 MB of split-K partials
   return DG_OK;
 }
 
@@ -161,6 +180,7 @@ static int run_phase(dg_ctx* h, PhaseGraph& g, int nact, cudaStream_t s, F&& bod
     cudaGraphExecDestroy(g.exec);
     g.exec = nullptr;
   }
+  CaptureGuard cap_guard;  // no device-wide operation of another thread during the capture
   const long long l0 = g_launch_count.load();
   DG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   const int rc = body();
@@ -501,6 +521,10 @@ static int boundary_gausssum(dg_ctx* h, const double* f, int nsrc, T* g, BcAxisT
     c.sC2 = L1 * L2;
     c.alpha = 1.0;
     c.beta = 0.0;
+    if (sizeof(T) == 4) {  // K = N_G L over few output tiles: split K (FP32 path)
+      c.work = h->gemm_ws.p;
+      c.work_elems = (long long)(h->gemm_ws.bytes / sizeof(float));
+    }
     DG_CK(launch_gemm<T>(c, s));
     face_off += 2 * L1 * L2;
   }
@@ -915,6 +939,7 @@ int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_ha
   if (!h) return DG_ERR_NO_MEMORY;
   h->mesh = *mesh;
   h->opts = o;
+  DeviceWideGuard guard;  // set-up allocates, copies synchronously and launches on the legacy stream
   int rc = setup(h);
   if (rc == DG_OK && o.precision == DG_PREC_MIXED_LEARNED && o.nn_weights_path) rc = nn_load_file(h, o.nn_weights_path);
   h->opts.nn_weights_path = nullptr;  // the caller's string is not kept
@@ -929,6 +954,7 @@ int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_ha
 
 void dg_destroy(dg_handle h) {
   if (!h) return;
+  DeviceWideGuard guard;
   for (auto& L : h->levels) {
     if (L.dop) cudaFree(L.dop);
     if (L.dtr) cudaFree(L.dtr);

@@ -82,6 +82,10 @@ struct GemmArgs {
   void* C;
   long long sCm, sCn, sC1, sC2;
   double alpha, beta;
+  // optional workspace (elements of the GEMM's type) for splitting a long K
+  // across blocks when there are few output tiles (FP32 path); null = no split
+  void* work;
+  long long work_elems;
 };
 
 // ---------------------------------------------------------------------------

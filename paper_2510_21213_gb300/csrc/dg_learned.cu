@@ -266,6 +266,7 @@ static int coarse_guess(dg_ctx* h, int nsrc, const int* dact, int nact, cudaStre
           D.ax[d].lift[1][a] = ds * D.tr[a];
         }
       }
+      DeviceWideGuard guard;
       DG_CK(h->dlift_op.ensure(sizeof(LevelOp)));
       DG_CK(cudaMemcpy(h->dlift_op.p, &D, sizeof(LevelOp), cudaMemcpyHostToDevice));
     }
@@ -434,12 +435,14 @@ extern "C" {
 
 int dg_nn_set_params(dg_handle h, const float* params_host) {
   if (!h || !params_host) return DG_ERR_INVALID_ARG;
+  DeviceWideGuard guard;
   if (h->levels[0].op.n1 > NN_MAXN1) return DG_ERR_UNSUPPORTED;
   return nn_set(h, params_host);
 }
 
 int dg_nn_get_params(dg_handle h, float* params_host) {
   if (!h || !params_host || !h->nn.have) return DG_ERR_INVALID_ARG;
+  DeviceWideGuard guard;
   DG_CK(cudaDeviceSynchronize());
   DG_CK(cudaMemcpy(params_host, h->nn.prm.p, sizeof(float) * NN_NPARAM, cudaMemcpyDeviceToHost));
   return DG_OK;
