@@ -176,8 +176,9 @@ constexpr int TCB = 72;  // padded row of the B tile
 
 // With nsplit > 1, block z covers batch (batch_base + z / nsplit) and the K
 // range [kc (z % nsplit), kc (z % nsplit + 1)); its compensated partial sum goes
-// to work[split][batch][m][n] and k_gemm_splitk_reduce finishes C.
-__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base, int nsplit, int kc) {
+// to work[split][batch - batch_base][m][n] (nbc batches per launch) and
+// k_gemm_splitk_reduce finishes C.
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base, int nsplit, int kc, int nbc) {
   __shared__ unsigned sAh[64][TCA], sAl[64][TCA];
   __shared__ unsigned sBh[16][TCB], sBl[16][TCB];
   const int bz = batch_base + (int)blockIdx.z / nsplit;
@@ -289,8 +290,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base, int
         if (m >= g.M || n >= g.N) continue;
         const float v = sum[i][j][e] + car[i][j][e];
         if (nsplit > 1) {
-          const long long nb = (long long)g.nb1 * g.nb2;
-          ((float*)g.work)[(((long long)split * nb + bz) * g.M + m) * g.N + n] = v;
+          ((float*)g.work)[(((long long)split * nbc + (bz - batch_base)) * g.M + m) * g.N + n] = v;
           continue;
         }
         float* cp = C + (long long)m * g.sCm + (long long)n * g.sCn;
@@ -298,16 +298,16 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g, int batch_base, int
       }
 }
 
-// C = alpha sum_split work[split] (+ beta C), splits added in order with TwoSum
-__global__ void k_gemm_splitk_reduce(GemmArgs g, int nsplit) {
-  const long long nb = (long long)g.nb1 * g.nb2;
-  const long long mn = (long long)g.M * g.N, total = nb * mn;
+// C = alpha sum_split work[split] (+ beta C) for batches batch_base ..
+// batch_base + nbc - 1, splits added in order with TwoSum
+__global__ void k_gemm_splitk_reduce(GemmArgs g, int nsplit, int batch_base, int nbc) {
+  const long long mn = (long long)g.M * g.N, total = (long long)nbc * mn;
   const float* w = (const float*)g.work;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     float sum = 0.f, car = 0.f;
     for (int sp = 0; sp < nsplit; ++sp) two_sum_add(sum, car, w[(long long)sp * total + i]);
-    const long long bz = i / mn, r = i - bz * mn;
+    const long long bz = batch_base + i / mn, r = i % mn;
     const int m = (int)(r / g.N), n = (int)(r - (long long)m * g.N);
     const int b1 = (int)(bz / g.nb2), b2 = (int)(bz % g.nb2);
     float* cp = (float*)g.C + b1 * g.sC1 + b2 * g.sC2 + (long long)m * g.sCm + (long long)n * g.sCn;
@@ -323,25 +323,26 @@ cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t s) {
   const dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, 1);
   if (grid.y > 65535) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
-    // split a long K over blocks when the output tiles cannot fill the GPU
-    const long long tiles = (long long)grid.x * grid.y * nb;
+    // a long K is split over blocks into fixed 512-term ranges (from K alone,
+    // so a batch's sums do not depend on how many batches share the call);
+    // batches go through in chunks that fit the workspace
     int nsplit = 1;
-    if (g.work && g.K >= 1024 && tiles < 2 * 152) {
-      nsplit = (int)std::min<long long>(32, std::min<long long>((g.K + 255) / 256, (4 * 152 + tiles - 1) / tiles));
-      while (nsplit > 1 && (long long)nsplit * nb * g.M * g.N > g.work_elems) --nsplit;
-    }
+    if (g.work && g.K >= 1024) nsplit = std::min(32, (g.K + 511) / 512);
     const int kc = nsplit > 1 ? ((g.K + nsplit - 1) / nsplit + 15) / 16 * 16 : g.K;
     if (nsplit > 1) nsplit = (g.K + kc - 1) / kc;  // no empty split
-    const long long per = 65535 / nsplit;
+    long long per = 65535 / nsplit;
+    if (nsplit > 1) per = std::min<long long>(per, g.work_elems / ((long long)nsplit * g.M * g.N));
+    if (per < 1) return cudaErrorInvalidValue;  // workspace too small for one batch
     for (long long base = 0; base < nb; base += per) {
       const long long cnt = nb - base < per ? nb - base : per;
       count_launch();
-      k_gemm_tc<<<dim3(grid.x, grid.y, (unsigned)(cnt * nsplit)), 128, 0, s>>>(g, (int)base, nsplit, kc);
-    }
-    if (nsplit > 1) {
-      count_launch();
-      const long long total = nb * g.M * g.N;
-      k_gemm_splitk_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 152LL * 16), 256, 0, s>>>(g, nsplit);
+      k_gemm_tc<<<dim3(grid.x, grid.y, (unsigned)(cnt * nsplit)), 128, 0, s>>>(g, (int)base, nsplit, kc, (int)cnt);
+      if (nsplit > 1) {
+        count_launch();
+        const long long total = cnt * g.M * g.N;
+        k_gemm_splitk_reduce<<<(unsigned)std::min<long long>((total + 255) / 256, 152LL * 16), 256, 0, s>>>(
+            g, nsplit, (int)base, (int)cnt);
+      }
     }
   } else {
     for (long long base = 0; base < nb; base += 65535) {

@@ -72,3 +72,25 @@ def test_autotuner_chooses_and_caches(dgx):
     assert b2 == b1
     assert dgx.dg_autotune_batch(s.h, 3) == min(b1, 3)
     s.close()
+
+
+def test_many_lanes_with_overlapping_setup_and_capture(dgx):
+    """Eight uneven systems of the batched workload on four lanes, mixed form:
+    lanes set up handles while other lanes capture their PCG graphs. Every
+    build converges and matches a single build of the same system."""
+    specs = [inputs.batched_system(4000 + k) for k in range(8)]
+    args = []
+    for sp in specs:
+        m = sp.mesh
+        xyz, w = dgx.dg_mesh_node_coords(m.lo, m.hi, m.n, m.p)
+        args.append((m.lo, m.hi, m.n, m.p, torch.tensor(inputs.orbitals(sp, xyz, w), device="cuda")))
+    opts = dgx.dg_default_opts(precision=1, rtol=1e-8)
+    Ks, ehs, exs, sts = dgx.dg_exchange_build_multi(args, opts=opts, lanes=4)
+    assert all(x["status"] == 0 for st in sts for x in st)
+    for i in (0, len(specs) - 1):
+        m = specs[i].mesh
+        s = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=1, rtol=1e-8)
+        K, eh, ex, st = s.exchange_build(args[i][4])
+        assert np.abs(Ks[i] - K).max() <= 1e-12 * np.abs(K).max()
+        s.close()
+    dgx.dg_release_cached_handles()
