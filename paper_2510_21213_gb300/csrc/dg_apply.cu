@@ -29,8 +29,11 @@ namespace dg {
 #ifndef DG_APPLY_SMEM
 #define DG_APPLY_SMEM 36864   // shared-memory budget of the element slots (bytes)
 #endif
+#ifndef DG_SMEM_CARVEOUT
+#define DG_SMEM_CARVEOUT -1  // shared-memory carveout (percent) asked for the operator and patch kernels; -1: default
+#endif
 #ifndef DG_APPLY_MINB32
-#define DG_APPLY_MINB32 3     // resident blocks per SM asked of ptxas, FP32
+#define DG_APPLY_MINB32 4     // resident blocks per SM asked of ptxas, FP32
 #endif
 template <typename T, int N1>
 struct ApplyCfg {
@@ -45,7 +48,8 @@ struct ApplyCfg {
   // the load and trace phases use every thread of the block; the line passes
   // use the first EPB * TPE
   static constexpr int THREADS = EPB * TPE < DG_APPLY_THREADS ? DG_APPLY_THREADS : EPB * TPE;
-  static constexpr int MINB = sizeof(T) == 4 ? DG_APPLY_MINB32 : 2;  // resident blocks per SM asked of ptxas
+  // resident blocks per SM asked of ptxas (p = 8 keeps 3: at 4 its registers spill)
+  static constexpr int MINB = sizeof(T) == 4 ? (N1 >= 9 ? 3 : DG_APPLY_MINB32) : 2;
 };
 
 // one direction of the operator for LPT lines of one element:
@@ -265,6 +269,15 @@ static cudaError_t apply_n1(const LevelOp& hop, const LevelOp* dop, int mode, co
   // persistent-style grid: a few resident blocks per SM loop over element groups
   const long long cap = 152LL * (2048 / C::THREADS) * 2;
   if (blocks > cap) blocks = cap;
+#if DG_SMEM_CARVEOUT >= 0
+  static bool carve = false;  // ask for the largest shared-memory carveout (more resident blocks)
+  if (!carve) {
+    cudaFuncSetAttribute(k_apply<T, N1, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, DG_SMEM_CARVEOUT);
+    cudaFuncSetAttribute(k_apply<T, N1, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, DG_SMEM_CARVEOUT);
+    cudaFuncSetAttribute(k_apply<T, N1, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, DG_SMEM_CARVEOUT);
+    carve = true;
+  }
+#endif
   count_launch();
   if (mode == 0)
     k_apply<T, N1, 0><<<(unsigned)blocks, C::THREADS, 0, s>>>(dop, u, out, rin, act, nact);

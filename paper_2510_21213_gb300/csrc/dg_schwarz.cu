@@ -24,6 +24,9 @@ __host__ __device__ inline int sw_axis_off(const LevelOp* op, int d, int stride)
 // 1-D pass (line values and outputs in registers, the 1-D matrix streamed from
 // shared memory and reused across the three lines).
 // Tuning constants (compile-time; the defaults were chosen by timing on a GB300)
+#ifndef DG_SMEM_CARVEOUT
+#define DG_SMEM_CARVEOUT -1  // shared-memory carveout (percent) asked for the patch kernel; -1: default
+#endif
 // patch lines per thread, FP32: 2 for p = 1 and p >= 7, 3 otherwise (timed per degree)
 #ifdef DG_SW_LPT32
 #define DG_SW_LPT_OF(N1) DG_SW_LPT32
@@ -294,6 +297,13 @@ static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const doub
                               T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s) {
   using C = SwCfg<T, N1>;
   const long long items = (long long)nact * hop.E;
+#if DG_SMEM_CARVEOUT >= 0
+  static bool carve = false;
+  if (!carve) {
+    cudaFuncSetAttribute(k_schwarz_patch<T, N1>, cudaFuncAttributePreferredSharedMemoryCarveout, DG_SMEM_CARVEOUT);
+    carve = true;
+  }
+#endif
   count_launch();
   k_schwarz_patch<T, N1><<<(unsigned)((items + C::EPB - 1) / C::EPB), C::THREADS, 0, s>>>(dop, tabs, r, zp, act, nact);
   constexpr int NPE = N1 * N1 * N1;
