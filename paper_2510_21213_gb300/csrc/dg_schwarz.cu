@@ -33,11 +33,14 @@ __host__ __device__ inline int sw_axis_off(const LevelOp* op, int d, int stride)
 #else
 #define DG_SW_LPT_OF(N1) ((N1) == 2 || (N1) >= 8 ? 2 : 3)
 #endif
+#ifndef DG_SW_MINB32
+#define DG_SW_MINB32 4     // resident blocks per SM asked of ptxas, FP32
+#endif
 #ifndef DG_SW_THREADS
 #define DG_SW_THREADS 256  // thread budget per block
 #endif
 #ifndef DG_SW_SMEM
-#define DG_SW_SMEM 40960   // shared-memory budget of the patch slots (bytes)
+#define DG_SW_SMEM 32768   // shared-memory budget of the patch slots (bytes)
 #endif
 template <typename T, int N1>
 struct SwCfg {
@@ -47,7 +50,7 @@ struct SwCfg {
   // FP64 is bound by the FP64 pipe, one line per thread keeps registers in check
   static constexpr int LPT = sizeof(T) == 4 ? DG_SW_LPT_OF(N1) : 1;
   static constexpr int TPE = (LINES + LPT - 1) / LPT;  // threads per element
-  static constexpr int MINB = sizeof(T) == 4 ? 2 : 1;  // resident blocks per SM asked of ptxas
+  static constexpr int MINB = sizeof(T) == 4 ? DG_SW_MINB32 : 1;  // resident blocks per SM asked of ptxas
   static constexpr int PER_ELEM = (MP * MP * MP + 3 * MP * MP + 3 * MP) * (int)sizeof(T);
   static constexpr int EPB_T = DG_SW_THREADS / TPE < 1 ? 1 : DG_SW_THREADS / TPE;
   static constexpr int EPB_S = DG_SW_SMEM / PER_ELEM < 1 ? 1 : DG_SW_SMEM / PER_ELEM;
