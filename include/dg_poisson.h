@@ -188,6 +188,20 @@ int dg_pair_solve_batch(dg_handle h, const double* f_dev, int64_t B, double* v_d
 int dg_exchange_build(dg_handle h, const double* psi_dev, int32_t N, double* K_host, double* E_H,
                       double* E_X, dg_solve_stats* stats_host, void* cuda_stream);
 
+/* Part of an exchange build, for sharding one system's sources over GPUs
+ * (one handle per GPU, no communication inside the call). The sources are
+ * numbered as in dg_exchange_build's stats: 0 = Hartree density, 1.. = the
+ * pairs (i <= j) row-major; this call solves [src_begin, src_end) and returns
+ * in K_partial_host [N*N] (host) their contribution sum_s psi_i (psi_s v_sj)
+ * to K_ij (eq. fock_exchange, Sec. 6.1.2). The partial K of disjoint ranges
+ * covering 0 .. N(N+1)/2 add up to dg_exchange_build's K (up to the summation
+ * order); E_X = -1/2 tr of the sum. E_H (host, may be NULL) is set when the
+ * range holds source 0 and is 0 otherwise. stats_host: [src_end - src_begin]
+ * (may be NULL). An empty range returns K_partial = 0. DG_ERR_INVALID_ARG for
+ * a range outside 0 .. N(N+1)/2 + 1. */
+int dg_exchange_build_range(dg_handle h, const double* psi_dev, int32_t N, int64_t src_begin, int64_t src_end,
+                            double* K_partial_host, double* E_H, dg_solve_stats* stats_host, void* cuda_stream);
+
 /* Exchange builds of nsys independent systems with their own meshes and
  * orbital counts (uneven sizes), as one call. meshes [nsys] (host), psi_devs
  * [nsys] device pointers to [Ns[i]][Nq_i], K_hosts [nsys] host pointers to

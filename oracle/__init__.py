@@ -33,4 +33,5 @@ from .dg_oracle import (  # noqa: F401
     pair_list,
     poisson,
     exchange_build,
+    exchange_partial,
 )

@@ -578,6 +578,36 @@ def poisson(mesh, f, penalty_form=0, eps=0.125, method="auto", g=None):
     return v, g
 
 
+def exchange_partial(mesh, psi, src_begin, src_end, penalty_form=0, eps=0.125, method="auto"):
+    """The part of the exchange build that sources [src_begin, src_end) of the
+    list (0 = Hartree density rho, then the pairs of pair_list) contribute:
+    K_part[i, j] = sum_q W_q psi_i(q) sum_{pairs (s, j) in range} psi_s(q) v_sj(q)
+    (eq. fock_exchange, Sec. 6.1.2, summed over the listed pairs only; K is
+    linear in the pair potentials, so disjoint ranges add up to K) and E_H
+    (Sec. 2.3.1) if source 0 is in the range, else 0."""
+    psi = np.asarray(psi, dtype=np.float64)
+    N = psi.shape[0]
+    Wq = quad_weights(mesh)
+    pairs = pair_list(N)
+    idx = list(range(int(src_begin), int(src_end)))
+    if not idx:
+        return np.zeros((N, N)), 0.0
+    rho = np.sum(psi * psi, axis=0)
+    sources = np.stack([rho if k == 0 else psi[pairs[k - 1][0]] * psi[pairs[k - 1][1]] for k in idx])
+    v, _ = poisson(mesh, sources, penalty_form, eps, method)
+    Wacc = np.zeros_like(psi)
+    E_H = 0.0
+    for row, k in enumerate(idx):
+        if k == 0:
+            E_H = 0.5 * float(np.sum(Wq * rho * v[row]))
+            continue
+        s_, j = pairs[k - 1]
+        Wacc[j] += psi[s_] * v[row]
+        if s_ != j:
+            Wacc[s_] += psi[j] * v[row]
+    return (psi * Wq[None, :]) @ Wacc.T, E_H
+
+
 def exchange_build(mesh, psi, penalty_form=0, eps=0.125, method="auto", keep_potentials=False):
     """Hartree potential, pair potentials, K, E_H and E_X for orbitals psi [N, Nq]."""
     psi = np.asarray(psi, dtype=np.float64)

@@ -1129,9 +1129,12 @@ int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_s
   return worst;
 }
 
-int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host, double* E_H, double* E_X,
-                      dg_solve_stats* stats, void* stream) {
-  if (!h || N < 1 || !psi || !K_host) return DG_ERR_INVALID_ARG;
+// Exchange build over the sources [src_begin, src_end) of the list
+// 0 = Hartree density, then the pairs (i <= j) row-major: K_host receives
+// their contribution to K (the contributions of disjoint ranges add up to K),
+// E_H is set when the range holds source 0 (else 0), E_X = -1/2 tr K_host.
+static int exchange_build_range(dg_handle h, const double* psi, int32_t N, long long src_begin, long long src_end,
+                                double* K_host, double* E_H, double* E_X, dg_solve_stats* stats, void* stream) {
   cudaStream_t us = (cudaStream_t)stream;
   DG_CK(cudaEventRecord(h->ev_in, us));
   DG_CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
@@ -1139,7 +1142,7 @@ int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host,
   const long long Nq = h->Nq;
   const int P = N * (N + 1) / 2;
   const int nsrc_total = P + 1;
-  const int cap = std::max(1, std::min(default_batch(h), nsrc_total));
+  const int cap = std::max(1, std::min<int>(default_batch(h), (int)(src_end - src_begin)));
   DG_RET(prepare(h, cap));
   DG_CK(h->Wacc.ensure(sizeof(double) * N * Nq));
   const int nch = kmat_chunks(Nq);
@@ -1161,15 +1164,15 @@ int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host,
   int worst = DG_OK;
   double eh = 0.0;
   DevBuf lists;
-  for (int b0 = 0; b0 < nsrc_total; b0 += cap) {
-    const int nb = std::min(cap, nsrc_total - b0);
+  for (int b0 = (int)src_begin; b0 < (int)src_end; b0 += cap) {
+    const int nb = std::min(cap, (int)src_end - b0);
     DG_CK(cudaMemcpyAsync(h->pidx.p, si.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
     DG_CK(cudaMemcpyAsync(h->pidx.as<int>() + cap, sj.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
     DG_CK(launch_pair_sources(psi, N, h->pidx.as<int>(), h->pidx.as<int>() + cap, nb, Nq, h->f64.as<double>(), s));
     std::vector<int> finite;
     DG_RET(check_finite(h, h->f64.as<double>(), nb, finite, s));
     DG_RET(form_rhs(h, h->f64.as<double>(), nb, s));
-    const int rc = solve_chunk(h, nb, finite, stats ? stats + b0 : nullptr, s);
+    const int rc = solve_chunk(h, nb, finite, stats ? stats + (b0 - src_begin) : nullptr, s);
     if (rc == DG_ERR_CUDA || rc == DG_ERR_NO_MEMORY) return rc;
     if (rc != DG_OK && (worst == DG_OK || rc < worst)) worst = rc;
     const double* v = h->x64.as<double>();
@@ -1226,6 +1229,25 @@ int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host,
   }
   account(h);
   return worst;
+}
+
+int dg_exchange_build(dg_handle h, const double* psi, int32_t N, double* K_host, double* E_H, double* E_X,
+                      dg_solve_stats* stats, void* stream) {
+  if (!h || N < 1 || !psi || !K_host) return DG_ERR_INVALID_ARG;
+  return exchange_build_range(h, psi, N, 0, (long long)N * (N + 1) / 2 + 1, K_host, E_H, E_X, stats, stream);
+}
+
+int dg_exchange_build_range(dg_handle h, const double* psi, int32_t N, int64_t src_begin, int64_t src_end,
+                            double* K_partial_host, double* E_H, dg_solve_stats* stats, void* stream) {
+  if (!h || N < 1 || !psi || !K_partial_host) return DG_ERR_INVALID_ARG;
+  const long long total = (long long)N * (N + 1) / 2 + 1;
+  if (src_begin < 0 || src_end < src_begin || src_end > total) return DG_ERR_INVALID_ARG;
+  if (src_end == src_begin) {
+    std::memset(K_partial_host, 0, sizeof(double) * (size_t)N * N);
+    if (E_H) *E_H = 0.0;
+    return DG_OK;
+  }
+  return exchange_build_range(h, psi, N, src_begin, src_end, K_partial_host, E_H, nullptr, stats, stream);
 }
 
 }  // extern "C"

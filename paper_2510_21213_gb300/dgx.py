@@ -111,6 +111,8 @@ def load():
     lib.dg_mesh_node_coords.restype = C.c_int
     lib.dg_pair_solve_batch.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     lib.dg_exchange_build.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp]
+    lib.dg_exchange_build_range.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int64, vp, vp, vp, vp]
+    lib.dg_exchange_build_range.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -263,6 +265,24 @@ def dg_exchange_build(h, psi, stream=None, allow_unconverged=False):
                                     C.byref(ex), C.cast(st, C.c_void_p), _stream_ptr(stream))
     _check(code, "dg_exchange_build", h, allow)
     return K, eh.value, ex.value, _stats_list(st[:P])
+
+
+def dg_exchange_build_range(h, psi, src_begin, src_end, stream=None, allow_unconverged=False):
+    """Sources [src_begin, src_end) of an exchange build (0 = Hartree, then the
+    pairs): (partial K [N, N] numpy, E_H or 0, stats)."""
+    import torch
+
+    N = psi.shape[0]
+    K = np.empty((N, N), dtype=np.float64)
+    eh = C.c_double()
+    n = max(int(src_end) - int(src_begin), 1)
+    st = (dg_solve_stats * n)()
+    allow = (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_NONFINITE) if allow_unconverged else ()
+    code = load().dg_exchange_build_range(h, _dev_ptr(psi, torch.float64), N, int(src_begin), int(src_end),
+                                          K.ctypes.data_as(C.c_void_p), C.byref(eh), C.cast(st, C.c_void_p),
+                                          _stream_ptr(stream))
+    _check(code, "dg_exchange_build_range", h, allow)
+    return K, eh.value, _stats_list(st[:int(src_end) - int(src_begin)])
 
 
 def dg_apply_operator(h, u, level=0, out=None, stream=None):

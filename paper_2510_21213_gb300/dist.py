@@ -6,6 +6,10 @@ collectives are a barrier around a timed region and the maximum over ranks of
 its duration. Throughput is the work of all ranks over that maximum (weak
 scaling: the work per rank does not depend on the number of ranks).
 
+One system can also be sharded: the pair solves of one exchange build are
+independent too, so each rank solves a contiguous share of the sources and
+one all-reduce of the partial K (N^2 doubles) and E_H finishes the build.
+
 torch.distributed is plumbing here; any backend works (nccl on GPUs, gloo in
 the CPU tests).
 """
@@ -76,3 +80,45 @@ def aggregate_rate(units_per_rank, steps, max_seconds, world_size):
     if max_seconds <= 0:
         raise ValueError("non-positive time")
     return world_size * units_per_rank * steps / max_seconds
+
+
+# ---------------------------------------------------------------------------
+# one system sharded over ranks: each rank solves a contiguous range of the
+# sources (0 = Hartree density, then the pairs) and returns its part of K; one
+# all-reduce (sum) of the N x N partial K and of E_H gives the whole build
+# ---------------------------------------------------------------------------
+def shard_range(n_items, world_size, rank):
+    """[begin, end) of rank's share of n_items: contiguous, sizes differ by at
+    most one (the sources of one system cost about the same)."""
+    if world_size < 1 or not 0 <= rank < world_size:
+        raise ValueError("bad rank")
+    base, extra = divmod(int(n_items), int(world_size))
+    begin = rank * base + min(rank, extra)
+    return begin, begin + base + (1 if rank < extra else 0)
+
+
+def allreduce_sum(values, device="cpu"):
+    """Element-wise sum over ranks of a float64 array (every rank gets it)."""
+    import numpy as np
+    import torch
+
+    arr = np.asarray(values, dtype=np.float64)
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return arr.copy()
+    t = torch.tensor(arr, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return t.cpu().numpy()
+
+
+def sharded_exchange(partial, n_orbitals, world_size, rank, device="cpu"):
+    """Whole-system K, E_H and E_X = -1/2 tr K from this rank's share.
+    partial(begin, end) -> (K_partial [N, N], E_H or 0) computes the share
+    (the library's dg_exchange_build_range, or any stand-in with its contract)."""
+    import numpy as np
+
+    total = n_orbitals * (n_orbitals + 1) // 2 + 1
+    begin, end = shard_range(total, world_size, rank)
+    K_part, eh = partial(begin, end)
+    red = allreduce_sum(np.concatenate([np.asarray(K_part, dtype=np.float64).reshape(-1), [eh]]), device)
+    K = red[:-1].reshape(n_orbitals, n_orbitals)
+    return K, float(red[-1]), -0.5 * float(np.trace(K))

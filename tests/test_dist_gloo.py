@@ -58,3 +58,61 @@ def test_single_rank_defaults(monkeypatch):
     assert pd.rank_seed(2, 0) == 2
     with pytest.raises(ValueError):
         pd.aggregate_rate(1, 1, 0.0, 1)
+
+
+def test_shard_range_covers_and_balances():
+    from paper_2510_21213_gb300 import dist as pd
+
+    for n in (0, 1, 4, 56, 2081):
+        for ws in (1, 2, 3, 8):
+            parts = [pd.shard_range(n, ws, r) for r in range(ws)]
+            assert parts[0][0] == 0 and parts[-1][1] == n
+            assert all(parts[r][1] == parts[r + 1][0] for r in range(ws - 1))
+            sizes = [e - b for b, e in parts]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        pd.shard_range(10, 2, 2)
+
+
+def _sharded_worker(rank, ws, port, out):
+    os.environ.update({"WORLD_SIZE": str(ws), "RANK": str(rank), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import numpy as np
+
+    import oracle
+    from paper_2510_21213_gb300 import dist as pd
+    from paper_2510_21213_gb300 import inputs
+
+    ws_, rank_, _ = pd.init("gloo")
+    spec = inputs.tiny_system()
+    m = oracle.Mesh(spec.mesh.lo, spec.mesh.hi, spec.mesh.n, spec.mesh.p)
+    psi = inputs.orbitals(spec, oracle.node_coords(m), oracle.quad_weights(m))
+    K, eh, ex = pd.sharded_exchange(lambda b, e: oracle.exchange_partial(m, psi, b, e), psi.shape[0], ws_, rank_)
+    out[rank_] = (np.asarray(K).tolist(), eh, ex)
+    pd.finish()
+
+
+def test_sharded_exchange_on_two_gloo_ranks():
+    """One system's exchange build split over two CPU ranks (each computes its
+    share of the sources with the oracle) and reduced by all-reduce: the same
+    K, E_H and E_X as the whole build."""
+    import numpy as np
+
+    import oracle
+    from paper_2510_21213_gb300 import inputs
+
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_sharded_worker, args=(2, port, out), nprocs=2, start_method="spawn")
+        res = dict(out)
+    spec = inputs.tiny_system()
+    m = oracle.Mesh(spec.mesh.lo, spec.mesh.hi, spec.mesh.n, spec.mesh.p)
+    psi = inputs.orbitals(spec, oracle.node_coords(m), oracle.quad_weights(m))
+    ref = oracle.exchange_build(m, psi)
+    for r in (0, 1):
+        K, eh, ex = res[r]
+        K = np.asarray(K)
+        assert np.abs(K - ref["K"]).max() <= 1e-12 * np.abs(ref["K"]).max()
+        assert abs(eh - ref["E_H"]) <= 1e-12 * abs(ref["E_H"])
+        assert abs(ex - ref["E_X"]) <= 1e-12 * abs(ref["E_X"])
