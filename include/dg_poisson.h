@@ -202,6 +202,19 @@ int dg_exchange_build(dg_handle h, const double* psi_dev, int32_t N, double* K_h
 int dg_exchange_build_range(dg_handle h, const double* psi_dev, int32_t N, int64_t src_begin, int64_t src_end,
                             double* K_partial_host, double* E_H, dg_solve_stats* stats_host, void* cuda_stream);
 
+/* Adaptively compressed exchange operator of the handle's last whole
+ * dg_exchange_build (the compressed exchange the HF SCF of Sec. 7.2 applies;
+ * V_X of Sec. 2.3.1 eq. exchange on the occupied space): for m trial vectors
+ * U_dev [m][Nq] (device, FP64)
+ *     Y_dev = V_X^ACE U = -W K_s^-1 (W^T diag(W_q) U),  K_s = (K + K^T) / 2,
+ * with W_j = sum_s psi_s v_sj the build's exchange accumulation and K its
+ * exchange matrix; Y_dev [m][Nq] (device). V_X^ACE has rank N, is symmetric
+ * and negative semidefinite in the quadrature inner product and maps psi_i
+ * to -W_i = V_X psi_i. DG_ERR_INVALID_ARG if the handle has no whole build
+ * (a failed build or a dg_exchange_build_range call clears it) or N * m >
+ * 4096; DG_ERR_BREAKDOWN if K_s is not positive definite. */
+int dg_ace_apply(dg_handle h, const double* U_dev, int64_t m, double* Y_dev, void* cuda_stream);
+
 /* Exchange builds of nsys independent systems with their own meshes and
  * orbital counts (uneven sizes), as one call. meshes [nsys] (host), psi_devs
  * [nsys] device pointers to [Ns[i]][Nq_i], K_hosts [nsys] host pointers to

@@ -34,4 +34,5 @@ from .dg_oracle import (  # noqa: F401
     poisson,
     exchange_build,
     exchange_partial,
+    ace_apply,
 )

@@ -630,3 +630,17 @@ def exchange_build(mesh, psi, penalty_form=0, eps=0.125, method="auto", keep_pot
     if keep_potentials:
         out["v_pairs"] = vpair
     return out
+
+
+def ace_apply(build, Wq, U):
+    """Adaptively compressed exchange operator of an exchange build (the
+    compressed V_X of Sec. 2.3.1 eq. exchange that the HF SCF of Sec. 7.2
+    applies): V_X^ACE u = -W Ks^-1 (W^T diag(Wq) u), Ks = (K + K^T) / 2, with W
+    the build's exchange accumulation W_j = sum_s psi_s v_sj (= -V_X psi_j)
+    and K_ij = <psi_i, W_j>. U: [m, Nq]; returns [m, Nq]."""
+    W = np.asarray(build["W"], dtype=np.float64)
+    K = np.asarray(build["K"], dtype=np.float64)
+    Ks = 0.5 * (K + K.T)
+    C = W @ (np.asarray(U, dtype=np.float64) * Wq[None, :]).T  # [N, m]
+    Z = np.linalg.solve(Ks, C)
+    return -(W.T @ Z).T

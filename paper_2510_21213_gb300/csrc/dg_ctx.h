@@ -160,6 +160,11 @@ struct dg_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   dg::NNState nn;             // learned initial guess (DG_PREC_MIXED_LEARNED)
   dg::DevBuf dlift_op;        // fine-level LevelOp whose lift tables carry (sigma_c - sigma) (coarse guess)
+  // adaptively compressed exchange from the last whole exchange build: W (in
+  // Wacc) and K, valid while ace_N > 0
+  int ace_N = 0;
+  std::vector<double> ace_K;  // [N*N] row-major
+  dg::DevBuf ace_part, ace_C;
   ~dg_ctx() {
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);

@@ -1227,6 +1227,13 @@ static int exchange_build_range(dg_handle h, const double* psi, int32_t N, long 
     for (int i = 0; i < N; ++i) tr += K_host[(size_t)i * N + i];
     *E_X = -0.5 * tr;
   }
+  // a whole build leaves W (Wacc) and K for the compressed exchange operator
+  if (src_begin == 0 && src_end == nsrc_total && worst == DG_OK) {
+    h->ace_K.assign(K_host, K_host + (size_t)N * N);
+    h->ace_N = N;
+  } else {
+    h->ace_N = 0;
+  }
   account(h);
   return worst;
 }

@@ -113,6 +113,8 @@ def load():
     lib.dg_exchange_build.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp]
     lib.dg_exchange_build_range.argtypes = [vp, vp, C.c_int32, C.c_int64, C.c_int64, vp, vp, vp, vp]
     lib.dg_exchange_build_range.restype = C.c_int
+    lib.dg_ace_apply.argtypes = [vp, vp, C.c_int64, vp, vp]
+    lib.dg_ace_apply.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -283,6 +285,17 @@ def dg_exchange_build_range(h, psi, src_begin, src_end, stream=None, allow_uncon
                                           _stream_ptr(stream))
     _check(code, "dg_exchange_build_range", h, allow)
     return K, eh.value, _stats_list(st[:int(src_end) - int(src_begin)])
+
+
+def dg_ace_apply(h, U, stream=None):
+    """Compressed exchange operator of the last whole exchange build applied to
+    U (CUDA float64 [m, Nq]); returns V_X^ACE U, same shape."""
+    import torch
+
+    Y = torch.empty_like(U)
+    _check(load().dg_ace_apply(h, _dev_ptr(U, torch.float64), U.shape[0], _dev_ptr(Y, torch.float64),
+                               _stream_ptr(stream)), "dg_ace_apply", h)
+    return Y
 
 
 def dg_apply_operator(h, u, level=0, out=None, stream=None):

@@ -54,3 +54,35 @@ def test_ranges_add_up_to_the_whole_build(dgx, precision):
     with pytest.raises(dgx.DGError):
         dgx.dg_exchange_build_range(s.h, psi, 0, total + 1)
     s.close()
+
+
+def test_ace_operator_vs_oracle(dgx):
+    """dg_ace_apply after a whole build equals the oracle's compressed exchange
+    operator of the oracle's build (FP64, 1e-9), maps psi_i to -W_i, and is
+    refused without a whole build."""
+    import oracle
+
+    spec = inputs.chain_system(n=2, p=4, n_orb=3)
+    m = spec.mesh
+    s = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, rtol=1e-12)
+    xyz, w = s.node_coords()
+    psi_h = inputs.orbitals(spec, xyz, w)
+    psi = torch.tensor(psi_h, device="cuda")
+    U = torch.tensor(np.random.default_rng(8).standard_normal((5, s.Nq)), device="cuda")
+    with pytest.raises(dgx.DGError):  # no build yet
+        dgx.dg_ace_apply(s.h, U)
+    s.exchange_build(psi)
+    om = oracle.Mesh(m.lo, m.hi, m.n, m.p)
+    ref = oracle.exchange_build(om, psi_h, method="fdm")
+    Wq = oracle.quad_weights(om)
+    got = dgx.dg_ace_apply(s.h, U).cpu().numpy()
+    want = oracle.ace_apply(ref, Wq, U.cpu().numpy())
+    assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
+    # exact on the occupied orbitals up to the discretisation-level asymmetry of K
+    asym = np.abs(ref["K"] - ref["K"].T).max() / np.abs(ref["K"]).max()
+    gp = dgx.dg_ace_apply(s.h, psi).cpu().numpy()
+    assert np.abs(gp + ref["W"]).max() <= (1e-9 + 10 * asym) * np.abs(ref["W"]).max()
+    dgx.dg_exchange_build_range(s.h, psi, 0, 2)  # a partial build clears the operator
+    with pytest.raises(dgx.DGError):
+        dgx.dg_ace_apply(s.h, U)
+    s.close()

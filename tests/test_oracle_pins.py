@@ -297,3 +297,28 @@ def test_gaussian_sum_route_matches_direct_quadrature():
     c, a, err = oracle.gauss_sum_1_over_r(0.03, 42.0, 1e-10)
     r = np.exp(np.linspace(math.log(0.03), math.log(42.0), 777))
     assert np.abs((np.exp(-np.outer(r * r, a)) @ c) * r - 1.0).max() <= 1e-10 and err <= 1e-10
+
+
+def test_ace_operator_pins():
+    """The compressed exchange operator: exact on the occupied orbitals
+    (V_X psi_i = -W_i), symmetric and negative semidefinite in the quadrature
+    inner product, and zero on the W_q-orthogonal complement of span(W)."""
+    spec = inputs.chain_system(n=2, p=4, n_orb=3)
+    m = oracle.Mesh(spec.mesh.lo, spec.mesh.hi, spec.mesh.n, spec.mesh.p)
+    Wq = oracle.quad_weights(m)
+    psi = inputs.orbitals(spec, oracle.node_coords(m), Wq)
+    build = oracle.exchange_build(m, psi)
+    W, K = build["W"], build["K"]
+    asym = np.abs(K - K.T).max() / np.abs(K).max()
+    got = oracle.ace_apply(build, Wq, psi)
+    assert np.abs(got + W).max() <= (1e-10 + 10 * asym) * np.abs(W).max()
+    rng = np.random.default_rng(4)
+    U = rng.standard_normal((4, Wq.size))
+    AU = oracle.ace_apply(build, Wq, U)
+    G = (U * Wq) @ AU.T  # <u_a, A u_b>
+    assert np.abs(G - G.T).max() <= 1e-12 * np.abs(G).max()
+    assert np.linalg.eigvalsh(0.5 * (G + G.T)).max() <= 1e-12 * np.abs(G).max()
+    # component of U orthogonal (in the W_q inner product) to span(W): mapped to zero
+    Gw = (W * Wq) @ W.T
+    Up = U - (np.linalg.solve(Gw, (W * Wq) @ U.T)).T @ W
+    assert np.abs(oracle.ace_apply(build, Wq, Up)).max() <= 1e-10 * np.abs(AU).max()
