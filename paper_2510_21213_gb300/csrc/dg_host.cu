@@ -1135,6 +1135,7 @@ int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_s
 // E_H is set when the range holds source 0 (else 0), E_X = -1/2 tr K_host.
 static int exchange_build_range(dg_handle h, const double* psi, int32_t N, long long src_begin, long long src_end,
                                 double* K_host, double* E_H, double* E_X, dg_solve_stats* stats, void* stream) {
+  h->ace_N = 0;  // W and K are rewritten below; valid again only after a whole, successful build
   cudaStream_t us = (cudaStream_t)stream;
   DG_CK(cudaEventRecord(h->ev_in, us));
   DG_CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
