@@ -115,6 +115,7 @@ typedef struct {
   int32_t coarse_penalty; /* 0: each multigrid level uses the penalty of its own p and h;
                              1: every level uses the fine level's penalty (Galerkin-consistent hierarchy) */
   int32_t coarse_smoother_degree; /* Chebyshev degree on the levels below the finest (0 = smoother_degree) */
+  int32_t p1_smoother;   /* smoother of the degree-1 levels below the finest: -1 = as `smoother`, else DG_SMOOTH_* */
 } dg_solver_opts;
 
 typedef struct {

@@ -890,6 +890,7 @@ void dg_default_opts(dg_solver_opts* o) {
   o->verbose = 0;
   o->coarse_penalty = 0;
   o->coarse_smoother_degree = 0;
+  o->p1_smoother = -1;
 }
 
 const char* dg_error_string(int status) {
@@ -930,7 +931,7 @@ int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_ha
       o.smoother_degree < 1 || o.smoother_degree > 16 || o.batch < 0 ||
       (o.smoother != DG_SMOOTH_JACOBI && o.smoother != DG_SMOOTH_SCHWARZ) ||
       (o.coarse_penalty != 0 && o.coarse_penalty != 1) || o.coarse_smoother_degree < 0 ||
-      o.coarse_smoother_degree > 16)
+      o.coarse_smoother_degree > 16 || o.p1_smoother < -1 || o.p1_smoother > 1)
     return DG_ERR_INVALID_ARG;
   if (o.cheb_range <= 1.0) o.cheb_range = 10.0;
   if (o.inner_rtol <= 0.0) o.inner_rtol = 1e-4;

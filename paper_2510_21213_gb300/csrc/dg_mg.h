@@ -24,7 +24,8 @@ struct MG {
     LevelWork& W = w->lev[l];
     T* res = W.res.as<T>();
     T* d = W.d.as<T>();
-    const bool sw = h->opts.smoother == DG_SMOOTH_SCHWARZ;
+    const bool sw = (l > 0 && L.op.p == 1 && h->opts.p1_smoother >= 0 ? h->opts.p1_smoother : h->opts.smoother) ==
+                    DG_SMOOTH_SCHWARZ;
     // sw: the smoother preconditioner is M_S (z = M_S res), else D^-1 (fused)
     const T* invD = sw ? nullptr : W.invD.as<T>();
     const long long Nq = L.op.Nq;

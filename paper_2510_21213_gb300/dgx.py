@@ -58,6 +58,7 @@ class dg_solver_opts(C.Structure):
         ("verbose", C.c_int32),
         ("coarse_penalty", C.c_int32),
         ("coarse_smoother_degree", C.c_int32),
+        ("p1_smoother", C.c_int32),
     ]
 
 
