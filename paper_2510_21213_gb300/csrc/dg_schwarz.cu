@@ -40,32 +40,50 @@ __host__ __device__ inline int sw_axis_off(const LevelOp* op, int d, int stride)
 #define DG_SW_THREADS 256  // thread budget per block
 #endif
 #ifndef DG_SW_SMEM
-#define DG_SW_SMEM 32768   // shared-memory budget of the patch slots (bytes)
+#define DG_SW_SMEM 36864   // shared-memory budget of the patch slots (bytes)
 #endif
+// Padded FP32 patch layout in shared memory: node (i, j, k) of a patch at
+// i + MP j + SY k, patch slots SE apart. The plane and slot strides were
+// chosen by counting shared-memory wavefronts of the six 1-D passes for every
+// degree (lanes of a warp on lines of one or two patches): the unpadded layout
+// puts the y lines MP^2 words apart, a 2-way bank conflict for most MP.
+__host__ __device__ constexpr int sw_pad_sy(int N1) {
+  return N1 == 2 ? 16 : N1 == 3 ? 39 : N1 == 4 ? 39 : N1 == 6 ? 73 : N1 == 7 ? 85 : N1 == 8 ? 109
+                                                                                   : (N1 + 2) * (N1 + 2);
+}
+__host__ __device__ constexpr int sw_pad_se(int N1) {
+  return N1 == 2 ? 69 : N1 == 3 ? 201 : N1 == 4 ? 238 : N1 == 6 ? 598 : N1 == 7 ? 795 : N1 == 8 ? 1106
+                                                      : N1 == 9 ? 1332 : (N1 + 2) * (N1 + 2) * (N1 + 2);
+}
+
 template <typename T, int N1>
 struct SwCfg {
   static constexpr int MP = N1 + 2;
+  // plane and slot strides of the shared patch buffer (FP64 keeps the dense layout)
+  static constexpr int SY = sizeof(T) == 4 ? sw_pad_sy(N1) : MP * MP;
+  static constexpr int SE = sizeof(T) == 4 ? sw_pad_se(N1) : MP * MP * MP;
+  static_assert(SY >= MP * MP && SE >= MP * SY, "patch layout overlaps");
   static constexpr int LINES = MP * MP;
   // FP32: two or three lines per thread (shared-memory traffic per FMA / LPT);
   // FP64 is bound by the FP64 pipe, one line per thread keeps registers in check
   static constexpr int LPT = sizeof(T) == 4 ? DG_SW_LPT_OF(N1) : 1;
   static constexpr int TPE = (LINES + LPT - 1) / LPT;  // threads per element
   static constexpr int MINB = sizeof(T) == 4 ? DG_SW_MINB32 : 1;  // resident blocks per SM asked of ptxas
-  static constexpr int PER_ELEM = (MP * MP * MP + 3 * MP * MP + 3 * MP) * (int)sizeof(T);
+  static constexpr int PER_ELEM = (SE + 3 * MP * MP + 3 * MP) * (int)sizeof(T);
   static constexpr int EPB_T = DG_SW_THREADS / TPE < 1 ? 1 : DG_SW_THREADS / TPE;
   static constexpr int EPB_S = DG_SW_SMEM / PER_ELEM < 1 ? 1 : DG_SW_SMEM / PER_ELEM;
   static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;
   static constexpr int THREADS = EPB * TPE;
 };
 
-// One 1-D pass over up to three lines l = lt + TPE s of one patch.
-// dir 0: x lines (j, k) stride 1; dir 1: y lines (i, k) stride MP; dir 2: z
-// lines (i, j) stride MP^2. Forward: v[q] <- sum_i S[i][q] v[i]; backward:
+// One 1-D pass over the lines l = lt + TPE s (s < LPT) of one patch, node
+// (i, j, k) at i + MP j + SY k. dir 0: x lines (j, k) stride 1; dir 1: y lines
+// (i, k) stride MP; dir 2: z lines (i, j) stride SY. Forward: v[q] <- sum_i S[i][q] v[i]; backward:
 // v[i] <- sum_q S[i][q] v[q].
-template <typename T, int MP, int TPE, int LPT, int DIR, bool BACKWARD>
+template <typename T, int MP, int SY, int TPE, int LPT, int DIR, bool BACKWARD>
 __device__ __forceinline__ void sw_pass3(T* __restrict__ buf, const T* __restrict__ S, int lt) {
   constexpr int MP2 = MP * MP;
-  constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? MP : MP2);
+  constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? MP : SY);
   int base[LPT];
   bool ok[LPT];
 #pragma unroll
@@ -73,7 +91,7 @@ __device__ __forceinline__ void sw_pass3(T* __restrict__ buf, const T* __restric
     const int l = lt + TPE * s;
     ok[s] = l < MP2;
     const int l1 = l % MP, l2 = l / MP;
-    base[s] = ok[s] ? (DIR == 0 ? (l1 + MP * l2) * MP : (DIR == 1 ? l1 + MP2 * l2 : l1 + MP * l2)) : 0;
+    base[s] = ok[s] ? (DIR == 0 ? l1 * MP + l2 * SY : (DIR == 1 ? l1 + SY * l2 : l1 + MP * l2)) : 0;
   }
   if (!BACKWARD) {
     // o[q] = sum_i S[i][q] v[i]: inputs streamed row by row, outputs in registers
@@ -101,29 +119,47 @@ __device__ __forceinline__ void sw_pass3(T* __restrict__ buf, const T* __restric
         for (int q = 0; q < MP; ++q) buf[base[s] + q * stride] = o[s][q];
       }
   } else {
-    // o[i] = sum_q S[i][q] v[q]: inputs in registers, each output written when done
+    // o[i] = sum_q S[i][q] v[q]: inputs in registers, IB outputs per line at
+    // a time (LPT * IB independent sums in q order), each written when done
+    constexpr int IB = MP % 3 == 0 ? 3 : 2;
     T v[LPT][MP];
 #pragma unroll
     for (int s = 0; s < LPT; ++s)
 #pragma unroll
       for (int q = 0; q < MP; ++q) v[s][q] = buf[base[s] + q * stride];
 #pragma unroll 1
-    for (int i = 0; i < MP; ++i) {
-      T acc[LPT];
+    for (int i0 = 0; i0 < MP; i0 += IB) {
+      T acc[IB][LPT];
 #pragma unroll
-      for (int s = 0; s < LPT; ++s) acc[s] = (T)0;
+      for (int ib = 0; ib < IB; ++ib)
+#pragma unroll
+        for (int s = 0; s < LPT; ++s) acc[ib][s] = (T)0;
+      const int nb = MP - i0 < IB ? MP - i0 : IB;
 #pragma unroll
       for (int q = 0; q < MP; ++q) {
-        const T sv = S[i * MP + q];
 #pragma unroll
-        for (int s = 0; s < LPT; ++s) acc[s] += sv * v[s][q];
+        for (int ib = 0; ib < IB; ++ib) {
+          const T sv = ib < nb ? S[(i0 + ib) * MP + q] : (T)0;
+#pragma unroll
+          for (int s = 0; s < LPT; ++s) acc[ib][s] += sv * v[s][q];
+        }
       }
 #pragma unroll
-      for (int s = 0; s < LPT; ++s)
-        if (ok[s]) buf[base[s] + i * stride] = acc[s];
+      for (int ib = 0; ib < IB; ++ib)
+        if (ib < nb) {
+#pragma unroll
+          for (int s = 0; s < LPT; ++s)
+            if (ok[s]) buf[base[s] + (i0 + ib) * stride] = acc[ib][s];
+        }
     }
   }
 }
+
+// Division by the patch eigenvalue sum: FP32 takes the fast approximate
+// quotient (within 2 ulp; the sums are positive and far from the range
+// limits), FP64 the exact one.
+__device__ __forceinline__ float sw_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sw_div(double a, double b) { return a / b; }
 
 template <typename T, int N1>
 __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
@@ -131,28 +167,39 @@ __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
                     T* __restrict__ zp, const int* __restrict__ act, int nact) {
   using C = SwCfg<T, N1>;
   constexpr int MP = C::MP, MP2 = MP * MP, MP3 = MP * MP * MP, NPE = N1 * N1 * N1, STR = 2 + MP2 + MP;
+  constexpr int SY = C::SY, SE = C::SE;
   constexpr int EPB = C::EPB, NT = C::THREADS, TPE = C::TPE, LPT = C::LPT;
   __shared__ T sS[EPB][3][MP2];
   __shared__ T sL[EPB][3][MP];
-  __shared__ T buf[EPB][MP3];
+  __shared__ T buf[EPB][SE];
   __shared__ int sm[EPB][3], soL[EPB][3];
+  __shared__ int spos[EPB][4];  // element of each slot (-1: none) and its (x, y, z) position
+  __shared__ long long srhs[EPB];
   const int nx = op->n[0], ny = op->n[1];
   const int E = op->E;
   const long long Nq = op->Nq;
+  // the runtime divisions (item -> source, element -> position) once per slot
+  if (threadIdx.x < EPB) {
+    const long long it = (long long)blockIdx.x * EPB + threadIdx.x;
+    const bool v = it < (long long)nact * E;
+    const int ee = v ? (int)(it % E) : 0;
+    spos[threadIdx.x][0] = v ? ee : -1;
+    spos[threadIdx.x][1] = ee % nx;
+    spos[threadIdx.x][2] = (ee / nx) % ny;
+    spos[threadIdx.x][3] = ee / (nx * ny);
+    srhs[threadIdx.x] = v ? act[it / E] : 0;
+  }
+  __syncthreads();
   const int slot = threadIdx.x / TPE, lt = threadIdx.x % TPE;
-  const long long items = (long long)nact * E;
-  const long long item = (long long)blockIdx.x * EPB + slot;
-  const bool valid = item < items;
-  const int e = valid ? (int)(item % E) : 0;
-  const long long rhs = valid ? act[item / E] : 0;
-  const int pos[3] = {e % nx, (e / nx) % ny, e / (nx * ny)};
+  const bool valid = spos[slot][0] >= 0;
+  const int e = valid ? spos[slot][0] : 0;
+  const long long rhs = srhs[slot];
+  const int pos[3] = {spos[slot][1], spos[slot][2], spos[slot][3]};
   // patch tables of the EPB elements
   for (int t = threadIdx.x; t < EPB * 3 * STR; t += NT) {
     const int sl = t / (3 * STR), rem = t % (3 * STR);
     const int d = rem / STR, k = rem % STR;
-    const long long it = (long long)blockIdx.x * EPB + sl;
-    const int ee = it < items ? (int)(it % E) : 0;
-    const int pd = d == 0 ? ee % nx : (d == 1 ? (ee / nx) % ny : ee / (nx * ny));
+    const int pd = spos[sl][1 + d];
     const double* tb = tabs + sw_axis_off(op, d, STR) + (long long)pd * STR;
     if (k < 2) {
       if (k == 0)
@@ -177,7 +224,7 @@ __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
     const T* rr = r + rhs * Nq;
     for (int row = lt; row < MP2; row += TPE) {
       const int j = row % MP, k = row / MP;
-      T* brow = b + row * MP;
+      T* brow = b + j * MP + k * SY;
       if (j >= my || k >= mz) {
 #pragma unroll
         for (int i = 0; i < MP; ++i) brow[i] = (T)0;
@@ -197,14 +244,14 @@ __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
       for (; i < MP; ++i) brow[i] = (T)0;
     }
   } else {
-    for (int t = lt; t < MP3; t += TPE) b[t] = (T)0;
+    for (int t = lt; t < SE; t += TPE) b[t] = (T)0;
   }
   __syncthreads();
-  sw_pass3<T, MP, TPE, LPT, 0, false>(b, sS[slot][0], lt);
+  sw_pass3<T, MP, SY, TPE, LPT, 0, false>(b, sS[slot][0], lt);
   __syncthreads();
-  sw_pass3<T, MP, TPE, LPT, 1, false>(b, sS[slot][1], lt);
+  sw_pass3<T, MP, SY, TPE, LPT, 1, false>(b, sS[slot][1], lt);
   __syncthreads();
-  sw_pass3<T, MP, TPE, LPT, 2, false>(b, sS[slot][2], lt);
+  sw_pass3<T, MP, SY, TPE, LPT, 2, false>(b, sS[slot][2], lt);
   // scale by 1 / (lx + ly + lz) along this thread's z lines (i, j)
 #pragma unroll
   for (int s = 0; s < LPT; ++s) {
@@ -213,21 +260,21 @@ __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
       const int l1 = l % MP, l2 = l / MP;
 #pragma unroll
       for (int k = 0; k < MP; ++k) {
-        const int t = l + MP2 * k;
+        const int t = l + SY * k;
         const bool in = l1 < mx && l2 < my && k < mz;
-        b[t] = in ? b[t] / (sL[slot][0][l1] + sL[slot][1][l2] + sL[slot][2][k]) : (T)0;
+        b[t] = in ? sw_div(b[t], sL[slot][0][l1] + sL[slot][1][l2] + sL[slot][2][k]) : (T)0;
       }
     }
   }
-  sw_pass3<T, MP, TPE, LPT, 2, true>(b, sS[slot][2], lt);
+  sw_pass3<T, MP, SY, TPE, LPT, 2, true>(b, sS[slot][2], lt);
   __syncthreads();
-  sw_pass3<T, MP, TPE, LPT, 1, true>(b, sS[slot][1], lt);
+  sw_pass3<T, MP, SY, TPE, LPT, 1, true>(b, sS[slot][1], lt);
   __syncthreads();
-  sw_pass3<T, MP, TPE, LPT, 0, true>(b, sS[slot][0], lt);
+  sw_pass3<T, MP, SY, TPE, LPT, 0, true>(b, sS[slot][0], lt);
   __syncthreads();
   if (!valid) return;
   T* out = zp + (rhs * E + e) * (long long)MP3;
-  for (int t = lt; t < MP3; t += TPE) out[t] = b[t];
+  for (int t = lt; t < MP3; t += TPE) out[t] = b[t % MP2 + SY * (t / MP2)];
 }
 
 // mode 0: z = M r; 1: d = c1 M r, x = d; 2: d = c1 M r, x += d; 3: d = c1 d + c2 M r, x += d
@@ -245,8 +292,10 @@ __global__ void __launch_bounds__(N1 * N1 * N1 < 64 ? 64 : N1 * N1 * N1)
   const int loc = threadIdx.x;
   if (loc >= NPE) return;
   const int a = loc % N1, bb = (loc / N1) % N1, c = loc / (N1 * N1);
-  for (int e = blockIdx.x; e < E; e += gridDim.x) {
-    const int ex = e % nx, exy = e / nx, ey = exy % ny, ez = exy / ny;
+  // element position, advanced by the grid stride without runtime divisions
+  const int g = gridDim.x, sx = g % nx, sy = (g / nx) % ny, sz = g / (nx * ny);
+  int ex = blockIdx.x % nx, ey = (blockIdx.x / nx) % ny, ez = blockIdx.x / (nx * ny);
+  for (int e = blockIdx.x; e < E; e += g) {
     const int ix = a + (ex > 0), iy = bb + (ey > 0), iz = c + (ez > 0);
     // neighbour along each axis whose patch also covers this node, if any
     int dx = 0, jx = 0, dy = 0, jy = 0, dz = 0, jz = 0;
@@ -292,6 +341,13 @@ __global__ void __launch_bounds__(N1 * N1 * N1 < 64 ? 64 : N1 * N1 * N1)
       z[gi] = v;
       x[gi] += v;
     }
+    ex += sx;
+    int carry = ex >= nx;
+    ex -= carry ? nx : 0;
+    ey += sy + carry;
+    carry = ey >= ny;
+    ey -= carry ? ny : 0;
+    ez += sz + carry;
   }
 }
 
