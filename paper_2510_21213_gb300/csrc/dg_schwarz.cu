@@ -33,6 +33,9 @@ __host__ __device__ inline int sw_axis_off(const LevelOp* op, int d, int stride)
 #else
 #define DG_SW_LPT_OF(N1) ((N1) == 2 || (N1) >= 8 ? 2 : 3)
 #endif
+#ifndef DG_GATHER_WAVE
+#define DG_GATHER_WAVE 8   // gather grid: at most this many blocks per SM per source list (0: one block per element)
+#endif
 #ifndef DG_SW_MINB32
 #define DG_SW_MINB32 4     // resident blocks per SM asked of ptxas, FP32
 #endif
@@ -277,25 +280,34 @@ __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
   for (int t = lt; t < MP3; t += TPE) out[t] = b[t % MP2 + SY * (t / MP2)];
 }
 
+// Gather block shape: GE elements of NPE nodes per block (several small
+// elements per block on the coarse levels), one thread per node.
+template <int N1>
+struct GatherCfg {
+  static constexpr int NPE = N1 * N1 * N1;
+  static constexpr int GE = 256 / NPE < 1 ? 1 : 256 / NPE;
+  static constexpr int THREADS = GE * NPE;
+};
+
 // mode 0: z = M r; 1: d = c1 M r, x = d; 2: d = c1 M r, x += d; 3: d = c1 d + c2 M r, x += d
-// (d is passed in z). One block per element (grid-stride), one thread per node.
+// (d is passed in z). GE elements per block and iteration (grid-stride), one thread per node.
 template <typename T, int N1, int MODE>
-__global__ void __launch_bounds__(N1 * N1 * N1 < 64 ? 64 : N1 * N1 * N1)
+__global__ void __launch_bounds__(GatherCfg<N1>::THREADS)
     k_schwarz_gather(const LevelOp* __restrict__ op, const T* __restrict__ zp, T* __restrict__ z, T* __restrict__ x,
                      T c1, T c2, const int* __restrict__ act) {
-  constexpr int MP = N1 + 2, MP3 = MP * MP * MP, NPE = N1 * N1 * N1;
+  constexpr int MP = N1 + 2, MP3 = MP * MP * MP, NPE = N1 * N1 * N1, GE = GatherCfg<N1>::GE;
   const int nx = op->n[0], ny = op->n[1], nz = op->n[2];
   const int E = op->E;
   const long long Nq = op->Nq;
   const long long rhs = act[blockIdx.y];
   const T* zr = zp + rhs * E * (long long)MP3;
-  const int loc = threadIdx.x;
-  if (loc >= NPE) return;
+  const int slot = threadIdx.x / NPE, loc = threadIdx.x % NPE;
   const int a = loc % N1, bb = (loc / N1) % N1, c = loc / (N1 * N1);
   // element position, advanced by the grid stride without runtime divisions
-  const int g = gridDim.x, sx = g % nx, sy = (g / nx) % ny, sz = g / (nx * ny);
-  int ex = blockIdx.x % nx, ey = (blockIdx.x / nx) % ny, ez = blockIdx.x / (nx * ny);
-  for (int e = blockIdx.x; e < E; e += g) {
+  const int g = gridDim.x * GE, sx = g % nx, sy = (g / nx) % ny, sz = g / (nx * ny);
+  const int e0 = blockIdx.x * GE + slot;
+  int ex = e0 % nx, ey = (e0 / nx) % ny, ez = e0 / (nx * ny);
+  for (int e = e0; e < E; e += g) {
     const int ix = a + (ex > 0), iy = bb + (ey > 0), iz = c + (ez > 0);
     // neighbour along each axis whose patch also covers this node, if any
     int dx = 0, jx = 0, dy = 0, jy = 0, dz = 0, jz = 0;
@@ -365,11 +377,12 @@ static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const doub
 #endif
   count_launch();
   k_schwarz_patch<T, N1><<<(unsigned)((items + C::EPB - 1) / C::EPB), C::THREADS, 0, s>>>(dop, tabs, r, zp, act, nact);
-  constexpr int NPE = N1 * N1 * N1;
-  constexpr int GT = NPE < 64 ? 64 : NPE;
-  long long gx = hop.E;
-  const long long cap = 152LL * 8 / (nact > 0 ? nact : 1) + 1;
+  constexpr int GT = GatherCfg<N1>::THREADS;
+  long long gx = (hop.E + GatherCfg<N1>::GE - 1) / GatherCfg<N1>::GE;
+#if DG_GATHER_WAVE > 0
+  const long long cap = 152LL * DG_GATHER_WAVE / (nact > 0 ? nact : 1) + 1;
   if (gx > cap) gx = cap;
+#endif
   const dim3 grid((unsigned)gx, (unsigned)nact);
   count_launch();
   switch (mode) {

@@ -150,10 +150,20 @@ __global__ void k_dot_partial(const T* __restrict__ u, const T* __restrict__ v, 
                               double* __restrict__ part, long long Nq, const int* __restrict__ act) {
   const long long off = (long long)act[blockIdx.y] * Nq;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Nq; i += (long long)gridDim.x * blockDim.x) {
-    double t = (double)u[off + i] * (double)v[off + i];
-    if (w) t *= w[i];
-    acc += t;
+  if (sizeof(T) == 4 && w == nullptr) {
+    // FP32 vectors (the inner solve): each thread's few terms (about 16 when
+    // Nq / 4096 blocks run) summed by FP32 FMA, then FP64 across threads; the
+    // FP64 pipe would otherwise bound the kernel
+    float accf = 0.0f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Nq; i += (long long)gridDim.x * blockDim.x)
+      accf = fmaf((float)u[off + i], (float)v[off + i], accf);
+    acc = (double)accf;
+  } else {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Nq; i += (long long)gridDim.x * blockDim.x) {
+      double t = (double)u[off + i] * (double)v[off + i];
+      if (w) t *= w[i];
+      acc += t;
+    }
   }
   __shared__ double sh[VT / 32];
   acc = warp_sum(acc);
@@ -313,11 +323,258 @@ __global__ void k_restrict(const TransferOp* __restrict__ tr, const T* __restric
   for (int t = threadIdx.x; t < npc; t += blockDim.x) rc[rhs * Nqc + (long long)ec * npc + t] = (T)so[t];
 }
 
+// Fixed-size transfers: the degree pairs of the hierarchy (p -> floor(p/2),
+// and the degree-1 h-transfer) compiled with their sizes, several coarse
+// elements per block, arithmetic in the vector precision T. The per-node
+// summation order is that of the generic kernels above (stage by stage, terms
+// in index order), so the FP64 results are the same.
+template <int N1F, int N1C>
+struct PXferCfg {
+  static constexpr int NPC = N1C * N1C * N1C, NPF = N1F * N1F * N1F;
+  static constexpr int EPB = 1024 / NPF < 1 ? 1 : 1024 / NPF;  // coarse elements per block
+  static constexpr int THREADS = 256;
+};
+
+// p-transfer prolongation, xf += P xc: the fine element is the coarse element.
+template <typename T, int N1F, int N1C>
+__global__ void __launch_bounds__(256) k_prolong_p(const TransferOp* __restrict__ tr, const T* __restrict__ xc,
+                                                   T* __restrict__ xf, int E, long long Nqc, long long Nqf,
+                                                   const int* __restrict__ act) {
+  using C = PXferCfg<N1F, N1C>;
+  constexpr int NPC = C::NPC, NPF = C::NPF, EPB = C::EPB, NT = C::THREADS;
+  constexpr int S1 = N1C * N1C * N1F, S2 = N1C * N1F * N1F;
+  __shared__ T sI[N1F * N1C];
+  __shared__ T sc[EPB * NPC];
+  __shared__ T s1[EPB * S1];
+  __shared__ T s2[EPB * S2];
+  const long long rhs = act[blockIdx.y];
+  const int e0 = blockIdx.x * EPB;
+  const int ne = E - e0 < EPB ? E - e0 : EPB;
+  for (int i = threadIdx.x; i < N1F * N1C; i += NT) sI[i] = (T)tr->I[0][i];
+  const T* src = xc + rhs * Nqc + (long long)e0 * NPC;
+  for (int t = threadIdx.x; t < ne * NPC; t += NT) sc[t] = src[t];
+  __syncthreads();
+  // x: s1[el][k][j][a] = sum_i I[a,i] c[el][k][j][i]
+  for (int t = threadIdx.x; t < ne * S1; t += NT) {
+    const int el = t / S1, r = t % S1, a = r % N1F, jk = r / N1F;
+    T acc = (T)0;
+#pragma unroll
+    for (int i = 0; i < N1C; ++i) acc += sI[a * N1C + i] * sc[el * NPC + jk * N1C + i];
+    s1[t] = acc;
+  }
+  __syncthreads();
+  // y: s2[el][k][b][a] = sum_j I[b,j] s1[el][k][j][a]
+  for (int t = threadIdx.x; t < ne * S2; t += NT) {
+    const int el = t / S2, r = t % S2, a = r % N1F, b = (r / N1F) % N1F, kk = r / (N1F * N1F);
+    T acc = (T)0;
+#pragma unroll
+    for (int j = 0; j < N1C; ++j) acc += sI[b * N1C + j] * s1[el * S1 + (kk * N1C + j) * N1F + a];
+    s2[t] = acc;
+  }
+  __syncthreads();
+  // z, added into the fine elements (contiguous: same element order)
+  T* dst = xf + rhs * Nqf + (long long)e0 * NPF;
+  for (int t = threadIdx.x; t < ne * NPF; t += NT) {
+    const int el = t / NPF, r = t % NPF, ab = r % (N1F * N1F), c = r / (N1F * N1F);
+    T acc = (T)0;
+#pragma unroll
+    for (int kk = 0; kk < N1C; ++kk) acc += sI[c * N1C + kk] * s2[el * S2 + kk * N1F * N1F + ab];
+    dst[t] = dst[t] + acc;
+  }
+}
+
+// p-transfer restriction, rc = P^T rf.
+template <typename T, int N1F, int N1C>
+__global__ void __launch_bounds__(256) k_restrict_p(const TransferOp* __restrict__ tr, const T* __restrict__ rf,
+                                                    T* __restrict__ rc, int E, long long Nqc, long long Nqf,
+                                                    const int* __restrict__ act) {
+  using C = PXferCfg<N1F, N1C>;
+  constexpr int NPC = C::NPC, NPF = C::NPF, EPB = C::EPB, NT = C::THREADS;
+  constexpr int S1 = N1F * N1F * N1C, S2 = N1F * N1C * N1C;
+  __shared__ T sI[N1F * N1C];
+  __shared__ T sf[EPB * NPF];
+  __shared__ T s1[EPB * S1];
+  __shared__ T s2[EPB * S2];
+  const long long rhs = act[blockIdx.y];
+  const int e0 = blockIdx.x * EPB;
+  const int ne = E - e0 < EPB ? E - e0 : EPB;
+  for (int i = threadIdx.x; i < N1F * N1C; i += NT) sI[i] = (T)tr->I[0][i];
+  const T* src = rf + rhs * Nqf + (long long)e0 * NPF;
+  for (int t = threadIdx.x; t < ne * NPF; t += NT) sf[t] = src[t];
+  __syncthreads();
+  // x^T: s1[el][c][b][i] = sum_a I[a,i] f[el][c][b][a]
+  for (int t = threadIdx.x; t < ne * S1; t += NT) {
+    const int el = t / S1, r = t % S1, i = r % N1C, bc = r / N1C;
+    T acc = (T)0;
+#pragma unroll
+    for (int a = 0; a < N1F; ++a) acc += sI[a * N1C + i] * sf[el * NPF + bc * N1F + a];
+    s1[t] = acc;
+  }
+  __syncthreads();
+  // y^T: s2[el][c][j][i] = sum_b I[b,j] s1[el][c][b][i]
+  for (int t = threadIdx.x; t < ne * S2; t += NT) {
+    const int el = t / S2, r = t % S2, i = r % N1C, j = (r / N1C) % N1C, c = r / (N1C * N1C);
+    T acc = (T)0;
+#pragma unroll
+    for (int b = 0; b < N1F; ++b) acc += sI[b * N1C + j] * s1[el * S1 + (c * N1F + b) * N1C + i];
+    s2[t] = acc;
+  }
+  __syncthreads();
+  // z^T: rc[el][k][j][i] = sum_c I[c,k] s2[el][c][j][i]
+  T* dst = rc + rhs * Nqc + (long long)e0 * NPC;
+  for (int t = threadIdx.x; t < ne * NPC; t += NT) {
+    const int el = t / NPC, r = t % NPC, ji = r % (N1C * N1C), kk = r / (N1C * N1C);
+    T acc = (T)0;
+#pragma unroll
+    for (int c = 0; c < N1F; ++c) acc += sI[c * N1C + kk] * s2[el * S2 + c * N1C * N1C + ji];
+    dst[t] = acc;
+  }
+}
+
+// Degree-1 h-transfer prolongation: one thread per fine node, 4 coarse
+// elements (8 children of 8 nodes each) per block of 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_h(const TransferOp* __restrict__ tr, const T* __restrict__ xc,
+                                                   T* __restrict__ xf, int nxc, int nyc, int E, long long Nqc,
+                                                   long long Nqf, const int* __restrict__ act) {
+  __shared__ T sI[2][4];
+  const long long rhs = act[blockIdx.y];
+  if (threadIdx.x < 8) sI[threadIdx.x >> 2][threadIdx.x & 3] = (T)tr->I[threadIdx.x >> 2][threadIdx.x & 3];
+  __syncthreads();
+  const int ec = blockIdx.x * 4 + (threadIdx.x >> 6);
+  if (ec >= E) return;
+  const int ch = (threadIdx.x >> 3) & 7, node = threadIdx.x & 7;
+  const int cx = ch & 1, cy = (ch >> 1) & 1, cz = ch >> 2;
+  const int a = node & 1, b = (node >> 1) & 1, c = node >> 2;
+  const T* Ix = sI[cx];
+  const T* Iy = sI[cy];
+  const T* Iz = sI[cz];
+  const T* cc = xc + rhs * Nqc + (long long)ec * 8;
+  T cv[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) cv[q] = cc[q];
+  // s1[k][j] = sum_i Ix[a,i] c[k][j][i]; s2[k] = sum_j Iy[b,j] s1[k][j]; out = sum_k Iz[c,k] s2[k]
+  T s2v[2];
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    T s1v[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      T acc = (T)0;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) acc += Ix[a * 2 + i] * cv[(kk * 2 + j) * 2 + i];
+      s1v[j] = acc;
+    }
+    T acc = (T)0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc += Iy[b * 2 + j] * s1v[j];
+    s2v[kk] = acc;
+  }
+  T acc = (T)0;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) acc += Iz[c * 2 + kk] * s2v[kk];
+  const int ecx = ec % nxc, ecy = (ec / nxc) % nyc, ecz = ec / (nxc * nyc);
+  const long long ef = (long long)(2 * ecx + cx) + (long long)(2 * nxc) * ((2 * ecy + cy) + (long long)(2 * nyc) * (2 * ecz + cz));
+  T* dst = xf + rhs * Nqf + ef * 8 + node;
+  *dst = *dst + acc;
+}
+
+// Degree-1 h-transfer restriction: one thread per coarse node, the children
+// summed in order; 32 coarse elements per block of 256 threads.
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_h(const TransferOp* __restrict__ tr, const T* __restrict__ rf,
+                                                    T* __restrict__ rc, int nxc, int nyc, int E, long long Nqc,
+                                                    long long Nqf, const int* __restrict__ act) {
+  __shared__ T sI[2][4];
+  const long long rhs = act[blockIdx.y];
+  if (threadIdx.x < 8) sI[threadIdx.x >> 2][threadIdx.x & 3] = (T)tr->I[threadIdx.x >> 2][threadIdx.x & 3];
+  __syncthreads();
+  const int ec = blockIdx.x * 32 + (threadIdx.x >> 3);
+  if (ec >= E) return;
+  const int node = threadIdx.x & 7;
+  const int i = node & 1, j = (node >> 1) & 1, kk = node >> 2;
+  const int ecx = ec % nxc, ecy = (ec / nxc) % nyc, ecz = ec / (nxc * nyc);
+  T so = (T)0;
+  for (int ch = 0; ch < 8; ++ch) {
+    const int cx = ch & 1, cy = (ch >> 1) & 1, cz = ch >> 2;
+    const T* Ix = sI[cx];
+    const T* Iy = sI[cy];
+    const T* Iz = sI[cz];
+    const long long ef = (long long)(2 * ecx + cx) + (long long)(2 * nxc) * ((2 * ecy + cy) + (long long)(2 * nyc) * (2 * ecz + cz));
+    const T* f = rf + rhs * Nqf + ef * 8;
+    T fv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) fv[q] = f[q];
+    // s1[c][b] = sum_a Ix[a,i] f[c][b][a]; s2[c] = sum_b Iy[b,j] s1[c][b]; so += sum_c Iz[c,kk] s2[c]
+    T s2v[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      T s1v[2];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        T acc = (T)0;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) acc += Ix[a * 2 + i] * fv[(c * 2 + b) * 2 + a];
+        s1v[b] = acc;
+      }
+      T acc = (T)0;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) acc += Iy[b * 2 + j] * s1v[b];
+      s2v[c] = acc;
+    }
+    T acc = (T)0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) acc += Iz[c * 2 + kk] * s2v[c];
+    so += acc;
+  }
+  rc[rhs * Nqc + (long long)ec * 8 + node] = so;
+}
+
+template <typename T, int N1F, int N1C>
+static void launch_xfer_p(bool prolong, const TransferOp* dtr, const LevelOp& fine, const LevelOp& coarse,
+                          const T* in, T* out, const int* act, int nact, cudaStream_t s) {
+  using C = PXferCfg<N1F, N1C>;
+  const dim3 grid((unsigned)((coarse.E + C::EPB - 1) / C::EPB), (unsigned)nact);
+  count_launch();
+  if (prolong)
+    k_prolong_p<T, N1F, N1C><<<grid, C::THREADS, 0, s>>>(dtr, in, out, coarse.E, coarse.Nq, fine.Nq, act);
+  else
+    k_restrict_p<T, N1F, N1C><<<grid, C::THREADS, 0, s>>>(dtr, in, out, coarse.E, coarse.Nq, fine.Nq, act);
+}
+
+// Fixed-size transfer for the level pair if one is compiled; false otherwise.
+template <typename T>
+static bool launch_xfer_fixed(bool prolong, const TransferOp& htr, const TransferOp* dtr, const LevelOp& fine,
+                              const LevelOp& coarse, const T* in, T* out, const int* act, int nact, cudaStream_t s) {
+  if (htr.kind == 1) {
+    if (htr.n1f != 2 || htr.n1c != 2) return false;
+    count_launch();
+    if (prolong)
+      k_prolong_h<T><<<dim3((unsigned)((coarse.E + 3) / 4), (unsigned)nact), 256, 0, s>>>(
+          dtr, in, out, coarse.n[0], coarse.n[1], coarse.E, coarse.Nq, fine.Nq, act);
+    else
+      k_restrict_h<T><<<dim3((unsigned)((coarse.E + 31) / 32), (unsigned)nact), 256, 0, s>>>(
+          dtr, in, out, coarse.n[0], coarse.n[1], coarse.E, coarse.Nq, fine.Nq, act);
+    return true;
+  }
+  const int key = htr.n1f * 16 + htr.n1c;
+  switch (key) {
+    case 3 * 16 + 2: launch_xfer_p<T, 3, 2>(prolong, dtr, fine, coarse, in, out, act, nact, s); return true;
+    case 4 * 16 + 2: launch_xfer_p<T, 4, 2>(prolong, dtr, fine, coarse, in, out, act, nact, s); return true;
+    case 5 * 16 + 3: launch_xfer_p<T, 5, 3>(prolong, dtr, fine, coarse, in, out, act, nact, s); return true;
+    case 6 * 16 + 3: launch_xfer_p<T, 6, 3>(prolong, dtr, fine, coarse, in, out, act, nact, s); return true;
+    case 7 * 16 + 4: launch_xfer_p<T, 7, 4>(prolong, dtr, fine, coarse, in, out, act, nact, s); return true;
+    case 8 * 16 + 4: launch_xfer_p<T, 8, 4>(prolong, dtr, fine, coarse, in, out, act, nact, s); return true;
+    case 9 * 16 + 5: launch_xfer_p<T, 9, 5>(prolong, dtr, fine, coarse, in, out, act, nact, s); return true;
+    default: return false;
+  }
+}
+
 template <typename T>
 cudaError_t launch_prolong_add(const TransferOp& htr, const TransferOp* dtr, const LevelOp& fine,
                                const LevelOp& coarse, const T* xc, T* xf, const int* act, int nact, cudaStream_t s) {
   if (nact == 0) return cudaSuccess;
-  (void)htr;
+  if (launch_xfer_fixed<T>(true, htr, dtr, fine, coarse, xc, xf, act, nact, s)) return cudaGetLastError();
   count_launch();
   k_prolong_add<T><<<dim3(coarse.E, nact), 128, 0, s>>>(dtr, xc, xf, coarse.n[0], coarse.n[1], coarse.n[2],
                                                          coarse.Nq, fine.Nq, act);
@@ -327,7 +584,7 @@ template <typename T>
 cudaError_t launch_restrict(const TransferOp& htr, const TransferOp* dtr, const LevelOp& fine,
                             const LevelOp& coarse, const T* rf, T* rc, const int* act, int nact, cudaStream_t s) {
   if (nact == 0) return cudaSuccess;
-  (void)htr;
+  if (launch_xfer_fixed<T>(false, htr, dtr, fine, coarse, rf, rc, act, nact, s)) return cudaGetLastError();
   count_launch();
   k_restrict<T><<<dim3(coarse.E, nact), 128, 0, s>>>(dtr, rf, rc, coarse.n[0], coarse.n[1], coarse.n[2], coarse.Nq,
                                                       fine.Nq, act);
