@@ -14,6 +14,7 @@
 
 namespace dg {
 
+
 // Launch layout: EPB elements per block; in the three 1-D passes each thread
 // owns LPT lines of one element (line values in registers, the 1-D block rows
 // streamed from shared memory and reused across the lines). Loads of the
@@ -104,6 +105,41 @@ __device__ __forceinline__ void ap_pass(const T* __restrict__ su, T* __restrict_
   }
 }
 
+// Traces (value and reference normal derivative) of the neighbours across the
+// two faces of direction D of every slot: st[sl][2 D + side][0 / 1][tt].
+template <typename T, int N1, int EPB, int NT, int D>
+__device__ __forceinline__ void ap_traces(const T* __restrict__ u, const long long* sbase, const int (*snb)[6],
+                                          const T (*sTr)[N1], T* __restrict__ st, int tid) {
+  constexpr int NF = N1 * N1, NE = EPB * 2 * NF;
+  constexpr int SD = D == 0 ? 1 : (D == 1 ? N1 : NF);
+#pragma unroll 1
+  for (int t = tid; t < NE; t += NT) {
+    const int sl = t / (2 * NF), rem = t % (2 * NF), side = rem / NF, tt = rem % NF;
+    const long long b0 = sbase[sl];
+    const int nb = snb[sl][2 * D + side];
+    T val = 0, der = 0;
+    if (b0 >= 0 && nb != 0) {
+      const int t1 = tt % N1, t2 = tt / N1;
+      const int base = D == 0 ? N1 * t1 + NF * t2 : (D == 1 ? t1 + NF * t2 : t1 + N1 * t2);
+      const T* un = u + b0 + (long long)nb * (N1 * NF) + base;
+      T vals[N1];
+#pragma unroll
+      for (int i = 0; i < N1; ++i) vals[i] = un[i * SD];
+      // the -d neighbour meets us at its right end, the +d neighbour at its left end
+      const T* tv = side == 0 ? sTr[1] : sTr[0];
+      const T* td = side == 0 ? sTr[3] : sTr[2];
+#pragma unroll
+      for (int i = 0; i < N1; ++i) {
+        val += tv[i] * vals[i];
+        der += td[i] * vals[i];
+      }
+    }
+    T* dst = st + ((sl * 6 + 2 * D + side) * 2) * NF + tt;
+    dst[0] = val;
+    dst[NF] = der;
+  }
+}
+
 template <typename T, int N1, int MODE>
 __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS, ApplyCfg<T, N1>::MINB)
     k_apply(const LevelOp* __restrict__ op, const T* __restrict__ u, T* __restrict__ out,
@@ -176,55 +212,11 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS, ApplyCfg<T, N1>::MIN
       const long long b0 = sbase[sl];
       su[sl][loc] = b0 >= 0 ? u[b0 + loc] : (T)0;
     }
-    // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d);
-    // two traces per thread and iteration so that 2 N1 loads are in flight
-    for (int t0 = tid; t0 < EPB * 6 * NF; t0 += 2 * NT) {
-      T vals[2][N1];
-      int tts[2], fs[2], sls[2];
-      bool has[2];
-#pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        const int t = t0 + w * NT;
-        const int sl = t / (6 * NF), rem = t - sl * (6 * NF);
-        const int f = rem / NF, tt = rem - f * NF;
-        sls[w] = sl;
-        fs[w] = f;
-        tts[w] = tt;
-        has[w] = false;
-        if (t < EPB * 6 * NF) {
-          const long long b0 = sbase[sl];
-          const int nb = snb[sl][f];
-          has[w] = b0 >= 0 && nb != 0;
-          if (has[w]) {
-            const int d = f >> 1;
-            const T* un = u + b0 + (long long)nb * NPE;
-            const int t1 = tt % N1, t2 = tt / N1;
-            const int base = d == 0 ? N1 * t1 + NF * t2 : (d == 1 ? t1 + NF * t2 : t1 + N1 * t2);
-            const int sd = d == 0 ? 1 : (d == 1 ? N1 : NF);
-#pragma unroll
-            for (int i = 0; i < N1; ++i) vals[w][i] = un[base + i * sd];
-          }
-        }
-      }
-#pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        if (t0 + w * NT >= EPB * 6 * NF) continue;
-        T val = 0, der = 0;
-        if (has[w]) {
-          // the -d neighbour meets us at its right end, the +d neighbour at its left end
-          const int side = fs[w] & 1;
-          const T* tv = side == 0 ? sTr[1] : sTr[0];
-          const T* td = side == 0 ? sTr[3] : sTr[2];
-#pragma unroll
-          for (int i = 0; i < N1; ++i) {
-            val += tv[i] * vals[w][i];
-            der += td[i] * vals[w][i];
-          }
-        }
-        st[sls[w]][fs[w]][0][tts[w]] = val;
-        st[sls[w]][fs[w]][1][tts[w]] = der;
-      }
-    }
+    // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d),
+    // one direction at a time so that the line stride is a constant
+    ap_traces<T, N1, EPB, NT, 0>(u, sbase, snb, sTr, &st[0][0][0][0], tid);
+    ap_traces<T, N1, EPB, NT, 1>(u, sbase, snb, sTr, &st[0][0][0][0], tid);
+    ap_traces<T, N1, EPB, NT, 2>(u, sbase, snb, sTr, &st[0][0][0][0], tid);
     __syncthreads();
     if (slot < EPB) {
       ap_pass<T, N1, LPT, TPE, 0, false>(su[slot], sacc[slot], sK[0][sty[slot][0]], sC[0][0], &st[slot][0][0][0],
