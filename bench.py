@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
     ap.add_argument("--no-learned", action="store_true", help="skip timing the learned form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-jk", action="store_true", help="skip timing the J/K action on trial functions")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -436,6 +437,31 @@ def run_ours(args):
                    "weights": os.path.relpath(weights, ROOT)}
         solver_l.close()
 
+    # Hartree and exchange actions on trial functions (the eigensolver's operator
+    # application): the occupied orbitals as the m = N trial functions, so that
+    # <psi_i, X psi_j> must reproduce -K of the build
+    jk = None
+    if not args.no_jk and prec != dgx.DG_PREC_FP64 and N <= 16:  # 1 + N^2 solves per call
+        _, wq = solver.node_coords()
+        wq_d = torch.tensor(wq, device="cuda")
+        solver.jk_apply(psi_dev, psi_dev)
+        torch.cuda.synchronize()
+        jtimes = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush_l2(flush)
+            t0.record()
+            JU, XU, stj = solver.jk_apply(psi_dev, psi_dev)
+            t1.record()
+            t1.synchronize()
+            jtimes.append(t0.elapsed_time(t1))
+        jtot = pd.max_over_ranks(sum(jtimes) / 1e3, device="cuda")
+        nsolve = 1 + N * N
+        Kj = -((psi_dev * wq_d) @ XU.T).cpu().numpy()
+        jk = {"value": pd.aggregate_rate(nsolve, len(jtimes), jtot, ws), "unit": "trial_solves/s",
+              "trial_functions": N, "solves_per_call": nsolve, "ms_per_call": jtot / len(jtimes) * 1e3,
+              "mean_iters": float(np.mean([x["iters"] for x in stj])),
+              "K_rel_diff_vs_build": float(np.abs(Kj - K).max() / np.abs(K).max())}
+
     # roofline of the dominant kernel (the smoother patch solve; see profiles/)
     B = min(P + 1, 64)
     rf = kernel_roofline(solver, B, args.precision, torch)
@@ -485,6 +511,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "plain_fp64": plain,
             "learned": learned,
+            "jk_action": jk,
             "solver": {"mean_iters": float(np.mean(iters)), "max_iters": int(max(iters)),
                        "max_rel_residual": resid, "all_converged": status_ok,
                        "outer_refinements": int(max(s["outer_refinements"] for s in stats)),

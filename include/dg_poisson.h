@@ -216,6 +216,26 @@ int dg_exchange_build_range(dg_handle h, const double* psi_dev, int32_t N, int64
  * 4096; DG_ERR_BREAKDOWN if K_s is not positive definite. */
 int dg_ace_apply(dg_handle h, const double* U_dev, int64_t m, double* Y_dev, void* cuda_stream);
 
+/* Hartree and exchange actions on m trial functions (the operators of
+ * Sec. 2.3.1 that an eigensolver applies; the same auxiliary-grid solves as
+ * dg_exchange_build, Sec. 6.1, with a trial function in place of the second
+ * orbital). For psi_dev [N][Nq] (device, read only, FP64) and trial values at
+ * the fine-level nodes U_dev [m][Nq] (device, read only, FP64):
+ *     JU[k](q) = v_H(q) u_k(q),               -lap v_H  = 4 pi sum_j psi_j^2
+ *     XU[k](q) = -sum_j psi_j(q) v_jk(q),     -lap v_jk = 4 pi psi_j u_k
+ * each v with its own Coulomb boundary data and solved to the handle's rtol.
+ * JU_dev, XU_dev: [m][Nq] (device, written); either may be NULL to skip that
+ * operator (the Hartree solve is made only for JU). The sum over j runs in
+ * ascending j. Solves: (JU ? 1 : 0) + (XU ? N m : 0), numbered in that order
+ * (the Hartree density first, then u_0 with psi_0 .. psi_{N-1}, then u_1 ...);
+ * stats_host: one entry per solve (host, may be NULL). Applied to the
+ * orbitals themselves, XU = -W of the exchange build and
+ * <psi_i, XU_j> = -K_ij. Returns DG_OK when every solve reached rtol, else the
+ * worst per-solve status (as dg_pair_solve_batch); DG_ERR_INVALID_ARG for N or
+ * m < 1, a NULL psi_dev or U_dev, or both outputs NULL. */
+int dg_jk_apply(dg_handle h, const double* psi_dev, int32_t N, const double* U_dev, int64_t m, double* JU_dev,
+                double* XU_dev, dg_solve_stats* stats_host, void* cuda_stream);
+
 /* Exchange builds of nsys independent systems with their own meshes and
  * orbital counts (uneven sizes), as one call. meshes [nsys] (host), psi_devs
  * [nsys] device pointers to [Ns[i]][Nq_i], K_hosts [nsys] host pointers to

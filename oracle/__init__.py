@@ -35,4 +35,5 @@ from .dg_oracle import (  # noqa: F401
     exchange_build,
     exchange_partial,
     ace_apply,
+    jk_apply,
 )

@@ -644,3 +644,31 @@ def ace_apply(build, Wq, U):
     C = W @ (np.asarray(U, dtype=np.float64) * Wq[None, :]).T  # [N, m]
     Z = np.linalg.solve(Ks, C)
     return -(W.T @ Z).T
+
+
+def jk_apply(mesh, psi, U, penalty_form=0, eps=0.125, method="auto", hartree=True, exchange=True):
+    """Hartree and exchange operators of Sec. 2.3.1 applied to trial functions
+    u_k given by their values at the fine-level nodes (the action an
+    eigensolver needs, Sec. 6.1: the same auxiliary-grid Poisson solves as the
+    exchange build, with the trial function in place of the second orbital):
+      (J u_k)(q) = v_H(q) u_k(q),             -lap v_H  = 4 pi sum_j psi_j^2
+      (X u_k)(q) = -sum_j psi_j(q) v_jk(q),   -lap v_jk = 4 pi psi_j u_k
+    Each v solves the discrete SIPDG problem of Sec. 6.3 / 6.4 exactly, with the
+    source's own Coulomb boundary data. psi: [N, Nq]; U: [m, Nq]. Returns
+    (JU, XU), each [m, Nq], or None for an operator not asked for."""
+    psi = np.asarray(psi, dtype=np.float64)
+    U = np.asarray(U, dtype=np.float64)
+    N, m = psi.shape[0], U.shape[0]
+    JU = XU = None
+    if hartree:
+        rho = np.sum(psi * psi, axis=0)
+        vH, _ = poisson(mesh, rho[None, :], penalty_form, eps, method)
+        JU = vH[0][None, :] * U
+    if exchange:
+        XU = np.zeros_like(U)
+        for k in range(m):
+            sources = psi * U[k][None, :]  # row j: psi_j u_k
+            v, _ = poisson(mesh, sources, penalty_form, eps, method)
+            for j in range(N):  # j ascending
+                XU[k] -= psi[j] * v[j]
+    return JU, XU

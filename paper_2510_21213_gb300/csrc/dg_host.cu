@@ -1259,4 +1259,101 @@ int dg_exchange_build_range(dg_handle h, const double* psi, int32_t N, int64_t s
   return exchange_build_range(h, psi, N, src_begin, src_end, K_partial_host, E_H, nullptr, stats, stream);
 }
 
+// Hartree and exchange actions on trial functions (Sec. 2.3.1): the solves of
+// psi_j u_k (and of the density for J) in batches, J u = v_H u formed from the
+// Hartree solve, X u_k accumulated per trial function over j in ascending order
+// and negated at the end.
+int dg_jk_apply(dg_handle h, const double* psi, int32_t N, const double* U, int64_t m, double* JU, double* XU,
+                dg_solve_stats* stats, void* stream) {
+  if (!h || N < 1 || m < 1 || !psi || !U || (!JU && !XU)) return DG_ERR_INVALID_ARG;
+  const long long nJ = JU ? 1 : 0;
+  const long long total = nJ + (XU ? (long long)N * m : 0);
+  if (m > 65535 || total > (1LL << 30)) return DG_ERR_INVALID_ARG;
+  cudaStream_t us = (cudaStream_t)stream;
+  DG_CK(cudaEventRecord(h->ev_in, us));
+  DG_CK(cudaStreamWaitEvent(h->ws, h->ev_in, 0));
+  cudaStream_t s = h->ws;
+  const long long Nq = h->Nq;
+  // solve list: the density (row index -1) for J, then psi_j u_k with j fastest
+  std::vector<int> sa((size_t)total), sb((size_t)total);
+  {
+    size_t t = 0;
+    if (JU) {
+      sa[t] = -1;
+      sb[t++] = 0;
+    }
+    if (XU)
+      for (int k = 0; k < (int)m; ++k)
+        for (int j = 0; j < N; ++j, ++t) {
+          sa[t] = j;
+          sb[t] = k;
+        }
+  }
+  const int cap = (int)std::max<long long>(1, std::min<long long>(default_batch(h), total));
+  DG_RET(prepare(h, cap));
+  if (XU) DG_CK(cudaMemsetAsync(XU, 0, sizeof(double) * (size_t)m * Nq, s));
+  DevBuf idx, lists;
+  DG_CK(idx.ensure(sizeof(int) * 2 * (size_t)std::max<long long>(cap, m)));
+  int* ia = idx.as<int>();
+  int* ib = ia + std::max<long long>(cap, m);
+  int worst = DG_OK;
+  for (long long b0 = 0; b0 < total; b0 += cap) {
+    const int nb = (int)std::min<long long>(cap, total - b0);
+    DG_CK(cudaMemcpyAsync(ia, sa.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    DG_CK(cudaMemcpyAsync(ib, sb.data() + b0, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    DG_CK(launch_row_products(psi, N, U, ia, ib, nb, Nq, 1.0, h->f64.as<double>(), s));
+    std::vector<int> finite;
+    DG_RET(check_finite(h, h->f64.as<double>(), nb, finite, s));
+    DG_RET(form_rhs(h, h->f64.as<double>(), nb, s));
+    const int rc = solve_chunk(h, nb, finite, stats ? stats + b0 : nullptr, s);
+    if (rc == DG_ERR_CUDA || rc == DG_ERR_NO_MEMORY) return rc;
+    if (rc != DG_OK && (worst == DG_OK || rc < worst)) worst = rc;
+    const double* v = h->x64.as<double>();
+    std::vector<int> ja, jb;
+    if (JU && b0 == 0) {
+      // J u_k = v_H u_k, v_H in slot 0
+      ja.assign((size_t)m, 0);
+      jb.resize((size_t)m);
+      for (int k = 0; k < (int)m; ++k) jb[k] = k;
+      DG_CK(cudaMemcpyAsync(ia, ja.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+      DG_CK(cudaMemcpyAsync(ib, jb.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+      DG_CK(launch_row_products(v, 1, U, ia, ib, (int)m, Nq, 1.0, JU, s));
+    }
+    // XU_k += psi_j v_(jk) for the batch's exchange solves, per k in ascending j
+    std::vector<int> ptr((size_t)m + 1, 0), eb, es;
+    if (XU) {
+      std::vector<std::vector<std::pair<int, int>>> per((size_t)m);
+      for (int k = 0; k < nb; ++k) {
+        const long long g = b0 + k;
+        if (sa[g] < 0) continue;
+        per[sb[g]].push_back({k, sa[g]});
+      }
+      for (int k = 0; k < (int)m; ++k) {
+        for (auto& e : per[k]) {
+          eb.push_back(e.first);
+          es.push_back(e.second);
+        }
+        ptr[k + 1] = (int)eb.size();
+      }
+    }
+    if (!eb.empty()) {
+      std::vector<int> pack;
+      pack.insert(pack.end(), ptr.begin(), ptr.end());
+      pack.insert(pack.end(), eb.begin(), eb.end());
+      pack.insert(pack.end(), es.begin(), es.end());
+      DG_CK(lists.ensure(sizeof(int) * pack.size()));
+      DG_CK(cudaMemcpyAsync(lists.p, pack.data(), sizeof(int) * pack.size(), cudaMemcpyHostToDevice, s));
+      const int* dl = lists.as<int>();
+      DG_CK(launch_exch_accum(psi, v, XU, dl, dl + m + 1, dl + m + 1 + eb.size(), (int)m, Nq, s));
+    }
+    DG_CK(cudaStreamSynchronize(s));  // the index lists are host temporaries
+  }
+  if (XU) DG_CK(launch_scale(XU, (long long)m * Nq, -1.0, s));
+  DG_CK(cudaStreamSynchronize(s));
+  DG_CK(cudaEventRecord(h->ev_out, s));
+  DG_CK(cudaStreamWaitEvent(us, h->ev_out, 0));
+  account(h);
+  return worst;
+}
+
 }  // extern "C"

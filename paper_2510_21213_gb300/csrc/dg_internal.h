@@ -139,6 +139,9 @@ cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double*
 // sources and right-hand sides
 cudaError_t launch_pair_sources(const double* psi, int N, const int* pi, const int* pj, int nsrc, long long Nq,
                                 double* f, cudaStream_t s);
+cudaError_t launch_row_products(const double* A, int NA, const double* B, const int* ia, const int* ib, int n,
+                                long long Nq, double c, double* out, cudaStream_t s);
+cudaError_t launch_scale(double* x, long long n, double c, cudaStream_t s);
 cudaError_t launch_rhs_volume(const double* f, const double* W, double* b, long long Nq, int nsrc,
                               cudaStream_t s);
 cudaError_t launch_finite_flags(const double* f, long long Nq, int nsrc, int* flags, cudaStream_t s);

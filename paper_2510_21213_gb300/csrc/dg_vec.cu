@@ -652,6 +652,49 @@ cudaError_t launch_pair_sources(const double* psi, int N, const int* pi, const i
   return cudaGetLastError();
 }
 
+// out[b] = c A[ia[b]] B[ib[b]] pointwise; ia[b] < 0: c sum_k A_k^2 over the NA
+// rows of A (the density). Sources of the trial-function solves and the
+// Hartree action v_H u.
+__global__ void k_row_products(const double* __restrict__ A, int NA, const double* __restrict__ B,
+                               const int* __restrict__ ia, const int* __restrict__ ib, long long Nq, double c,
+                               double* __restrict__ out) {
+  const int b = blockIdx.y;
+  const int i = ia[b], j = ib[b];
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < Nq; q += (long long)gridDim.x * blockDim.x) {
+    double v;
+    if (i < 0) {
+      v = 0.0;
+      for (int k = 0; k < NA; ++k) {
+        const double t = A[(long long)k * Nq + q];
+        v += t * t;
+      }
+    } else {
+      v = A[(long long)i * Nq + q] * B[(long long)j * Nq + q];
+    }
+    out[(long long)b * Nq + q] = c * v;
+  }
+}
+
+cudaError_t launch_row_products(const double* A, int NA, const double* B, const int* ia, const int* ib, int n,
+                                long long Nq, double c, double* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  count_launch();
+  k_row_products<<<vgrid(Nq, n), VT, 0, s>>>(A, NA, B, ia, ib, Nq, c, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_scale(double* __restrict__ x, long long n, double c) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    x[q] *= c;
+}
+
+cudaError_t launch_scale(double* x, long long n, double c, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  count_launch();
+  k_scale<<<vgrid(n, 1), VT, 0, s>>>(x, n, c);
+  return cudaGetLastError();
+}
+
 __global__ void k_rhs_volume(const double* __restrict__ f, const double* __restrict__ W, double* __restrict__ b,
                              long long Nq) {
   const long long off = (long long)blockIdx.y * Nq;

@@ -116,6 +116,8 @@ def load():
     lib.dg_exchange_build_range.restype = C.c_int
     lib.dg_ace_apply.argtypes = [vp, vp, C.c_int64, vp, vp]
     lib.dg_ace_apply.restype = C.c_int
+    lib.dg_jk_apply.argtypes = [vp, vp, C.c_int32, vp, C.c_int64, vp, vp, vp, vp]
+    lib.dg_jk_apply.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -297,6 +299,26 @@ def dg_ace_apply(h, U, stream=None):
     _check(load().dg_ace_apply(h, _dev_ptr(U, torch.float64), U.shape[0], _dev_ptr(Y, torch.float64),
                                _stream_ptr(stream)), "dg_ace_apply", h)
     return Y
+
+
+def dg_jk_apply(h, psi, U, hartree=True, exchange=True, stream=None, allow_unconverged=False):
+    """Hartree and exchange actions on trial functions U (CUDA float64 [m, Nq])
+    for orbitals psi (CUDA float64 [N, Nq]): (J U or None, X U or None, stats),
+    J u = v_H u and X u = -sum_j psi_j v_(psi_j u)."""
+    import torch
+
+    N, m = psi.shape[0], U.shape[0]
+    JU = torch.empty_like(U) if hartree else None
+    XU = torch.empty_like(U) if exchange else None
+    n = (1 if hartree else 0) + (N * m if exchange else 0)
+    st = (dg_solve_stats * max(n, 1))()
+    allow = (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_NONFINITE) if allow_unconverged else ()
+    code = load().dg_jk_apply(h, _dev_ptr(psi, torch.float64), N, _dev_ptr(U, torch.float64), m,
+                              _dev_ptr(JU, torch.float64) if hartree else None,
+                              _dev_ptr(XU, torch.float64) if exchange else None, C.cast(st, C.c_void_p),
+                              _stream_ptr(stream))
+    _check(code, "dg_jk_apply", h, allow)
+    return JU, XU, _stats_list(st[:n])
 
 
 def dg_apply_operator(h, u, level=0, out=None, stream=None):
@@ -536,6 +558,9 @@ class PoissonSolver:
 
     def exchange_build(self, psi, **kw):
         return dg_exchange_build(self.h, psi, **kw)
+
+    def jk_apply(self, psi, U, **kw):
+        return dg_jk_apply(self.h, psi, U, **kw)
 
     def apply(self, u, level=0):
         return dg_apply_operator(self.h, u, level)

@@ -322,3 +322,42 @@ def test_ace_operator_pins():
     Gw = (W * Wq) @ W.T
     Up = U - (np.linalg.solve(Gw, (W * Wq) @ U.T)).T @ W
     assert np.abs(oracle.ace_apply(build, Wq, Up)).max() <= 1e-10 * np.abs(AU).max()
+
+
+def test_jk_action_pins():
+    """The Hartree and exchange actions on trial functions (Sec. 2.3.1):
+    on the occupied orbitals the exchange action is minus the build's
+    accumulation W (so <psi_i, X psi_j> = -K_ij) and sum_i <psi_i, J psi_i> =
+    2 E_H; for one orbital J psi + X psi = 0 (no self-interaction); X is
+    linear and negative semidefinite up to the asymmetry of the boundary
+    data."""
+    spec = inputs.chain_system(n=2, p=4, n_orb=3)
+    m = oracle.Mesh(spec.mesh.lo, spec.mesh.hi, spec.mesh.n, spec.mesh.p)
+    Wq = oracle.quad_weights(m)
+    psi = inputs.orbitals(spec, oracle.node_coords(m), Wq)
+    build = oracle.exchange_build(m, psi)
+    W, K = build["W"], build["K"]
+    JU, XU = oracle.jk_apply(m, psi, psi)
+    assert np.abs(XU + W).max() <= 1e-12 * np.abs(W).max()
+    assert np.abs((psi * Wq) @ XU.T + K).max() <= 1e-12 * np.abs(K).max()
+    assert abs(float(np.sum(Wq * psi * JU)) - 2.0 * build["E_H"]) <= 1e-12 * abs(build["E_H"])
+    # one orbital: the pair source psi psi is the density, so X psi = -J psi
+    J1, X1 = oracle.jk_apply(m, psi[:1], psi[:1])
+    assert np.abs(J1 + X1).max() <= 1e-12 * np.abs(J1).max()
+    # linearity in the trial function, and the operator flags
+    rng = np.random.default_rng(11)
+    U = rng.standard_normal((3, Wq.size))
+    JU, XU = oracle.jk_apply(m, psi, U)
+    Jc, Xc = oracle.jk_apply(m, psi, (2.0 * U[0] - 3.0 * U[1])[None, :], hartree=True, exchange=True)
+    assert np.abs(Xc[0] - (2.0 * XU[0] - 3.0 * XU[1])).max() <= 1e-11 * np.abs(XU).max()
+    assert np.abs(Jc[0] - (2.0 * JU[0] - 3.0 * JU[1])).max() <= 1e-11 * np.abs(JU).max()
+    assert oracle.jk_apply(m, psi, U, exchange=False)[1] is None
+    assert oracle.jk_apply(m, psi, U, hartree=False)[0] is None
+    # <u_a, X u_b>: symmetric up to the boundary-data asymmetry seen in K, and
+    # its symmetric part negative semidefinite to the same order
+    asym = np.abs(K - K.T).max() / np.abs(K).max()
+    G = (U * Wq) @ XU.T
+    scale = np.abs(G).max()
+    assert np.abs(G - G.T).max() <= (1e-12 + 10 * asym) * scale
+    assert np.linalg.eigvalsh(0.5 * (G + G.T)).max() <= (1e-12 + 10 * asym) * scale
+    assert np.all(np.diag(G) < 0)
