@@ -8,9 +8,13 @@ route, multigrid-preconditioned CG to 1e-8), the exchange accumulation, the K
 contraction and the energies. value = pair solves of all ranks / max-over-ranks
 time. Inputs (orbital values at the nodes) are resident in HBM for `value`;
 `e2e` copies them from pinned host memory every step and reads K back.
+Beside them: the plain FP64 and learned forms of the same build, and the
+Hartree/exchange action on trial functions (`jk_action`, the orbitals as the
+trial functions).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload chain10|mixed64|tiny] [--precision mixed|fp64]
+                  [--workload chain10|mixed64|batched32|tiny] [--precision mixed|fp64|learned]
+                  [--no-plain] [--no-learned] [--no-cpu] [--no-jk]
 """
 
 from __future__ import annotations
