@@ -269,6 +269,17 @@ int dg_autotune_batch(dg_handle h, int32_t max_sources, int32_t* batch);
 int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u_dev, void* out_dev,
                       int64_t B, void* cuda_stream);
 
+/* Grid transfer between multigrid levels `level` and `level` + 1 (Sec. 6.4:
+ * GL interpolation from degree p_c to p on the same mesh, or from a degree-1
+ * element to its 8 children), applied to B fields. direction 0
+ * (prolongation): out = P in, in_dev [B][Nq_(level+1)], out_dev
+ * [B][Nq_level]; direction 1 (restriction): out = P^T in, in_dev
+ * [B][Nq_level], out_dev [B][Nq_(level+1)]. Device arrays, FP64 (fp32 == 0)
+ * or FP32 (fp32 == 1). Exposed for tests and kernel timing; stream-ordered,
+ * no synchronisation. DG_ERR_INVALID_ARG unless 0 <= level < levels - 1. */
+int dg_apply_transfer(dg_handle h, int32_t level, int32_t direction, int32_t fp32, const void* in_dev,
+                      void* out_dev, int64_t B, void* cuda_stream);
+
 /* Preconditioner of the multigrid smoother of level `level` applied to B
  * fields: z = M r with M the additive Schwarz operator sum_P R_P^T A_P^-1 R_P
  * (DG_SMOOTH_SCHWARZ) or D^-1 (DG_SMOOTH_JACOBI); on the coarsest level M is

@@ -36,4 +36,5 @@ from .dg_oracle import (  # noqa: F401
     exchange_partial,
     ace_apply,
     jk_apply,
+    transfer_matrix,
 )

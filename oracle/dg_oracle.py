@@ -672,3 +672,34 @@ def jk_apply(mesh, psi, U, penalty_form=0, eps=0.125, method="auto", hartree=Tru
             for j in range(N):  # j ascending
                 XU[k] -= psi[j] * v[j]
     return JU, XU
+
+
+def transfer_matrix(fine, coarse):
+    """Prolongation P [fine.Nq, coarse.Nq] between nested levels of the hp
+    hierarchy (Sec. 6.4): a coarse DG function, given by its values at the
+    coarse GL nodes, evaluated at the fine nodes. Each fine node lies inside
+    one coarse element (the fine elements are the coarse ones or their
+    children); its row holds the coarse element's tensor Lagrange basis at the
+    node's reference coordinates (sparse: n1c^3 entries per row). Restriction
+    is P^T."""
+    xf = node_coords(fine)
+    xi, _ = gauss_legendre(coarse.n1)
+    hc = np.asarray(coarse.h, dtype=np.float64)
+    ec = np.floor((xf - coarse.lo[None, :]) / hc[None, :]).astype(np.int64)
+    ec = np.clip(ec, 0, np.asarray(coarse.n)[None, :] - 1)
+    L = []
+    for d in range(3):
+        t = 2.0 * (xf[:, d] - (coarse.lo[d] + ec[:, d] * hc[d])) / hc[d] - 1.0
+        Ld, _ = lagrange_eval(xi, t)
+        L.append(Ld)  # [Nq_f, n1c]
+    n1 = coarse.n1
+    e = ec[:, 0] + coarse.n[0] * (ec[:, 1] + coarse.n[1] * ec[:, 2])
+    rows, cols, vals = [], [], []
+    for k in range(n1):
+        for j in range(n1):
+            for i in range(n1):
+                rows.append(np.arange(fine.Nq))
+                cols.append(e * coarse.npe + i + n1 * (j + n1 * k))
+                vals.append(L[0][:, i] * L[1][:, j] * L[2][:, k])
+    return scipy.sparse.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                                   shape=(fine.Nq, coarse.Nq))

@@ -1049,6 +1049,46 @@ int dg_apply_operator(dg_handle h, int32_t level, int32_t fp32, const void* u, v
   return DG_OK;
 }
 
+int dg_apply_transfer(dg_handle h, int32_t level, int32_t direction, int32_t fp32, const void* in, void* out,
+                      int64_t B, void* stream) {
+  if (!h || level < 0 || level >= h->nlev - 1 || (direction != 0 && direction != 1) || B < 0 ||
+      (B > 0 && (!in || !out)))
+    return DG_ERR_INVALID_ARG;
+  if (B == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cap = (int)std::min<int64_t>(B, 65535);
+  DG_RET(ensure_common(h, cap));
+  const Level& L = h->levels[level];
+  const Level& Cl = h->levels[level + 1];
+  const long long nqf = L.op.Nq, nqc = Cl.op.Nq;
+  for (int64_t b0 = 0; b0 < B; b0 += cap) {
+    const int nb = (int)std::min<int64_t>(cap, B - b0);
+    std::vector<int> a(nb);
+    for (int k = 0; k < nb; ++k) a[k] = k;
+    DG_RET(upload_act(h, a, s));
+    const int* act = h->act.as<int>();
+    if (direction == 0) {
+      if (fp32) {
+        float* o = (float*)out + b0 * nqf;
+        DG_CK(launch_zero<float>(o, nqf, act, nb, s));
+        DG_CK(launch_prolong_add<float>(L.tr, L.dtr, L.op, Cl.op, (const float*)in + b0 * nqc, o, act, nb, s));
+      } else {
+        double* o = (double*)out + b0 * nqf;
+        DG_CK(launch_zero<double>(o, nqf, act, nb, s));
+        DG_CK(launch_prolong_add<double>(L.tr, L.dtr, L.op, Cl.op, (const double*)in + b0 * nqc, o, act, nb, s));
+      }
+    } else {
+      if (fp32)
+        DG_CK(launch_restrict<float>(L.tr, L.dtr, L.op, Cl.op, (const float*)in + b0 * nqf, (float*)out + b0 * nqc,
+                                     act, nb, s));
+      else
+        DG_CK(launch_restrict<double>(L.tr, L.dtr, L.op, Cl.op, (const double*)in + b0 * nqf,
+                                      (double*)out + b0 * nqc, act, nb, s));
+    }
+  }
+  return DG_OK;
+}
+
 int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r, void* z, int64_t B, void* stream) {
   if (!h || level < 0 || level >= h->nlev || B < 0 || (B > 0 && (!r || !z))) return DG_ERR_INVALID_ARG;
   if (B == 0) return DG_OK;

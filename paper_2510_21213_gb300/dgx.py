@@ -118,6 +118,8 @@ def load():
     lib.dg_ace_apply.restype = C.c_int
     lib.dg_jk_apply.argtypes = [vp, vp, C.c_int32, vp, C.c_int64, vp, vp, vp, vp]
     lib.dg_jk_apply.restype = C.c_int
+    lib.dg_apply_transfer.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
+    lib.dg_apply_transfer.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -331,6 +333,21 @@ def dg_apply_operator(h, u, level=0, out=None, stream=None):
     code = load().dg_apply_operator(h, level, fp32, _dev_ptr(u), _dev_ptr(out, u.dtype), u.shape[0],
                                     _stream_ptr(stream))
     _check(code, "dg_apply_operator", h)
+    return out
+
+
+def dg_apply_transfer(h, x, level, direction, nq_out, stream=None):
+    """Grid transfer between levels `level` and `level` + 1: direction 0
+    prolongs x [B, Nq_(level+1)] to [B, Nq_level], direction 1 restricts x
+    [B, Nq_level] to [B, Nq_(level+1)] (CUDA float64 or float32); nq_out is
+    the output level's node count."""
+    import torch
+
+    out = torch.empty((x.shape[0], int(nq_out)), dtype=x.dtype, device=x.device)
+    fp32 = 1 if x.dtype == torch.float32 else 0
+    code = load().dg_apply_transfer(h, level, direction, fp32, _dev_ptr(x), _dev_ptr(out, x.dtype), x.shape[0],
+                                    _stream_ptr(stream))
+    _check(code, "dg_apply_transfer", h)
     return out
 
 

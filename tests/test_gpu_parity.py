@@ -277,3 +277,35 @@ def test_mixed_precision_exchange_build_error_bounds(dgx):
     assert abs(eh - ref["E_H"]) <= 1e-6 * abs(ref["E_H"])
     assert abs(ex - ref["E_X"]) <= 1e-6 * abs(ref["E_X"])
     s.close()
+
+
+@pytest.mark.parametrize("lo,hi,n,p", [
+    ([-2.0, -1.0, 0.5], [2.0, 1.5, 2.0], (2, 4, 2), 6),
+    ([-3.0] * 3, [3.0] * 3, (4, 4, 4), 7),
+    ([-1.0, -2.0, -1.5], [1.0, 2.0, 2.0], (4, 2, 4), 8),
+    ([-1.0] * 3, [1.0] * 3, (6, 6, 6), 5),
+    ([-2.0] * 3, [2.0] * 3, (8, 8, 8), 2),
+])
+def test_transfers_all_levels(dgx, lo, hi, n, p):
+    """Prolongation and restriction between every pair of levels against the
+    oracle's interpolation matrix P (built from node coordinates) and P^T."""
+    s = dgx.PoissonSolver(lo, hi, n, p)
+    meshes = level_meshes(lo, hi, n, p)
+    assert s.info.levels == len(meshes)
+    rng = np.random.default_rng(2)
+    for l in range(len(meshes) - 1):
+        fine, coarse = meshes[l], meshes[l + 1]
+        P = oracle.transfer_matrix(fine, coarse)
+        uc = rng.standard_normal((3, coarse.Nq))
+        rf = rng.standard_normal((3, fine.Nq))
+        for dt, tol in ((torch.float64, 1e-13), (torch.float32, 2e-6)):
+            got = dgx.dg_apply_transfer(s.h, torch.tensor(uc, device="cuda", dtype=dt), l, 0, fine.Nq)
+            ref = (P @ uc.T).T
+            assert np.abs(got.cpu().double().numpy() - ref).max() <= tol * np.abs(ref).max(), (l, dt)
+            got = dgx.dg_apply_transfer(s.h, torch.tensor(rf, device="cuda", dtype=dt), l, 1, coarse.Nq)
+            ref = (P.T @ rf.T).T
+            assert np.abs(got.cpu().double().numpy() - ref).max() <= tol * np.abs(ref).max(), (l, dt)
+    with pytest.raises(dgx.DGError):
+        dgx.dg_apply_transfer(s.h, torch.zeros((1, meshes[-1].Nq), device="cuda", dtype=torch.float64),
+                              len(meshes) - 1, 0, 1)
+    s.close()

@@ -361,3 +361,37 @@ def test_jk_action_pins():
     assert np.abs(G - G.T).max() <= (1e-12 + 10 * asym) * scale
     assert np.linalg.eigvalsh(0.5 * (G + G.T)).max() <= (1e-12 + 10 * asym) * scale
     assert np.all(np.diag(G) < 0)
+
+
+def test_transfer_matrix_reproduces_piecewise_polynomials():
+    """Prolongation of the hp hierarchy (Sec. 6.4): a field that is, in every
+    coarse element, a polynomial of the coarse degree plus its own constant is
+    reproduced exactly at the fine nodes, for p-transfers (same mesh) and the
+    degree-1 h-transfer (8 children). The per-element constants check that
+    every fine node is given its own coarse element."""
+    rng = np.random.default_rng(8)
+    lo, hi = np.array([-2.0, -1.0, 0.5]), np.array([2.0, 1.5, 2.5])
+    cases = [((2, 3, 2), 6, (2, 3, 2), 3), ((2, 2, 2), 3, (2, 2, 2), 1), ((4, 2, 6), 1, (2, 1, 3), 1)]
+    for nf, pf, nc, pc in cases:
+        fine, coarse = oracle.Mesh(lo, hi, nf, pf), oracle.Mesh(lo, hi, nc, pc)
+        jump = rng.standard_normal(coarse.E)
+
+        def field(x, e):
+            X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+            poly = 0.3 + X ** pc * Y - 2.0 * Z ** pc + X * Y ** max(pc - 1, 0) * Z
+            return poly + jump[e]
+
+        xc = oracle.node_coords(coarse)
+        ec = np.repeat(np.arange(coarse.E), coarse.npe)
+        xf = oracle.node_coords(fine)
+        hc = coarse.h
+        idx = np.clip(np.floor((xf - coarse.lo) / hc).astype(int), 0, np.asarray(coarse.n) - 1)
+        ef = idx[:, 0] + coarse.n[0] * (idx[:, 1] + coarse.n[1] * idx[:, 2])
+        P = oracle.transfer_matrix(fine, coarse)
+        got = P @ field(xc, ec)
+        ref = field(xf, ef)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (nf, pf, nc, pc)
+        # a field of one degree more is not reproduced (the interpolation is not over-exact)
+        if pf > pc:
+            bad = P @ (xc[:, 0] ** (pc + 1)) - xf[:, 0] ** (pc + 1)
+            assert np.abs(bad).max() > 1e-6
