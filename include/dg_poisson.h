@@ -315,6 +315,15 @@ int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r_de
 int dg_apply_smoother_noalloc(dg_handle h, int32_t level, int32_t fp32, const void* r_dev, void* z_dev, int64_t B,
                               void* cuda_stream);
 
+/* Right-hand side of the pair solves for B sources (steps S1-S4: Sec. 6.1.2
+ * and Sec. 6.3): b = 4 pi W f + the Nitsche load of the source's Coulomb
+ * boundary data g(f), i.e. sum over boundary faces of int g (sigma v -
+ * d_n v) against every test function v, exactly as the solves form it (the
+ * handle's boundary route and, in the mixed modes, the FP32 Gaussian-sum
+ * tables). f_dev, b_dev: [B][Nq] device FP64. Exposed for tests; returns after
+ * synchronising the stream. */
+int dg_form_rhs(dg_handle h, const double* f_dev, int64_t B, double* b_dev, void* cuda_stream);
+
 /* Boundary data g of Sec. 6.3 for B sources f_dev [B][Nq] (device): g_dev
  * [B][n_face_nodes] (device, FP64; the Gaussian-sum route is evaluated in FP32
  * with a 1e-7 table when the handle is in a mixed mode, as in the solves), faces in the order -x,+x,-y,+y,-z,+z, each

@@ -1141,6 +1141,21 @@ int dg_boundary_data(dg_handle h, int32_t route, const double* f, int64_t B, dou
   return DG_OK;
 }
 
+int dg_form_rhs(dg_handle h, const double* f, int64_t B, double* b, void* stream) {
+  if (!h || B < 0 || (B > 0 && (!f || !b))) return DG_ERR_INVALID_ARG;
+  if (B == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int cap = std::max(1, std::min(default_batch(h), (int)std::min<int64_t>(B, 65535)));
+  DG_RET(prepare(h, cap));
+  for (int64_t b0 = 0; b0 < B; b0 += cap) {
+    const int nb = (int)std::min<int64_t>(cap, B - b0);
+    DG_RET(form_rhs(h, f + b0 * h->Nq, nb, s));
+    DG_CK(cudaMemcpyAsync(b + b0 * h->Nq, h->b64.p, sizeof(double) * h->Nq * nb, cudaMemcpyDeviceToDevice, s));
+  }
+  DG_CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
 int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_solve_stats* stats, void* stream) {
   if (!h || B < 0 || (B > 0 && (!f || !v))) return DG_ERR_INVALID_ARG;
   if (B == 0) return DG_OK;

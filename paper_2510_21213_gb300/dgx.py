@@ -120,6 +120,8 @@ def load():
     lib.dg_jk_apply.restype = C.c_int
     lib.dg_apply_transfer.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_apply_transfer.restype = C.c_int
+    lib.dg_form_rhs.argtypes = [vp, vp, C.c_int64, vp, vp]
+    lib.dg_form_rhs.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -334,6 +336,17 @@ def dg_apply_operator(h, u, level=0, out=None, stream=None):
                                     _stream_ptr(stream))
     _check(code, "dg_apply_operator", h)
     return out
+
+
+def dg_form_rhs(h, f, stream=None):
+    """Right-hand sides b = 4 pi W f + Nitsche load of g(f) of the solves for
+    sources f (CUDA float64 [B, Nq]); returns b, same shape."""
+    import torch
+
+    b = torch.empty_like(f)
+    _check(load().dg_form_rhs(h, _dev_ptr(f, torch.float64), f.shape[0], _dev_ptr(b, torch.float64),
+                              _stream_ptr(stream)), "dg_form_rhs", h)
+    return b
 
 
 def dg_apply_transfer(h, x, level, direction, nq_out, stream=None):

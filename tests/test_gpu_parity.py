@@ -112,6 +112,32 @@ def test_boundary_data(dgx, route):
     s.close()
 
 
+@pytest.mark.parametrize("precision,route,form", [(0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0)])
+def test_right_hand_side(dgx, precision, route, form):
+    """b = 4 pi W f + Nitsche load of g(f) (steps S1-S4) against the oracle's
+    load vector with the direct Coulomb boundary data: the volume part to
+    round-off, the boundary load within the route's accuracy (R1 the
+    definition, R2 the 1e-12 FP64 or 1e-7 FP32 Gaussian sum)."""
+    lo, hi, n, p = [-4.0, -3.0, -3.5], [4.0, 3.5, 3.0], (3, 3, 3), 4
+    m = oracle.Mesh(lo, hi, n, p)
+    rng = np.random.default_rng(27)
+    f = np.concatenate([_gauss_sources(m, [[0.3, -0.2, 0.1], [1.0, 0.5, -0.7]], [1.5, 0.7]),
+                        rng.standard_normal((1, m.Nq))])
+    s = dgx.PoissonSolver(lo, hi, n, p, precision=precision, bc_route=route, penalty_form=form)
+    b = dgx.dg_form_rhs(s.h, torch.tensor(f, device="cuda")).cpu().numpy()
+    g = oracle.boundary_data_direct(m, f)
+    vol = 4.0 * math.pi * oracle.quad_weights(m) * f
+    tol = {(0, 0): 1e-12, (0, 1): 1e-10, (1, 1): 2e-5}[(precision, route)]
+    for k in range(f.shape[0]):
+        ref = oracle.rhs(m, f[k], [gf[k] for gf in g], penalty_form=form)
+        lift_ref = ref - vol[k]
+        interior = np.abs(lift_ref) == 0.0  # nodes of no boundary element
+        assert interior.any() and not interior.all()
+        assert np.abs(b[k][interior] - ref[interior]).max() <= 1e-14 * np.abs(ref).max()
+        assert np.abs((b[k] - vol[k]) - lift_ref).max() <= tol * np.abs(lift_ref).max(), k
+    s.close()
+
+
 @pytest.mark.parametrize("lo,hi,n,p,B", [
     ([-8.0] * 3, [8.0] * 3, (4, 4, 4), 4, 3),
     ([-4.0, -3.0, -3.5], [4.0, 3.5, 3.0], (2, 2, 4), 3, 5),
