@@ -232,7 +232,8 @@ int dg_ace_apply(dg_handle h, const double* U_dev, int64_t m, double* Y_dev, voi
  * orbitals themselves, XU = -W of the exchange build and
  * <psi_i, XU_j> = -K_ij. Returns DG_OK when every solve reached rtol, else the
  * worst per-solve status (as dg_pair_solve_batch); DG_ERR_INVALID_ARG for N or
- * m < 1, a NULL psi_dev or U_dev, or both outputs NULL. */
+ * m < 1, m > 65535, more than 2^30 solves, a NULL psi_dev or U_dev, or both
+ * outputs NULL. */
 int dg_jk_apply(dg_handle h, const double* psi_dev, int32_t N, const double* U_dev, int64_t m, double* JU_dev,
                 double* XU_dev, dg_solve_stats* stats_host, void* cuda_stream);
 
