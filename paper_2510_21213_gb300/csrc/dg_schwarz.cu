@@ -282,10 +282,13 @@ __global__ void __launch_bounds__(SwCfg<T, N1>::THREADS, SwCfg<T, N1>::MINB)
 
 // Gather block shape: GE elements of NPE nodes per block (several small
 // elements per block on the coarse levels), one thread per node.
+#ifndef DG_GATHER_THREADS
+#define DG_GATHER_THREADS 256  // thread budget of a gather block (at least one element)
+#endif
 template <int N1>
 struct GatherCfg {
   static constexpr int NPE = N1 * N1 * N1;
-  static constexpr int GE = 256 / NPE < 1 ? 1 : 256 / NPE;
+  static constexpr int GE = DG_GATHER_THREADS / NPE < 1 ? 1 : DG_GATHER_THREADS / NPE;
   static constexpr int THREADS = GE * NPE;
 };
 
