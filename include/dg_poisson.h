@@ -116,6 +116,9 @@ typedef struct {
                              1: every level uses the fine level's penalty (Galerkin-consistent hierarchy) */
   int32_t coarse_smoother_degree; /* Chebyshev degree on the levels below the finest (0 = smoother_degree) */
   int32_t p1_smoother;   /* smoother of the degree-1 levels below the finest: -1 = as `smoother`, else DG_SMOOTH_* */
+  int32_t gauss_construction; /* Gaussian-sum 1/r: 0 = tabulated short sums (nonnegative least-squares fits,
+                                 about 3-5x fewer terms), the trapezoidal rule where no table applies;
+                                 1 = trapezoidal rule only */
 } dg_solver_opts;
 
 typedef struct {

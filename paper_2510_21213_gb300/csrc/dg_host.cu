@@ -793,7 +793,7 @@ static int setup(dg_ctx* h) {
       diag2 += (m.hi[d] - m.lo[d]) * (m.hi[d] - m.lo[d]);
     }
     auto build_tables = [&](double tol, GaussSum& gs, int& NG, BcAxisTables* bct, bool fp32) -> int {
-      gs = make_gauss_sum(rmin * 0.999, std::sqrt(diag2) * 1.001, tol);
+      gs = make_gauss_sum(rmin * 0.999, std::sqrt(diag2) * 1.001, tol, h->opts.gauss_construction == 0);
       NG = (int)gs.c.size();
       if (NG == 0) {
         h->err = "could not build the Gaussian-sum 1/r table";
@@ -891,6 +891,7 @@ void dg_default_opts(dg_solver_opts* o) {
   o->coarse_penalty = 0;
   o->coarse_smoother_degree = 0;
   o->p1_smoother = -1;
+  o->gauss_construction = 0;
 }
 
 const char* dg_error_string(int status) {
@@ -931,7 +932,8 @@ int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_ha
       o.smoother_degree < 1 || o.smoother_degree > 16 || o.batch < 0 ||
       (o.smoother != DG_SMOOTH_JACOBI && o.smoother != DG_SMOOTH_SCHWARZ) ||
       (o.coarse_penalty != 0 && o.coarse_penalty != 1) || o.coarse_smoother_degree < 0 ||
-      o.coarse_smoother_degree > 16 || o.p1_smoother < -1 || o.p1_smoother > 1)
+      o.coarse_smoother_degree > 16 || o.p1_smoother < -1 || o.p1_smoother > 1 ||
+      (o.gauss_construction != 0 && o.gauss_construction != 1))
     return DG_ERR_INVALID_ARG;
   if (o.cheb_range <= 1.0) o.cheb_range = 10.0;
   if (o.inner_rtol <= 0.0) o.inner_rtol = 1e-4;

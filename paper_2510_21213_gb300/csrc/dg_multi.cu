@@ -173,10 +173,10 @@ static std::map<std::string, dg_ctx*> g_cache;
 static std::string cache_key(const dg_mesh_desc& m, const dg_solver_opts& o, int lane) {
   char buf[512];
   std::snprintf(buf, sizeof(buf), "%.17g,%.17g,%.17g,%.17g,%.17g,%.17g|%d,%d,%d|%d|%d,%.17g,%d,%.17g,%d,%d,%.17g,%d,%d,"
-                "%.17g,%.17g,%d,%d,%d|%d",
+                "%.17g,%.17g,%d,%d,%d,%d|%d",
                 m.lo[0], m.lo[1], m.lo[2], m.hi[0], m.hi[1], m.hi[2], m.n[0], m.n[1], m.n[2], m.p, o.precision, o.rtol,
                 o.max_iter, o.penalty_eps, o.penalty_form, o.bc_route, o.bc_tol, o.smoother, o.smoother_degree,
-                o.cheb_range, o.inner_rtol, o.coarse_penalty, o.coarse_smoother_degree, o.p1_smoother, lane);
+                o.cheb_range, o.inner_rtol, o.coarse_penalty, o.coarse_smoother_degree, o.p1_smoother, o.gauss_construction, lane);
   std::string k(buf);
   if (o.nn_weights_path) k += std::string("|") + o.nn_weights_path;
   return k;

@@ -9,6 +9,7 @@
 #include <cstring>
 
 #include "dg_setup.h"
+#include "dg_gauss_tables.h"
 
 namespace dg {
 
@@ -380,10 +381,52 @@ std::vector<double> level_dense(const LevelOp& L) {
 // largest of a decreasing sequence whose measured max relative error on
 // [rmin, rmax] is below tol.
 // ---------------------------------------------------------------------------
-GaussSum make_gauss_sum(double rmin, double rmax, double tol) {
+// max over log-spaced r in [rmin, rmax] of |r sum_k c_k exp(-a_k r^2) - 1|
+static double gauss_sum_error(const std::vector<double>& c, const std::vector<double>& a, double rmin, double rmax) {
+  const int nsamp = 3000;
+  double err = 0.0;
+  for (int i = 0; i < nsamp; ++i) {
+    const double r = std::exp(std::log(rmin) + (std::log(rmax) - std::log(rmin)) * i / (nsamp - 1));
+    double s = 0.0;
+    for (size_t k = 0; k < c.size(); ++k) s += c[k] * std::exp(-a[k] * r * r);
+    err = std::max(err, std::fabs(s * r - 1.0));
+  }
+  return err;
+}
+
+// Tabulated short sums (gen_gauss_tables.py): an entry fitted on [1, R] with
+// R >= rmax / rmin and tolerance <= tol, rescaled to [rmin, rmax]
+// (alpha / rmin^2, c / rmin) and accepted after the same sampled check; the
+// fewest-term entry that passes is taken.
+static bool tabulated_gauss_sum(double rmin, double rmax, double tol, GaussSum& G) {
+  const double R = rmax / rmin;
+  int best = -1;
+  for (int e = 0; e < gtab::kEntries; ++e) {
+    const gtab::Entry& T = gtab::kEntry[e];
+    if (T.tol > tol || T.R < R) continue;
+    if (best >= 0 && gtab::kEntry[best].n <= T.n) continue;
+    best = e;
+  }
+  if (best < 0) return false;
+  const gtab::Entry& T = gtab::kEntry[best];
+  std::vector<double> c(T.n), a(T.n);
+  for (int k = 0; k < T.n; ++k) {
+    c[k] = gtab::kCoef[T.off + k] / rmin;
+    a[k] = gtab::kAlpha[T.off + k] / (rmin * rmin);
+  }
+  const double err = gauss_sum_error(c, a, rmin, rmax);
+  if (!(err <= tol)) return false;
+  G.c = c;
+  G.a = a;
+  G.relerr = err;
+  return true;
+}
+
+GaussSum make_gauss_sum(double rmin, double rmax, double tol, bool tabulated) {
   GaussSum G;
   G.rmin = rmin;
   G.rmax = rmax;
+  if (tabulated && tabulated_gauss_sum(rmin, rmax, tol, G)) return G;
   const double t_lo = std::log(tol * std::sqrt(M_PI) / (2.0 * rmax));
   double xs = 0.5;
   while (std::erfc(xs) > 0.5 * tol) xs += 0.01;

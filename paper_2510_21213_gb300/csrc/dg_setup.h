@@ -29,6 +29,6 @@ std::vector<double> schwarz_tables(const LevelOp& L);
 void build_transfer(TransferOp& T, const LevelOp& fine, const LevelOp& coarse);
 bool spd_inverse(std::vector<double>& A, int n);
 std::vector<double> level_dense(const LevelOp& L);
-GaussSum make_gauss_sum(double rmin, double rmax, double tol);
+GaussSum make_gauss_sum(double rmin, double rmax, double tol, bool tabulated = true);
 
 }  // namespace dg

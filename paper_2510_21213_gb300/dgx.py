@@ -59,6 +59,7 @@ class dg_solver_opts(C.Structure):
         ("coarse_penalty", C.c_int32),
         ("coarse_smoother_degree", C.c_int32),
         ("p1_smoother", C.c_int32),
+        ("gauss_construction", C.c_int32),
     ]
 
 
