@@ -340,6 +340,21 @@ int dg_boundary_data(dg_handle h, int32_t route, const double* f_dev, int64_t B,
 /* Number of CUDA kernels this library has launched in the calling process
  * since it was loaded (all handles, all streams). For profiling and for
  * benchmarks that report how many of the library's kernels ran. */
+/* The Gaussian-sum approximation of 1/r that the setup builds for the
+ * boundary data (Sec. 6.3, Gaussian-sum approximation): accurate to relative
+ * tolerance tol on the distances [rmin, rmax], by the construction
+ * `construction` (as dg_solver_opts.gauss_construction: 0 tabulated short sum
+ * with the trapezoidal rule as fallback, 1 trapezoidal rule). Host only; needs
+ * no GPU. n_terms (host) receives its length and relerr (host, may be NULL) its
+ * measured max relative error on 3000 log-spaced distances; c_host and
+ * alpha_host (host, [max_terms], may be NULL) receive the coefficients and
+ * exponents of 1/r ~ sum_k c_k exp(-alpha_k r^2). DG_ERR_INVALID_ARG for
+ * rmin <= 0, rmax <= rmin, tol <= 0, a construction other than 0 or 1, or
+ * max_terms smaller than the sum when c_host or alpha_host is given;
+ * DG_ERR_UNSUPPORTED when no sum meets tol. */
+int dg_gauss_sum(double rmin, double rmax, double tol, int32_t construction, int32_t max_terms, int32_t* n_terms,
+                 double* relerr, double* c_host, double* alpha_host);
+
 int64_t dg_kernel_launch_count(void);
 
 /* Releases the handle and all device memory it owns. NULL is ignored. */

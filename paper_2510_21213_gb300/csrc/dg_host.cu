@@ -1143,6 +1143,23 @@ int dg_boundary_data(dg_handle h, int32_t route, const double* f, int64_t B, dou
   return DG_OK;
 }
 
+int dg_gauss_sum(double rmin, double rmax, double tol, int32_t construction, int32_t max_terms, int32_t* n_terms,
+                 double* relerr, double* c, double* alpha) {
+  if (!(rmin > 0.0) || !(rmax > rmin) || !(tol > 0.0) || (construction != 0 && construction != 1) || !n_terms)
+    return DG_ERR_INVALID_ARG;
+  const GaussSum gs = make_gauss_sum(rmin, rmax, tol, construction == 0);
+  const int n = (int)gs.c.size();
+  if (n == 0) return DG_ERR_UNSUPPORTED;
+  if ((c || alpha) && max_terms < n) return DG_ERR_INVALID_ARG;
+  *n_terms = n;
+  if (relerr) *relerr = gs.relerr;
+  for (int k = 0; k < n; ++k) {
+    if (c) c[k] = gs.c[k];
+    if (alpha) alpha[k] = gs.a[k];
+  }
+  return DG_OK;
+}
+
 int dg_form_rhs(dg_handle h, const double* f, int64_t B, double* b, void* stream) {
   if (!h || B < 0 || (B > 0 && (!f || !b))) return DG_ERR_INVALID_ARG;
   if (B == 0) return DG_OK;

@@ -123,6 +123,8 @@ def load():
     lib.dg_apply_transfer.restype = C.c_int
     lib.dg_form_rhs.argtypes = [vp, vp, C.c_int64, vp, vp]
     lib.dg_form_rhs.restype = C.c_int
+    lib.dg_gauss_sum.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32, vp, vp, vp, vp]
+    lib.dg_gauss_sum.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -337,6 +339,20 @@ def dg_apply_operator(h, u, level=0, out=None, stream=None):
                                     _stream_ptr(stream))
     _check(code, "dg_apply_operator", h)
     return out
+
+
+def dg_gauss_sum(rmin, rmax, tol, construction=0):
+    """The Gaussian sum 1/r ~ sum_k c_k exp(-alpha_k r^2) the setup builds for
+    [rmin, rmax] at relative tolerance tol (host only): (c, alpha, relerr)."""
+    n = C.c_int32()
+    err = C.c_double()
+    _check(load().dg_gauss_sum(rmin, rmax, tol, construction, 0, C.byref(n), C.byref(err), None, None),
+           "dg_gauss_sum")
+    c = np.empty(n.value)
+    a = np.empty(n.value)
+    _check(load().dg_gauss_sum(rmin, rmax, tol, construction, n.value, C.byref(n), C.byref(err),
+                               c.ctypes.data_as(C.c_void_p), a.ctypes.data_as(C.c_void_p)), "dg_gauss_sum")
+    return c, a, err.value
 
 
 def dg_form_rhs(h, f, stream=None):

@@ -50,3 +50,42 @@ def test_entries_are_shorter_than_the_trapezoidal_sums():
             continue
         c, _, _ = oracle.gauss_sum_1_over_r(1.0, R, tol)
         assert int(n) * 2 < len(c), (R, tol, int(n), len(c))
+
+
+def _chain10_range():
+    """The distance range the setup uses for chain10 (box [-12, 12]^3, 8^3
+    elements, p = 6): the first interior node's distance to a face, and the
+    box diagonal, widened by 0.1 %."""
+    xi, _ = oracle.gauss_legendre(7)
+    rmin = (1.0 - xi.max()) * 3.0 / 2.0 * 0.999
+    rmax = 24.0 * math.sqrt(3.0) * 1.001
+    return rmin, rmax
+
+
+def _check(c, a, rmin, rmax):
+    r = np.exp(np.linspace(math.log(rmin), math.log(rmax), 20000))
+    s = (c[None, :] * np.exp(-a[None, :] * (r * r)[:, None])).sum(axis=1)
+    return np.abs(r * s - 1.0).max()
+
+
+def test_setup_sums_through_the_c_abi():
+    from paper_2510_21213_gb300 import dgx
+
+    rmin, rmax = _chain10_range()
+    for tol, most in ((1e-7, 40), (1e-12, 60)):
+        c0, a0, e0 = dgx.dg_gauss_sum(rmin, rmax, tol, 0)
+        c1, a1, e1 = dgx.dg_gauss_sum(rmin, rmax, tol, 1)
+        assert len(c0) <= most < len(c1), (tol, len(c0), len(c1))
+        for c, a, e in ((c0, a0, e0), (c1, a1, e1)):
+            assert e <= tol
+            assert _check(c, a, rmin, rmax) <= tol
+    # a ratio beyond the tables (R = 1e6): the tabulated construction falls back to the trapezoidal rule
+    cf, _, ef = dgx.dg_gauss_sum(1e-6, 1.0, 1e-7, 0)
+    ct, _, _ = dgx.dg_gauss_sum(1e-6, 1.0, 1e-7, 1)
+    assert len(cf) == len(ct) and ef <= 1e-7
+    lib = dgx.load()
+    n = dgx.C.c_int32()
+    for bad in ((0.0, 1.0, 1e-7, 0), (1.0, 0.5, 1e-7, 0), (0.1, 1.0, 0.0, 0), (0.1, 1.0, 1e-7, 2)):
+        assert lib.dg_gauss_sum(*bad, 0, dgx.C.byref(n), None, None, None) == dgx.DG_ERR_INVALID_ARG
+    assert lib.dg_gauss_sum(0.1, 1.0, 1e-7, 0, 1, dgx.C.byref(n), None,
+                            np.zeros(1).ctypes.data_as(dgx.C.c_void_p), None) == dgx.DG_ERR_INVALID_ARG
