@@ -362,7 +362,7 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
     DG_RET(upload_act(h, todo, s));
     const int* dact = h->act.as<int>();
     const int nt = (int)todo.size();
-    // relative reduction asked of this round, per source: enough for the
+    // relative reduction asked of this refinement round, per source: enough for the
     // true residual to reach rtol (FP64), at most inner_rtol (mixed)
     std::vector<double> tolv(h->cap, 1.0), rl(h->cap, 1.0);
     int remaining = 1;
