@@ -1,0 +1,118 @@
+"""Pins of the octree auxiliary-mesh oracle (Sec. 6.2) against facts outside
+it: without refinement it is the uniform oracle; on meshes with 2:1 hanging
+faces the SIPDG problem reproduces Q_p polynomial solutions to round-off
+(this pins every face, hanging or not, and the Nitsche terms); the matrix is
+symmetric and positive definite; the tree stays 2:1 balanced; the density
+indicator drives refinement where the density varies."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import octree
+
+
+def _u(P):
+    return P[:, 0] ** 2 * P[:, 1] - 3.0 * P[:, 2] + P[:, 0] * P[:, 1] * P[:, 2] ** 2 + 0.5
+
+
+def _lap_u(P):
+    return 2.0 * P[:, 1] + 2.0 * P[:, 0] * P[:, 1]
+
+
+LO, HI = [-1.0, -1.5, -1.0], [1.0, 1.5, 2.0]
+
+
+def test_unrefined_octree_is_the_uniform_oracle():
+    t = octree.OctreeMesh(LO, HI, (2, 2, 2), 2)
+    m = oracle.Mesh(LO, HI, (2, 2, 2), 2)
+    assert np.abs(t.node_coords() - oracle.node_coords(m)).max() < 1e-14
+    assert np.abs(t.quad_weights() - oracle.quad_weights(m)).max() < 1e-15
+    A = octree.assemble(t)
+    Ad = oracle.assemble_dense(m)
+    assert np.abs(A - Ad).max() <= 1e-12 * np.abs(Ad).max()
+
+
+def _refined(p):
+    t = octree.OctreeMesh(LO, HI, (2, 2, 2), p)
+    t.refine([(0, 0, 0, 0)])
+    t.refine([(1, 1, 1, 1)])  # level-2 cells next to level-0 leaves: balancing must split those
+    t.balance()
+    return t
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_hanging_faces_reproduce_polynomials(p):
+    t = _refined(p)
+    assert t.is_balanced()
+    levels = {k[0] for k in t.leaves}
+    assert levels == {0, 1, 2}
+    A = octree.assemble(t)
+    scale = np.abs(A).max()
+    assert np.abs(A - A.T).max() <= 1e-13 * scale
+    assert np.linalg.eigvalsh(A).min() > 0.0
+    x = t.node_coords()
+    b = octree.rhs(t, -_lap_u(x) / (4.0 * math.pi), g=_u)
+    v = np.linalg.solve(A, b)
+    ref = _u(x)
+    assert np.abs(v - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_wrong_hanging_face_fails_reproduction(monkeypatch):
+    """A planted mistake: hanging faces integrated with the larger element's
+    size in the face weights. Polynomial reproduction must fail."""
+    t = _refined(2)
+    real = octree._face_quadrature
+
+    def wrong(mesh, K, d, s, xq, wq):
+        axes, w = real(mesh, K, d, s, xq, wq)
+        nb = mesh.neighbour_cell(K, d, s)
+        L = mesh.leaf_covering(*nb) if nb is not None else None
+        if L is not None and L[0] < K[0]:
+            w = w * 4.0
+        return axes, w
+
+    monkeypatch.setattr(octree, "_face_quadrature", wrong)
+    A = octree.assemble(t)
+    x = t.node_coords()
+    b = octree.rhs(t, -_lap_u(x) / (4.0 * math.pi), g=_u)
+    v = np.linalg.solve(A, b)
+    assert np.abs(v - _u(x)).max() > 1e-4 * np.abs(_u(x)).max()
+
+
+def test_weights_and_exactness_on_the_refined_mesh():
+    p = 3
+    t = _refined(p)
+    W = t.quad_weights()
+    x = t.node_coords()
+    vol = np.prod(np.asarray(HI) - np.asarray(LO))
+    assert abs(W.sum() - vol) < 1e-13 * vol
+    a = 2 * p + 1
+    got = np.sum(W * (x[:, 0] + 2.0) ** a * x[:, 1] ** 2 * x[:, 2])
+    ref = (((HI[0] + 2.0) ** (a + 1) - (LO[0] + 2.0) ** (a + 1)) / (a + 1) * (HI[1] ** 3 - LO[1] ** 3) / 3
+           * (HI[2] ** 2 - LO[2] ** 2) / 2)
+    assert abs(got - ref) < 1e-11 * abs(ref)
+
+
+def test_density_refinement_is_local_and_balanced():
+    c = np.array([0.3, -0.4, 0.6])
+
+    def rho(P):
+        r2 = np.sum((P - c) ** 2, axis=1)
+        return (8.0 / math.pi) ** 1.5 * np.exp(-8.0 * r2)
+
+    t = octree.OctreeMesh(LO, HI, (2, 2, 2), 3)
+    octree.refine_to_density(t, rho, delta=1e-5, max_level=3)
+    assert t.is_balanced()
+    for k in t.leaves:
+        if k[0] < 3:
+            assert octree.density_indicator(t, k, rho) <= 1e-5
+    # the finest leaves sit where the density is
+    deepest = max(k[0] for k in t.leaves)
+    assert deepest >= 2
+    centres = [t.origin(k) + t.h(k) / 2 for k in t.leaves if k[0] == deepest]
+    assert min(np.linalg.norm(cc - c) for cc in centres) < 0.5
+    far = [k for k in t.leaves if np.linalg.norm(t.origin(k) + t.h(k) / 2 - c) > 2.0]
+    assert far and max(k[0] for k in far) <= 1
