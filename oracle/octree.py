@@ -326,3 +326,30 @@ def refine_to_density(mesh, rho, delta, max_level):
             return mesh
         mesh.refine(split)
         mesh.balance()
+
+
+def coulomb_boundary_data(mesh, f):
+    """The Dirichlet data of Sec. 6.3 as a callable: g(x) = sum_q W_q f_q / |x - x_q|
+    over the octree's nodes (the quadrature sum of the free-space potential)."""
+    xq = mesh.node_coords()
+    wf = mesh.quad_weights() * np.asarray(f, dtype=np.float64)
+
+    def g(P):
+        P = np.atleast_2d(P)
+        out = np.empty(P.shape[0])
+        for i0 in range(0, P.shape[0], 256):
+            d = np.linalg.norm(P[i0:i0 + 256, None, :] - xq[None, :, :], axis=2)
+            out[i0:i0 + 256] = d ** -1 @ wf
+        return out
+
+    return g
+
+
+def poisson(mesh, f, penalty_form=0, eps=0.125):
+    """v solving -Lap v = 4 pi f on the octree with the Coulomb-quadrature
+    Dirichlet data (dense Cholesky; small meshes only)."""
+    import scipy.linalg
+
+    A = assemble(mesh, penalty_form, eps)
+    b = rhs(mesh, f, coulomb_boundary_data(mesh, f), penalty_form, eps)
+    return scipy.linalg.cho_solve(scipy.linalg.cho_factor(A), b)

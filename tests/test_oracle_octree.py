@@ -116,3 +116,34 @@ def test_density_refinement_is_local_and_balanced():
     assert min(np.linalg.norm(cc - c) for cc in centres) < 0.5
     far = [k for k in t.leaves if np.linalg.norm(t.origin(k) + t.h(k) / 2 - c) > 2.0]
     assert far and max(k[0] for k in far) <= 1
+
+
+def test_adaptive_mesh_beats_uniform_for_a_gaussian_charge():
+    """The potential of a normalised Gaussian charge is erf(sqrt(a) r)/r. An
+    octree refined by the density indicator reaches a smaller nodal error than
+    the uniform mesh with fewer nodes (the reason for adapting the auxiliary
+    mesh, Sec. 6.2; measured 2752 nodes at 6.5e-2 against 4096 at 8.9e-2)."""
+    from scipy.special import erf
+
+    a = 6.0
+    c = np.array([1.4, -1.6, 1.5])
+    lo, hi = [-3.0] * 3, [3.0] * 3
+
+    def rho(P):
+        r2 = np.sum((P - c) ** 2, axis=1)
+        return (a / math.pi) ** 1.5 * np.exp(-a * r2)
+
+    def exact(P):
+        r = np.linalg.norm(P - c, axis=1)
+        return erf(math.sqrt(a) * r) / r
+
+    def err(t):
+        x = t.node_coords()
+        v = octree.poisson(t, rho(x))
+        return np.abs(v - exact(x)).max() / exact(x).max()
+
+    ad = octree.OctreeMesh(lo, hi, (2, 2, 2), 3)
+    octree.refine_to_density(ad, rho, delta=3e-3, max_level=2)
+    un = octree.OctreeMesh(lo, hi, (4, 4, 4), 3)
+    e_ad, e_un = err(ad), err(un)
+    assert ad.Nq < un.Nq and e_ad < 0.8 * e_un, (ad.Nq, e_ad, un.Nq, e_un)
