@@ -269,8 +269,9 @@ def assemble(mesh, penalty_form=0, eps=0.125, nq_extra=2):
 
 def rhs(mesh, f, g=None, penalty_form=0, eps=0.125, nq_extra=2):
     """Load vector: 4 pi W f (pointwise quadrature at the nodes) plus, on each
-    boundary face, int_F g (sigma v - d_n v) with g a callable of [P, 3]
-    physical points evaluated at the face's Gauss points (None: zero data)."""
+    boundary face, int_F g (sigma v - d_n v), with g a callable of [P, 3]
+    physical points sampled at the face's GL nodes and interpolated to the
+    face's Gauss points, as the uniform oracle does (None: zero data)."""
     b = FOUR_PI * mesh.quad_weights() * np.asarray(f, dtype=np.float64)
     if g is None:
         return b
@@ -284,10 +285,16 @@ def rhs(mesh, f, g=None, penalty_form=0, eps=0.125, nq_extra=2):
         axes, wf = _face_quadrature(mesh, K, d, s, xq, wq)
         hK = mesh.h(K)
         phi, grad = _basis_on_grid(xi, _ref(mesh, K, axes), hK)
-        X, Y, Z = np.meshgrid(axes[0], axes[1], axes[2], indexing="ij")
+        # g at the face GL nodes, interpolated to the Gauss points
+        o = mesh.origin(K)
+        gl = [axes[ax] if ax == d else o[ax] + (xi + 1.0) * hK[ax] / 2.0 for ax in range(3)]
+        X, Y, Z = np.meshgrid(gl[0], gl[1], gl[2], indexing="ij")
         pts = np.stack([X.transpose(2, 1, 0).ravel(), Y.transpose(2, 1, 0).ravel(), Z.transpose(2, 1, 0).ravel()],
                        axis=1)
-        gv = np.asarray(g(pts), dtype=np.float64)
+        t0, t1 = [ax for ax in range(3) if ax != d]
+        G = np.asarray(g(pts), dtype=np.float64).reshape(mesh.n1, mesh.n1)  # [t1][t0]
+        Lq, _ = lagrange_eval(xi, xq)  # [nq, n1]
+        gv = (Lq @ G @ Lq.T).ravel()  # [t1 Gauss][t0 Gauss], t0 fastest
         sig = penalty(mesh.p, hK[d], penalty_form, eps)
         dn = grad[:, :, d] * s
         b[index[K] * npe:(index[K] + 1) * npe] += np.einsum("q,q,qi->i", wf, gv, sig * phi - dn)
@@ -353,3 +360,31 @@ def poisson(mesh, f, penalty_form=0, eps=0.125):
     A = assemble(mesh, penalty_form, eps)
     b = rhs(mesh, f, coulomb_boundary_data(mesh, f), penalty_form, eps)
     return scipy.linalg.cho_solve(scipy.linalg.cho_factor(A), b)
+
+
+def exchange_build(mesh, psi, penalty_form=0, eps=0.125):
+    """Hartree solve, pair solves, W_j = sum_s psi_s v_sj, K = Psi^T diag(W_q) W,
+    E_H and E_X (Sec. 6.1, eq. fock_exchange) on the octree; the same source
+    list and conventions as the uniform oracle's exchange_build."""
+    import scipy.linalg
+
+    psi = np.asarray(psi, dtype=np.float64)
+    N = psi.shape[0]
+    Wq = mesh.quad_weights()
+    A = scipy.linalg.cho_factor(assemble(mesh, penalty_form, eps))
+
+    def solve(f):
+        return scipy.linalg.cho_solve(A, rhs(mesh, f, coulomb_boundary_data(mesh, f), penalty_form, eps))
+
+    rho = np.sum(psi * psi, axis=0)
+    vH = solve(rho)
+    Wacc = np.zeros_like(psi)
+    for i in range(N):
+        for j in range(i, N):
+            v = solve(psi[i] * psi[j])
+            Wacc[j] += psi[i] * v
+            if i != j:
+                Wacc[i] += psi[j] * v
+    K = (psi * Wq[None, :]) @ Wacc.T
+    return {"K": K, "E_H": 0.5 * float(np.sum(Wq * rho * vH)), "E_X": -0.5 * float(np.trace(K)), "W": Wacc,
+            "v_H": vH}

@@ -147,3 +147,17 @@ def test_adaptive_mesh_beats_uniform_for_a_gaussian_charge():
     un = octree.OctreeMesh(lo, hi, (4, 4, 4), 3)
     e_ad, e_un = err(ad), err(un)
     assert ad.Nq < un.Nq and e_ad < 0.8 * e_un, (ad.Nq, e_ad, un.Nq, e_un)
+
+
+def test_unrefined_exchange_build_is_the_uniform_one():
+    from paper_2510_21213_gb300 import inputs
+
+    spec = inputs.tiny_system()
+    m = oracle.Mesh(spec.mesh.lo, spec.mesh.hi, (2, 2, 2), 3)
+    t = octree.OctreeMesh(spec.mesh.lo, spec.mesh.hi, (2, 2, 2), 3)
+    psi = inputs.orbitals(spec, oracle.node_coords(m), oracle.quad_weights(m))
+    ref = oracle.exchange_build(m, psi, method="dense")
+    got = octree.exchange_build(t, psi)
+    assert np.abs(got["K"] - ref["K"]).max() <= 1e-10 * np.abs(ref["K"]).max()
+    assert abs(got["E_H"] - ref["E_H"]) <= 1e-10 * abs(ref["E_H"])
+    assert abs(got["E_X"] - ref["E_X"]) <= 1e-10 * abs(ref["E_X"])
