@@ -355,6 +355,26 @@ int dg_boundary_data(dg_handle h, int32_t route, const double* f_dev, int64_t B,
 int dg_gauss_sum(double rmin, double rmax, double tol, int32_t construction, int32_t max_terms, int32_t* n_terms,
                  double* relerr, double* c_host, double* alpha_host);
 
+/* Density callback of the octree refinement: out[i] = rho(xyz[3 i], xyz[3 i + 1],
+ * xyz[3 i + 2]) for i < n (host arrays); user is passed through. */
+typedef void (*dg_density_fn)(const double* xyz, int64_t n, double* out, void* user);
+
+/* Adaptive octree auxiliary mesh (Sec. 6.2), host side: the uniform root grid
+ * `root` (box, n per axis, degree p) refined by 8-child splits of every leaf
+ * whose indicator Q = |I_K(rho) - sum over its children of I_C(rho)| (degree-p
+ * tensor Gauss-Legendre rules) exceeds delta, while its level is below
+ * max_level, and kept 2:1 balanced across faces; repeated until no leaf is
+ * split. leaves_host: [max_leaves][4] (host, may be NULL to query the count)
+ * receives (level, ix, iy, iz) of every leaf, the leaf occupying
+ * [lo + i h_level, lo + (i + 1) h_level] with h_level = (hi - lo) / (n 2^level),
+ * in element order (root cell x-fastest, then level, z, y, x); n_leaves (host)
+ * the count. Host only; needs no GPU. DG_ERR_INVALID_ARG for a bad root mesh,
+ * delta <= 0, max_level outside 0..20, a NULL rho, or max_leaves below the
+ * count when leaves_host is given; DG_ERR_NO_MEMORY beyond 2^24 leaves. The GPU
+ * operator on this mesh is not part of the library yet. */
+int dg_octree_refine(const dg_mesh_desc* root, double delta, int32_t max_level, dg_density_fn rho, void* user,
+                     int32_t max_leaves, int32_t* leaves_host, int32_t* n_leaves);
+
 int64_t dg_kernel_launch_count(void);
 
 /* Releases the handle and all device memory it owns. NULL is ignored. */

@@ -125,6 +125,8 @@ def load():
     lib.dg_form_rhs.restype = C.c_int
     lib.dg_gauss_sum.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32, vp, vp, vp, vp]
     lib.dg_gauss_sum.restype = C.c_int
+    lib.dg_octree_refine.argtypes = [vp, C.c_double, C.c_int32, DENSITY_FN, vp, C.c_int32, vp, vp]
+    lib.dg_octree_refine.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -339,6 +341,31 @@ def dg_apply_operator(h, u, level=0, out=None, stream=None):
                                     _stream_ptr(stream))
     _check(code, "dg_apply_operator", h)
     return out
+
+
+DENSITY_FN = C.CFUNCTYPE(None, C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_double), C.c_void_p)
+
+
+def dg_octree_refine(lo, hi, n, p, rho, delta, max_level):
+    """Leaves (level, ix, iy, iz) [E, 4] of the octree that refines the root
+    grid by the density indicator; rho maps points [k, 3] to values [k]
+    (host only)."""
+    if np.isscalar(n):
+        n = (n, n, n)
+    desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
+
+    def cb(xyz, k, out, _user):
+        pts = np.ctypeslib.as_array(xyz, shape=(int(k), 3))
+        np.ctypeslib.as_array(out, shape=(int(k),))[:] = np.asarray(rho(pts), dtype=np.float64)
+
+    fn = DENSITY_FN(cb)
+    cnt = C.c_int32()
+    _check(load().dg_octree_refine(C.byref(desc), delta, max_level, fn, None, 0, None, C.byref(cnt)),
+           "dg_octree_refine")
+    leaves = np.empty((cnt.value, 4), dtype=np.int32)
+    _check(load().dg_octree_refine(C.byref(desc), delta, max_level, fn, None, cnt.value,
+                                   leaves.ctypes.data_as(C.c_void_p), C.byref(cnt)), "dg_octree_refine")
+    return leaves
 
 
 def dg_gauss_sum(rmin, rmax, tol, construction=0):

@@ -161,3 +161,28 @@ def test_unrefined_exchange_build_is_the_uniform_one():
     assert np.abs(got["K"] - ref["K"]).max() <= 1e-10 * np.abs(ref["K"]).max()
     assert abs(got["E_H"] - ref["E_H"]) <= 1e-10 * abs(ref["E_H"])
     assert abs(got["E_X"] - ref["E_X"]) <= 1e-10 * abs(ref["E_X"])
+
+
+def test_library_octree_equals_the_oracle():
+    """The library's host-side octree construction (dg_octree_refine) gives the
+    oracle's leaves, in the oracle's element order."""
+    from paper_2510_21213_gb300 import dgx
+
+    c = np.array([0.3, -0.4, 0.6])
+
+    def rho(P):
+        r2 = np.sum((P - c) ** 2, axis=1)
+        return (8.0 / math.pi) ** 1.5 * np.exp(-8.0 * r2)
+
+    for p, delta, ml in ((3, 1e-5, 3), (2, 1e-4, 2)):
+        t = octree.OctreeMesh(LO, HI, (2, 2, 2), p)
+        octree.refine_to_density(t, rho, delta=delta, max_level=ml)
+        got = dgx.dg_octree_refine(LO, HI, (2, 2, 2), p, rho, delta, ml)
+        assert [tuple(r) for r in got] == t.leaf_list()
+        assert len({k[0] for k in t.leaves}) > 1
+    lib = dgx.load()
+    n = dgx.C.c_int32()
+    desc = dgx.dg_mesh_desc((dgx.C.c_double * 3)(*LO), (dgx.C.c_double * 3)(*HI), (dgx.C.c_int32 * 3)(2, 2, 2), 2)
+    fn = dgx.DENSITY_FN(lambda xyz, k, out, u: None)
+    assert lib.dg_octree_refine(dgx.C.byref(desc), 0.0, 2, fn, None, 0, None, dgx.C.byref(n)) == dgx.DG_ERR_INVALID_ARG
+    assert lib.dg_octree_refine(dgx.C.byref(desc), 1e-3, 21, fn, None, 0, None, dgx.C.byref(n)) == dgx.DG_ERR_INVALID_ARG
