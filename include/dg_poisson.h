@@ -375,6 +375,22 @@ typedef void (*dg_density_fn)(const double* xyz, int64_t n, double* out, void* u
 int dg_octree_refine(const dg_mesh_desc* root, double delta, int32_t max_level, dg_density_fn rho, void* user,
                      int32_t max_leaves, int32_t* leaves_host, int32_t* n_leaves);
 
+/* Face connectivity of a 2:1 balanced set of octree leaves over `root` (as
+ * dg_octree_refine returns them; leaves_host [n_leaves][4], host). For leaf e
+ * and face f = 2 d + s (s = 1 for the +d face), entry o = 6 e + f:
+ *   kind_host[o]: 0 boundary, 1 same-size neighbour, 2 larger neighbour (this
+ *     face is a quarter of its face), 3 four smaller neighbours;
+ *   nb_host[4 o + j]: the neighbour leaf indices (kinds 1 and 2: j = 0; kind 3:
+ *     j = b0 + 2 b1 with b0, b1 the position along the lower and the higher
+ *     tangential axis), -1 elsewhere;
+ *   pos_host[o]: for kind 2 the quarter of the larger face, b0 + 2 b1 as
+ *     above, else -1.
+ * Host arrays, written. Host only; needs no GPU. DG_ERR_INVALID_ARG for a bad
+ * root mesh, leaves outside the root grid or repeated, or a set that is not a
+ * 2:1 balanced partition along some face. */
+int dg_octree_faces(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t* kind_host,
+                    int32_t* nb_host, int32_t* pos_host);
+
 int64_t dg_kernel_launch_count(void);
 
 /* Releases the handle and all device memory it owns. NULL is ignored. */

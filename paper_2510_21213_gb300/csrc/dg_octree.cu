@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <map>
 #include <set>
 #include <vector>
 
@@ -164,6 +165,69 @@ int dg_octree_refine(const dg_mesh_desc* root, double delta, int32_t max_level, 
     if ((long long)v.size() > max_leaves) return DG_ERR_INVALID_ARG;
     for (size_t i = 0; i < v.size(); ++i)
       for (int j = 0; j < 4; ++j) leaves_host[4 * i + j] = v[i][j];
+  }
+  return DG_OK;
+}
+
+int dg_octree_faces(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_leaves, int32_t* kind, int32_t* nb,
+                    int32_t* pos) {
+  if (!root || !leaves || n_leaves < 1 || !kind || !nb || !pos) return DG_ERR_INVALID_ARG;
+  Octree t;
+  for (int d = 0; d < 3; ++d) {
+    if (root->n[d] < 1 || !(root->hi[d] > root->lo[d])) return DG_ERR_INVALID_ARG;
+    t.lo[d] = root->lo[d];
+    t.n[d] = root->n[d];
+    t.H[d] = (root->hi[d] - root->lo[d]) / root->n[d];
+  }
+  t.p = root->p;
+  std::map<Leaf, int> index;
+  for (int e = 0; e < n_leaves; ++e) {
+    const Leaf k{leaves[4 * e], leaves[4 * e + 1], leaves[4 * e + 2], leaves[4 * e + 3]};
+    if (k[0] < 0 || k[0] > 20) return DG_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+      if (k[1 + d] < 0 || k[1 + d] >= t.extent(k[0], d)) return DG_ERR_INVALID_ARG;
+    if (!index.emplace(k, e).second) return DG_ERR_INVALID_ARG;
+    t.leaves.insert(k);
+  }
+  for (int e = 0; e < n_leaves; ++e) {
+    const Leaf k{leaves[4 * e], leaves[4 * e + 1], leaves[4 * e + 2], leaves[4 * e + 3]};
+    for (int d = 0; d < 3; ++d)
+      for (int sd = 0; sd < 2; ++sd) {
+        const int f = 2 * d + sd, side = sd ? 1 : -1;
+        const long long o = 6LL * e + f;
+        for (int j = 0; j < 4; ++j) nb[4 * o + j] = -1;
+        pos[o] = -1;
+        Leaf c, L;
+        if (!t.neighbour(k, d, side, c)) {
+          kind[o] = 0;  // boundary
+          continue;
+        }
+        if (t.covering(c[0], c[1], c[2], c[3], L)) {
+          if (L[0] == k[0]) {
+            kind[o] = 1;
+          } else if (L[0] == k[0] - 1) {
+            kind[o] = 2;  // this face is a quarter of L's face: its two tangential bits
+            const int t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+            pos[o] = (k[1 + t0] & 1) | ((k[1 + t1] & 1) << 1);
+          } else {
+            return DG_ERR_INVALID_ARG;  // not 2:1 balanced
+          }
+          nb[4 * o] = index.at(L);
+          continue;
+        }
+        // four smaller neighbours: the level + 1 cells touching this face
+        kind[o] = 3;
+        const int t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+        for (int j = 0; j < 4; ++j) {
+          Leaf s{k[0] + 1, 2 * k[1], 2 * k[2], 2 * k[3]};
+          s[1 + d] = sd ? 2 * k[1 + d] + 2 : 2 * k[1 + d] - 1;
+          s[1 + t0] += j & 1;
+          s[1 + t1] += j >> 1;
+          auto it = index.find(s);
+          if (it == index.end()) return DG_ERR_INVALID_ARG;  // not 2:1 balanced or not a leaf set
+          nb[4 * o + j] = it->second;
+        }
+      }
   }
   return DG_OK;
 }

@@ -127,6 +127,8 @@ def load():
     lib.dg_gauss_sum.restype = C.c_int
     lib.dg_octree_refine.argtypes = [vp, C.c_double, C.c_int32, DENSITY_FN, vp, C.c_int32, vp, vp]
     lib.dg_octree_refine.restype = C.c_int
+    lib.dg_octree_faces.argtypes = [vp, vp, C.c_int32, vp, vp, vp]
+    lib.dg_octree_faces.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -366,6 +368,23 @@ def dg_octree_refine(lo, hi, n, p, rho, delta, max_level):
     _check(load().dg_octree_refine(C.byref(desc), delta, max_level, fn, None, cnt.value,
                                    leaves.ctypes.data_as(C.c_void_p), C.byref(cnt)), "dg_octree_refine")
     return leaves
+
+
+def dg_octree_faces(lo, hi, n, p, leaves):
+    """Face connectivity of octree leaves [E, 4]: (kind [E, 6], nb [E, 6, 4],
+    pos [E, 6]) as documented for dg_octree_faces (host only)."""
+    if np.isscalar(n):
+        n = (n, n, n)
+    desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
+    leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+    E = leaves.shape[0]
+    kind = np.empty((E, 6), dtype=np.int32)
+    nb = np.empty((E, 6, 4), dtype=np.int32)
+    pos = np.empty((E, 6), dtype=np.int32)
+    _check(load().dg_octree_faces(C.byref(desc), leaves.ctypes.data_as(C.c_void_p), E,
+                                  kind.ctypes.data_as(C.c_void_p), nb.ctypes.data_as(C.c_void_p),
+                                  pos.ctypes.data_as(C.c_void_p)), "dg_octree_faces")
+    return kind, nb, pos
 
 
 def dg_gauss_sum(rmin, rmax, tol, construction=0):

@@ -186,3 +186,41 @@ def test_library_octree_equals_the_oracle():
     fn = dgx.DENSITY_FN(lambda xyz, k, out, u: None)
     assert lib.dg_octree_refine(dgx.C.byref(desc), 0.0, 2, fn, None, 0, None, dgx.C.byref(n)) == dgx.DG_ERR_INVALID_ARG
     assert lib.dg_octree_refine(dgx.C.byref(desc), 1e-3, 21, fn, None, 0, None, dgx.C.byref(n)) == dgx.DG_ERR_INVALID_ARG
+
+
+def test_library_face_connectivity_is_reciprocal():
+    """dg_octree_faces on a mesh with hanging faces: every same-size face is
+    seen from both sides, every hanging face from its small side (kind 2, at
+    its quarter) appears among the large side's four neighbours (kind 3) at
+    that quarter, and boundary faces lie on the box."""
+    from paper_2510_21213_gb300 import dgx
+
+    t = _refined(2)
+    leaves = np.array(t.leaf_list(), dtype=np.int32)
+    kind, nb, pos = dgx.dg_octree_faces(LO, HI, (2, 2, 2), 2, leaves)
+    E = len(leaves)
+    assert set(np.unique(kind)) == {0, 1, 2, 3}
+    for e in range(E):
+        lv = leaves[e][0]
+        for f in range(6):
+            d, side = f // 2, (1 if f % 2 else -1)
+            opp = 2 * d + (0 if side > 0 else 1)
+            k = kind[e, f]
+            if k == 0:
+                cell = leaves[e][1 + d] + side
+                assert cell < 0 or cell >= t.n[d] * 2 ** lv
+            elif k == 1:
+                L = nb[e, f, 0]
+                assert leaves[L][0] == lv and kind[L, opp] == 1 and nb[L, opp, 0] == e
+            elif k == 2:
+                L = nb[e, f, 0]
+                assert leaves[L][0] == lv - 1 and kind[L, opp] == 3 and nb[L, opp, pos[e, f]] == e
+            else:
+                for j in range(4):
+                    s = nb[e, f, j]
+                    assert leaves[s][0] == lv + 1 and kind[s, opp] == 2 and nb[s, opp, 0] == e and pos[s, opp] == j
+    with pytest.raises(dgx.DGError):  # an unbalanced set is rejected
+        bad = octree.OctreeMesh(LO, HI, (2, 2, 2), 2)
+        bad.refine([(0, 0, 0, 0)])
+        bad.refine([(1, 1, 1, 1)])  # no balance()
+        dgx.dg_octree_faces(LO, HI, (2, 2, 2), 2, np.array(bad.leaf_list(), dtype=np.int32))
