@@ -391,6 +391,20 @@ int dg_octree_refine(const dg_mesh_desc* root, double delta, int32_t max_level, 
 int dg_octree_faces(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t* kind_host,
                     int32_t* nb_host, int32_t* pos_host);
 
+/* SIPDG operator on octree leaves (Sec. 3.4 eq. sip_bilinear with symmetric
+ * Nitsche boundary terms; Sec. 6.2 mesh): out = A u for B fields, matrix-free
+ * on the GPU. Faces between leaves of different size are integrated on the
+ * quarters of the larger face; the penalty (p+1)^2/(eps h) (penalty_form 0) or
+ * (p+1)^2/(eps h^2) (1) uses the smaller leaf. root, leaves_host [n_leaves][4]
+ * (host): a 2:1 balanced leaf set as from dg_octree_refine; u_dev, out_dev
+ * [B][n_leaves][(p+1)^3] device FP64, element-blocked in leaf order, nodes
+ * x-fastest. Builds its connectivity and tables per call (device memory
+ * allocated and freed inside) and synchronises the stream before it returns.
+ * DG_ERR_INVALID_ARG for a bad mesh or leaf set, penalty arguments, or B
+ * outside 0..65535. */
+int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t penalty_form,
+                    double penalty_eps, const double* u_dev, double* out_dev, int64_t B, void* cuda_stream);
+
 int64_t dg_kernel_launch_count(void);
 
 /* Releases the handle and all device memory it owns. NULL is ignored. */

@@ -129,6 +129,8 @@ def load():
     lib.dg_octree_refine.restype = C.c_int
     lib.dg_octree_faces.argtypes = [vp, vp, C.c_int32, vp, vp, vp]
     lib.dg_octree_faces.restype = C.c_int
+    lib.dg_octree_apply.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, vp, vp, C.c_int64, vp]
+    lib.dg_octree_apply.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -385,6 +387,21 @@ def dg_octree_faces(lo, hi, n, p, leaves):
                                   kind.ctypes.data_as(C.c_void_p), nb.ctypes.data_as(C.c_void_p),
                                   pos.ctypes.data_as(C.c_void_p)), "dg_octree_faces")
     return kind, nb, pos
+
+
+def dg_octree_apply(lo, hi, n, p, leaves, u, penalty_form=0, penalty_eps=0.125, stream=None):
+    """A u on octree leaves [E, 4] for u (CUDA float64 [B, E (p+1)^3])."""
+    import torch
+
+    if np.isscalar(n):
+        n = (n, n, n)
+    desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
+    leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+    out = torch.empty_like(u)
+    _check(load().dg_octree_apply(C.byref(desc), leaves.ctypes.data_as(C.c_void_p), leaves.shape[0], penalty_form,
+                                  penalty_eps, _dev_ptr(u, torch.float64), _dev_ptr(out, torch.float64), u.shape[0],
+                                  _stream_ptr(stream)), "dg_octree_apply")
+    return out
 
 
 def dg_gauss_sum(rmin, rmax, tol, construction=0):
