@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip timing the learned form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-jk", action="store_true", help="skip timing the J/K action on trial functions")
+    ap.add_argument("--octree-apply", action="store_true",
+                    help="time the SIPDG operator on a density-refined octree instead of the exchange build")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -530,8 +532,51 @@ def run_ours(args):
     pd.finish()
 
 
+def run_octree_apply(args):
+    """The SIPDG operator on an adaptive octree (dg_octree_apply): the chain10
+    box with a 4^3 root grid at p = 6, refined by the density indicator for the
+    chain's ten atom-centred Gaussians (exponent 2, delta 1e-5, up to level 2: 344 leaves),
+    applied to 8 fields. One step = one call (connectivity and tables built per
+    call, then the kernel)."""
+    import torch
+
+    from paper_2510_21213_gb300 import build, dgx
+
+    build.build()
+    lo, hi, n, p = [-12.0] * 3, [12.0] * 3, (4, 4, 4), 6
+    atoms = np.array([[-6.3 + 1.4 * k, 0.0, 0.0] for k in range(10)])
+
+    def rho(P):
+        r2 = ((P[:, None, :] - atoms[None, :, :]) ** 2).sum(-1)
+        return (2.0 / math.pi) ** 1.5 * np.exp(-2.0 * r2).sum(1)
+
+    leaves = dgx.dg_octree_refine(lo, hi, n, p, rho, 1e-5, 2)
+    E, npe, B = leaves.shape[0], (p + 1) ** 3, 8
+    u = torch.randn(B, E * npe, dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        dgx.dg_octree_apply(lo, hi, n, p, leaves, u)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        dgx.dg_octree_apply(lo, hi, n, p, leaves, u)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    sec = sum(times) / len(times)
+    levels = np.bincount(leaves[:, 0]).tolist()
+    print(json.dumps({"metric": "octree SIPDG operator applications, DOF/s", "value": B * E * npe / sec,
+                      "unit": "dof/s", "ms_per_step": sec * 1e3, "steps": args.steps, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": "octree-apply: chain10 box, 4^3 roots, p=6",
+                                                      "leaves": E, "leaves_per_level": levels, "fields": B,
+                                                      "timing": "host wall clock around each call (connectivity, "
+                                                                "tables and kernel)"}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.octree_apply:
+        run_octree_apply(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched32":
