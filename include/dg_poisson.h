@@ -310,8 +310,12 @@ int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r_de
  * The handle itself comes from dg_poisson_setup, which does allocate.
  *
  * The first call on each device looks the static arrays up
- * (cudaGetSymbolAddress) and writes the source list once, with that device
- * current: make that first call before any stream capture. Every call shares
+ * (cudaGetSymbolAddress) and writes the source list once (a synchronous
+ * copy), with that device current. That set-up holds the library's
+ * device-wide lock, so the graph captures of the library's own multi-system
+ * build are not disturbed by it; a capture the caller runs is invisible to
+ * the library: make that first call before any stream capture of the
+ * caller's. Every call shares
  * the scratch and overwrites it (nothing in it has to start at zero); calls
  * that overlap on the GPU, on any stream or handle, race on it. Stream-ordered;
  * returns without synchronising the stream. r_dev, z_dev: [B][Nq_level] device
@@ -400,8 +404,12 @@ int dg_octree_faces(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * [B][n_leaves][(p+1)^3] device FP64, element-blocked in leaf order, nodes
  * x-fastest. Builds its connectivity and tables per call (device memory
  * allocated and freed inside) and synchronises the stream before it returns.
- * DG_ERR_INVALID_ARG for a bad mesh or leaf set, penalty arguments, or B
- * outside 0..65535. */
+ * u_dev and out_dev must not overlap (out is written while other blocks still
+ * read u): overlapping buffers return DG_ERR_INVALID_ARG. The function takes
+ * no array lengths: the caller guarantees both hold B * n_leaves * (p+1)^3
+ * doubles. DG_ERR_INVALID_ARG for a bad mesh or leaf set (a leaf lying inside
+ * another leaf of the set included), penalty arguments, or B outside
+ * 0..65535. */
 int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t penalty_form,
                     double penalty_eps, const double* u_dev, double* out_dev, int64_t B, void* cuda_stream);
 

@@ -237,7 +237,7 @@ def assemble(mesh, penalty_form=0, eps=0.125, nq_extra=2):
         _, g = _basis_on_grid(xi, [xq] * 3, h)
         e = index[K]
         s_ = slice(e * npe, (e + 1) * npe)
-        A[s_, s_] += np.einsum("q,qid,qjd->ij", wvol * (h[0] * h[1] * h[2] / 8.0), g, g)
+        A[s_, s_] += np.einsum("q,qid,qjd->ij", wvol * (h[0] * h[1] * h[2] / 8.0), g, g, optimize=True)
     for (K, L, d, s) in _faces(mesh):
         axes, wf = _face_quadrature(mesh, K, d, s, xq, wq)
         nrm = np.zeros(3)
@@ -261,8 +261,9 @@ def assemble(mesh, penalty_form=0, eps=0.125, nq_extra=2):
             jump = np.concatenate([pm[:, :, None] * nrm, pp[:, :, None] * (-nrm)], axis=1)
             avg = np.concatenate([0.5 * gm, 0.5 * gp], axis=1)
             idx = np.concatenate([im, ip])
-        loc = (-np.einsum("q,qid,qjd->ij", wf, jump, avg) - np.einsum("q,qid,qjd->ij", wf, avg, jump)
-               + sig * np.einsum("q,qid,qjd->ij", wf, jump, jump))
+        loc = (-np.einsum("q,qid,qjd->ij", wf, jump, avg, optimize=True)
+               - np.einsum("q,qid,qjd->ij", wf, avg, jump, optimize=True)
+               + sig * np.einsum("q,qid,qjd->ij", wf, jump, jump, optimize=True))
         A[np.ix_(idx, idx)] += loc
     return A
 

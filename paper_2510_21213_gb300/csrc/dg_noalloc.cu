@@ -39,6 +39,10 @@ static cudaError_t noalloc_setup(NoAllocDev& out) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   NoAllocDev& d = g_noalloc_dev[dev];
   if (!d.scratch) {
+    // the symbol lookup and the synchronous copy are device-wide operations:
+    // hold them off while another thread of this process captures a graph
+    // (the multi-system build captures on its lanes)
+    DeviceWideGuard guard;
     void* sp = nullptr;
     void* ap = nullptr;
     e = cudaGetSymbolAddress(&sp, g_noalloc_scratch);

@@ -131,6 +131,14 @@ bool octree_faces(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_lea
     if (!index.emplace(k, e).second) return false;
     t.leaves.insert(k);
   }
+  // a partition: no leaf may lie inside another leaf of the set
+  for (int e = 0; e < n_leaves; ++e) {
+    const Leaf k{leaves[4 * e], leaves[4 * e + 1], leaves[4 * e + 2], leaves[4 * e + 3]};
+    for (int lv = k[0] - 1; lv >= 0; --lv) {
+      const int sh = k[0] - lv;
+      if (index.count(Leaf{lv, k[1] >> sh, k[2] >> sh, k[3] >> sh})) return false;
+    }
+  }
   for (int e = 0; e < n_leaves; ++e) {
     const Leaf k{leaves[4 * e], leaves[4 * e + 1], leaves[4 * e + 2], leaves[4 * e + 3]};
     for (int d = 0; d < 3; ++d)
@@ -489,6 +497,12 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
       !(penalty_eps > 0.0) || B < 0 || B > 65535 || n_leaves < 1 || (B > 0 && (!u || !out)))
     return DG_ERR_INVALID_ARG;
   const int E = n_leaves;
+  if (B > 0) {
+    // out is written while other blocks still read u: the two must not overlap
+    const size_t bytes = sizeof(double) * (size_t)B * (size_t)E * (size_t)((root->p + 1) * (root->p + 1) * (root->p + 1));
+    const char *u0 = (const char*)u, *o0 = (const char*)out;
+    if (u0 < o0 + bytes && o0 < u0 + bytes) return DG_ERR_INVALID_ARG;
+  }
   std::vector<int32_t> kind(6 * (size_t)E), nb(24 * (size_t)E), pos(6 * (size_t)E);
   if (!octree_faces(root, leaves, n_leaves, kind.data(), nb.data(), pos.data())) return DG_ERR_INVALID_ARG;
   if (B == 0) return DG_OK;

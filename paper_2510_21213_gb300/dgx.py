@@ -395,8 +395,14 @@ def dg_octree_apply(lo, hi, n, p, leaves, u, penalty_form=0, penalty_eps=0.125, 
 
     if np.isscalar(n):
         n = (n, n, n)
-    desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
     leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+    # the C entry takes no lengths: u must be [B, n_leaves * (p+1)^3] for this leaf set
+    if leaves.ndim != 2 or leaves.shape[1] != 4:
+        raise ValueError(f"leaves must be [n_leaves, 4], got {tuple(leaves.shape)}")
+    width = leaves.shape[0] * (int(p) + 1) ** 3
+    if u.ndim != 2 or u.shape[1] != width:
+        raise ValueError(f"u must be [B, {width}] (n_leaves * (p+1)^3), got {tuple(u.shape)}")
+    desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), int(p))
     out = torch.empty_like(u)
     _check(load().dg_octree_apply(C.byref(desc), leaves.ctypes.data_as(C.c_void_p), leaves.shape[0], penalty_form,
                                   penalty_eps, _dev_ptr(u, torch.float64), _dev_ptr(out, torch.float64), u.shape[0],

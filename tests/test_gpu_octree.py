@@ -38,7 +38,7 @@ def _one_split(p):
 
 
 @pytest.mark.parametrize("mesh,p,form", [("three", 1, 0), ("three", 2, 0), ("three", 3, 1), ("one", 5, 0),
-                                         ("one", 6, 0), ("flat", 3, 0)])
+                                         ("one", 6, 0), ("flat", 3, 0), ("one", 7, 0), ("one", 8, 1)])
 def test_octree_operator_vs_oracle(dgx, mesh, p, form):
     if mesh == "three":
         t = _three_levels(p)
@@ -56,3 +56,17 @@ def test_octree_operator_vs_oracle(dgx, mesh, p, form):
     got = dgx.dg_octree_apply(LO, HI, n, p, leaves, torch.tensor(u, device="cuda"), penalty_form=form).cpu().numpy()
     ref = (A @ u.T).T
     assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_octree_apply_refuses_aliased_fields(dgx):
+    """out is written while other blocks still read u: an in-place call is
+    refused (DG_ERR_INVALID_ARG) instead of racing."""
+    t = _one_split(2)
+    leaves = np.array(t.leaf_list(), dtype=np.int32)
+    u = torch.zeros((2, t.Nq), dtype=torch.float64, device="cuda")
+    lib = dgx.load()
+    desc = dgx.dg_mesh_desc((dgx.C.c_double * 3)(*LO), (dgx.C.c_double * 3)(*HI), (dgx.C.c_int32 * 3)(2, 1, 1), 2)
+    ptr = dgx.C.c_void_p(u.data_ptr())
+    rc = lib.dg_octree_apply(dgx.C.byref(desc), leaves.ctypes.data_as(dgx.C.c_void_p), leaves.shape[0], 0, 0.125,
+                             ptr, ptr, 2, None)
+    assert rc == dgx.DG_ERR_INVALID_ARG

@@ -224,3 +224,31 @@ def test_library_face_connectivity_is_reciprocal():
         bad.refine([(0, 0, 0, 0)])
         bad.refine([(1, 1, 1, 1)])  # no balance()
         dgx.dg_octree_faces(LO, HI, (2, 2, 2), 2, np.array(bad.leaf_list(), dtype=np.int32))
+
+
+def test_library_rejects_overlapping_leaves():
+    """A leaf together with one of its own descendants is not a partition of
+    the box: dg_octree_faces refuses it (the root cell (0,0,0,0), its eight
+    children and the cell (0,1,0,0) would otherwise all get face kinds)."""
+    from paper_2510_21213_gb300 import dgx
+
+    leaves = [(0, 0, 0, 0), (0, 1, 0, 0)] + [(1, a, b, c) for c in range(2) for b in range(2) for a in range(2)]
+    with pytest.raises(dgx.DGError):
+        dgx.dg_octree_faces(LO, HI, (2, 1, 1), 2, np.array(leaves, dtype=np.int32))
+    # the same set without the parent is accepted
+    dgx.dg_octree_faces(LO, HI, (2, 1, 1), 2, np.array(leaves[1:], dtype=np.int32))
+
+
+def test_octree_apply_checks_field_shape_before_any_launch():
+    """dg_octree_apply takes no lengths, so the binding refuses a field whose
+    width is not n_leaves * (p+1)^3 before the library is called (CPU
+    tensors: nothing reaches a device)."""
+    torch = pytest.importorskip("torch")
+    from paper_2510_21213_gb300 import dgx
+
+    t = _refined(2)
+    leaves = np.array(t.leaf_list(), dtype=np.int32)
+    width = len(leaves) * 27
+    for bad in (torch.zeros(width), torch.zeros(2, width - 1), torch.zeros(2, width + 27)):
+        with pytest.raises(ValueError):
+            dgx.dg_octree_apply(LO, HI, (2, 2, 2), 2, leaves, bad)
