@@ -128,6 +128,9 @@ typedef struct {
   int32_t used_fallback;     /* 1 if a learned guess was rejected and the plain solver used */
   double rel_residual;       /* final FP64 true relative residual */
   double guess_rel_residual; /* FP64 relative residual of the initial guess (1 for the zero guess) */
+  double self_energy;        /* Coulomb self-energy of the source, (f|f) = sum_q W_q f(q) v(q) (Sec. 2.3.1):
+                                for a pair density f = psi_i psi_j the integral (ij|ij), for the density
+                                rho = 2 E_H; FP64, from the returned v */
 } dg_solve_stats;
 
 typedef struct {
@@ -188,7 +191,10 @@ int dg_pair_solve_batch(dg_handle h, const double* f_dev, int64_t B, double* v_d
  * W_j = sum_s psi_s v_sj, K = Psi^T diag(W_q) W and the energies.
  * K_host: [N*N] row-major K_ij (host). E_H, E_X: host scalars (may be NULL).
  * stats_host: [N(N+1)/2 + 1] (host, may be NULL): entry 0 is the Hartree
- * solve, then the pairs in the documented order. */
+ * solve, then the pairs in the documented order; their self_energy fields
+ * hold (rho|rho) = 2 E_H and the pair self-energies (ij|ij) of step S13
+ * (Sec. 2.3.1, Sec. 6.1.2), from the pair potentials before they are
+ * consumed by the accumulation. */
 int dg_exchange_build(dg_handle h, const double* psi_dev, int32_t N, double* K_host, double* E_H,
                       double* E_X, dg_solve_stats* stats_host, void* cuda_stream);
 

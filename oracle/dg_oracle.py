@@ -421,11 +421,16 @@ def gauss_sum_1_over_r(rmin, rmax, tol):
     raise RuntimeError("Gaussian-sum step search failed")
 
 
-def boundary_data_gausssum(mesh, f, tol=1e-12):
+def boundary_data_gausssum(mesh, f, tol=1e-12, chunk=8):
     """Dirichlet data of Sec. 6.3 with 1/r replaced by the Gaussian sum of
     Sec. 5.2, evaluated on the tensor grid as three 1-D contractions per term
-    and face. f: [nf, Nq]. Returns the same layout as boundary_data_direct."""
+    and face. f: [nf, Nq]. Returns the same layout as boundary_data_direct.
+    Sources are processed chunk at a time (memory only; every source's sums
+    are the same)."""
     f = np.atleast_2d(np.asarray(f, dtype=np.float64))
+    if f.shape[0] > chunk:
+        parts = [boundary_data_gausssum(mesh, f[i:i + chunk], tol, chunk) for i in range(0, f.shape[0], chunk)]
+        return [np.concatenate([pp[face] for pp in parts]) for face in range(6)]
     xq = [axis_nodes(mesh, d) for d in range(3)]
     xi, _ = gauss_legendre(mesh.n1)
     rmin = min((1.0 - xi[-1]) * mesh.h[d] / 2.0 for d in range(3))
@@ -436,28 +441,29 @@ def boundary_data_gausssum(mesh, f, tol=1e-12):
     out = [np.zeros((f.shape[0], mesh.L[[ax for ax in range(3) if ax != d][0]],
                      mesh.L[[ax for ax in range(3) if ax != d][1]])) for d in range(3) for _ in range(2)]
     W = quad_weights(mesh)
-    for r_ in range(f.shape[0]):
-        F = np.empty(mesh.Nq)
-        F[perm] = W * f[r_]
-        F = F.reshape(Lz, Ly, Lx)  # [Z, Y, X]
-        for d in range(3):
-            t = [ax for ax in range(3) if ax != d]
-            for side in range(2):
-                face = mesh.lo[d] if side == 0 else mesh.hi[d]
-                GN = np.exp(-np.outer(a, (xq[d] - face) ** 2))  # [k, L_d]
-                # contraction along the normal axis for all terms k at once
-                if d == 0:
-                    T = np.tensordot(F, GN, axes=([2], [1])).transpose(2, 1, 0)  # [k, y, z]
-                elif d == 1:
-                    T = np.tensordot(F, GN, axes=([1], [1])).transpose(2, 1, 0)  # [k, x, z]
-                else:
-                    T = np.tensordot(F, GN, axes=([0], [1])).transpose(2, 1, 0)  # [k, x, y]
-                acc = np.zeros((mesh.L[t[0]], mesh.L[t[1]]))
-                for k in range(len(c)):
-                    G1 = np.exp(-a[k] * (xq[t[0]][:, None] - xq[t[0]][None, :]) ** 2)
-                    G2 = np.exp(-a[k] * (xq[t[1]][:, None] - xq[t[1]][None, :]) ** 2)
-                    acc += c[k] * (G1 @ T[k] @ G2.T)
-                out[2 * d + side][r_] = acc
+    nf = f.shape[0]
+    F = np.empty((nf, mesh.Nq))
+    F[:, perm] = W[None, :] * f
+    F = F.reshape(nf, Lz, Ly, Lx)  # [source, Z, Y, X]
+    for d in range(3):
+        t = [ax for ax in range(3) if ax != d]
+        for side in range(2):
+            face = mesh.lo[d] if side == 0 else mesh.hi[d]
+            GN = np.exp(-np.outer(a, (xq[d] - face) ** 2))  # [k, L_d]
+            # contraction along the normal axis for all terms k at once
+            if d == 0:
+                T = np.tensordot(F, GN, axes=([3], [1])).transpose(0, 3, 2, 1)  # [src, k, y, z]
+            elif d == 1:
+                T = np.tensordot(F, GN, axes=([2], [1])).transpose(0, 3, 2, 1)  # [src, k, x, z]
+            else:
+                T = np.tensordot(F, GN, axes=([1], [1])).transpose(0, 3, 2, 1)  # [src, k, x, y]
+            # every source accumulates its terms k in ascending order
+            acc = np.zeros((nf, mesh.L[t[0]], mesh.L[t[1]]))
+            for k in range(len(c)):
+                G1 = np.exp(-a[k] * (xq[t[0]][:, None] - xq[t[0]][None, :]) ** 2)
+                G2 = np.exp(-a[k] * (xq[t[1]][:, None] - xq[t[1]][None, :]) ** 2)
+                acc += c[k] * (G1[None, :, :] @ T[:, k] @ G2.T[None, :, :])
+            out[2 * d + side][:] = acc
     return out
 
 
@@ -578,13 +584,17 @@ def poisson(mesh, f, penalty_form=0, eps=0.125, method="auto", g=None):
     return v, g
 
 
-def exchange_partial(mesh, psi, src_begin, src_end, penalty_form=0, eps=0.125, method="auto"):
+def exchange_partial(mesh, psi, src_begin, src_end, penalty_form=0, eps=0.125, method="auto", g_route="direct",
+                     with_self=False):
     """The part of the exchange build that sources [src_begin, src_end) of the
     list (0 = Hartree density rho, then the pairs of pair_list) contribute:
     K_part[i, j] = sum_q W_q psi_i(q) sum_{pairs (s, j) in range} psi_s(q) v_sj(q)
     (eq. fock_exchange, Sec. 6.1.2, summed over the listed pairs only; K is
     linear in the pair potentials, so disjoint ranges add up to K) and E_H
-    (Sec. 2.3.1) if source 0 is in the range, else 0."""
+    (Sec. 2.3.1) if source 0 is in the range, else 0. g_route "gausssum"
+    takes the Dirichlet data from boundary_data_gausssum at 1e-12 instead of
+    the direct quadrature (for meshes where the direct sum is too slow).
+    with_self: also return the sources' self-energies (f|f) = sum_q W_q f v."""
     psi = np.asarray(psi, dtype=np.float64)
     N = psi.shape[0]
     Wq = quad_weights(mesh)
@@ -594,7 +604,8 @@ def exchange_partial(mesh, psi, src_begin, src_end, penalty_form=0, eps=0.125, m
         return np.zeros((N, N)), 0.0
     rho = np.sum(psi * psi, axis=0)
     sources = np.stack([rho if k == 0 else psi[pairs[k - 1][0]] * psi[pairs[k - 1][1]] for k in idx])
-    v, _ = poisson(mesh, sources, penalty_form, eps, method)
+    g = boundary_data_gausssum(mesh, sources, tol=1e-12) if g_route == "gausssum" else None
+    v, _ = poisson(mesh, sources, penalty_form, eps, method, g=g)
     Wacc = np.zeros_like(psi)
     E_H = 0.0
     for row, k in enumerate(idx):
@@ -605,18 +616,24 @@ def exchange_partial(mesh, psi, src_begin, src_end, penalty_form=0, eps=0.125, m
         Wacc[j] += psi[s_] * v[row]
         if s_ != j:
             Wacc[s_] += psi[j] * v[row]
-    return (psi * Wq[None, :]) @ Wacc.T, E_H
+    K_part = (psi * Wq[None, :]) @ Wacc.T
+    if with_self:
+        return K_part, E_H, np.sum(Wq[None, :] * sources * v, axis=1)
+    return K_part, E_H
 
 
-def exchange_build(mesh, psi, penalty_form=0, eps=0.125, method="auto", keep_potentials=False):
-    """Hartree potential, pair potentials, K, E_H and E_X for orbitals psi [N, Nq]."""
+def exchange_build(mesh, psi, penalty_form=0, eps=0.125, method="auto", keep_potentials=False, g_route="direct"):
+    """Hartree potential, pair potentials, K, E_H and E_X for orbitals psi [N, Nq].
+    g_route "gausssum": Dirichlet data from boundary_data_gausssum at 1e-12
+    (pinned against the direct quadrature) instead of the direct sum."""
     psi = np.asarray(psi, dtype=np.float64)
     N = psi.shape[0]
     Wq = quad_weights(mesh)
     pairs = pair_list(N)
     rho = np.sum(psi * psi, axis=0)
     sources = np.stack([rho] + [psi[i] * psi[j] for (i, j) in pairs])
-    v, _ = poisson(mesh, sources, penalty_form, eps, method)
+    g = boundary_data_gausssum(mesh, sources, tol=1e-12) if g_route == "gausssum" else None
+    v, _ = poisson(mesh, sources, penalty_form, eps, method, g=g)
     vH, vpair = v[0], v[1:]
     Wacc = np.zeros_like(psi)
     for k, (s, j) in enumerate(pairs):
@@ -626,7 +643,11 @@ def exchange_build(mesh, psi, penalty_form=0, eps=0.125, method="auto", keep_pot
     K = (psi * Wq[None, :]) @ Wacc.T
     E_H = 0.5 * float(np.sum(Wq * rho * vH))
     E_X = -0.5 * float(np.trace(K))
-    out = {"K": K, "E_H": E_H, "E_X": E_X, "v_H": vH, "W": Wacc, "pairs": pairs}
+    # Coulomb self-energy of every source (Sec. 2.3.1): (f|f) = int f v, by the
+    # same pointwise quadrature; for a pair density the integral (ij|ij), for
+    # the density (rho|rho) = 2 E_H
+    self_e = np.sum(Wq[None, :] * sources * v, axis=1)
+    out = {"K": K, "E_H": E_H, "E_X": E_X, "v_H": vH, "W": Wacc, "pairs": pairs, "self": self_e}
     if keep_potentials:
         out["v_pairs"] = vpair
     return out

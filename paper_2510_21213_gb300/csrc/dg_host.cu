@@ -407,6 +407,7 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
     S.used_fallback = fbk[k];
     S.rel_residual = finite[k] ? rel[k] : NAN;
     S.guess_rel_residual = finite[k] ? grel[k] : NAN;
+    S.self_energy = 0.0;  // set by the callers that hold the sources
     if (!finite[k])
       S.status = DG_ERR_NONFINITE;
     else if (!(rel[k] <= rtol))
@@ -417,6 +418,21 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
     if (S.status != DG_OK && (worst == DG_OK || S.status < worst)) worst = S.status;
   }
   return worst;
+}
+
+// Coulomb self-energy of each source of the chunk, (f|f) = sum_q W_q f(q) v(q)
+// with v = x64 (Sec. 2.3.1; (ij|ij) for a pair density), into out[0..nsrc).
+static int self_energies(dg_ctx* h, const double* f, int nsrc, std::vector<double>& out, cudaStream_t s) {
+  out.assign(nsrc, 0.0);
+  if (nsrc == 0) return DG_OK;
+  std::vector<int> all(nsrc);
+  for (int k = 0; k < nsrc; ++k) all[k] = k;
+  DG_RET(upload_act(h, all, s));
+  DG_CK(launch_dot<double>(f, h->x64.as<double>(), h->d_W.as<double>(), scal(h, S_G1), h->part.as<double>(), h->Nq,
+                           h->act.as<int>(), nsrc, s));
+  DG_CK(cudaMemcpyAsync(out.data(), scal(h, S_G1), sizeof(double) * nsrc, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  return DG_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1195,6 +1211,11 @@ int dg_pair_solve_batch(dg_handle h, const double* f, int64_t B, double* v, dg_s
     const int rc = solve_chunk(h, nb, finite, stats ? stats + b0 : nullptr, s);
     if (rc == DG_ERR_CUDA || rc == DG_ERR_NO_MEMORY) return rc;
     if (rc != DG_OK && (worst == DG_OK || rc < worst)) worst = rc;
+    if (stats) {
+      std::vector<double> se;
+      DG_RET(self_energies(h, fc, nb, se, s));
+      for (int k = 0; k < nb; ++k) stats[b0 + k].self_energy = se[k];
+    }
     DG_CK(cudaMemcpyAsync(v + b0 * h->Nq, h->x64.p, sizeof(double) * h->Nq * nb, cudaMemcpyDeviceToDevice, s));
   }
   DG_CK(cudaStreamSynchronize(s));
@@ -1252,17 +1273,13 @@ static int exchange_build_range(dg_handle h, const double* psi, int32_t N, long 
     if (rc == DG_ERR_CUDA || rc == DG_ERR_NO_MEMORY) return rc;
     if (rc != DG_OK && (worst == DG_OK || rc < worst)) worst = rc;
     const double* v = h->x64.as<double>();
-    if (b0 == 0) {
-      // E_H = 1/2 sum_q W_q rho v_H (source 0 holds rho)
-      std::vector<int> a0{0};
-      DG_RET(upload_act(h, a0, s));
-      DG_CK(launch_dot<double>(h->f64.as<double>(), v, h->d_W.as<double>(), scal(h, S_RR), h->part.as<double>(), Nq,
-                               h->act.as<int>(), 1, s));
-      double val = 0.0;
-      DG_CK(cudaMemcpyAsync(&val, scal(h, S_RR), sizeof(double), cudaMemcpyDeviceToHost, s));
-      DG_CK(cudaStreamSynchronize(s));
-      eh = 0.5 * val;
-    }
+    // self-energies (f|f) = sum_q W_q f v of the chunk's sources: the pair
+    // self-energies (ij|ij), and for source 0 (rho) E_H = (rho|rho) / 2
+    std::vector<double> se;
+    DG_RET(self_energies(h, h->f64.as<double>(), nb, se, s));
+    if (stats)
+      for (int k = 0; k < nb; ++k) stats[b0 - src_begin + k].self_energy = se[k];
+    if (b0 == 0) eh = 0.5 * se[0];
     // W_j += psi_s v_sj and W_s += psi_j v_sj (s != j), per orbital in fixed order
     std::vector<std::vector<std::pair<int, int>>> per(N);
     for (int k = 0; k < nb; ++k) {
@@ -1382,6 +1399,11 @@ int dg_jk_apply(dg_handle h, const double* psi, int32_t N, const double* U, int6
     const int rc = solve_chunk(h, nb, finite, stats ? stats + b0 : nullptr, s);
     if (rc == DG_ERR_CUDA || rc == DG_ERR_NO_MEMORY) return rc;
     if (rc != DG_OK && (worst == DG_OK || rc < worst)) worst = rc;
+    if (stats) {
+      std::vector<double> se;
+      DG_RET(self_energies(h, h->f64.as<double>(), nb, se, s));
+      for (int k = 0; k < nb; ++k) stats[b0 + k].self_energy = se[k];
+    }
     const double* v = h->x64.as<double>();
     std::vector<int> ja, jb;
     if (JU && b0 == 0) {

@@ -71,6 +71,7 @@ class dg_solve_stats(C.Structure):
         ("used_fallback", C.c_int32),
         ("rel_residual", C.c_double),
         ("guess_rel_residual", C.c_double),
+        ("self_energy", C.c_double),
     ]
 
 
@@ -250,7 +251,7 @@ def dg_mesh_node_coords(lo, hi, n, p):
 def _stats_list(arr):
     return [{"iters": s.iters, "outer_refinements": s.outer_refinements, "status": s.status,
              "used_fallback": s.used_fallback, "rel_residual": s.rel_residual,
-             "guess_rel_residual": s.guess_rel_residual} for s in arr]
+             "guess_rel_residual": s.guess_rel_residual, "self_energy": s.self_energy} for s in arr]
 
 
 def dg_pair_solve_batch(h, f, v=None, stream=None, allow_unconverged=False):
@@ -674,6 +675,9 @@ class PoissonSolver:
 
     def exchange_build(self, psi, **kw):
         return dg_exchange_build(self.h, psi, **kw)
+
+    def exchange_build_range(self, psi, src_begin, src_end, **kw):
+        return dg_exchange_build_range(self.h, psi, src_begin, src_end, **kw)
 
     def jk_apply(self, psi, U, **kw):
         return dg_jk_apply(self.h, psi, U, **kw)

@@ -231,7 +231,8 @@ def _tiny_continuum():
     i1212 = S * S * i1111
     i1122 = math.erf(1.4) / 1.4
     i1112 = S * math.erf(0.7) / 0.7
-    return {"K11": i1111 + i1212, "K12": 2.0 * i1112, "E_H": 0.5 * (2 * i1111 + 2 * i1122)}
+    return {"K11": i1111 + i1212, "K12": 2.0 * i1112, "E_H": 0.5 * (2 * i1111 + 2 * i1122), "i1111": i1111,
+            "i1212": i1212}
 
 
 def test_tiny_system_converges_to_continuum():
@@ -242,8 +243,12 @@ def test_tiny_system_converges_to_continuum():
         m = oracle.Mesh([-8.0] * 3, [8.0] * 3, n, p)
         psi = inputs.orbitals(spec, oracle.node_coords(m))
         r = oracle.exchange_build(m, psi, method="fdm")
-        errs.append(max(abs(r["K"][0, 0] - ref["K11"]), abs(r["K"][0, 1] - ref["K12"]), abs(r["E_H"] - ref["E_H"])))
+        # pair self-energies (11|11), (12|12), (22|22): sources 1, 2, 3 of the list
+        se = r["self"]
+        errs.append(max(abs(r["K"][0, 0] - ref["K11"]), abs(r["K"][0, 1] - ref["K12"]), abs(r["E_H"] - ref["E_H"]),
+                        abs(se[1] - ref["i1111"]), abs(se[3] - ref["i1111"]), abs(se[2] - ref["i1212"])))
         assert abs(r["E_X"] + 0.5 * np.trace(r["K"])) < 1e-15
+        assert abs(se[0] - 2.0 * r["E_H"]) < 1e-14 * se[0]
     assert errs[0] > 10 * errs[1]
     assert errs[1] < 5e-3
 
