@@ -146,6 +146,8 @@ typedef struct {
   int64_t workspace_bytes; /* device workspace currently held by the handle */
   int32_t n_gauss_fp32; /* terms of the FP32 Gaussian sum of the mixed modes (0 in FP64 mode) */
   double gauss_relerr_fp32; /* its measured max relative error */
+  int32_t batch;        /* sources the solve calls process together (opts.batch, or the default that
+                           fills about 8 GB of FP64 fine-level vectors) */
 } dg_info;
 
 typedef struct dg_ctx* dg_handle;

@@ -986,6 +986,7 @@ int dg_get_info(dg_handle h, dg_info* info) {
   std::memset(info, 0, sizeof(*info));
   info->Nq = h->Nq;
   info->levels = h->nlev;
+  info->batch = default_batch(h);
   for (int l = 0; l < h->nlev && l < 16; ++l) {
     info->level_n[l] = h->levels[l].op.n[0];
     info->level_p[l] = h->levels[l].op.p;

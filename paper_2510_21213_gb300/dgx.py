@@ -90,6 +90,7 @@ class dg_info(C.Structure):
         ("workspace_bytes", C.c_int64),
         ("n_gauss_fp32", C.c_int32),
         ("gauss_relerr_fp32", C.c_double),
+        ("batch", C.c_int32),
     ]
 
 
