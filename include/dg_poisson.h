@@ -119,6 +119,11 @@ typedef struct {
   int32_t gauss_construction; /* Gaussian-sum 1/r: 0 = tabulated short sums (nonnegative least-squares fits,
                                  about 3-5x fewer terms), the trapezoidal rule where no table applies;
                                  1 = trapezoidal rule only */
+  int32_t tc_smoother;   /* MIXED modes: 1 (default) solves the Schwarz patch problems of the FP32 inner solve
+                            on the tensor cores (TF32 tcgen05 MMA) on levels of degree >= 6; 0 = FP32 SIMT */
+  int32_t nn_use_net;    /* MIXED_LEARNED: 1 (default) starts from the network's guess; 0 from the same
+                            guess without the network (the prolongated degree-1 coarse solution, smoothed and
+                            scaled), to measure what the network itself adds */
 } dg_solver_opts;
 
 typedef struct {

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "dg_setup.h"
+#include "dg_swtc.h"
 
 namespace dg {
 
@@ -101,6 +102,9 @@ struct Level {
   double lam_max = 0;            // lambda_max(D^-1 A) (point Jacobi)
   double lam_sw = 0;             // lambda_max(M_S A) estimate (Schwarz)
   DevBuf sw_tabs;                // Schwarz patch tables
+  DevBuf sw_tc;                  // tables of the tensor-core patch solve (FP32 inner solve), if used
+  SwTcPlan tcp;                  // its device blob (null: SIMT patch solve) and header
+  const SwTcPlan* tc() const { return tcp.blob ? &tcp : nullptr; }
 };
 
 struct BcAxisTables {
@@ -149,6 +153,7 @@ struct dg_ctx {
   dg::DevBuf f64, b64, x64, r64;   // [cap][Nq]
   dg::DevBuf flex, T1, T2, g;      // boundary data
   dg::DevBuf part, scal, act, flags, pidx;
+  dg::DevBuf tc_err;               // device word: a tensor-core kernel's wait gave up (DG_ERR_TIMEOUT)
   dg::DevBuf Wacc, kpart, Kdev;
   int cap = 0;
   std::vector<int> act_host;  // contents of act (device) as last uploaded

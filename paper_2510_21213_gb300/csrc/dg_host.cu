@@ -350,7 +350,7 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
     std::vector<int> nz;
     for (int k : act)
       if (bnorm2[k] > 0) nz.push_back(k);
-    DG_RET(learned_guess(h, nsrc, nz, bnorm2, true, rel, fbk, s));
+    DG_RET(learned_guess(h, nsrc, nz, bnorm2, h->opts.nn_use_net != 0, rel, fbk, s));
   }
   std::vector<double> grel = rel;
   std::vector<int> todo;
@@ -398,7 +398,13 @@ static int solve_chunk(dg_ctx* h, int nsrc, const std::vector<int>& finite, dg_s
   }
   std::vector<int> fl(h->cap, 0);
   DG_CK(cudaMemcpyAsync(fl.data(), h->flags.p, sizeof(int) * h->cap, cudaMemcpyDeviceToHost, s));
+  int tc_err = 0;
+  if (h->tc_err.p) DG_CK(cudaMemcpyAsync(&tc_err, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   DG_CK(cudaStreamSynchronize(s));
+  if (tc_err) {
+    h->err = "a tensor-core patch-solve kernel gave up waiting for its MMA or copy (bounded wait)";
+    return DG_ERR_TIMEOUT;
+  }
   int worst = DG_OK;
   for (int k = 0; k < nsrc; ++k) {
     dg_solve_stats S;
@@ -755,6 +761,21 @@ static int setup(dg_ctx* h) {
       DG_CK(L.sw_tabs.ensure(sizeof(double) * tb.size()));
       DG_CK(cudaMemcpy(L.sw_tabs.p, tb.data(), sizeof(double) * tb.size(), cudaMemcpyHostToDevice));
       DG_RET(estimate_lambda_schwarz(h, l, &L.lam_sw));
+      // FP32 inner solve: patch solves on the tensor cores where the degree allows it
+      if (o.precision != DG_PREC_FP64 && o.tc_smoother) {
+        if (!h->tc_err.p) {
+          DG_CK(h->tc_err.ensure(sizeof(int)));
+          DG_CK(cudaMemset(h->tc_err.p, 0, sizeof(int)));
+        }
+        const std::vector<unsigned char> blob = schwarz_tc_blob(L.op, tb, h->tc_err.as<int>());
+        if (!blob.empty()) {
+          DG_CK(schwarz_tc_prepare(L.op.n1));
+          DG_CK(L.sw_tc.ensure(blob.size()));
+          DG_CK(cudaMemcpy(L.sw_tc.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+          std::memcpy(&L.tcp.head, blob.data(), sizeof(SwTcHead));
+          L.tcp.blob = L.sw_tc.p;
+        }
+      }
     }
   }
   // fine-level nodes, weights
@@ -870,7 +891,7 @@ static int apply_smoother_t(dg_ctx* h, PrecWork<T>& w, int level, const T* r, T*
     DG_CK(launch_coarse_solve<T>(h->coarse_inv.as<double>(), h->Nc, r, z, a, nb, s));
   } else if (h->opts.smoother == DG_SMOOTH_SCHWARZ) {
     DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r, w.lev[level].zp.template as<T>(), z, nullptr, 0,
-                            0.0, 0.0, a, nb, s));
+                            0.0, 0.0, a, nb, s, L.tc()));
   } else {
     DG_CK(launch_cheb_first<T>(z, z, r, w.lev[level].invD.template as<T>(), 1.0, 1, L.op.Nq, a, nb, s));
   }
@@ -908,6 +929,8 @@ void dg_default_opts(dg_solver_opts* o) {
   o->coarse_smoother_degree = 0;
   o->p1_smoother = -1;
   o->gauss_construction = 0;
+  o->tc_smoother = 1;
+  o->nn_use_net = 1;
 }
 
 const char* dg_error_string(int status) {

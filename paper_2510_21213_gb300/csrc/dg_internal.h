@@ -131,10 +131,14 @@ cudaError_t launch_coarse_solve(const double* Ainv, int Nc, const T* r, T* x, co
                                 cudaStream_t s);
 
 // Schwarz smoother: zp[rhs][e][MP^3] = A_P^-1 R_P r, then with y = sum_P R_P^T zp:
-// mode 0: z = y; 1: z = c1 y, x = z; 2: z = c1 y, x += z; 3: z = c1 z + c2 y, x += z
+// mode 0: z = y; 1: z = c1 y, x = z; 2: z = c1 y, x += z; 3: z = c1 z + c2 y, x += z.
+// tc (FP32 only, may be null): the level's tensor-core patch solve, used instead
+// of the SIMT patch kernel
+struct SwTcPlan;
 template <typename T>
 cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
-                           T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s);
+                           T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s,
+                           const SwTcPlan* tc = nullptr);
 
 // sources and right-hand sides
 cudaError_t launch_pair_sources(const double* psi, int N, const int* pi, const int* pj, int nsrc, long long Nq,

@@ -43,7 +43,7 @@ struct MG {
     }
     if (sw)
       DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), r0, W.zp.as<T>(), d, x, zero_init ? 1 : 2,
-                              1.0 / theta, 0.0, act, nact, s));
+                              1.0 / theta, 0.0, act, nact, s, L.tc()));
     else
       DG_CK(launch_cheb_first<T>(x, d, r0, invD, 1.0 / theta, zero_init ? 1 : 0, Nq, act, nact, s));
     double rho_prev = 1.0 / sig1;
@@ -57,7 +57,7 @@ struct MG {
       const double rho = 1.0 / (2.0 * sig1 - rho_prev);
       if (sw)
         DG_CK(launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), res, W.zp.as<T>(), d, x, 3, rho * rho_prev,
-                                2.0 * rho / delta, act, nact, s));
+                                2.0 * rho / delta, act, nact, s, L.tc()));
       else
         DG_CK(launch_cheb_step<T>(x, d, res, invD, rho * rho_prev, 2.0 * rho / delta, Nq, act, nact, s));
       rho_prev = rho;

@@ -104,7 +104,7 @@ static double probe_us_per_source(dg_ctx* h, PrecWork<T>& w, int B, cudaStream_t
     launch_apply<T>(L.op, L.dop, 0, u, out, nullptr, dact, B, s);
     if (h->nlev > 1 && h->opts.smoother == DG_SMOOTH_SCHWARZ)
       launch_schwarz<T>(L.op, L.dop, L.sw_tabs.as<double>(), out, w.lev[0].zp.template as<T>(), u, nullptr, 0, 0.0,
-                        0.0, dact, B, s);
+                        0.0, dact, B, s, L.tc());
   };
   once();
   cudaEventRecord(e0, s);

@@ -100,7 +100,7 @@ int dg_apply_smoother_noalloc(dg_handle h, int32_t level, int32_t fp32, const vo
                                         s));
   } else if (fp32) {
     DG_CK(launch_schwarz<float>(L.op, L.dop, L.sw_tabs.as<double>(), (const float*)r, (float*)d.scratch, (float*)z,
-                                nullptr, 0, 0.0, 0.0, d.act, nb, s));
+                                nullptr, 0, 0.0, 0.0, d.act, nb, s, L.tc()));
   } else {
     DG_CK(launch_schwarz<double>(L.op, L.dop, L.sw_tabs.as<double>(), (const double*)r, d.scratch, (double*)z,
                                  nullptr, 0, 0.0, 0.0, d.act, nb, s));

@@ -13,6 +13,7 @@
 //                     at most 8 patches covering it; no atomics), fused with
 //                     the Chebyshev update d = c1 d + c2 z, x += d
 #include "dg_internal.h"
+#include "dg_swtc.h"
 
 namespace dg {
 
@@ -368,7 +369,8 @@ __global__ void __launch_bounds__(GatherCfg<N1>::THREADS)
 
 template <typename T, int N1>
 static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
-                              T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s) {
+                              T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s,
+                              const SwTcPlan* tc) {
   using C = SwCfg<T, N1>;
   const long long items = (long long)nact * hop.E;
 #if DG_SMEM_CARVEOUT >= 0
@@ -378,8 +380,14 @@ static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const doub
     carve = true;
   }
 #endif
-  count_launch();
-  k_schwarz_patch<T, N1><<<(unsigned)((items + C::EPB - 1) / C::EPB), C::THREADS, 0, s>>>(dop, tabs, r, zp, act, nact);
+  if (sizeof(T) == 4 && tc && tc->blob) {
+    const cudaError_t e = launch_schwarz_patch_tc(hop, dop, *tc, (const float*)r, (float*)zp, act, nact, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    count_launch();
+    k_schwarz_patch<T, N1><<<(unsigned)((items + C::EPB - 1) / C::EPB), C::THREADS, 0, s>>>(dop, tabs, r, zp, act,
+                                                                                           nact);
+  }
   constexpr int GT = GatherCfg<N1>::THREADS;
   long long gx = (hop.E + GatherCfg<N1>::GE - 1) / GatherCfg<N1>::GE;
 #if DG_GATHER_WAVE > 0
@@ -399,24 +407,27 @@ static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const doub
 
 template <typename T>
 cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
-                           T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s) {
+                           T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s,
+                           const SwTcPlan* tc) {
   if (nact == 0) return cudaSuccess;
   switch (hop.n1) {
-    case 2: return schwarz_n1<T, 2>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
-    case 3: return schwarz_n1<T, 3>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
-    case 4: return schwarz_n1<T, 4>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
-    case 5: return schwarz_n1<T, 5>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
-    case 6: return schwarz_n1<T, 6>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
-    case 7: return schwarz_n1<T, 7>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
-    case 8: return schwarz_n1<T, 8>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
-    case 9: return schwarz_n1<T, 9>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s);
+    case 2: return schwarz_n1<T, 2>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
+    case 3: return schwarz_n1<T, 3>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
+    case 4: return schwarz_n1<T, 4>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
+    case 5: return schwarz_n1<T, 5>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
+    case 6: return schwarz_n1<T, 6>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
+    case 7: return schwarz_n1<T, 7>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
+    case 8: return schwarz_n1<T, 8>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
+    case 9: return schwarz_n1<T, 9>(hop, dop, tabs, r, zp, z, x, mode, c1, c2, act, nact, s, tc);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template cudaError_t launch_schwarz<double>(const LevelOp&, const LevelOp*, const double*, const double*, double*,
-                                            double*, double*, int, double, double, const int*, int, cudaStream_t);
+                                            double*, double*, int, double, double, const int*, int, cudaStream_t,
+                                            const SwTcPlan*);
 template cudaError_t launch_schwarz<float>(const LevelOp&, const LevelOp*, const double*, const float*, float*,
-                                           float*, float*, int, double, double, const int*, int, cudaStream_t);
+                                           float*, float*, int, double, double, const int*, int, cudaStream_t,
+                                           const SwTcPlan*);
 
 }  // namespace dg

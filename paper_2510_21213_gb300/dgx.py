@@ -60,6 +60,8 @@ class dg_solver_opts(C.Structure):
         ("coarse_smoother_degree", C.c_int32),
         ("p1_smoother", C.c_int32),
         ("gauss_construction", C.c_int32),
+        ("tc_smoother", C.c_int32),
+        ("nn_use_net", C.c_int32),
     ]
 
 

@@ -1,10 +1,17 @@
-"""What the trained network gains: on held-out systems (seeds never used in
-training) at the configuration the network was trained for (16^3 elements,
-p = 7, 64 orbitals, 32 atoms), pair solves of the learned form against the
-mixed form without the network, both to the same FP64 true residual 1e-8.
+"""What the learned initial guess gains, on held-out systems (seeds 900-907,
+never used in training) at the configuration the network was trained for
+(16^3 elements, p = 7, 64 orbitals, 32 atoms): pair solves from three starting
+points, all to the same FP64 true residual 1e-8:
+  zero     the mixed form, x0 = 0;
+  coarse   the learned form's guess without its network: the degree-1 coarse
+           solution prolongated, smoothed and scaled (nn_use_net = 0);
+  network  the learned form: the network's correction of that coarse solution.
 
-The solutions must agree (the network only moves the starting point); the
-learned form must need fewer PCG iterations on average."""
+The solutions must agree (the guess only moves the starting point). The
+coarse guess must save iterations over x0 = 0; the network's guess is checked
+not to cost iterations over x0 = 0, and its mean against the coarse guess
+alone is reported: the network is credited only with what it adds to the
+coarse guess, not with the coarse guess's own gain."""
 
 import numpy as np
 import pytest
@@ -14,8 +21,8 @@ from paper_2510_21213_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-HELD_OUT = (900, 901)
-PAIRS_PER_SYSTEM = 24
+HELD_OUT = tuple(range(900, 908))
+PAIRS_PER_SYSTEM = 16
 
 
 @pytest.fixture(scope="module")
@@ -31,33 +38,43 @@ def dgx():
     return dgx
 
 
-def test_learned_guess_cuts_iterations_on_held_out_systems(dgx):
+def test_learned_guess_on_held_out_systems(dgx):
     lo, hi, n, p = [-12.0] * 3, [12.0] * 3, (16, 16, 16), 7
     kw = dict(bc_route=dgx.DG_BC_GAUSSSUM, rtol=1e-8)
-    mixed = dgx.PoissonSolver(lo, hi, n, p, precision=dgx.DG_PREC_MIXED, **kw)
-    learned = dgx.PoissonSolver(lo, hi, n, p, precision=dgx.DG_PREC_MIXED_LEARNED,
-                                nn_weights_path=dgx.default_nn_weights(7), **kw)
-    xyz, w = mixed.node_coords()
+    w7 = dgx.default_nn_weights(7)
+    forms = {
+        "zero": dgx.PoissonSolver(lo, hi, n, p, precision=dgx.DG_PREC_MIXED, **kw),
+        "coarse": dgx.PoissonSolver(lo, hi, n, p, precision=dgx.DG_PREC_MIXED_LEARNED, nn_weights_path=w7,
+                                    nn_use_net=0, **kw),
+        "network": dgx.PoissonSolver(lo, hi, n, p, precision=dgx.DG_PREC_MIXED_LEARNED, nn_weights_path=w7, **kw),
+    }
+    xyz, w = forms["zero"].node_coords()
     xyz_d = torch.tensor(xyz, device="cuda")
     w_d = torch.tensor(w, device="cuda")
     rng = np.random.default_rng(7)
-    it_m, it_l, fb = [], [], 0
+    its = {k: [] for k in forms}
+    fb = 0
     for seed in HELD_OUT:
         spec = inputs.random_system(seed=seed, n=16, p=7, n_orb=64, n_atoms=32)
         psi = inputs.orbitals_torch(spec, xyz_d, w_d)
         pairs = [tuple(sorted(rng.integers(0, 64, size=2))) for _ in range(PAIRS_PER_SYSTEM)]
         f = torch.stack([psi[i] * psi[j] for i, j in pairs]).contiguous()
-        vm, sm = mixed.solve(f)
-        vl, sl = learned.solve(f)
-        assert all(s["status"] == 0 and s["rel_residual"] <= 1e-8 for s in sm + sl)
+        v = {}
+        for name, s in forms.items():
+            v[name], st = s.solve(f)
+            assert all(x["status"] == 0 and x["rel_residual"] <= 1e-8 for x in st)
+            its[name] += [x["iters"] for x in st]
+            if name == "network":
+                fb += sum(x["used_fallback"] for x in st)
         # same solution within the mixed form's stated bound at rtol 1e-8
-        err = ((vl - vm).abs().amax(dim=1) / vm.abs().amax(dim=1)).max().item()
-        assert err < 2e-5
-        it_m += [s["iters"] for s in sm]
-        it_l += [s["iters"] for s in sl]
-        fb += sum(s["used_fallback"] for s in sl)
-    print(f"held-out pairs {len(it_m)}: mean PCG iterations mixed {np.mean(it_m):.2f}, learned {np.mean(it_l):.2f}, "
-          f"fallbacks {fb}")
-    assert np.mean(it_l) < np.mean(it_m)
-    mixed.close()
-    learned.close()
+        for name in ("coarse", "network"):
+            err = ((v[name] - v["zero"]).abs().amax(dim=1) / v["zero"].abs().amax(dim=1)).max().item()
+            assert err < 2e-5, (name, err)
+    mean = {k: float(np.mean(x)) for k, x in its.items()}
+    print(f"held-out pairs {len(its['zero'])}: mean PCG iterations zero {mean['zero']:.2f}, "
+          f"coarse guess {mean['coarse']:.2f}, network {mean['network']:.2f} "
+          f"(network - coarse {mean['network'] - mean['coarse']:+.2f}); fallbacks {fb}")
+    assert mean["coarse"] < mean["zero"]
+    assert mean["network"] <= mean["zero"]
+    for s in forms.values():
+        s.close()
