@@ -58,11 +58,13 @@ bool swtc_geometry(int n1, SwTcGeom& g) {
   g.sbo = g.kc * SWTC_LBO;
   g.a_bytes = ((mp2 + 7) / 8) * g.sbo;
   // patches per item: MP rows of the B operand each, at a stride of SWTC_CS rows
-  // (D columns), so that every tensor-memory load starts at a multiple of 4
-  g.np = g.mp == 11 ? 10 : 21;  // the B operand must fit next to two A factors
+  // (D columns), so that every tensor-memory load starts at a multiple of 4;
+  // two stages of B must fit next to the two factors
+  g.np = g.mp == 11 ? 4 : 10;
   g.ncol = (g.np * SWTC_CS + 15) / 16 * 16;
   g.b_bytes = (g.ncol / 8) * g.sbo;
-  return 2 * (size_t)g.a_bytes + g.b_bytes + sizeof(SwTcShared) <= 232448;
+  return 2 * (size_t)g.a_bytes + SWTC_BSLOTS * (size_t)g.b_bytes + sizeof(SwTcShared) <= 232448 &&
+         g.np <= SWTC_NPMAX && SWTC_DSLOTS * g.ncol <= SWTC_TMEM_COLS;
 }
 
 // Host tables of the tensor-core patch solve of one level (layout in
@@ -96,6 +98,7 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
     if ((int)rep[d].size() > SWTC_MAXCLS) return {};
     off += (size_t)L.n[d] * STR;
   }
+  if (L.n[0] * L.n[1] > SWTC_MAXCOLS || L.n[2] > SWTC_MAXNZ) return {};
   auto tab = [&](int d, int pos) {
     size_t o = 0;
     for (int dd = 0; dd < d; ++dd) o += (size_t)L.n[dd] * STR;
@@ -110,6 +113,8 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
   H.nz = L.n[2];
   H.err = err_dev;
   const int ncx = (int)rep[0].size(), ncy = (int)rep[1].size(), ncz = (int)rep[2].size();
+  H.ncx = ncx;
+  H.ncy = ncy;
   H.ncz = ncz;
   // segments: class pairs (cx, cy) with their element columns (ex, ey)
   std::vector<int> cols;
@@ -183,9 +188,22 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
 }
 
 // ---------------------------------------------------------------------------
-// kernel
+// kernel: a pipeline over work items, each CTA taking a contiguous range.
+// Warp roles: producers decode an item and fill its B operand (2 slots),
+// the MMA thread issues MMA 1 as soon as a B is full and MMA 2 as soon as the
+// consumers have rewritten it, consumers run the z-step of item i and then
+// read out item i - 1 (accumulators in 3 TMEM slots, item descriptions in 4).
+// Every hand-off is an mbarrier; every wait is bounded.
 // ---------------------------------------------------------------------------
 constexpr long long kWaitLimit = 1LL << 31;  // clock cycles (about a second) before a wait gives up
+
+__device__ __forceinline__ bool swtc_wait(SwTcShared& sh, const SwTcHead* H, unsigned long long* bar,
+                                          uint32_t parity) {
+  if (tc::mbar_wait(tc::smem_addr(bar), parity, kWaitLimit)) return true;
+  atomicExch(H->err, DG_ERR_TIMEOUT);
+  atomicExch(&sh.abort, 1);
+  return false;
+}
 
 template <int N1>
 __global__ void __launch_bounds__(SWTC_THREADS, 1)
@@ -195,228 +213,317 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ SwTcShared sh;
   const SwTcHead* H = (const SwTcHead*)blob;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;
-  const int L = 32 * quad + lane;  // TMEM lane of this thread: mode / node (j, l) = (L / MP, L % MP)
-  const bool active = L < MP2;
-  const int a_bytes = H->geom.a_bytes, sbo = H->geom.sbo, NP = H->geom.np, kc = H->geom.kc;
-  const int ncol = H->geom.ncol;
-  unsigned char* sA0 = dsm;
-  unsigned char* sA1 = dsm + a_bytes;
-  unsigned char* sB = dsm + 2 * a_bytes;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int a_bytes = H->geom.a_bytes, b_bytes = H->geom.b_bytes, sbo = H->geom.sbo, NP = H->geom.np;
+  const int kc = H->geom.kc, ncol = H->geom.ncol, nseg = H->nseg;
+  const long long off_a = H->off_a;
+  unsigned char* sAf = dsm;
+  unsigned char* sAi = dsm + a_bytes;
+  unsigned char* sB0 = dsm + 2 * a_bytes;
   const int nx = H->nx, ny = H->ny, nz = H->nz;
   const int E = nx * ny * nz;
   const long long Nq = (long long)E * NPE;
-  const int* cols = (const int*)(blob + H->off_cols);
-  const int* zcls = (const int*)(blob + H->off_zcls);
-  // ---- set-up: barriers, tensor memory, z tables, zeroed B operand
+  // ---- set-up: barriers, tensor memory, staged tables, item offsets, zeroed B
   if (tid == 0) {
-    tc::mbar_init(tc::smem_addr(&sh.mbar_tma), 1);
-    tc::mbar_init(tc::smem_addr(&sh.mbar_mma), 1);
+    for (int b = 0; b < SWTC_BSLOTS; ++b) {
+      tc::mbar_init(tc::smem_addr(&sh.full[b]), SWTC_PRODUCERS);
+      tc::mbar_init(tc::smem_addr(&sh.b2[b]), SWTC_CONSUMERS);
+    }
+    for (int d = 0; d < SWTC_DSLOTS; ++d) {
+      tc::mbar_init(tc::smem_addr(&sh.d1[d]), 1);
+      tc::mbar_init(tc::smem_addr(&sh.d2[d]), 1);
+      tc::mbar_init(tc::smem_addr(&sh.empty[d]), SWTC_CONSUMERS);
+    }
+    tc::mbar_init(tc::smem_addr(&sh.tma_f), 1);
+    tc::mbar_init(tc::smem_addr(&sh.tma_i), 1);
     tc::mbar_init_fence();
     sh.abort = 0;
+    int acc = 0;
+    for (int sg = 0; sg < nseg; ++sg) {
+      sh.item0[sg] = acc;
+      acc += (int)(((long long)H->seg_ncol[sg] * nz * nact + NP - 1) / NP);
+    }
+    sh.item0[nseg] = acc;
   }
   if (warp == 0) tc::tmem_alloc(&sh.tmem, SWTC_TMEM_COLS);
   {
     const float* zt = (const float*)(blob + H->off_z);
     for (int i = tid; i < H->ncz * SWTC_ZSTR(MP); i += SWTC_THREADS) sh.z[i] = zt[i];
-    const int nseg = H->nseg;
-    if (tid == 0) {
-      int acc = 0;
-      for (int s = 0; s < nseg; ++s) {
-        sh.item0[s] = acc;
-        acc += (int)(((long long)H->seg_ncol[s] * nz * nact + NP - 1) / NP);
-      }
-      sh.item0[nseg] = acc;
+    for (int i = tid; i < nseg; i += SWTC_THREADS) {
+      sh.seg_col0[i] = H->seg_col0[i];
+      sh.seg_ncol[i] = H->seg_ncol[i];
+      sh.seg_cx[i] = (unsigned char)H->seg_cx[i];
+      sh.seg_cy[i] = (unsigned char)H->seg_cy[i];
     }
-    uint4* b4 = (uint4*)sB;
-    for (int i = tid; i < H->geom.b_bytes / 16; i += SWTC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
+    const int* cols = (const int*)(blob + H->off_cols);
+    for (int i = tid; i < nx * ny; i += SWTC_THREADS) sh.cols[i] = make_short2((short)cols[2 * i], (short)cols[2 * i + 1]);
+    const int* zc = (const int*)(blob + H->off_zcls);
+    for (int i = tid; i < nz; i += SWTC_THREADS) sh.zcls[i] = (unsigned char)zc[i];
+    for (int i = tid; i < nact && i < SWTC_MAXACT; i += SWTC_THREADS) sh.act[i] = (unsigned short)act[i];
+    const float* xy = (const float*)(blob + H->off_xy);
+    for (int i = tid; i < 2 * SWTC_MAXCLS * (MP + 1); i += SWTC_THREADS) {
+      const int d = i / (SWTC_MAXCLS * (MP + 1)), rem = i % (SWTC_MAXCLS * (MP + 1));
+      const int c = rem / (MP + 1), k = rem % (MP + 1);
+      if (c < (d == 0 ? H->ncx : H->ncy)) sh.lxy[d][c][k] = xy[(d == 0 ? 0 : H->off_y) + (size_t)c * (MP + 1) + k];
+    }
+    uint4* b4 = (uint4*)sB0;
+    for (int i = tid; i < SWTC_BSLOTS * b_bytes / 16; i += SWTC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
   }
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = sh.tmem;
-  const uint32_t tlane = tmem + ((uint32_t)(32 * quad) << 16);
-  const uint32_t mbar_tma = tc::smem_addr(&sh.mbar_tma), mbar_mma = tc::smem_addr(&sh.mbar_mma);
-  const uint32_t idesc = tc::idesc_tf32(128, ncol);
-  uint32_t ph_mma = 0, ph_tma = 0;
-  int cur_seg = -1;
-  // per-thread constants of the current segment and z class
-  float lxy = 0.f;
-  bool vxy = false;
-  int cur_cz = -1;
-  float S[MP][MP], inv[MP];
-  const int total = sh.item0[H->nseg];
-  const int jj = L / MP, ll = L % MP;
-  for (int it = blockIdx.x; it < total; it += gridDim.x) {
-    // ---- decode the item: segment, patches (source, element, z position)
-    int seg = 0;
-    while (sh.item0[seg + 1] <= it) ++seg;
-    const long long q0 = (long long)(it - sh.item0[seg]) * NP;
-    const int ncs = H->seg_ncol[seg];
-    const long long per_z = (long long)ncs * nact;
-    const int np = (int)std::min<long long>(NP, per_z * nz - q0);
-    if (tid < np) {
-      const long long q = q0 + tid;
-      const int ez = (int)(q / per_z);
-      const long long rem = q - (long long)ez * per_z;
-      const int colrel = (int)(rem / nact), a = (int)(rem - (long long)colrel * nact);
-      const int ex = cols[2 * (H->seg_col0[seg] + colrel)], ey = cols[2 * (H->seg_col0[seg] + colrel) + 1];
-      sh.src[tid] = act[a];
-      sh.elem[tid] = ex + nx * (ey + ny * ez);
-      sh.ez[tid] = ez;
-      sh.ex[tid] = ex;
-      sh.ey[tid] = ey;
-    }
-    // ---- new class pair: bulk-copy its two Kronecker factors (no MMA reads them now)
-    if (seg != cur_seg) {
-      if (tid == 0) {
-        const unsigned char* src = blob + H->off_a + (size_t)seg * 2 * a_bytes;
-        tc::mbar_expect_tx(mbar_tma, 2u * (uint32_t)a_bytes);
-        tc::bulk_g2s(sA0, src, (uint32_t)a_bytes, mbar_tma);
-        tc::bulk_g2s(sA1, src + a_bytes, (uint32_t)a_bytes, mbar_tma);
+  // each CTA takes a contiguous range of items, so that it rarely crosses into
+  // another class pair (a new pair costs a reload of both factors)
+  const int total = sh.item0[nseg];
+  const int per_cta = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int first = (int)blockIdx.x * per_cta;
+  const int nmine = max(0, min(per_cta, total - first));
+
+  if (tid >= SWTC_CONSUMERS && tid < SWTC_CONSUMERS + SWTC_PRODUCERS) {
+    // ================= producers: decode and fill =================
+    const int L = tid - SWTC_CONSUMERS;  // B column (j, l) this thread fills
+    const int jj = L / MP, ll = L % MP;
+    for (int li = 0; li < nmine; ++li) {
+      const int b = li % SWTC_BSLOTS;
+      // B slot free once MMA 2 of item li - 2 is done; description slot free
+      // once item li - 4 is read out
+      bool ok = li < SWTC_BSLOTS ||
+                swtc_wait(sh, H, &sh.d2[(li - SWTC_BSLOTS) % SWTC_DSLOTS], ((li - SWTC_BSLOTS) / SWTC_DSLOTS) & 1);
+      ok = ok && (li < SWTC_ISLOTS || swtc_wait(sh, H, &sh.empty[(li - SWTC_ISLOTS) % SWTC_DSLOTS],
+                                                ((li - SWTC_ISLOTS) / SWTC_DSLOTS) & 1));
+      // all producers leave together (they share a named barrier)
+      if (tc::named_barrier_or(1, SWTC_PRODUCERS, !ok || sh.abort != 0)) break;
+      const int it = first + li;
+      SwTcItem& I = sh.item[li % SWTC_ISLOTS];
+      int seg = 0;
+      while (sh.item0[seg + 1] <= it) ++seg;
+      // patch counts of a segment stay below 2^31 (columns x sources x z positions)
+      const int q0 = (it - sh.item0[seg]) * NP;
+      const int per_z = sh.seg_ncol[seg] * nact;
+      const int np = min(NP, per_z * nz - q0);
+      if (L < np) {
+        const int q = q0 + L;
+        const int ez = q / per_z;
+        const int rem = q - ez * per_z;
+        const int colrel = rem / nact, a = rem - colrel * nact;
+        const short2 c = sh.cols[sh.seg_col0[seg] + colrel];
+        I.src[L] = a < SWTC_MAXACT ? (int)sh.act[a] : act[a];
+        I.ex[L] = c.x;
+        I.ey[L] = c.y;
+        I.ez[L] = (short)ez;
+        I.cz[L] = (short)sh.zcls[ez];
+        I.elem[L] = c.x + nx * (c.y + ny * ez);
       }
-      const float* xy = (const float*)(blob + H->off_xy);
-      const float* tx = xy + (size_t)H->seg_cx[seg] * (MP + 1);
-      const float* ty = xy + H->off_y + (size_t)H->seg_cy[seg] * (MP + 1);
-      if (active) {
-        lxy = tx[ll] + ty[jj];
-        vxy = ll < (int)tx[MP] && jj < (int)ty[MP];
+      // z offsets of every (patch, z-node): the same for all (x, y) of the patch
+      if (L < np * MP) {
+        const int i = L / MP, k = L - (L / MP) * MP;
+        const int q = q0 + i;
+        const int ez = q / per_z;
+        const int oLz = ez > 0, mz = N1 + oLz + (ez < nz - 1);
+        const int Z = ez * N1 - oLz + k;
+        const int EZ = Z / N1;
+        I.zoff[i][k] = k < mz ? EZ * nx * ny * NPE + N1 * N1 * (Z - EZ * N1) : -1;
       }
-      cur_cz = -1;
-    }
-    __syncthreads();
-    // ---- fill B: row (i, k), column (j, l) = residual at patch node (l, j, k)
-    if (active) {
-      for (int i = half; i < np; i += 2) {
-        const int e = sh.elem[i];
-        const int ex = sh.ex[i], ey = sh.ey[i], ez = sh.ez[i];
-        const int oLx = ex > 0, oLy = ey > 0, oLz = ez > 0;
-        const int mx = N1 + oLx + (ex < nx - 1), my = N1 + oLy + (ey < ny - 1), mz = N1 + oLz + (ez < nz - 1);
-        const int X = ex * N1 - oLx + ll, Y = ey * N1 - oLy + jj;
-        const bool vx = ll < mx && jj < my;
-        const int EX = vx ? X / N1 : 0, EY = vx ? Y / N1 : 0;
-        const long long bxy =
-            (long long)sh.src[i] * Nq + (long long)(EX + nx * EY) * NPE + (X - EX * N1) + N1 * (Y - EY * N1);
-        (void)e;
+      if (L == 0) {
+        I.np = np;
+        I.seg = seg;
+      }
+      tc::named_barrier(1, SWTC_PRODUCERS);
+      unsigned char* sB = sB0 + b * b_bytes;
+      if (L < MP2) {
+        // this thread's column of B: byte offset of row 0 in its 4-column group
+        unsigned char* col = sB + (L / 4) * SWTC_LBO + (L % 4) * 4;
+        for (int i = 0; i < np; ++i) {
+          const int ex = I.ex[i], ey = I.ey[i];
+          const int oLx = ex > 0, oLy = ey > 0;
+          const int mx = N1 + oLx + (ex < nx - 1), my = N1 + oLy + (ey < ny - 1);
+          const int X = ex * N1 - oLx + ll, Y = ey * N1 - oLy + jj;
+          const bool vx = ll < mx && jj < my;
+          const int EX = vx ? X / N1 : 0, EY = vx ? Y / N1 : 0;
+          const float* pxy = r + (long long)I.src[i] * Nq + (EX + nx * EY) * NPE + (X - EX * N1) + N1 * (Y - EY * N1);
 #pragma unroll
-        for (int k = 0; k < MP; ++k) {
-          const int Z = ez * N1 - oLz + k;
-          const bool v = vx && k < mz;
-          const int EZ = v ? Z / N1 : 0;
-          const float* g = v ? r + bxy + (long long)EZ * nx * ny * NPE + (long long)N1 * N1 * (Z - EZ * N1) : r;
-          const int row = i * SWTC_CS + k;
-          tc::cp_async4(sB + (size_t)(row / 8) * sbo + (size_t)(L / 4) * SWTC_LBO + (size_t)(row % 8) * 16 +
-                            (size_t)(L % 4) * 4,
-                        g, v ? 4u : 0u);
+          for (int k = 0; k < MP; ++k) {
+            const int zo = I.zoff[i][k];
+            const bool v = vx && zo >= 0;
+            const int row = i * SWTC_CS + k;
+            tc::cp_async4(col + (row >> 3) * sbo + (row & 7) * 16, v ? pxy + zo : r, v ? 4u : 0u);
+          }
         }
       }
+      tc::cp_async_wait_all();
+      tc::fence_proxy_async();
+      tc::mbar_arrive(tc::smem_addr(&sh.full[b]));
     }
-    tc::cp_async_wait_all();
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    // ---- MMA 1: D = A_fwd x B^T
-    if (tid == 0) {
-      tc::fence_after_sync();
-      bool ok = true;
-      if (seg != cur_seg) {
-        ok = tc::mbar_wait(mbar_tma, ph_tma, kWaitLimit);
-        ph_tma ^= 1;
-      }
-      if (!ok) {
-        atomicExch(H->err, DG_ERR_TIMEOUT);
-        sh.abort = 1;
-      } else {
+  } else if (tid >= SWTC_CONSUMERS + SWTC_PRODUCERS) {
+    // ================= MMA issuer (one thread) =================
+    if (tid == SWTC_CONSUMERS + SWTC_PRODUCERS) {
+      const uint32_t idesc = tc::idesc_tf32(128, ncol);
+      int seg_f = -1, seg_i = -1;
+      uint32_t ph_f = 0, ph_i = 0;
+      // MMA 2 of item k: after the consumers rewrote its B
+      auto mma2 = [&](int k) -> bool {
+        const int b = k % SWTC_BSLOTS, d = k % SWTC_DSLOTS;
+        if (!swtc_wait(sh, H, &sh.b2[b], (k / SWTC_BSLOTS) & 1)) return false;
+        const int seg = sh.item[k % SWTC_ISLOTS].seg;
+        if (seg != seg_i) {
+          // the inverse factor is read by MMA 2 of item k - 1: let it finish first
+          if (k >= 1 && !swtc_wait(sh, H, &sh.d2[(k - 1) % SWTC_DSLOTS], ((k - 1) / SWTC_DSLOTS) & 1)) return false;
+          tc::mbar_expect_tx(tc::smem_addr(&sh.tma_i), (uint32_t)a_bytes);
+          tc::bulk_g2s(sAi, blob + off_a + ((size_t)seg * 2 + 1) * a_bytes, (uint32_t)a_bytes,
+                       tc::smem_addr(&sh.tma_i));
+          if (!swtc_wait(sh, H, &sh.tma_i, ph_i)) return false;
+          ph_i ^= 1;
+          seg_i = seg;
+        }
+        tc::fence_after_sync();
+        const uint32_t sb = tc::smem_addr(sB0 + b * b_bytes);
         for (int s = 0; s < kc / 2; ++s)
-          tc::mma_tf32(tmem, tc::desc_kmajor(tc::smem_addr(sA0) + s * 2 * SWTC_LBO, SWTC_LBO, sbo),
-                       tc::desc_kmajor(tc::smem_addr(sB) + s * 2 * SWTC_LBO, SWTC_LBO, sbo), idesc, s > 0);
-        tc::mma_commit(mbar_mma);
-      }
-    }
-    cur_seg = seg;
-    __syncthreads();
-    if (sh.abort) break;
-    if (!tc::mbar_wait(mbar_mma, ph_mma, kWaitLimit)) {
-      atomicExch(H->err, DG_ERR_TIMEOUT);
-      sh.abort = 1;
-    }
-    ph_mma ^= 1;
-    tc::fence_after_sync();
-    __syncthreads();
-    if (sh.abort) break;
-    // ---- z-step: Sz^T, scaling, Sz along each patch's z line, back into B
-    for (int i = half; i < np; i += 2) {
-      float t[SWTC_CS];
-      tc::tmem_ld_x4<SWTC_CS / 4>(tlane + i * SWTC_CS, t);
-      tc::tmem_wait_ld();
-      const int cz = zcls[sh.ez[i]];
-      if (cz != cur_cz) {
-        cur_cz = cz;
-        const float* zt = sh.z + cz * SWTC_ZSTR(MP);
-        const int mzc = (int)zt[MP2 + MP];
-#pragma unroll
-        for (int a = 0; a < MP; ++a)
-#pragma unroll
-          for (int b = 0; b < MP; ++b) S[a][b] = zt[a * MP + b];
-#pragma unroll
-        for (int b = 0; b < MP; ++b) inv[b] = (vxy && b < mzc) ? 1.0f / (lxy + zt[MP2 + b]) : 0.0f;
-      }
-      if (active) {
-        float u[MP];
-#pragma unroll
-        for (int b = 0; b < MP; ++b) {
-          float acc = 0.f;
-#pragma unroll
-          for (int a = 0; a < MP; ++a) acc = fmaf(S[a][b], t[a], acc);
-          u[b] = acc * inv[b];
+          tc::mma_tf32(tmem + d * ncol, tc::desc_kmajor(tc::smem_addr(sAi) + s * 2 * SWTC_LBO, SWTC_LBO, sbo),
+                       tc::desc_kmajor(sb + s * 2 * SWTC_LBO, SWTC_LBO, sbo), idesc, s > 0);
+        tc::mma_commit(tc::smem_addr(&sh.d2[d]));
+        return true;
+      };
+      for (int li = 0; li < nmine; ++li) {
+        const int b = li % SWTC_BSLOTS, d = li % SWTC_DSLOTS;
+        if (!swtc_wait(sh, H, &sh.full[b], (li / SWTC_BSLOTS) & 1)) break;
+        // accumulator slot free once item li - 3 is read out
+        if (li >= SWTC_DSLOTS &&
+            !swtc_wait(sh, H, &sh.empty[(li - SWTC_DSLOTS) % SWTC_DSLOTS], ((li - SWTC_DSLOTS) / SWTC_DSLOTS) & 1))
+          break;
+        const int seg = sh.item[li % SWTC_ISLOTS].seg;
+        if (seg != seg_f) {
+          if (li >= 1 && !swtc_wait(sh, H, &sh.d1[(li - 1) % SWTC_DSLOTS], ((li - 1) / SWTC_DSLOTS) & 1)) break;
+          tc::mbar_expect_tx(tc::smem_addr(&sh.tma_f), (uint32_t)a_bytes);
+          tc::bulk_g2s(sAf, blob + off_a + (size_t)seg * 2 * a_bytes, (uint32_t)a_bytes, tc::smem_addr(&sh.tma_f));
+          if (!swtc_wait(sh, H, &sh.tma_f, ph_f)) break;
+          ph_f ^= 1;
+          seg_f = seg;
         }
-#pragma unroll
-        for (int a = 0; a < MP; ++a) {
-          float acc = 0.f;
-#pragma unroll
-          for (int b = 0; b < MP; ++b) acc = fmaf(S[a][b], u[b], acc);
-          const int row = i * SWTC_CS + a;
-          *(float*)(sB + (size_t)(row / 8) * sbo + (size_t)(L / 4) * SWTC_LBO + (size_t)(row % 8) * 16 +
-                    (size_t)(L % 4) * 4) = tc::to_tf32(acc);
-        }
+        tc::fence_after_sync();
+        const uint32_t sb = tc::smem_addr(sB0 + b * b_bytes);
+        for (int s = 0; s < kc / 2; ++s)
+          tc::mma_tf32(tmem + d * ncol, tc::desc_kmajor(tc::smem_addr(sAf) + s * 2 * SWTC_LBO, SWTC_LBO, sbo),
+                       tc::desc_kmajor(sb + s * 2 * SWTC_LBO, SWTC_LBO, sbo), idesc, s > 0);
+        tc::mma_commit(tc::smem_addr(&sh.d1[d]));
+        if (li >= 1 && !mma2(li - 1)) break;
       }
+      if (nmine >= 1 && !sh.abort) mma2(nmine - 1);
     }
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    // ---- MMA 2: D = A_inv x B^T
-    if (tid == 0) {
+  } else {
+    // ================= consumers: z-step of item li, output of item li - 1 =================
+    const int L = tid;  // TMEM lane: mode (j', l') for the z-step, node (j, l) for the output
+    const int jj = L / MP, ll = L % MP;
+    const bool active = L < MP2;
+    const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+    float S[MP][MP], inv[MP];
+    float lxy = 0.f;
+    bool vxy = false;
+    int cur_seg = -1, cur_cz = -1;
+    // output of item k: patch node (l, j, k') of each patch
+    auto output = [&](int k) -> bool {
+      const int d = k % SWTC_DSLOTS;
+      const bool ok = swtc_wait(sh, H, &sh.d2[d], (k / SWTC_DSLOTS) & 1);
+      if (__any_sync(0xffffffffu, !ok || sh.abort != 0)) return false;
       tc::fence_after_sync();
-      for (int s = 0; s < kc / 2; ++s)
-        tc::mma_tf32(tmem, tc::desc_kmajor(tc::smem_addr(sA1) + s * 2 * SWTC_LBO, SWTC_LBO, sbo),
-                     tc::desc_kmajor(tc::smem_addr(sB) + s * 2 * SWTC_LBO, SWTC_LBO, sbo), idesc, s > 0);
-      tc::mma_commit(mbar_mma);
-    }
-    if (!tc::mbar_wait(mbar_mma, ph_mma, kWaitLimit)) {
-      atomicExch(H->err, DG_ERR_TIMEOUT);
-      sh.abort = 1;
-    }
-    ph_mma ^= 1;
-    tc::fence_after_sync();
-    __syncthreads();
-    if (sh.abort) break;
-    // ---- output: patch node (l, j, k) of patch i
-    for (int i = half; i < np; i += 2) {
-      float v[SWTC_CS];
-      tc::tmem_ld_x4<SWTC_CS / 4>(tlane + i * SWTC_CS, v);
-      tc::tmem_wait_ld();
-      if (active) {
-        float* out = zp + ((long long)sh.src[i] * E + sh.elem[i]) * MP3 + L;
+      const SwTcItem& I = sh.item[k % SWTC_ISLOTS];
+      const uint32_t tcol = tlane + d * ncol;
+      const int np = I.np;
+      uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
+      tc::tmem_ld12_async(tcol, nx12);
+      for (int i = 0; i < np; ++i) {
+        tc::tmem_wait12(nx12);
+        float v[SWTC_CS];
 #pragma unroll
-        for (int k = 0; k < MP; ++k) out[k * MP2] = v[k];
+        for (int c = 0; c < SWTC_CS; ++c) v[c] = __uint_as_float(nx12[c]);
+        if (i + 1 < np) tc::tmem_ld12_async(tcol + (i + 1) * SWTC_CS, nx12);
+        if (active) {
+          float* out = zp + ((long long)I.src[i] * E + I.elem[i]) * MP3 + L;
+#pragma unroll
+          for (int c = 0; c < MP; ++c) out[c * MP2] = v[c];
+        }
       }
+      tc::fence_before_sync();
+      tc::mbar_arrive(tc::smem_addr(&sh.empty[d]));
+      return true;
+    };
+    int li = 0;
+    for (; li < nmine; ++li) {
+      const int b = li % SWTC_BSLOTS, d = li % SWTC_DSLOTS;
+      // full[b] (the producers' item description) then d1[d] (MMA 1 done); full[b]
+      // cannot move on before this thread's z-step of the item (b2[b] -> MMA 2)
+      const bool ok = swtc_wait(sh, H, &sh.full[b], (li / SWTC_BSLOTS) & 1) &&
+                      swtc_wait(sh, H, &sh.d1[d], (li / SWTC_DSLOTS) & 1);
+      // tensor-memory loads are warp-collective: a warp leaves as a whole
+      if (__any_sync(0xffffffffu, !ok || sh.abort != 0)) break;
+      tc::fence_after_sync();
+      const SwTcItem& I = sh.item[li % SWTC_ISLOTS];
+      const int np = I.np;
+      if (I.seg != cur_seg) {
+        cur_seg = I.seg;
+        const float* tx = sh.lxy[0][sh.seg_cx[cur_seg]];
+        const float* ty = sh.lxy[1][sh.seg_cy[cur_seg]];
+        lxy = active ? tx[ll] + ty[jj] : 0.f;
+        vxy = active && ll < (int)tx[MP] && jj < (int)ty[MP];
+        cur_cz = -1;
+      }
+      unsigned char* sB = sB0 + b * b_bytes;
+      const uint32_t tcol = tlane + d * ncol;
+      // z-step: Sz^T, scaling, Sz along each patch's z line, back into B as TF32
+      uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
+      tc::tmem_ld12_async(tcol, nx12);
+      for (int i = 0; i < np; ++i) {
+        tc::tmem_wait12(nx12);
+        float t[SWTC_CS];
+#pragma unroll
+        for (int c = 0; c < SWTC_CS; ++c) t[c] = __uint_as_float(nx12[c]);
+        if (i + 1 < np) tc::tmem_ld12_async(tcol + (i + 1) * SWTC_CS, nx12);
+        const int cz = I.cz[i];
+        if (cz != cur_cz) {
+          cur_cz = cz;
+          const float* zt = sh.z + cz * SWTC_ZSTR(MP);
+          const int mzc = (int)zt[MP2 + MP];
+#pragma unroll
+          for (int a = 0; a < MP; ++a)
+#pragma unroll
+            for (int c = 0; c < MP; ++c) S[a][c] = zt[a * MP + c];
+#pragma unroll
+          for (int c = 0; c < MP; ++c) inv[c] = (vxy && c < mzc) ? 1.0f / (lxy + zt[MP2 + c]) : 0.0f;
+        }
+        if (active) {
+          // both contractions as MP independent accumulators updated per step
+          float u[MP], w[MP];
+#pragma unroll
+          for (int c = 0; c < MP; ++c) u[c] = S[0][c] * t[0];
+#pragma unroll
+          for (int a = 1; a < MP; ++a)
+#pragma unroll
+            for (int c = 0; c < MP; ++c) u[c] = fmaf(S[a][c], t[a], u[c]);
+#pragma unroll
+          for (int c = 0; c < MP; ++c) u[c] *= inv[c];
+#pragma unroll
+          for (int a = 0; a < MP; ++a) w[a] = S[a][0] * u[0];
+#pragma unroll
+          for (int c = 1; c < MP; ++c)
+#pragma unroll
+            for (int a = 0; a < MP; ++a) w[a] = fmaf(S[a][c], u[c], w[a]);
+          unsigned char* col = sB + (L / 4) * SWTC_LBO + (L % 4) * 4;
+#pragma unroll
+          for (int a = 0; a < MP; ++a) {
+            const int row = i * SWTC_CS + a;
+            *(float*)(col + (row >> 3) * sbo + (row & 7) * 16) = tc::to_tf32(w[a]);
+          }
+        }
+      }
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      tc::mbar_arrive(tc::smem_addr(&sh.b2[b]));
+      if (li >= 1 && !output(li - 1)) break;
     }
-    tc::fence_before_sync();
-    __syncthreads();
+    if (li == nmine && nmine >= 1) output(nmine - 1);
   }
-  // ---- teardown
+  // ---- teardown (every role has left its loop)
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -428,7 +535,7 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
 template <int N1>
 static cudaError_t launch_tc_n1(const LevelOp* dop, const unsigned char* blob, const SwTcGeom& g, const float* r,
                                 float* zp, const int* act, int nact, long long items, cudaStream_t s) {
-  const int smem = 2 * g.a_bytes + g.b_bytes;
+  const int smem = 2 * g.a_bytes + SWTC_BSLOTS * g.b_bytes;
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -444,7 +551,7 @@ static cudaError_t launch_tc_n1(const LevelOp* dop, const unsigned char* blob, c
 cudaError_t schwarz_tc_prepare(int n1) {
   SwTcGeom g;
   if (!swtc_geometry(n1, g)) return cudaErrorInvalidValue;
-  const int smem = 2 * g.a_bytes + g.b_bytes;
+  const int smem = 2 * g.a_bytes + SWTC_BSLOTS * g.b_bytes;
   switch (n1) {
     case 7: return cudaFuncSetAttribute(k_schwarz_patch_tc<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     case 8: return cudaFuncSetAttribute(k_schwarz_patch_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

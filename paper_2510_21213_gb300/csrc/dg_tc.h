@@ -84,6 +84,29 @@ __device__ __forceinline__ void tmem_ld_x4(uint32_t taddr, float* v) {
   for (int g = 0; g < G; ++g) tmem_ld4(taddr + 4 * g, v + 4 * g);
 }
 
+// Asynchronous form for software pipelining: the 12 destination registers are
+// filled some time after the load issues; tmem_wait12 waits for every
+// outstanding load of the thread and names the registers as its outputs, so
+// no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_ld12_async(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr + 4));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+               : "r"(taddr + 8));
+}
+__device__ __forceinline__ void tmem_wait12(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11])
+               :
+               : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // mbarriers and bulk copies
 // ---------------------------------------------------------------------------
@@ -91,6 +114,9 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
@@ -125,6 +151,21 @@ __device__ __forceinline__ void cp_async4(void* dst_smem, const void* src, uint3
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// barrier over the `count` threads of the warps that use barrier `id` (1..15)
+__device__ __forceinline__ void named_barrier(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// the same barrier, returning whether `pred` holds in any participating thread
+__device__ __forceinline__ bool named_barrier_or(int id, int count, bool pred) {
+  uint32_t out;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %3, 0;\nbar.red.or.pred q, %1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(out)
+      : "r"(id), "r"(count), "r"((uint32_t)pred)
+      : "memory");
+  return out != 0;
+}
 
 // round to TF32 (nearest, ties away), kept in an FP32 container
 __device__ __forceinline__ float to_tf32(float x) {
