@@ -273,9 +273,12 @@ void dg_release_cached_handles(void);
 /* Autotuner: times the fine-level operator and smoother for source-batch
  * sizes 8..512 (within ~2 GB of vectors) and sets the handle's batch to the
  * smallest size within 10 % of the best time per source (at most
- * max_sources). Results are cached per GPU name, mesh and precision in
- * $DG_AUTOTUNE_CACHE (default ~/.cache/dgx_autotune.jsonl). *batch receives
- * the choice. */
+ * max_sources). In the mixed modes, where the fine level's patch solves run
+ * on the tensor cores, it then times the tile shapes of that kernel (2, 4, 6,
+ * 8 or 10 patches per work item, i.e. MMA widths N of 32-128 columns) at that
+ * batch and keeps the fastest; the shape changes no result. Results are
+ * cached per GPU name, mesh and precision in $DG_AUTOTUNE_CACHE (default
+ * ~/.cache/dgx_autotune.jsonl). *batch receives the batch choice. */
 int dg_autotune_batch(dg_handle h, int32_t max_sources, int32_t* batch);
 
 /* Matrix-free SIPDG operator of multigrid level `level` (0 = fine) applied to
@@ -425,6 +428,17 @@ int dg_octree_faces(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * 0..65535. */
 int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t penalty_form,
                     double penalty_eps, const double* u_dev, double* out_dev, int64_t B, void* cuda_stream);
+
+/* Exercises the bounded wait used by every tensor-core kernel of this library
+ * (their pipeline hand-offs are mbarrier waits that give up after about a
+ * second and report DG_ERR_TIMEOUT instead of hanging): one warp waits on an
+ * mbarrier that it arrives on (arrive != 0) or that nothing ever arrives on
+ * (arrive == 0), for at most limit_cycles SM clock cycles (1 .. 2^34). Returns
+ * DG_OK when the wait completed, DG_ERR_TIMEOUT when it gave up (the CUDA
+ * context stays usable), DG_ERR_INVALID_ARG for a limit out of range. The
+ * paper has no counterpart: this is a test hook for the failure path.
+ * Synchronises the stream; allocates and frees one int. */
+int dg_wait_probe(int32_t arrive, int64_t limit_cycles, void* cuda_stream);
 
 int64_t dg_kernel_launch_count(void);
 

@@ -104,7 +104,7 @@ struct Level {
   DevBuf sw_tabs;                // Schwarz patch tables
   DevBuf sw_tc;                  // tables of the tensor-core patch solve (FP32 inner solve), if used
   SwTcPlan tcp;                  // its device blob (null: SIMT patch solve) and header
-  const SwTcPlan* tc() const { return tcp.blob ? &tcp : nullptr; }
+  const SwTcPlan* tc() const { return tcp.blob && !tcp.off ? &tcp : nullptr; }
 };
 
 struct BcAxisTables {

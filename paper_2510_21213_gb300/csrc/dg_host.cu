@@ -773,6 +773,7 @@ static int setup(dg_ctx* h) {
           DG_CK(L.sw_tc.ensure(blob.size()));
           DG_CK(cudaMemcpy(L.sw_tc.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
           std::memcpy(&L.tcp.head, blob.data(), sizeof(SwTcHead));
+          L.tcp.geom = L.tcp.head.geom;
           L.tcp.blob = L.sw_tc.p;
         }
       }

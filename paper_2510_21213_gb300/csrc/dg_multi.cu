@@ -31,6 +31,7 @@ namespace dg {
 struct TuneEntry {
   int batch = 0;
   double us_per_source = 0.0;
+  int tc_np = -1;  // fine-level patch solve: patches per tensor-core item, 0 = SIMT kernel, -1 = not tuned
 };
 
 static std::mutex g_tune_mu;
@@ -52,12 +53,12 @@ static void tune_load_locked() {
   char line[512];
   while (std::fgets(line, sizeof(line), f)) {
     char key[256];
-    int batch = 0;
+    int batch = 0, tc_np = -1;
     double us = 0.0;
-    // {"key": "...", "batch": B, "us_per_source": U}
-    if (std::sscanf(line, " {\"key\": \"%255[^\"]\", \"batch\": %d, \"us_per_source\": %lf", key, &batch, &us) == 3 &&
-        batch > 0)
-      g_tune[key] = TuneEntry{batch, us};
+    // {"key": "...", "batch": B, "us_per_source": U, "tc_np": P}
+    const int got = std::sscanf(line, " {\"key\": \"%255[^\"]\", \"batch\": %d, \"us_per_source\": %lf, \"tc_np\": %d",
+                                key, &batch, &us, &tc_np);
+    if (got >= 3 && batch > 0) g_tune[key] = TuneEntry{batch, us, got == 4 ? tc_np : -1};
   }
   std::fclose(f);
 }
@@ -69,8 +70,8 @@ static void tune_store_locked() {
   FILE* f = std::fopen(path.c_str(), "w");
   if (!f) return;  // cache is an optimisation only
   for (const auto& kv : g_tune)
-    std::fprintf(f, "{\"key\": \"%s\", \"batch\": %d, \"us_per_source\": %.6g}\n", kv.first.c_str(), kv.second.batch,
-                 kv.second.us_per_source);
+    std::fprintf(f, "{\"key\": \"%s\", \"batch\": %d, \"us_per_source\": %.6g, \"tc_np\": %d}\n", kv.first.c_str(),
+                 kv.second.batch, kv.second.us_per_source, kv.second.tc_np);
   std::fclose(f);
 }
 
@@ -119,16 +120,67 @@ static double probe_us_per_source(dg_ctx* h, PrecWork<T>& w, int B, cudaStream_t
   return 1000.0 * ms / reps / B;
 }
 
+// Applies a tuned patch-solve variant to the fine level: np > 0 tensor-core
+// items of np patches, 0 the SIMT kernel (no change without a tensor-core plan).
+static void apply_tc_choice(dg_ctx* h, int np) {
+  SwTcPlan& P = h->levels[0].tcp;
+  if (!P.blob || np < 0) return;
+  ++h->buf_gen;  // captured PCG phases embed the old variant: capture again
+  SwTcGeom g;
+  if (np == 0) {
+    P.off = true;
+  } else if (swtc_geometry(h->levels[0].op.n1, g, np)) {
+    P.geom = g;
+    P.off = false;
+  }
+}
+
+// Tile shape of the fine level's tensor-core patch solve (patches per work
+// item, i.e. the MMA width N), timed at batch B with the operator + smoother
+// probe; the fastest is kept. The shape does not change any result (every
+// output element is the same sum in the same order whatever the item size),
+// so tuned and untuned builds agree exactly; the switch to the SIMT kernel,
+// which changes the rounding, is left to the caller (tc_smoother). -1 without
+// a plan.
+static int autotune_tc(dg_ctx* h, int B, cudaStream_t s) {
+  SwTcPlan& P = h->levels[0].tcp;
+  if (!P.blob || P.off || h->opts.precision == DG_PREC_FP64) return -1;
+  const SwTcGeom keep = P.geom;
+  std::vector<int> cand;
+  for (int np : {2, 4, 6, 8, 10}) {
+    SwTcGeom g;
+    if (swtc_geometry(h->levels[0].op.n1, g, np)) cand.push_back(np);
+  }
+  int pick = keep.np;
+  double best = 1e300;
+  for (int np : cand) {
+    apply_tc_choice(h, np);
+    const double t = probe_us_per_source<float>(h, h->w32, B, s);
+    if (t < best) {
+      best = t;
+      pick = np;
+    }
+  }
+  P.geom = keep;
+  P.off = false;
+  apply_tc_choice(h, pick);
+  return pick;
+}
+
 // Batch size for a handle: the smallest candidate whose per-source time is
 // within 10 % of the best candidate's (bigger batches cost memory and leave
-// fewer sources for other lanes). Result cached per device name and mesh.
+// fewer sources for other lanes), then the fine level's patch-solve variant.
+// Results cached per device name and mesh.
 int autotune_batch(dg_ctx* h, int max_sources, cudaStream_t s) {
   const std::string key = tune_key(h);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     tune_load_locked();
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) return std::min(it->second.batch, std::max(1, max_sources));
+    if (it != g_tune.end()) {
+      apply_tc_choice(h, it->second.tc_np);
+      return std::min(it->second.batch, std::max(1, max_sources));
+    }
   }
   // candidates bounded by memory: about 2 GB of fine-level vectors per handle
   const long long per_source = h->Nq * 8LL * 16;
@@ -156,9 +208,10 @@ int autotune_batch(dg_ctx* h, int max_sources, cudaStream_t s) {
       pick_t = t[i];
       break;
     }
+  const int tc_np = f32 ? autotune_tc(h, pick, s) : -1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[key] = TuneEntry{pick, pick_t};
+    g_tune[key] = TuneEntry{pick, pick_t, tc_np};
     tune_store_locked();
   }
   return std::min(pick, std::max(1, max_sources));

@@ -49,7 +49,7 @@ inline float host_tf32(float x) {
 
 }  // namespace
 
-bool swtc_geometry(int n1, SwTcGeom& g) {
+bool swtc_geometry(int n1, SwTcGeom& g, int np) {
   g.mp = n1 + 2;
   const int mp2 = g.mp * g.mp;
   if (n1 < 7 || n1 > 9) return false;
@@ -60,7 +60,9 @@ bool swtc_geometry(int n1, SwTcGeom& g) {
   // patches per item: MP rows of the B operand each, at a stride of SWTC_CS rows
   // (D columns), so that every tensor-memory load starts at a multiple of 4;
   // two stages of B must fit next to the two factors
-  g.np = g.mp == 11 ? 4 : 10;
+  const int np_max = g.mp == 11 ? 4 : 10;
+  if (np < 0 || np > np_max) return false;
+  g.np = np > 0 ? np : np_max;
   g.ncol = (g.np * SWTC_CS + 15) / 16 * 16;
   g.b_bytes = (g.ncol / 8) * g.sbo;
   return 2 * (size_t)g.a_bytes + SWTC_BSLOTS * (size_t)g.b_bytes + sizeof(SwTcShared) <= 232448 &&
@@ -207,15 +209,15 @@ __device__ __forceinline__ bool swtc_wait(SwTcShared& sh, const SwTcHead* H, uns
 
 template <int N1>
 __global__ void __launch_bounds__(SWTC_THREADS, 1)
-    k_schwarz_patch_tc(const LevelOp* __restrict__ op, const unsigned char* __restrict__ blob,
+    k_schwarz_patch_tc(const LevelOp* __restrict__ op, const unsigned char* __restrict__ blob, const SwTcGeom geom,
                        const float* __restrict__ r, float* __restrict__ zp, const int* __restrict__ act, int nact) {
   constexpr int MP = N1 + 2, MP2 = MP * MP, MP3 = MP2 * MP, NPE = N1 * N1 * N1;
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ SwTcShared sh;
   const SwTcHead* H = (const SwTcHead*)blob;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int a_bytes = H->geom.a_bytes, b_bytes = H->geom.b_bytes, sbo = H->geom.sbo, NP = H->geom.np;
-  const int kc = H->geom.kc, ncol = H->geom.ncol, nseg = H->nseg;
+  const int a_bytes = geom.a_bytes, b_bytes = geom.b_bytes, sbo = geom.sbo, NP = geom.np;
+  const int kc = geom.kc, ncol = geom.ncol, nseg = H->nseg;
   const long long off_a = H->off_a;
   unsigned char* sAf = dsm;
   unsigned char* sAi = dsm + a_bytes;
@@ -299,15 +301,16 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       SwTcItem& I = sh.item[li % SWTC_ISLOTS];
       int seg = 0;
       while (sh.item0[seg + 1] <= it) ++seg;
-      // patch counts of a segment stay below 2^31 (columns x sources x z positions)
+      // patch q of a segment: column fastest (x, then y), then z, then source,
+      // so an item's patches are neighbours along x and share their halo rows
+      // (counts stay below 2^31: columns x sources x z positions)
       const int q0 = (it - sh.item0[seg]) * NP;
-      const int per_z = sh.seg_ncol[seg] * nact;
-      const int np = min(NP, per_z * nz - q0);
+      const int ncs = sh.seg_ncol[seg];
+      const int np = min(NP, ncs * nz * nact - q0);
       if (L < np) {
         const int q = q0 + L;
-        const int ez = q / per_z;
-        const int rem = q - ez * per_z;
-        const int colrel = rem / nact, a = rem - colrel * nact;
+        const int colrel = q % ncs, zq = q / ncs;
+        const int ez = zq % nz, a = zq / nz;
         const short2 c = sh.cols[sh.seg_col0[seg] + colrel];
         I.src[L] = a < SWTC_MAXACT ? (int)sh.act[a] : act[a];
         I.ex[L] = c.x;
@@ -319,8 +322,7 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       // z offsets of every (patch, z-node): the same for all (x, y) of the patch
       if (L < np * MP) {
         const int i = L / MP, k = L - (L / MP) * MP;
-        const int q = q0 + i;
-        const int ez = q / per_z;
+        const int ez = ((q0 + i) / ncs) % nz;
         const int oLz = ez > 0, mz = N1 + oLz + (ez < nz - 1);
         const int Z = ez * N1 - oLz + k;
         const int EZ = Z / N1;
@@ -542,7 +544,7 @@ static cudaError_t launch_tc_n1(const LevelOp* dop, const unsigned char* blob, c
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(items, nsm));
   count_launch();
-  k_schwarz_patch_tc<N1><<<grid, SWTC_THREADS, smem, s>>>(dop, blob, r, zp, act, nact);
+  k_schwarz_patch_tc<N1><<<grid, SWTC_THREADS, smem, s>>>(dop, blob, g, r, zp, act, nact);
   return cudaGetLastError();
 }
 
@@ -563,7 +565,7 @@ cudaError_t schwarz_tc_prepare(int n1) {
 cudaError_t launch_schwarz_patch_tc(const LevelOp& hop, const LevelOp* dop, const SwTcPlan& plan, const float* r,
                                     float* zp, const int* act, int nact, cudaStream_t s) {
   const SwTcHead& head = plan.head;
-  const SwTcGeom& g = head.geom;
+  const SwTcGeom& g = plan.geom;
   long long items = 0;
   for (int k = 0; k < head.nseg; ++k) items += ((long long)head.seg_ncol[k] * head.nz * nact + g.np - 1) / g.np;
   const unsigned char* b = (const unsigned char*)plan.blob;

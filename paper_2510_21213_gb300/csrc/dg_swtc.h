@@ -87,13 +87,19 @@ struct SwTcShared {
   float lxy[2][SWTC_MAXCLS][12];  // per x / y class: lambda [MP], m
 };
 
-// a level's tensor-core patch solve: device blob and a host copy of its header
+// a level's tensor-core patch solve: device blob, a host copy of its header,
+// and the operand geometry in use (patches per item; the autotuner may pick
+// another count, or switch the level to the SIMT patch kernel)
 struct SwTcPlan {
   const void* blob = nullptr;
   SwTcHead head;
+  SwTcGeom geom;
+  bool off = false;
 };
 
-bool swtc_geometry(int n1, SwTcGeom& g);
+// operand geometry for degree n1 - 1 with np patches per item (0: the default,
+// the largest count that fits); false if the degree or count does not fit
+bool swtc_geometry(int n1, SwTcGeom& g, int np = 0);
 std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<double>& tabs, int* err_dev);
 cudaError_t schwarz_tc_prepare(int n1);
 cudaError_t launch_schwarz_patch_tc(const LevelOp& hop, const LevelOp* dop, const SwTcPlan& plan, const float* r,

@@ -43,7 +43,8 @@ def test_fullsize_sampled_sources_fp64(setup):
     for k in range(f.shape[0]):
         assert st[k]["status"] == 0 and st[k]["rel_residual"] <= 1e-12
         err = np.abs(v[k] - ref[k]).max() / np.abs(ref[k]).max()
-        assert err < 1e-9, (k, err)
+        print(f"FP64 source {k}: max |v - v_oracle| / max |v_oracle| = {err:.2e}")
+        assert err < 1e-10, (k, err)
     s.close()
 
 
