@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "learned"])
     ap.add_argument("--sources-per-step", type=int, default=0,
                     help="sources of the build per step (0: three library batches, at most the whole build)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="sources solved together by the library (0: its default, about 8 GB of FP64 vectors)")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain FP64 form")
     ap.add_argument("--no-learned", action="store_true", help="skip timing the learned form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -215,15 +217,18 @@ def run_steps(solver, psi_dev, ranges, first, count, torch, flush, stream, pin=N
 
 
 def kernel_roofline(solver, B, precision, torch, nrep=20):
-    """Average launch duration of the fine-level operator and smoother (CUDA
-    events on the launching stream) and their algorithmic work."""
+    """Average launch duration (CUDA events on the launching stream) of the
+    fine-level patch solves (the dominant kernel), of the whole smoother
+    application (patch solves + gather) and of the operator, with their
+    algorithmic work."""
     Nq = solver.Nq
     n1 = solver.info.level_p[0] + 1
     dt = torch.float64 if precision == "fp64" else torch.float32
     u = torch.randn((B, Nq), dtype=dt, device="cuda")
     res = {}
     stream = torch.cuda.current_stream()
-    for name, fn in (("apply", lambda: solver.apply(u)), ("smoother", lambda: solver.smoother(u))):
+    for name, fn in (("apply", lambda: solver.apply(u)), ("smoother", lambda: solver.smoother(u)),
+                     ("patch", lambda: solver.patch_solves(u))):
         fn()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -239,15 +244,17 @@ def kernel_roofline(solver, B, precision, torch, nrep=20):
     # mass scaling, traces 6 faces x n1^2 x 2 x n1 MACs per element
     apply_flops = Nq * (3 * (2 * n1 + 8) + 5) + E * 6 * n1 * n1 * 2 * 2 * n1
     m = n1 + 2
-    # patch solve: six 1-D passes of m^4 MACs and the eigenvalue scaling per patch
-    sm_flops = E * (6 * 2 * m ** 4 + m ** 3)
+    # patch solve by fast diagonalisation: six 1-D passes of m^4 MACs and the
+    # eigenvalue scaling per patch
+    patch_flops = E * (6 * 2 * m ** 4 + m ** 3)
     s = 8 if precision == "fp64" else 4
-    apply_bytes = 2 * Nq * s
-    sm_bytes = 2 * Nq * s  # the smoother application: r in, z out
     return {
-        "apply_ms": res["apply"], "smoother_ms": res["smoother"], "B": B,
-        "apply_flops": apply_flops * B, "apply_bytes": apply_bytes * B,
-        "smoother_flops": sm_flops * B, "smoother_bytes": sm_bytes * B,
+        "apply_ms": res["apply"], "smoother_ms": res["smoother"], "patch_ms": res["patch"], "B": B, "E": E, "m": m,
+        "apply_flops": apply_flops * B, "apply_bytes": 2 * Nq * s * B,
+        "patch_flops": patch_flops * B,
+        # the patch kernel's own input and output: the residual in, the patch solutions out
+        "patch_bytes": (Nq + E * m ** 3) * s * B,
+        "smoother_bytes": 2 * Nq * s * B,
     }
 
 
@@ -413,7 +420,7 @@ def run_ours(args):
     weights = dgx.default_nn_weights(m.p)
     if prec == dgx.DG_PREC_MIXED_LEARNED and weights is None:
         raise SystemExit(f"no trained network weights for p = {m.p}")
-    solver = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=prec, rtol=1e-8,
+    solver = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=prec, rtol=1e-8, batch=args.batch,
                                nn_weights_path=weights if prec == dgx.DG_PREC_MIXED_LEARNED else None)
     xyz, w = solver.node_coords()
     psi_host = make_inputs(spec, xyz, w)
@@ -453,7 +460,7 @@ def run_ours(args):
     del dev_buf, pin
 
     def other_form(form_prec, nsteps, **kw):
-        sv = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=form_prec, rtol=1e-8, **kw)
+        sv = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=form_prec, rtol=1e-8, batch=args.batch, **kw)
         run_steps(sv, psi_dev, ranges, args.warmup, 1, torch, flush, stream)
         t, pr, (Kf, ehf, stf), Kfs = run_steps(sv, psi_dev, ranges, args.warmup, nsteps, torch, flush, stream)
         ftot = pd.max_over_ranks(sum(t) / 1e3, device="cuda")
@@ -506,26 +513,52 @@ def run_ours(args):
               "mean_iters": float(np.mean([x["iters"] for x in stj])),
               "K_rel_diff_vs_build": float(np.abs(Kj - K_full).max() / np.abs(K_full).max())}
 
-    # roofline of the dominant kernel (the fine-level smoother; see profiles/)
+    # roofline of the dominant kernel: the fine-level patch solves (see profiles/)
     B = min(solver.info.batch, P + 1)
     rf = kernel_roofline(solver, B, args.precision, torch)
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1906.3)
+    tc_used = args.precision != "fp64" and m.p >= 7
     alu_peak = FP32_PEAK_TFLOPS if args.precision != "fp64" else FP64_PEAK_TFLOPS
-    sm_tf = rf["smoother_flops"] / (rf["smoother_ms"] * 1e-3) / 1e12
-    sm_gbs = rf["smoother_bytes"] / (rf["smoother_ms"] * 1e-3) / 1e9
-    ap_tf = rf["apply_flops"] / (rf["apply_ms"] * 1e-3) / 1e12
-    ap_gbs = rf["apply_bytes"] / (rf["apply_ms"] * 1e-3) / 1e9
+    t = rf["patch_ms"] * 1e-3
+    # the roofline that bounds the kernel is the one with the longest ideal time
+    ideal = {"hbm": rf["patch_bytes"] / (hbm * 1e9)}
+    if tc_used:
+        # executed on the tensor cores: two dense m^2 x m^2 Kronecker factors per patch
+        # (TF32, K padded to 8) at the measured BF16 peak x the nominal TF32 / BF16 ratio
+        kpad = (rf["m"] ** 2 + 7) // 8 * 8
+        tc_flops = rf["B"] * rf["E"] * 2 * 2 * 128 * 12 * kpad
+        ideal["tensor"] = tc_flops / (bf16 * TF32_OVER_BF16 * 1e12)
+        ideal["alu"] = rf["B"] * rf["E"] * 2 * 2 * rf["m"] ** 3 / (alu_peak * 1e12)  # the z factor in FP32
+    else:
+        ideal["alu"] = rf["patch_flops"] / (alu_peak * 1e12)
+    bound = max(ideal, key=ideal.get)
+    if bound == "hbm":
+        ach, peak, unit = rf["patch_bytes"] / t / 1e9, hbm, "GB/s"
+        peak_source = "MEASURED_PEAKS.json hbm_gbs (copy bandwidth of this pool's GB300)"
+    elif bound == "tensor":
+        ach, peak, unit = tc_flops / t / 1e12, bf16 * TF32_OVER_BF16, "TFLOP/s"
+        peak_source = "MEASURED_PEAKS.json bf16_tflops x 1.1/2.25 (nominal TF32 / BF16)"
+    else:
+        ach, peak, unit = rf["patch_flops"] / t / 1e12, alu_peak, "TFLOP/s"
+        peak_source = ("FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts)" if args.precision != "fp64"
+                       else "FP64: 1.25 TFLOP/s dense (datasheet)")
+    kname = "k_schwarz_patch_tc" if tc_used else "k_schwarz_patch"
     roofline = {
-        "kernel": "fine-level Schwarz smoother application (k_schwarz_patch + k_schwarz_gather)",
-        "bound": "alu", "achieved": sm_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": sm_tf / alu_peak,
-        "traffic": measured_traffic(f"smoother_{args.workload}_{args.precision}_B{B}"),
-        "algorithmic_flops": rf["smoother_flops"], "algorithmic_bytes": rf["smoother_bytes"],
-        "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts)" if args.precision != "fp64"
-                        else "FP64: 1.25 TFLOP/s dense (datasheet)"),
-        "launch_ms": rf["smoother_ms"], "B": B, "hbm_gbs": sm_gbs, "hbm_frac_of_measured": sm_gbs / hbm,
-        "operator": {"launch_ms": rf["apply_ms"], "tflops": ap_tf, "frac_alu": ap_tf / alu_peak,
-                     "gbs": ap_gbs, "frac_hbm_of_measured": ap_gbs / hbm},
+        "kernel": f"{kname} (fine-level Schwarz patch solves, {rf['B']} sources)",
+        "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+        "traffic": measured_traffic(f"{kname}_{args.workload}_{args.precision}_B{rf['B']}"),
+        "algorithmic_bytes": rf["patch_bytes"], "algorithmic_flops": rf["patch_flops"],
+        "ideal_ms": {k: v * 1e3 for k, v in ideal.items()}, "peak_source": peak_source,
+        "launch_ms": rf["patch_ms"], "B": rf["B"],
+        "alu_view": {"tflops": rf["patch_flops"] / t / 1e12, "frac": rf["patch_flops"] / t / 1e12 / alu_peak},
+        "smoother_application": {"launch_ms": rf["smoother_ms"], "kernels": f"{kname} + k_schwarz_gather",
+                                 "gbs_r_in_z_out": rf["smoother_bytes"] / (rf["smoother_ms"] * 1e-3) / 1e9},
+        "operator": {"launch_ms": rf["apply_ms"], "tflops": rf["apply_flops"] / (rf["apply_ms"] * 1e-3) / 1e12,
+                     "frac_alu": rf["apply_flops"] / (rf["apply_ms"] * 1e-3) / 1e12 / alu_peak,
+                     "gbs": rf["apply_bytes"] / (rf["apply_ms"] * 1e-3) / 1e9,
+                     "frac_hbm_of_measured": rf["apply_bytes"] / (rf["apply_ms"] * 1e-3) / 1e9 / hbm},
     }
 
     cpu = None

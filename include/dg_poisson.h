@@ -119,8 +119,9 @@ typedef struct {
   int32_t gauss_construction; /* Gaussian-sum 1/r: 0 = tabulated short sums (nonnegative least-squares fits,
                                  about 3-5x fewer terms), the trapezoidal rule where no table applies;
                                  1 = trapezoidal rule only */
-  int32_t tc_smoother;   /* MIXED modes: 1 (default) solves the Schwarz patch problems of the FP32 inner solve
-                            on the tensor cores (TF32 tcgen05 MMA) on levels of degree >= 6; 0 = FP32 SIMT */
+  int32_t tc_smoother;   /* MIXED modes: Schwarz patch problems of the FP32 inner solve on the tensor cores
+                            (TF32 tcgen05 MMA). 1 (default): on levels of degree 7 and 8, where it is
+                            measured faster than the FP32 SIMT kernel; 2: also at degree 6; 0: off */
   int32_t nn_use_net;    /* MIXED_LEARNED: 1 (default) starts from the network's guess; 0 from the same
                             guess without the network (the prolongated degree-1 coarse solution, smoothed and
                             scaled), to measure what the network itself adds */
@@ -308,6 +309,19 @@ int dg_apply_transfer(dg_handle h, int32_t level, int32_t direction, int32_t fp3
  * call is stream-ordered and returns without synchronising the stream. */
 int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r_dev, void* z_dev, int64_t B,
                       void* cuda_stream);
+
+/* The patch solves of the Schwarz smoother on level `level` alone (Sec. 3.4:
+ * each element patch problem solved exactly by fast diagonalisation), without
+ * the gather that sums them: zp[b][e][(p+3)^3] = A_P(e)^-1 R_P(e) r_b, patch
+ * node (i, j, k) at i + (p+3)(j + (p+3)k), entries outside the domain 0.
+ * FP32 calls on a handle whose level uses the tensor-core kernel run that
+ * kernel. r_dev: [B][Nq_level]; zp_dev: [B][E_level][(p_level+3)^3]; device
+ * arrays, FP64 (fp32 == 0) or FP32 (fp32 == 1); B <= 65535; level below the
+ * coarsest. Exposed for tests and for timing the patch-solve kernel alone;
+ * stream-ordered, returns without synchronising. DG_ERR_UNSUPPORTED for a
+ * Jacobi handle. */
+int dg_apply_patch_solves(dg_handle h, int32_t level, int32_t fp32, const void* r_dev, void* zp_dev, int64_t B,
+                          void* cuda_stream);
 
 /* Same result as dg_apply_smoother, for callers that cannot allocate device
  * memory at call time: code running where cudaMalloc is forbidden or would

@@ -761,8 +761,9 @@ static int setup(dg_ctx* h) {
       DG_CK(L.sw_tabs.ensure(sizeof(double) * tb.size()));
       DG_CK(cudaMemcpy(L.sw_tabs.p, tb.data(), sizeof(double) * tb.size(), cudaMemcpyHostToDevice));
       DG_RET(estimate_lambda_schwarz(h, l, &L.lam_sw));
-      // FP32 inner solve: patch solves on the tensor cores where the degree allows it
-      if (o.precision != DG_PREC_FP64 && o.tc_smoother) {
+      // FP32 inner solve: patch solves on the tensor cores at degrees 7-8 (and 6
+      // when asked: there the SIMT kernel is as fast)
+      if (o.precision != DG_PREC_FP64 && o.tc_smoother > 0 && (L.op.n1 >= 8 || o.tc_smoother >= 2)) {
         if (!h->tc_err.p) {
           DG_CK(h->tc_err.ensure(sizeof(int)));
           DG_CK(cudaMemset(h->tc_err.p, 0, sizeof(int)));
@@ -1153,6 +1154,31 @@ int dg_apply_smoother(dg_handle h, int32_t level, int32_t fp32, const void* r, v
     else
       DG_RET(apply_smoother_t<double>(h, h->w64, level, (const double*)r + b0 * N, (double*)z + b0 * N, nb, s));
   }
+  return DG_OK;
+}
+
+int dg_apply_patch_solves(dg_handle h, int32_t level, int32_t fp32, const void* r, void* zp, int64_t B,
+                          void* stream) {
+  if (!h || level < 0 || level >= h->nlev - 1 || B < 0 || B > 65535 || (B > 0 && (!r || !zp)))
+    return DG_ERR_INVALID_ARG;
+  if (h->opts.smoother != DG_SMOOTH_SCHWARZ) {
+    h->err = "dg_apply_patch_solves: the handle's smoother is not the Schwarz smoother";
+    return DG_ERR_UNSUPPORTED;
+  }
+  if (B == 0) return DG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)B;
+  DG_RET(ensure_common(h, nb));
+  std::vector<int> a(nb);
+  for (int k = 0; k < nb; ++k) a[k] = k;
+  DG_RET(upload_act(h, a, s));
+  const Level& L = h->levels[level];
+  if (fp32)
+    DG_CK(launch_schwarz_patch<float>(L.op, L.dop, L.sw_tabs.as<double>(), (const float*)r, (float*)zp,
+                                      h->act.as<int>(), nb, s, L.tc()));
+  else
+    DG_CK(launch_schwarz_patch<double>(L.op, L.dop, L.sw_tabs.as<double>(), (const double*)r, (double*)zp,
+                                       h->act.as<int>(), nb, s, nullptr));
   return DG_OK;
 }
 

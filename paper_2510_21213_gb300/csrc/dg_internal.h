@@ -135,6 +135,10 @@ cudaError_t launch_coarse_solve(const double* Ainv, int Nc, const T* r, T* x, co
 // tc (FP32 only, may be null): the level's tensor-core patch solve, used instead
 // of the SIMT patch kernel
 struct SwTcPlan;
+// the patch solves alone: zp[rhs][e][MP^3] = A_P^-1 R_P r
+template <typename T>
+cudaError_t launch_schwarz_patch(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp,
+                                 const int* act, int nact, cudaStream_t s, const SwTcPlan* tc = nullptr);
 template <typename T>
 cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
                            T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s,

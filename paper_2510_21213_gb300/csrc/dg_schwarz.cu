@@ -405,6 +405,37 @@ static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const doub
   return cudaGetLastError();
 }
 
+// the patch solves alone (the first kernel of schwarz_n1)
+template <typename T, int N1>
+static cudaError_t schwarz_patch_n1(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp,
+                                    const int* act, int nact, cudaStream_t s, const SwTcPlan* tc) {
+  using C = SwCfg<T, N1>;
+  if (sizeof(T) == 4 && tc && tc->blob)
+    return launch_schwarz_patch_tc(hop, dop, *tc, (const float*)r, (float*)zp, act, nact, s);
+  const long long items = (long long)nact * hop.E;
+  count_launch();
+  k_schwarz_patch<T, N1><<<(unsigned)((items + C::EPB - 1) / C::EPB), C::THREADS, 0, s>>>(dop, tabs, r, zp, act,
+                                                                                         nact);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_schwarz_patch(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp,
+                                 const int* act, int nact, cudaStream_t s, const SwTcPlan* tc) {
+  if (nact == 0) return cudaSuccess;
+  switch (hop.n1) {
+    case 2: return schwarz_patch_n1<T, 2>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    case 3: return schwarz_patch_n1<T, 3>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    case 4: return schwarz_patch_n1<T, 4>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    case 5: return schwarz_patch_n1<T, 5>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    case 6: return schwarz_patch_n1<T, 6>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    case 7: return schwarz_patch_n1<T, 7>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    case 8: return schwarz_patch_n1<T, 8>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    case 9: return schwarz_patch_n1<T, 9>(hop, dop, tabs, r, zp, act, nact, s, tc);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename T>
 cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double* tabs, const T* r, T* zp, T* z,
                            T* x, int mode, double c1, double c2, const int* act, int nact, cudaStream_t s,
@@ -423,6 +454,10 @@ cudaError_t launch_schwarz(const LevelOp& hop, const LevelOp* dop, const double*
   }
 }
 
+template cudaError_t launch_schwarz_patch<double>(const LevelOp&, const LevelOp*, const double*, const double*,
+                                                  double*, const int*, int, cudaStream_t, const SwTcPlan*);
+template cudaError_t launch_schwarz_patch<float>(const LevelOp&, const LevelOp*, const double*, const float*, float*,
+                                                 const int*, int, cudaStream_t, const SwTcPlan*);
 template cudaError_t launch_schwarz<double>(const LevelOp&, const LevelOp*, const double*, const double*, double*,
                                             double*, double*, int, double, double, const int*, int, cudaStream_t,
                                             const SwTcPlan*);

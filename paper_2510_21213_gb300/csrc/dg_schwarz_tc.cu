@@ -301,16 +301,17 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       SwTcItem& I = sh.item[li % SWTC_ISLOTS];
       int seg = 0;
       while (sh.item0[seg + 1] <= it) ++seg;
-      // patch q of a segment: column fastest (x, then y), then z, then source,
-      // so an item's patches are neighbours along x and share their halo rows
-      // (counts stay below 2^31: columns x sources x z positions)
+      // patch q of a segment: source fastest, then column, then z (an item's
+      // patches share their element position and z class; counts stay below
+      // 2^31: columns x sources x z positions)
       const int q0 = (it - sh.item0[seg]) * NP;
-      const int ncs = sh.seg_ncol[seg];
-      const int np = min(NP, ncs * nz * nact - q0);
+      const int per_z = sh.seg_ncol[seg] * nact;
+      const int np = min(NP, per_z * nz - q0);
       if (L < np) {
         const int q = q0 + L;
-        const int colrel = q % ncs, zq = q / ncs;
-        const int ez = zq % nz, a = zq / nz;
+        const int ez = q / per_z;
+        const int rem = q - ez * per_z;
+        const int colrel = rem / nact, a = rem - colrel * nact;
         const short2 c = sh.cols[sh.seg_col0[seg] + colrel];
         I.src[L] = a < SWTC_MAXACT ? (int)sh.act[a] : act[a];
         I.ex[L] = c.x;
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       // z offsets of every (patch, z-node): the same for all (x, y) of the patch
       if (L < np * MP) {
         const int i = L / MP, k = L - (L / MP) * MP;
-        const int ez = ((q0 + i) / ncs) % nz;
+        const int ez = (q0 + i) / per_z;
         const int oLz = ez > 0, mz = N1 + oLz + (ez < nz - 1);
         const int Z = ez * N1 - oLz + k;
         const int EZ = Z / N1;

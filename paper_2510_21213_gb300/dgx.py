@@ -138,6 +138,7 @@ def load():
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
+    lib.dg_apply_patch_solves.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_exchange_build_multi.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp, vp, vp, C.c_int32, vp]
     lib.dg_exchange_build_multi.restype = C.c_int
     lib.dg_release_cached_handles.argtypes = []
@@ -467,6 +468,20 @@ def dg_apply_smoother(h, r, level=0, out=None, stream=None):
     return out
 
 
+def dg_apply_patch_solves(h, r, level=0, n_elem=None, p_level=None, stream=None):
+    """r: CUDA [B, Nq_level] float64 or float32; returns the Schwarz patch
+    solutions zp [B, E_level, (p_level+3)^3] (no gather)."""
+    import torch
+
+    mp3 = (p_level + 3) ** 3
+    zp = torch.empty((r.shape[0], n_elem, mp3), dtype=r.dtype, device=r.device)
+    fp32 = 1 if r.dtype == torch.float32 else 0
+    code = load().dg_apply_patch_solves(h, level, fp32, _dev_ptr(r), _dev_ptr(zp, r.dtype), r.shape[0],
+                                        _stream_ptr(stream))
+    _check(code, "dg_apply_patch_solves", h)
+    return zp
+
+
 def dg_boundary_data(h, f, route=DG_BC_GAUSSSUM, stream=None):
     """f: CUDA float64 [B, Nq]. Returns g [B, n_face_nodes] (faces -x,+x,-y,+y,-z,+z)."""
     import torch
@@ -690,6 +705,10 @@ class PoissonSolver:
 
     def smoother(self, r, level=0):
         return dg_apply_smoother(self.h, r, level)
+
+    def patch_solves(self, r, level=0):
+        n1 = self.info.level_p[level] + 1
+        return dg_apply_patch_solves(self.h, r, level, r.shape[1] // n1 ** 3, n1 - 1)
 
     def boundary_data(self, f, route=DG_BC_GAUSSSUM):
         return dg_boundary_data(self.h, f, route)
