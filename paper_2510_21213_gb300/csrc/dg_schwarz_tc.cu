@@ -18,8 +18,8 @@
 // D in tensor memory (FP32). The Kronecker factors depend on the x and y
 // position classes of the element (boundary, next to the boundary, interior),
 // so a work item holds patches of one class pair; its factors arrive by bulk
-// copy, its residual entries by 4-byte asynchronous copies (zero-filled
-// outside the domain). The output goes to the same patch buffer as the SIMT
+// copy, its residual entries by coalesced loads (zero outside the domain),
+// rounded to TF32 on their way into shared memory. The output goes to the same patch buffer as the SIMT
 // kernel's, [source][element][MP^3] (x fastest), for k_schwarz_gather.
 #include <algorithm>
 #include <cstring>
@@ -301,17 +301,18 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       SwTcItem& I = sh.item[li % SWTC_ISLOTS];
       int seg = 0;
       while (sh.item0[seg + 1] <= it) ++seg;
-      // patch q of a segment: source fastest, then column, then z (an item's
-      // patches share their element position and z class; counts stay below
+      // patch q of a segment: column fastest, then z, then source: each CTA
+      // sweeps a slab of one source's elements, so the residual rows it
+      // gathers as halos were loaded shortly before (by itself or by the CTAs
+      // on the neighbouring slabs) and are still in L2 (counts stay below
       // 2^31: columns x sources x z positions)
       const int q0 = (it - sh.item0[seg]) * NP;
-      const int per_z = sh.seg_ncol[seg] * nact;
-      const int np = min(NP, per_z * nz - q0);
+      const int ncs = sh.seg_ncol[seg];
+      const int np = min(NP, ncs * nz * nact - q0);
       if (L < np) {
         const int q = q0 + L;
-        const int ez = q / per_z;
-        const int rem = q - ez * per_z;
-        const int colrel = rem / nact, a = rem - colrel * nact;
+        const int colrel = q % ncs, zq = q / ncs;
+        const int ez = zq % nz, a = zq / nz;
         const short2 c = sh.cols[sh.seg_col0[seg] + colrel];
         I.src[L] = a < SWTC_MAXACT ? (int)sh.act[a] : act[a];
         I.ex[L] = c.x;
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       // z offsets of every (patch, z-node): the same for all (x, y) of the patch
       if (L < np * MP) {
         const int i = L / MP, k = L - (L / MP) * MP;
-        const int ez = (q0 + i) / per_z;
+        const int ez = ((q0 + i) / ncs) % nz;
         const int oLz = ez > 0, mz = N1 + oLz + (ez < nz - 1);
         const int Z = ez * N1 - oLz + k;
         const int EZ = Z / N1;
@@ -336,26 +337,40 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       tc::named_barrier(1, SWTC_PRODUCERS);
       unsigned char* sB = sB0 + b * b_bytes;
       if (L < MP2) {
-        // this thread's column of B: byte offset of row 0 in its 4-column group
+        // this thread's column of B: byte offset of row 0 in its 4-column group.
+        // Every value of the item is loaded first (all in flight at once), then
+        // rounded to TF32 and stored: coalesced loads, not one-element copies
         unsigned char* col = sB + (L / 4) * SWTC_LBO + (L % 4) * 4;
-        for (int i = 0; i < np; ++i) {
-          const int ex = I.ex[i], ey = I.ey[i];
-          const int oLx = ex > 0, oLy = ey > 0;
-          const int mx = N1 + oLx + (ex < nx - 1), my = N1 + oLy + (ey < ny - 1);
-          const int X = ex * N1 - oLx + ll, Y = ey * N1 - oLy + jj;
-          const bool vx = ll < mx && jj < my;
-          const int EX = vx ? X / N1 : 0, EY = vx ? Y / N1 : 0;
-          const float* pxy = r + (long long)I.src[i] * Nq + (EX + nx * EY) * NPE + (X - EX * N1) + N1 * (Y - EY * N1);
+        float v[SWTC_NPMAX][MP];
 #pragma unroll
-          for (int k = 0; k < MP; ++k) {
-            const int zo = I.zoff[i][k];
-            const bool v = vx && zo >= 0;
-            const int row = i * SWTC_CS + k;
-            tc::cp_async4(col + (row >> 3) * sbo + (row & 7) * 16, v ? pxy + zo : r, v ? 4u : 0u);
+        for (int i = 0; i < SWTC_NPMAX; ++i) {
+          if (i < np) {
+            const int ex = I.ex[i], ey = I.ey[i];
+            const int oLx = ex > 0, oLy = ey > 0;
+            const int mx = N1 + oLx + (ex < nx - 1), my = N1 + oLy + (ey < ny - 1);
+            const int X = ex * N1 - oLx + ll, Y = ey * N1 - oLy + jj;
+            const bool vx = ll < mx && jj < my;
+            const int EX = vx ? X / N1 : 0, EY = vx ? Y / N1 : 0;
+            const float* pxy =
+                r + (long long)I.src[i] * Nq + (EX + nx * EY) * NPE + (X - EX * N1) + N1 * (Y - EY * N1);
+#pragma unroll
+            for (int k = 0; k < MP; ++k) {
+              const int zo = I.zoff[i][k];
+              v[i][k] = (vx && zo >= 0) ? __ldg(pxy + zo) : 0.0f;
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < SWTC_NPMAX; ++i) {
+          if (i < np) {
+#pragma unroll
+            for (int k = 0; k < MP; ++k) {
+              const int row = i * SWTC_CS + k;
+              *(float*)(col + (row >> 3) * sbo + (row & 7) * 16) = tc::to_tf32(v[i][k]);
+            }
           }
         }
       }
-      tc::cp_async_wait_all();
       tc::fence_proxy_async();
       tc::mbar_arrive(tc::smem_addr(&sh.full[b]));
     }
@@ -442,9 +457,12 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
         for (int c = 0; c < SWTC_CS; ++c) v[c] = __uint_as_float(nx12[c]);
         if (i + 1 < np) tc::tmem_ld12_async(tcol + (i + 1) * SWTC_CS, nx12);
         if (active) {
+          // streaming stores: the patch solutions are read once, by the gather,
+          // long after; evict-first keeps L2 for the residual rows that
+          // neighbouring patches still gather
           float* out = zp + ((long long)I.src[i] * E + I.elem[i]) * MP3 + L;
 #pragma unroll
-          for (int c = 0; c < MP; ++c) out[c * MP2] = v[c];
+          for (int c = 0; c < MP; ++c) __stcs(out + c * MP2, v[c]);
         }
       }
       tc::fence_before_sync();
