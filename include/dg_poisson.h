@@ -404,8 +404,8 @@ typedef void (*dg_density_fn)(const double* xyz, int64_t n, double* out, void* u
  * in element order (root cell x-fastest, then level, z, y, x); n_leaves (host)
  * the count. Host only; needs no GPU. DG_ERR_INVALID_ARG for a bad root mesh,
  * delta <= 0, max_level outside 0..20, a NULL rho, or max_leaves below the
- * count when leaves_host is given; DG_ERR_NO_MEMORY beyond 2^24 leaves. The GPU
- * operator on this mesh is not part of the library yet. */
+ * count when leaves_host is given; DG_ERR_NO_MEMORY beyond 2^24 leaves. The
+ * operator and the solver on this mesh: dg_octree_apply, dg_octree_setup. */
 int dg_octree_refine(const dg_mesh_desc* root, double delta, int32_t max_level, dg_density_fn rho, void* user,
                      int32_t max_leaves, int32_t* leaves_host, int32_t* n_leaves);
 
@@ -442,6 +442,60 @@ int dg_octree_faces(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * 0..65535. */
 int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t penalty_form,
                     double penalty_eps, const double* u_dev, double* out_dev, int64_t B, void* cuda_stream);
+
+/* Poisson solver on the octree auxiliary mesh (Sec. 6.2 mesh, Sec. 6.3 boundary
+ * data, Sec. 6.1.2 exchange build). The handle keeps the leaves' connectivity,
+ * node coordinates, quadrature weights and preconditioner tables on the
+ * device; the system is the one dg_octree_apply applies (SIPDG, symmetric
+ * Nitsche boundary terms, hanging faces on the smaller face, penalty of the
+ * smaller leaf). It is solved in FP64 by PCG whose preconditioner inverts
+ * every leaf's diagonal block exactly by fast diagonalisation (the block is a
+ * Kronecker sum of 1-D leaf matrices and GL masses). Dirichlet data: the
+ * direct quadrature g(x) = sum_q W_q f(q) / |x - x_q| over all nodes at the GL
+ * nodes of every boundary face (Sec. 6.3), imposed weakly by the Nitsche load
+ * int_F g (sigma v - d_n v).
+ *
+ * dg_octree_setup: root, leaves_host [n_leaves][4] (host) as for
+ * dg_octree_apply; penalty_form / penalty_eps as there; rtol: FP64 true
+ * relative residual ||b - A v|| / ||b|| at which a solve stops (0 < rtol < 1);
+ * max_iter: PCG iteration limit (>= 1). Writes the handle to *out (NULL on
+ * failure). Fields are [.][Nq] FP64 with Nq = n_leaves (p+1)^3, element-blocked
+ * in leaf order, nodes x-fastest. DG_ERR_INVALID_ARG for a bad mesh, leaf set
+ * or argument; DG_ERR_UNSUPPORTED beyond 2^31 nodes; DG_ERR_NO_MEMORY,
+ * DG_ERR_CUDA. Release with dg_octree_destroy (NULL is ignored). Calls on one
+ * handle must not overlap; each synchronises its stream before it returns. */
+typedef struct dg_oct* dg_oct_handle;
+int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t penalty_form,
+                    double penalty_eps, double rtol, int32_t max_iter, dg_oct_handle* out);
+void dg_octree_destroy(dg_oct_handle h);
+/* Text of the last CUDA failure on the handle ("" if none). */
+const char* dg_octree_error_detail(dg_oct_handle h);
+
+/* Node coordinates xyz_dev [Nq][3] and quadrature weights w_dev [Nq] (device,
+ * written; either may be NULL, not both). W_q = w_a w_b w_c h_x h_y h_z / 8. */
+int dg_octree_node_coords(dg_oct_handle h, double* xyz_dev, double* w_dev, void* cuda_stream);
+
+/* The preconditioner alone: z = P r for B fields, P the exact inverse of the
+ * block diagonal of A (one block per leaf). r_dev, z_dev [B][Nq] device. */
+int dg_octree_precond(dg_oct_handle h, const double* r_dev, double* z_dev, int64_t B, void* cuda_stream);
+
+/* Solves -Lap v = 4 pi f with the Coulomb boundary data of f for B sources
+ * f_dev [B][Nq] (device, read). v_dev [B][Nq] (device, written; may be NULL),
+ * stats_host [B] (host, may be NULL): iterations, status, final FP64 true
+ * relative residual, self-energy (f|f) = sum_q W_q f v. Returns DG_OK or the
+ * worst per-source status (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN,
+ * DG_ERR_NONFINITE for a source with NaN or infinity, whose v is 0). */
+int dg_octree_solve(dg_oct_handle h, const double* f_dev, int64_t B, double* v_dev, dg_solve_stats* stats_host,
+                    void* cuda_stream);
+
+/* Exchange build on the octree (as dg_exchange_build): the Hartree solve for
+ * rho = sum_k psi_k^2, the N(N+1)/2 pair solves f = psi_i psi_j (i <= j), the
+ * accumulation W_j = sum_s psi_s v_sj, K = Psi^T diag(W_q) W (K_host [N*N]
+ * row-major, host), E_H = (rho|rho) / 2 and E_X = -tr K / 2 (host, may be
+ * NULL). psi_dev [N][Nq] device; stats_host [N(N+1)/2 + 1] (host, may be
+ * NULL), entry 0 the Hartree solve. N in 1..4096. Returns as dg_octree_solve. */
+int dg_octree_exchange_build(dg_oct_handle h, const double* psi_dev, int32_t N, double* K_host, double* E_H,
+                             double* E_X, dg_solve_stats* stats_host, void* cuda_stream);
 
 /* Exercises the bounded wait used by every tensor-core kernel of this library
  * (their pipeline hand-offs are mbarrier waits that give up after about a

@@ -17,6 +17,7 @@
 
 #include "dg_ctx.h"
 #include "dg_internal.h"
+#include "dg_octree.h"
 #include "dg_setup.h"
 
 namespace dg {
@@ -194,15 +195,6 @@ bool octree_faces(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_lea
 // with [u] = u_K - u_L along K's outward normal, sigma = (p+1)^2/(eps h) of
 // the smaller leaf, and the test-side contraction back onto the leaf's nodes.
 // ---------------------------------------------------------------------------
-struct OctTables {
-  double w[MAXN1];               // GL weights
-  double wq[MAXN1];              // Gauss weights (n1 points per face direction)
-  double S[MAXN1 * MAXN1];       // sum_q wq l_a'(xq) l_b'(xq)
-  double Lq[MAXN1 * MAXN1];      // [i][a] l_a(xq_i)
-  double Lh[2][MAXN1 * MAXN1];   // [c][i][a] l_a((xq_i + 2c - 1) / 2): a larger leaf's basis on half c
-  double Le[2][MAXN1];           // l_a(-1), l_a(+1)
-  double dLe[2][MAXN1];          // l_a'(-1), l_a'(+1)
-};
 
 __device__ __forceinline__ double oct_penalty(int p, double h, int form, double eps) {
   const double c = (double)((p + 1) * (p + 1));
@@ -214,7 +206,7 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
                                                       const int* __restrict__ kind, const int* __restrict__ nbr,
                                                       const int* __restrict__ pos, int E, int p, int pform,
                                                       double eps, const double* __restrict__ u,
-                                                      double* __restrict__ out) {
+                                                      double* __restrict__ out, const int* __restrict__ act) {
   constexpr int NPE = N1 * N1 * N1, NF = N1 * N1;
   __shared__ double sLq[NF], sLh[2][NF], sS[NF], sLe[2][N1], sdLe[2][N1], sw[N1], swq[N1];
   __shared__ double uK[NPE], acc[NPE], uN[NPE];
@@ -222,8 +214,9 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
       G2[NF];
   const int e = blockIdx.x;
   const int tid = threadIdx.x, NT = blockDim.x;
-  const double* ub = u + (long long)blockIdx.y * E * NPE;
-  double* ob = out + (long long)blockIdx.y * E * NPE;
+  const long long src = act ? act[blockIdx.y] : blockIdx.y;
+  const double* ub = u + src * E * NPE;
+  double* ob = out + src * E * NPE;
   for (int i = tid; i < NF; i += NT) {
     const int r = i / N1, c = i % N1;
     sLq[i] = T.Lq[r * N1 + c];
@@ -386,7 +379,7 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   for (int i = tid; i < NPE; i += NT) ob[(long long)e * NPE + i] = acc[i];
 }
 
-static void octree_tables(int n1, OctTables& T) {
+void octree_tables(int n1, OctTables& T) {
   std::memset(&T, 0, sizeof(T));
   double xi[MAXN1], w[MAXN1], xq[MAXN1], wq[MAXN1], L[MAXN1], dL[MAXN1];
   gauss_legendre(n1, xi, w);
@@ -422,6 +415,32 @@ static void octree_tables(int n1, OctTables& T) {
       for (int i = 0; i < n1; ++i) sum += wq[i] * dq[(size_t)i * n1 + a] * dq[(size_t)i * n1 + b];
       T.S[a * n1 + b] = sum;
     }
+}
+
+cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, const int* kind, const int* nb,
+                                const int* pos, int E, int p, int pform, double eps, const double* u, double* out,
+                                const int* act, int nact, cudaStream_t s) {
+  if (nact == 0 || E == 0) return cudaSuccess;
+  const dim3 grid((unsigned)E, (unsigned)nact);
+  count_launch();
+  switch (n1) {
+#define DG_OCT_CASE(N)                                                                             \
+  case N:                                                                                          \
+    k_octree_apply<N><<<grid, 256, 0, s>>>(T, hq, kind, nb, pos, E, p, pform, eps, u, out, act); \
+    break;
+    DG_OCT_CASE(2)
+    DG_OCT_CASE(3)
+    DG_OCT_CASE(4)
+    DG_OCT_CASE(5)
+    DG_OCT_CASE(6)
+    DG_OCT_CASE(7)
+    DG_OCT_CASE(8)
+    DG_OCT_CASE(9)
+#undef DG_OCT_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 }  // namespace dg
 
@@ -529,29 +548,9 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
     return rc;
   if ((rc = ck(cudaMemcpyAsync(dp.p, pos.data(), sizeof(int) * pos.size(), cudaMemcpyHostToDevice, s))) != DG_OK)
     return rc;
-  const dim3 grid((unsigned)E, (unsigned)B);
-  const double* dhq = dh.as<double>();
-  const int *dkd = dk.as<int>(), *dnb = dn.as<int>(), *dps = dp.as<int>();
-  const int pp = root->p;
-  count_launch();
-  switch (n1) {
-#define DG_OCT_CASE(N)                                                                                      \
-  case N:                                                                                                   \
-    k_octree_apply<N><<<grid, 256, 0, s>>>(T, dhq, dkd, dnb, dps, E, pp, penalty_form, penalty_eps, u, out); \
-    break;
-    DG_OCT_CASE(2)
-    DG_OCT_CASE(3)
-    DG_OCT_CASE(4)
-    DG_OCT_CASE(5)
-    DG_OCT_CASE(6)
-    DG_OCT_CASE(7)
-    DG_OCT_CASE(8)
-    DG_OCT_CASE(9)
-#undef DG_OCT_CASE
-    default:
-      return DG_ERR_INVALID_ARG;
-  }
-  if ((rc = ck(cudaGetLastError())) != DG_OK) return rc;
+  if ((rc = ck(launch_octree_apply(n1, T, dh.as<double>(), dk.as<int>(), dn.as<int>(), dp.as<int>(), E, root->p,
+                                   penalty_form, penalty_eps, u, out, nullptr, (int)B, s))) != DG_OK)
+    return rc;
   // the tables and connectivity are call-local: wait before they are freed
   return ck(cudaStreamSynchronize(s));
 }

@@ -135,6 +135,20 @@ def load():
     lib.dg_octree_faces.restype = C.c_int
     lib.dg_octree_apply.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, vp, vp, C.c_int64, vp]
     lib.dg_octree_apply.restype = C.c_int
+    lib.dg_octree_setup.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.POINTER(vp)]
+    lib.dg_octree_setup.restype = C.c_int
+    lib.dg_octree_destroy.argtypes = [vp]
+    lib.dg_octree_destroy.restype = None
+    lib.dg_octree_error_detail.argtypes = [vp]
+    lib.dg_octree_error_detail.restype = C.c_char_p
+    lib.dg_octree_node_coords.argtypes = [vp, vp, vp, vp]
+    lib.dg_octree_node_coords.restype = C.c_int
+    lib.dg_octree_precond.argtypes = [vp, vp, vp, C.c_int64, vp]
+    lib.dg_octree_precond.restype = C.c_int
+    lib.dg_octree_solve.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+    lib.dg_octree_solve.restype = C.c_int
+    lib.dg_octree_exchange_build.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp]
+    lib.dg_octree_exchange_build.restype = C.c_int
     lib.dg_apply_operator.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
     lib.dg_boundary_data.argtypes = [vp, C.c_int32, vp, C.c_int64, vp, C.POINTER(C.c_int64), vp]
     lib.dg_apply_smoother.argtypes = [vp, C.c_int32, C.c_int32, vp, vp, C.c_int64, vp]
@@ -716,6 +730,88 @@ class PoissonSolver:
     def close(self):
         if self.h:
             dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class OctreeSolver:
+    """Owns one octree solver handle (dg_octree_setup): the leaves [E, 4] of an
+    octree over the root grid (lo, hi, n, p), FP64 fields [B, E (p+1)^3]."""
+
+    def __init__(self, lo, hi, n, p, leaves, penalty_form=0, penalty_eps=0.125, rtol=1e-10, max_iter=5000):
+        if np.isscalar(n):
+            n = (n, n, n)
+        self.leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+        if self.leaves.ndim != 2 or self.leaves.shape[1] != 4:
+            raise ValueError(f"leaves must be [n_leaves, 4], got {tuple(self.leaves.shape)}")
+        self.p = int(p)
+        self.Nq = self.leaves.shape[0] * (self.p + 1) ** 3
+        desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), self.p)
+        h = C.c_void_p()
+        _check(load().dg_octree_setup(C.byref(desc), self.leaves.ctypes.data_as(C.c_void_p), self.leaves.shape[0],
+                                      penalty_form, penalty_eps, rtol, max_iter, C.byref(h)), "dg_octree_setup")
+        self.h = h
+
+    def _ck(self, code, where, allow=()):
+        if code != DG_OK and code not in allow:
+            raise DGError(code, where, load().dg_octree_error_detail(self.h).decode())
+        return code
+
+    def _field(self, t, name):
+        import torch
+
+        if t.ndim != 2 or t.shape[1] != self.Nq:
+            raise ValueError(f"{name} must be [B, {self.Nq}], got {tuple(t.shape)}")
+        return _dev_ptr(t, torch.float64)
+
+    def node_coords(self):
+        import torch
+
+        xyz = torch.empty((self.Nq, 3), dtype=torch.float64, device="cuda")
+        w = torch.empty((self.Nq,), dtype=torch.float64, device="cuda")
+        self._ck(load().dg_octree_node_coords(self.h, _dev_ptr(xyz), _dev_ptr(w), _stream_ptr(None)),
+                 "dg_octree_node_coords")
+        return xyz, w
+
+    def precond(self, r, stream=None):
+        import torch
+
+        z = torch.empty_like(r)
+        self._ck(load().dg_octree_precond(self.h, self._field(r, "r"), self._field(z, "z"), r.shape[0],
+                                          _stream_ptr(stream)), "dg_octree_precond")
+        return z
+
+    def solve(self, f, stream=None, allow_unconverged=False):
+        import torch
+
+        B = f.shape[0]
+        v = torch.empty_like(f)
+        st = (dg_solve_stats * max(B, 1))()
+        allow = (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_NONFINITE) if allow_unconverged else ()
+        self._ck(load().dg_octree_solve(self.h, self._field(f, "f"), B, self._field(v, "v"), C.cast(st, C.c_void_p),
+                                        _stream_ptr(stream)), "dg_octree_solve", allow)
+        return v, _stats_list(st[:B])
+
+    def exchange_build(self, psi, stream=None, allow_unconverged=False):
+        N = psi.shape[0]
+        P = N * (N + 1) // 2 + 1
+        K = np.zeros((N, N))
+        eh, ex = C.c_double(), C.c_double()
+        st = (dg_solve_stats * P)()
+        allow = (DG_ERR_NOT_CONVERGED, DG_ERR_BREAKDOWN, DG_ERR_NONFINITE) if allow_unconverged else ()
+        self._ck(load().dg_octree_exchange_build(self.h, self._field(psi, "psi"), N, K.ctypes.data_as(C.c_void_p),
+                                                 C.byref(eh), C.byref(ex), C.cast(st, C.c_void_p),
+                                                 _stream_ptr(stream)), "dg_octree_exchange_build", allow)
+        return K, eh.value, ex.value, _stats_list(st[:P])
+
+    def close(self):
+        if self.h:
+            load().dg_octree_destroy(self.h)
             self.h = None
 
     def __del__(self):

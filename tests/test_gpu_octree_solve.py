@@ -1,0 +1,144 @@
+"""Poisson solves and the exchange build on the octree auxiliary mesh
+(dg_octree_setup / dg_octree_solve / dg_octree_exchange_build) against the
+oracle's dense Cholesky solve on meshes with hanging faces (Sec. 6.2, 6.3)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import octree
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LO, HI = [-1.0, -1.5, -1.0], [1.0, 1.5, 2.0]
+
+
+@pytest.fixture(scope="module")
+def dgx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_21213_gb300 import build, dgx
+
+    build.build()
+    dgx.load()
+    return dgx
+
+
+def _three_levels(p, lo=LO, hi=HI):
+    t = octree.OctreeMesh(lo, hi, (2, 2, 2), p)
+    t.refine([(0, 0, 0, 0)])
+    t.refine([(1, 1, 1, 1)])
+    t.balance()
+    return t
+
+
+def _one_split(p):
+    t = octree.OctreeMesh(LO, HI, (2, 1, 1), p)
+    t.refine([(0, 1, 0, 0)])
+    return t
+
+
+def _solver(dgx, t, **kw):
+    return dgx.OctreeSolver(t.lo, t.hi, t.n, t.p, np.array(t.leaf_list(), dtype=np.int32), **kw)
+
+
+def _gauss_source(t, centre=(0.2, -0.1, 0.3), alpha=3.0):
+    x = t.node_coords()
+    d = x - np.asarray(centre)[None, :]
+    return np.exp(-alpha * np.einsum("qi,qi->q", d, d))
+
+
+@pytest.mark.parametrize("mesh,p,form", [("three", 2, 0), ("three", 3, 1), ("one", 5, 0), ("one", 8, 0)])
+def test_precond_is_the_inverse_of_the_diagonal_blocks(dgx, mesh, p, form):
+    """z = P r equals the exact inverse of the oracle matrix's leaf blocks
+    (the fast-diagonalisation factors of every leaf class)."""
+    t = _three_levels(p) if mesh == "three" else _one_split(p)
+    A = octree.assemble(t, penalty_form=form)
+    npe = t.npe
+    rng = np.random.default_rng(10 + p)
+    r = rng.standard_normal((2, t.Nq))
+    ref = np.empty_like(r)
+    for e in range(t.E):
+        s = slice(e * npe, (e + 1) * npe)
+        ref[:, s] = np.linalg.solve(A[s, s], r[:, s].T).T
+    s = _solver(dgx, t, penalty_form=form)
+    got = s.precond(torch.tensor(r, device="cuda")).cpu().numpy()
+    s.close()
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_node_coords_and_weights_are_the_oracle_ones(dgx):
+    t = _three_levels(3)
+    s = _solver(dgx, t)
+    xyz, w = s.node_coords()
+    s.close()
+    assert np.abs(xyz.cpu().numpy() - t.node_coords()).max() <= 1e-14
+    assert np.abs(w.cpu().numpy() - t.quad_weights()).max() <= 1e-15 * t.quad_weights().max() * 10
+
+
+@pytest.mark.parametrize("mesh,p,form", [("three", 3, 0), ("three", 2, 1), ("one", 6, 0)])
+def test_solve_matches_the_dense_oracle(dgx, mesh, p, form):
+    """Coulomb boundary data by direct quadrature, Nitsche load, PCG to rtol
+    1e-13: v equals the oracle's Cholesky solution of the same system."""
+    t = _three_levels(p) if mesh == "three" else _one_split(p)
+    f = np.stack([_gauss_source(t), _gauss_source(t, (-0.4, 0.5, 0.9), 1.5)])
+    ref = np.stack([octree.poisson(t, fk, penalty_form=form) for fk in f])
+    s = _solver(dgx, t, penalty_form=form, rtol=1e-13)
+    v, st = s.solve(torch.tensor(f, device="cuda"))
+    s.close()
+    v = v.cpu().numpy()
+    assert all(x["status"] == 0 and x["rel_residual"] <= 1e-13 for x in st)
+    assert np.abs(v - ref).max() <= 1e-10 * np.abs(ref).max()
+    W = t.quad_weights()
+    for k in range(2):
+        se_ref = float(np.sum(W * f[k] * ref[k]))
+        assert abs(st[k]["self_energy"] - se_ref) <= 1e-11 * abs(se_ref)
+
+
+def test_solve_edge_cases(dgx):
+    """A zero source gives v = 0 in no iterations; a source with a NaN is
+    reported (DG_ERR_NONFINITE, v = 0) and leaves the others bit-identical."""
+    t = _one_split(3)
+    s = _solver(dgx, t, rtol=1e-12)
+    f = _gauss_source(t)
+    bad = f.copy()
+    bad[5] = np.nan
+    both = torch.tensor(np.stack([f, np.zeros_like(f), bad, 2.0 * f]), device="cuda")
+    v, st = s.solve(both, allow_unconverged=True)
+    alone, st1 = s.solve(torch.tensor(np.stack([f, 2.0 * f]), device="cuda"))
+    s.close()
+    assert st[1]["status"] == 0 and st[1]["iters"] == 0 and float(v[1].abs().max()) == 0.0
+    assert st[2]["status"] == -5 and float(v[2].abs().max()) == 0.0
+    assert torch.equal(v[0], alone[0]) and torch.equal(v[3], alone[1])
+    assert st[0]["iters"] == st1[0]["iters"]
+
+
+def test_exchange_build_matches_the_oracle_on_a_refined_octree(dgx):
+    """Hartree and pair solves, accumulation, K and energies on an octree refined
+    by the density indicator of Sec. 6.2 around the two atoms of the tiny
+    system: equal to the oracle's dense exchange build."""
+    from paper_2510_21213_gb300 import inputs
+
+    spec = inputs.tiny_system()
+    lo, hi = list(spec.mesh.lo), list(spec.mesh.hi)
+    t = octree.OctreeMesh(lo, hi, (2, 2, 2), 3)
+
+    def rho(P):
+        return np.sum(inputs.orbitals(spec, P) ** 2, axis=0)
+
+    octree.refine_to_density(t, rho, 1e-3, 2)
+    assert t.E > 8 and any(k[0] == 2 for k in t.leaves)
+    psi = inputs.orbitals(spec, t.node_coords())
+    ref = octree.exchange_build(t, psi)
+    s = _solver(dgx, t, rtol=1e-13)
+    K, EH, EX, st = s.exchange_build(torch.tensor(psi, device="cuda"))
+    s.close()
+    assert all(x["status"] == 0 for x in st)
+    assert np.abs(K - ref["K"]).max() <= 1e-10 * np.abs(ref["K"]).max()
+    assert abs(EH - ref["E_H"]) <= 1e-10 * abs(ref["E_H"])
+    assert abs(EX - ref["E_X"]) <= 1e-10 * abs(ref["E_X"])
+    # the Hartree self-energy is 2 E_H
+    assert abs(st[0]["self_energy"] - 2.0 * EH) <= 1e-14 * abs(EH)

@@ -252,3 +252,41 @@ def test_octree_apply_checks_field_shape_before_any_launch():
     for bad in (torch.zeros(width), torch.zeros(2, width - 1), torch.zeros(2, width + 27)):
         with pytest.raises(ValueError):
             dgx.dg_octree_apply(LO, HI, (2, 2, 2), 2, leaves, bad)
+
+
+def test_octree_setup_rejects_bad_arguments_without_a_device():
+    """dg_octree_setup validates the mesh, the leaf set and its settings on the
+    host before any device work: each bad argument is DG_ERR_INVALID_ARG and
+    no handle is returned."""
+    from paper_2510_21213_gb300 import dgx
+
+    lib = dgx.load()
+    C = dgx.C
+    t = _refined(2)
+    leaves = np.array(t.leaf_list(), dtype=np.int32)
+    lp = leaves.ctypes.data_as(C.c_void_p)
+
+    def desc(p=2, n=(2, 2, 2)):
+        return dgx.dg_mesh_desc((C.c_double * 3)(*LO), (C.c_double * 3)(*HI), (C.c_int32 * 3)(*n), p)
+
+    good = dict(form=0, eps=0.125, rtol=1e-10, it=100)
+    cases = [dict(good, form=2), dict(good, eps=0.0), dict(good, rtol=0.0), dict(good, rtol=1.0),
+             dict(good, it=0)]
+    for c in cases:
+        h = C.c_void_p(1)
+        rc = lib.dg_octree_setup(C.byref(desc()), lp, len(leaves), c["form"], c["eps"], c["rtol"], c["it"],
+                                 C.byref(h))
+        assert rc == dgx.DG_ERR_INVALID_ARG and not h.value
+    h = C.c_void_p(1)
+    assert lib.dg_octree_setup(C.byref(desc(p=9)), lp, len(leaves), 0, 0.125, 1e-10, 100,
+                               C.byref(h)) == dgx.DG_ERR_INVALID_ARG and not h.value
+    # a leaf set that is not 2:1 balanced
+    bad = octree.OctreeMesh(LO, HI, (2, 2, 2), 2)
+    bad.refine([(0, 0, 0, 0)])
+    bad.refine([(1, 1, 1, 1)])
+    bl = np.array(bad.leaf_list(), dtype=np.int32)
+    assert lib.dg_octree_setup(C.byref(desc()), bl.ctypes.data_as(C.c_void_p), len(bl), 0, 0.125, 1e-10, 100,
+                               C.byref(h)) == dgx.DG_ERR_INVALID_ARG and not h.value
+    assert lib.dg_octree_setup(C.byref(desc()), lp, len(leaves), 0, 0.125, 1e-10, 100, None) == \
+        dgx.DG_ERR_INVALID_ARG
+    lib.dg_octree_destroy(None)
