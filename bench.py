@@ -90,8 +90,11 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip timing the learned form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-jk", action="store_true", help="skip timing the J/K action on trial functions")
-    ap.add_argument("--octree-apply", action="store_true",
-                    help="time the SIPDG operator on a density-refined octree instead of the exchange build")
+    ap.add_argument("--octree", action="store_true",
+                    help="time the exchange build on a density-refined octree instead of the uniform mesh")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time only the dominant kernels (operator, smoother, patch solves) at the bench's batch, "
+                         "without the exchange builds (the command the ncu captures of profiles/ run)")
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
@@ -422,6 +425,13 @@ def run_ours(args):
         raise SystemExit(f"no trained network weights for p = {m.p}")
     solver = dgx.PoissonSolver(m.lo, m.hi, m.n, m.p, precision=prec, rtol=1e-8, batch=args.batch,
                                nn_weights_path=weights if prec == dgx.DG_PREC_MIXED_LEARNED else None)
+    if args.kernels_only:
+        rf = kernel_roofline(solver, min(solver.info.batch, P + 1), args.precision, torch)
+        print(json.dumps({"kernels_only": True, "workload": args.workload, "precision": args.precision, **rf}),
+              flush=True)
+        solver.close()
+        pd.finish()
+        return
     xyz, w = solver.node_coords()
     psi_host = make_inputs(spec, xyz, w)
     psi_dev = torch.tensor(psi_host, device="cuda")
@@ -607,50 +617,76 @@ def run_ours(args):
     pd.finish()
 
 
-def run_octree_apply(args):
-    """The SIPDG operator on an adaptive octree (dg_octree_apply): the chain10
-    box with a 4^3 root grid at p = 6, refined by the density indicator for the
-    chain's ten atom-centred Gaussians (exponent 2, delta 1e-5, up to level 2: 344 leaves),
-    applied to 8 fields. One step = one call (connectivity and tables built per
-    call, then the kernel)."""
+def run_octree(args):
+    """Exchange build on an adaptive octree (dg_octree_setup /
+    dg_octree_exchange_build): the chain10 box [-12, 12]^3 with a 4^3 root grid
+    at p = 6, refined by the density indicator of the chain system's orbitals
+    (delta 1e-5, up to level 2), the chain's 10 orbitals evaluated at the
+    octree's nodes and orthonormalised with its weights; FP64, rtol 1e-8. One
+    step = one whole build (Hartree + 55 pairs), timed with CUDA events. Also
+    the operator alone on 8 fields (one kernel, CUDA events)."""
     import torch
 
-    from paper_2510_21213_gb300 import build, dgx
+    from paper_2510_21213_gb300 import build, dgx, inputs
 
     build.build()
-    lo, hi, n, p = [-12.0] * 3, [12.0] * 3, (4, 4, 4), 6
-    atoms = np.array([[-6.3 + 1.4 * k, 0.0, 0.0] for k in range(10)])
+    spec = inputs.chain_system()
+    lo, hi, n, p = list(spec.mesh.lo), list(spec.mesh.hi), tuple(spec.mesh.n), spec.mesh.p
 
     def rho(P):
-        r2 = ((P[:, None, :] - atoms[None, :, :]) ** 2).sum(-1)
-        return (2.0 / math.pi) ** 1.5 * np.exp(-2.0 * r2).sum(1)
+        return np.sum((spec.coeffs @ inputs.eval_primitives(spec, P)) ** 2, axis=0)
 
     leaves = dgx.dg_octree_refine(lo, hi, n, p, rho, 1e-5, 2)
-    E, npe, B = leaves.shape[0], (p + 1) ** 3, 8
-    u = torch.randn(B, E * npe, dtype=torch.float64, device="cuda")
+    s = dgx.OctreeSolver(lo, hi, n, p, leaves, rtol=1e-8)
+    xyz, w = s.node_coords()
+    psi = torch.tensor(inputs.orbitals(spec, xyz.cpu().numpy(), w.cpu().numpy()), device="cuda")
+    N = psi.shape[0]
+    P = N * (N + 1) // 2
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(max(args.warmup, 3)):
-        dgx.dg_octree_apply(lo, hi, n, p, leaves, u)
+        K, EH, EX, st = s.exchange_build(psi)
     torch.cuda.synchronize()
-    times = []
+    ms = []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        dgx.dg_octree_apply(lo, hi, n, p, leaves, u)
+        ev0.record()
+        K, EH, EX, st = s.exchange_build(psi)
+        ev1.record()
         torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
-    sec = sum(times) / len(times)
+        ms.append(ev0.elapsed_time(ev1))
+    t = sum(ms) / len(ms)
+    # the operator alone: 8 fields, one launch
+    B = 8
+    u = torch.randn(B, s.Nq, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(u)
+    for _ in range(3):
+        s.apply(u, out)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(20):
+        s.apply(u, out)
+    ev1.record()
+    torch.cuda.synchronize()
+    op_ms = ev0.elapsed_time(ev1) / 20
+    s.close()
     levels = np.bincount(leaves[:, 0]).tolist()
-    print(json.dumps({"metric": "octree SIPDG operator applications, DOF/s", "value": B * E * npe / sec,
-                      "unit": "dof/s", "ms_per_step": sec * 1e3, "steps": args.steps, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": "octree-apply: chain10 box, 4^3 roots, p=6",
-                                                      "leaves": E, "leaves_per_level": levels, "fields": B,
-                                                      "timing": "host wall clock around each call (connectivity, "
-                                                                "tables and kernel)"}}), flush=True)
+    print(json.dumps({"metric": "octree exchange build, pair solves/s", "value": (P + 1) / (t / 1e3),
+                      "unit": "pair_solves/s", "ms_per_step": t, "steps": args.steps, "warmup": max(args.warmup, 3),
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "octree: chain10 box, 4^3 roots, p=6, density-refined to level 2",
+                                 "leaves": int(leaves.shape[0]), "leaves_per_level": levels, "Nq": int(s.Nq),
+                                 "orbitals": N, "sources": P + 1, "rtol": 1e-8,
+                                 "mean_iters": float(np.mean([x["iters"] for x in st])),
+                                 "E_H": EH, "E_X": EX,
+                                 "timing": "CUDA events around each whole build (host-synchronised PCG)"},
+                      "operator": {"fields": B, "ms_per_application": op_ms,
+                                   "dof_per_s": B * s.Nq / (op_ms / 1e3),
+                                   "timing": "CUDA events over 20 launches of the operator kernel"}}), flush=True)
 
 
 def main():
     args = parse()
-    if args.octree_apply:
-        run_octree_apply(args)
+    if args.octree:
+        run_octree(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -475,6 +475,11 @@ const char* dg_octree_error_detail(dg_oct_handle h);
  * written; either may be NULL, not both). W_q = w_a w_b w_c h_x h_y h_z / 8. */
 int dg_octree_node_coords(dg_oct_handle h, double* xyz_dev, double* w_dev, void* cuda_stream);
 
+/* The operator on the handle's mesh: out = A u for B fields (0..65535), u_dev
+ * and out_dev [B][Nq] device, not overlapping (DG_ERR_INVALID_ARG). Stream
+ * ordered: launches one kernel and returns without synchronising. */
+int dg_octree_operator(dg_oct_handle h, const double* u_dev, double* out_dev, int64_t B, void* cuda_stream);
+
 /* The preconditioner alone: z = P r for B fields, P the exact inverse of the
  * block diagonal of A (one block per leaf). r_dev, z_dev [B][Nq] device. */
 int dg_octree_precond(dg_oct_handle h, const double* r_dev, double* z_dev, int64_t B, void* cuda_stream);

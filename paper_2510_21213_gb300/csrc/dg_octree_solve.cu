@@ -671,6 +671,18 @@ int dg_octree_node_coords(dg_oct_handle h, double* xyz_dev, double* w_dev, void*
   return DG_OK;
 }
 
+int dg_octree_operator(dg_oct_handle h, const double* u_dev, double* out_dev, int64_t B, void* stream) {
+  if (!h || B < 0 || B > 65535 || (B > 0 && (!u_dev || !out_dev))) return DG_ERR_INVALID_ARG;
+  if (B == 0) return DG_OK;
+  const size_t bytes = sizeof(double) * (size_t)B * (size_t)h->Nq;
+  const char *u0 = (const char*)u_dev, *o0 = (const char*)out_dev;
+  if (u0 < o0 + bytes && o0 < u0 + bytes) return DG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DG_CK(launch_octree_apply(h->n1, h->T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
+                            h->E, h->p, h->pform, h->eps, u_dev, out_dev, nullptr, (int)B, s));
+  return DG_OK;
+}
+
 int dg_octree_precond(dg_oct_handle h, const double* r_dev, double* z_dev, int64_t B, void* stream) {
   if (!h || B < 0 || (B > 0 && (!r_dev || !z_dev))) return DG_ERR_INVALID_ARG;
   if (B == 0) return DG_OK;

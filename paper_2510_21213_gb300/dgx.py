@@ -143,6 +143,8 @@ def load():
     lib.dg_octree_error_detail.restype = C.c_char_p
     lib.dg_octree_node_coords.argtypes = [vp, vp, vp, vp]
     lib.dg_octree_node_coords.restype = C.c_int
+    lib.dg_octree_operator.argtypes = [vp, vp, vp, C.c_int64, vp]
+    lib.dg_octree_operator.restype = C.c_int
     lib.dg_octree_precond.argtypes = [vp, vp, vp, C.c_int64, vp]
     lib.dg_octree_precond.restype = C.c_int
     lib.dg_octree_solve.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
@@ -777,6 +779,15 @@ class OctreeSolver:
         self._ck(load().dg_octree_node_coords(self.h, _dev_ptr(xyz), _dev_ptr(w), _stream_ptr(None)),
                  "dg_octree_node_coords")
         return xyz, w
+
+    def apply(self, u, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty_like(u)
+        self._ck(load().dg_octree_operator(self.h, self._field(u, "u"), self._field(out, "out"), u.shape[0],
+                                           _stream_ptr(stream)), "dg_octree_operator")
+        return out
 
     def precond(self, r, stream=None):
         import torch

@@ -142,3 +142,21 @@ def test_exchange_build_matches_the_oracle_on_a_refined_octree(dgx):
     assert abs(EX - ref["E_X"]) <= 1e-10 * abs(ref["E_X"])
     # the Hartree self-energy is 2 E_H
     assert abs(st[0]["self_energy"] - 2.0 * EH) <= 1e-14 * abs(EH)
+
+
+def test_handle_operator_is_dg_octree_apply(dgx):
+    """The handle's operator (tables and connectivity kept on the device) gives
+    bit for bit what the per-call dg_octree_apply gives, and refuses aliased
+    fields."""
+    t = _three_levels(4)
+    leaves = np.array(t.leaf_list(), dtype=np.int32)
+    u = torch.randn(3, t.Nq, dtype=torch.float64, device="cuda")
+    ref = dgx.dg_octree_apply(t.lo, t.hi, t.n, t.p, leaves, u)
+    s = _solver(dgx, t)
+    got = s.apply(u)
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
+    lib = dgx.load()
+    ptr = dgx.C.c_void_p(u.data_ptr())
+    assert lib.dg_octree_operator(s.h, ptr, ptr, 3, None) == dgx.DG_ERR_INVALID_ARG
+    s.close()
