@@ -448,17 +448,25 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * node coordinates, quadrature weights and preconditioner tables on the
  * device; the system is the one dg_octree_apply applies (SIPDG, symmetric
  * Nitsche boundary terms, hanging faces on the smaller face, penalty of the
- * smaller leaf). It is solved in FP64 by PCG whose preconditioner inverts
- * every leaf's diagonal block exactly by fast diagonalisation (the block is a
- * Kronecker sum of 1-D leaf matrices and GL masses). Dirichlet data: the
+ * smaller leaf). Every leaf's diagonal block is inverted exactly by fast
+ * diagonalisation (the block is a Kronecker sum of 1-D leaf matrices and GL
+ * masses): the leaf-block preconditioner P. Dirichlet data: the
  * direct quadrature g(x) = sum_q W_q f(q) / |x - x_q| over all nodes at the GL
  * nodes of every boundary face (Sec. 6.3), imposed weakly by the Nitsche load
- * int_F g (sigma v - d_n v).
+ * int_F g (sigma v - d_n v). Solved in FP64 by PCG (preconditioner below).
  *
  * dg_octree_setup: root, leaves_host [n_leaves][4] (host) as for
  * dg_octree_apply; penalty_form / penalty_eps as there; rtol: FP64 true
  * relative residual ||b - A v|| / ||b|| at which a solve stops (0 < rtol < 1);
- * max_iter: PCG iteration limit (>= 1). Writes the handle to *out (NULL on
+ * max_iter: PCG iteration limit (>= 1); precond: 1 (default) an hp-multigrid
+ * V-cycle, 0 the leaf-block inverse alone. The V-cycle (Sec. 6.4: degree
+ * coarsening, then the nested h-hierarchy) smooths each octree level by
+ * Chebyshev(3) on P^-1 A (P the leaf-block inverse, lambda_max(P^-1 A) by
+ * power iteration at set-up), coarsens the degree per leaf p -> max(1, p/2)
+ * down to 1, then restricts to the uniform root grid at degree 1 (every leaf
+ * lies in one root cell, so the root space is nested) and applies that grid's
+ * own multigrid V-cycle (a uniform solver handle, h-coarsening and a dense
+ * coarsest solve). Writes the handle to *out (NULL on
  * failure). Fields are [.][Nq] FP64 with Nq = n_leaves (p+1)^3, element-blocked
  * in leaf order, nodes x-fastest. DG_ERR_INVALID_ARG for a bad mesh, leaf set
  * or argument; DG_ERR_UNSUPPORTED beyond 2^31 nodes; DG_ERR_NO_MEMORY,
@@ -466,7 +474,7 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * handle must not overlap; each synchronises its stream before it returns. */
 typedef struct dg_oct* dg_oct_handle;
 int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t penalty_form,
-                    double penalty_eps, double rtol, int32_t max_iter, dg_oct_handle* out);
+                    double penalty_eps, double rtol, int32_t max_iter, int32_t precond, dg_oct_handle* out);
 void dg_octree_destroy(dg_oct_handle h);
 /* Text of the last CUDA failure on the handle ("" if none). */
 const char* dg_octree_error_detail(dg_oct_handle h);
@@ -480,8 +488,9 @@ int dg_octree_node_coords(dg_oct_handle h, double* xyz_dev, double* w_dev, void*
  * ordered: launches one kernel and returns without synchronising. */
 int dg_octree_operator(dg_oct_handle h, const double* u_dev, double* out_dev, int64_t B, void* cuda_stream);
 
-/* The preconditioner alone: z = P r for B fields, P the exact inverse of the
- * block diagonal of A (one block per leaf). r_dev, z_dev [B][Nq] device. */
+/* The handle's preconditioner alone for B fields: z = V(r), one V-cycle
+ * (precond 1), or z = P r, the exact inverse of A's leaf blocks (precond 0).
+ * r_dev, z_dev [B][Nq] device, not overlapping. Synchronises the stream. */
 int dg_octree_precond(dg_oct_handle h, const double* r_dev, double* z_dev, int64_t B, void* cuda_stream);
 
 /* Solves -Lap v = 4 pi f with the Coulomb boundary data of f for B sources

@@ -38,20 +38,33 @@
 
 #include "dg_ctx.h"
 #include "dg_internal.h"
+#include "dg_mg.h"
 #include "dg_octree.h"
 #include "dg_setup.h"
+
+// One level of the octree hierarchy: the leaves at degree p (the fine level,
+// then p-coarsened), with the tables of its operator and of its leaf-block
+// preconditioner, and its multigrid workspace.
+struct OctLevel {
+  int n1 = 0, p = 0;
+  long long Nq = 0;
+  dg::OctTables T;
+  dg::DevBuf cls;     // int [E][3]: 1-D class of each leaf axis
+  dg::DevBuf S, lam;  // per class: S [n1][n1] (row node, column mode), lambda [n1]
+  int ncls = 0;
+  double lam_max = 0;  // lambda_max(P^-1 A) estimate (power iteration at set-up)
+  dg::DevBuf I;        // [n1][n1c]: the next coarser level's basis at this level's nodes
+  dg::DevBuf x, b, res, d, z, q;  // V-cycle workspace, [cap][Nq] each
+};
 
 // Handle of the octree solver (opaque in the C ABI).
 struct dg_oct {
   std::string err;
-  int n1 = 0, p = 0, E = 0, pform = 0, max_iter = 0;
+  int n1 = 0, p = 0, E = 0, pform = 0, max_iter = 0, precond = 1;
   double eps = 0.125, rtol = 1e-10;
   long long Nq = 0;
-  dg::OctTables T;
   dg::DevBuf hq, kind, nb, pos;  // leaf sizes [E][3]; connectivity [E][6], [E][6][4], [E][6]
-  dg::DevBuf cls;                // int [E][3]: 1-D class of each axis
-  dg::DevBuf S, lam;             // per class: S [n1][n1] (row node, column mode), lambda [n1]
-  int ncls = 0;
+  std::vector<OctLevel> lv;      // lv[0]: the fine level
   dg::DevBuf xq, W;              // node coordinates [Nq][3], quadrature weights [Nq]
   int nbf = 0;                   // boundary faces
   dg::DevBuf xb;                 // their GL nodes [nbf][n1 * n1][3] (lower tangential axis fastest)
@@ -59,10 +72,24 @@ struct dg_oct {
   dg::DevBuf wgl;                // GL weights [n1]
   int nbl = 0;                   // leaves with a boundary face
   dg::DevBuf bleaf;              // [nbl][7]: leaf, then the boundary face index of each face or -1
+  // coarse correction of the V-cycle: the uniform root grid at degree 1 and
+  // its own h-hierarchy (a uniform solver handle), and the transfer to it
+  dg_ctx* root = nullptr;
+  long long Nq_root = 0;
+  int n_root = 0;                // root cells
+  dg::DevBuf rcell;              // int [E]: root cell of each leaf
+  dg::DevBuf rJ;                 // double [E][3][2][2]: root basis b at the leaf's degree-1 node a, per axis
+  dg::DevBuf rptr, rlist;        // root cell -> its leaves (CSR, leaf order)
+  dg::DevBuf rb, rx;             // root-level right-hand side and correction, [cap][Nq_root]
+  int cheb_k = 3;                // Chebyshev degree of the octree-level smoother
+  double cheb_range = 10.0;      // its interval [lambda_max / range, lambda_max]
   // workspace, sized for `cap` sources
   int cap = 0;
   dg::DevBuf f, g, b, x, r, z, pv, qv, scal, part, act, flags, pidx, lists, Wacc, kpart, Kdev;
   std::vector<int> act_host;
+  ~dg_oct() {
+    if (root) dg_destroy(root);
+  }
 };
 
 namespace dg {
@@ -240,20 +267,134 @@ __global__ void k_oct_copy(double* __restrict__ dst, const double* __restrict__ 
     dst[off + i] = src[off + i];
 }
 
+
+// p-transfers between octree levels, one leaf and source per block, sum-factorised
+// with I [n1f][n1c] (the coarse basis at the fine nodes):
+//   prolongation  xf += (I (x) I (x) I) xc,  restriction  rc = (I (x) I (x) I)^T rf
+__global__ void __launch_bounds__(128) k_oct_prolong_p(const double* __restrict__ I, int n1f, int n1c,
+                                                       const double* __restrict__ xc, double* __restrict__ xf,
+                                                       long long Nqc, long long Nqf, const int* __restrict__ act) {
+  __shared__ double sI[MAXN1 * MAXN1], c0[MAXN1 * MAXN1 * MAXN1], t1[MAXN1 * MAXN1 * MAXN1],
+      t2[MAXN1 * MAXN1 * MAXN1];
+  const int e = blockIdx.x;
+  const long long k = act[blockIdx.y];
+  const int npc = n1c * n1c * n1c, npf = n1f * n1f * n1f;
+  for (int i = threadIdx.x; i < n1f * n1c; i += blockDim.x) sI[i] = I[i];
+  for (int i = threadIdx.x; i < npc; i += blockDim.x) c0[i] = xc[k * Nqc + (long long)e * npc + i];
+  __syncthreads();
+  for (int t = threadIdx.x; t < n1c * n1c * n1f; t += blockDim.x) {  // t1[c'][b'][a]
+    const int a = t % n1f, r = t / n1f;
+    double acc = 0.0;
+    for (int j = 0; j < n1c; ++j) acc += sI[a * n1c + j] * c0[r * n1c + j];
+    t1[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n1c * n1f * n1f; t += blockDim.x) {  // t2[c'][b][a]
+    const int a = t % n1f, b = (t / n1f) % n1f, c = t / (n1f * n1f);
+    double acc = 0.0;
+    for (int j = 0; j < n1c; ++j) acc += sI[b * n1c + j] * t1[(c * n1c + j) * n1f + a];
+    t2[t] = acc;
+  }
+  __syncthreads();
+  double* dst = xf + k * Nqf + (long long)e * npf;
+  for (int t = threadIdx.x; t < npf; t += blockDim.x) {
+    const int ab = t % (n1f * n1f), c = t / (n1f * n1f);
+    double acc = 0.0;
+    for (int j = 0; j < n1c; ++j) acc += sI[c * n1c + j] * t2[j * n1f * n1f + ab];
+    dst[t] += acc;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_oct_restrict_p(const double* __restrict__ I, int n1f, int n1c,
+                                                        const double* __restrict__ rf, double* __restrict__ rc,
+                                                        long long Nqf, long long Nqc, const int* __restrict__ act) {
+  __shared__ double sI[MAXN1 * MAXN1], f0[MAXN1 * MAXN1 * MAXN1], t1[MAXN1 * MAXN1 * MAXN1],
+      t2[MAXN1 * MAXN1 * MAXN1];
+  const int e = blockIdx.x;
+  const long long k = act[blockIdx.y];
+  const int npc = n1c * n1c * n1c, npf = n1f * n1f * n1f;
+  for (int i = threadIdx.x; i < n1f * n1c; i += blockDim.x) sI[i] = I[i];
+  for (int i = threadIdx.x; i < npf; i += blockDim.x) f0[i] = rf[k * Nqf + (long long)e * npf + i];
+  __syncthreads();
+  for (int t = threadIdx.x; t < n1f * n1f * n1c; t += blockDim.x) {  // t1[c][b][a']
+    const int ac = t % n1c, r = t / n1c;
+    double acc = 0.0;
+    for (int a = 0; a < n1f; ++a) acc += sI[a * n1c + ac] * f0[r * n1f + a];
+    t1[t] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n1f * n1c * n1c; t += blockDim.x) {  // t2[c][b'][a']
+    const int ac = t % n1c, bc = (t / n1c) % n1c, c = t / (n1c * n1c);
+    double acc = 0.0;
+    for (int b = 0; b < n1f; ++b) acc += sI[b * n1c + bc] * t1[(c * n1f + b) * n1c + ac];
+    t2[t] = acc;
+  }
+  __syncthreads();
+  double* dst = rc + k * Nqc + (long long)e * npc;
+  for (int t = threadIdx.x; t < npc; t += blockDim.x) {
+    const int ab = t % (n1c * n1c), cc = t / (n1c * n1c);
+    double acc = 0.0;
+    for (int c = 0; c < n1f; ++c) acc += sI[c * n1c + cc] * t2[c * n1c * n1c + ab];
+    dst[t] = acc;
+  }
+}
+
+// degree-1 leaves <-> the degree-1 uniform root grid (each leaf lies in one
+// root cell; the root field restricted to a leaf is degree 1 there, so the
+// prolongation is exact): J[e][d][a][b] = root basis b at the leaf's node a
+__global__ void k_oct_prolong_root(const int* __restrict__ rcell, const double* __restrict__ J,
+                                   const double* __restrict__ xr, double* __restrict__ xf, int E, long long Nqr,
+                                   long long Nqf, const int* __restrict__ act) {
+  const long long k = act[blockIdx.y];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < E * 8; t += gridDim.x * blockDim.x) {
+    const int e = t >> 3, a = t & 1, b = (t >> 1) & 1, c = t >> 2 & 1;
+    const double* Je = J + 12LL * e;
+    const double* xe = xr + k * Nqr + 8LL * rcell[e];
+    double acc = 0.0;
+    for (int cc = 0; cc < 2; ++cc)
+      for (int bb = 0; bb < 2; ++bb)
+        for (int aa = 0; aa < 2; ++aa)
+          acc += Je[0 + 2 * a + aa] * Je[4 + 2 * b + bb] * Je[8 + 2 * c + cc] * xe[aa + 2 * bb + 4 * cc];
+    xf[k * Nqf + t] += acc;
+  }
+}
+
+__global__ void k_oct_restrict_root(const int* __restrict__ rptr, const int* __restrict__ rlist,
+                                    const double* __restrict__ J, const double* __restrict__ rf,
+                                    double* __restrict__ rr, int nroot, long long Nqr, long long Nqf,
+                                    const int* __restrict__ act) {
+  const long long k = act[blockIdx.y];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nroot * 8; t += gridDim.x * blockDim.x) {
+    const int rc = t >> 3, aa = t & 1, bb = (t >> 1) & 1, cc = t >> 2 & 1;
+    double acc = 0.0;
+    for (int i = rptr[rc]; i < rptr[rc + 1]; ++i) {
+      const int e = rlist[i];
+      const double* Je = J + 12LL * e;
+      const double* re = rf + k * Nqf + 8LL * e;
+      for (int c = 0; c < 2; ++c)
+        for (int b = 0; b < 2; ++b)
+          for (int a = 0; a < 2; ++a)
+            acc += Je[0 + 2 * a + aa] * Je[4 + 2 * b + bb] * Je[8 + 2 * c + cc] * re[a + 2 * b + 4 * c];
+    }
+    rr[k * Nqr + t] = acc;
+  }
+}
+
 }  // namespace dg
 
 namespace dg {
 
-static cudaError_t launch_bjac(const dg_oct* h, const double* r, double* z, const int* act, int nact, cudaStream_t s) {
+static cudaError_t launch_bjac(const dg_oct* h, const OctLevel& L, const double* r, double* z, const int* act,
+                               int nact, cudaStream_t s) {
   if (nact == 0) return cudaSuccess;
   const dim3 grid((unsigned)h->E, (unsigned)nact);
-  const int* c = h->cls.as<int>();
-  const double *S = h->S.as<double>(), *l = h->lam.as<double>();
+  const int* c = L.cls.as<int>();
+  const double *S = L.S.as<double>(), *l = L.lam.as<double>();
   count_launch();
-  switch (h->n1) {
+  switch (L.n1) {
 #define DG_BJ(N)                                                              \
   case N:                                                                     \
-    k_oct_bjac<N><<<grid, 128, 0, s>>>(c, S, l, r, z, h->Nq, act);            \
+    k_oct_bjac<N><<<grid, 128, 0, s>>>(c, S, l, r, z, L.Nq, act);             \
     break;
     DG_BJ(2) DG_BJ(3) DG_BJ(4) DG_BJ(5) DG_BJ(6) DG_BJ(7) DG_BJ(8) DG_BJ(9)
 #undef DG_BJ
@@ -261,6 +402,12 @@ static cudaError_t launch_bjac(const dg_oct* h, const double* r, double* z, cons
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+static cudaError_t oct_apply(const dg_oct* h, const OctLevel& L, const double* u, double* out, const int* act,
+                             int nact, cudaStream_t s) {
+  return launch_octree_apply(L.n1, L.T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
+                             h->E, L.p, h->pform, h->eps, u, out, act, nact, s);
 }
 
 static cudaError_t launch_oct_lift(const dg_oct* h, const double* g, double* b, int nsrc, cudaStream_t s) {
@@ -318,6 +465,22 @@ static int oct_ws(dg_oct* h, int cap) {
   if (cap <= h->cap) return DG_OK;
   const size_t vec = sizeof(double) * (size_t)cap * (size_t)h->Nq;
   for (DevBuf* v : {&h->f, &h->b, &h->x, &h->r, &h->z, &h->pv, &h->qv}) DG_CK(v->ensure(vec));
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    OctLevel& L = h->lv[l];
+    const size_t lvec = sizeof(double) * (size_t)cap * (size_t)L.Nq;
+    for (DevBuf* v : {&L.res, &L.d, &L.z, &L.q}) DG_CK(v->ensure(lvec));
+    if (l > 0)
+      for (DevBuf* v : {&L.x, &L.b}) DG_CK(v->ensure(lvec));
+  }
+  if (h->root) {
+    DG_CK(h->rb.ensure(sizeof(double) * (size_t)cap * (size_t)h->Nq_root));
+    DG_CK(h->rx.ensure(sizeof(double) * (size_t)cap * (size_t)h->Nq_root));
+    const int rc = prepare(h->root, cap);
+    if (rc != DG_OK) {
+      h->err = "root-grid workspace: " + h->root->err;
+      return rc;
+    }
+  }
   DG_CK(h->g.ensure(sizeof(double) * (size_t)cap * h->nbf * h->n1 * h->n1));
   DG_CK(h->scal.ensure(sizeof(double) * O_NSLOT * (size_t)cap));
   DG_CK(h->part.ensure(sizeof(double) * 304 * (size_t)cap));
@@ -363,6 +526,132 @@ static int oct_finite(dg_oct* h, const double* f, int nsrc, std::vector<int>& fi
   return DG_OK;
 }
 
+
+// Chebyshev smoothing of A x = b on octree level l: the semi-iteration on
+// P^-1 A (P the leaf-block preconditioner) over [lambda / range, lambda],
+// lambda = 1.1 x the level's power-iteration estimate. On exit, if want_res,
+// the level's res holds b - A x.
+static int oct_cheb(dg_oct* h, int l, const double* b, double* x, bool zero_init, bool want_res, const int* act,
+                    int n, cudaStream_t s) {
+  OctLevel& L = h->lv[l];
+  double *res = L.res.as<double>(), *d = L.d.as<double>(), *z = L.z.as<double>(), *q = L.q.as<double>();
+  const double bmax = 1.1 * L.lam_max, amin = bmax / h->cheb_range;
+  const double theta = 0.5 * (bmax + amin), delta = 0.5 * (bmax - amin), sig1 = theta / delta;
+  const dim3 vg = ogrid(L.Nq, n);
+  auto resid = [&]() -> int {
+    DG_CK(oct_apply(h, L, x, q, act, n, s));
+    count_launch();
+    k_oct_sub<<<vg, OT, 0, s>>>(res, b, q, L.Nq, act);
+    DG_CK(cudaGetLastError());
+    return DG_OK;
+  };
+  const double* r0 = b;
+  if (!zero_init) {
+    DG_RET(resid());
+    r0 = res;
+  }
+  DG_CK(launch_bjac(h, L, r0, z, act, n, s));
+  DG_CK(launch_cheb_first<double>(x, d, z, nullptr, 1.0 / theta, zero_init ? 1 : 0, L.Nq, act, n, s));
+  double rho_prev = 1.0 / sig1;
+  for (int j = 2; j <= h->cheb_k; ++j) {
+    DG_RET(resid());
+    const double rho = 1.0 / (2.0 * sig1 - rho_prev);
+    DG_CK(launch_bjac(h, L, res, z, act, n, s));
+    DG_CK(launch_cheb_step<double>(x, d, z, nullptr, rho * rho_prev, 2.0 * rho / delta, L.Nq, act, n, s));
+    rho_prev = rho;
+  }
+  if (want_res) DG_RET(resid());
+  return DG_OK;
+}
+
+// x = V(b) on octree level l (x overwritten): smoothing, restriction to the
+// next coarser degree (or, from degree 1, to the uniform root grid and its own
+// V-cycle), prolongation of the correction, smoothing
+static int oct_vcycle(dg_oct* h, int l, const double* b, double* x, const int* act, int n, cudaStream_t s) {
+  OctLevel& L = h->lv[l];
+  DG_RET(oct_cheb(h, l, b, x, true, true, act, n, s));
+  const double* res = L.res.as<double>();
+  if (l + 1 < (int)h->lv.size()) {
+    OctLevel& C = h->lv[l + 1];
+    count_launch();
+    k_oct_restrict_p<<<dim3((unsigned)h->E, (unsigned)n), 128, 0, s>>>(L.I.as<double>(), L.n1, C.n1, res,
+                                                                        C.b.as<double>(), L.Nq, C.Nq, act);
+    DG_CK(cudaGetLastError());
+    DG_RET(oct_vcycle(h, l + 1, C.b.as<double>(), C.x.as<double>(), act, n, s));
+    count_launch();
+    k_oct_prolong_p<<<dim3((unsigned)h->E, (unsigned)n), 128, 0, s>>>(L.I.as<double>(), L.n1, C.n1,
+                                                                       C.x.as<double>(), x, C.Nq, L.Nq, act);
+    DG_CK(cudaGetLastError());
+  } else {
+    const unsigned gr = (unsigned)std::min<long long>(4096, (h->n_root * 8LL + 255) / 256);
+    count_launch();
+    k_oct_restrict_root<<<dim3(gr, (unsigned)n), 256, 0, s>>>(h->rptr.as<int>(), h->rlist.as<int>(),
+                                                               h->rJ.as<double>(), res, h->rb.as<double>(),
+                                                               h->n_root, h->Nq_root, L.Nq, act);
+    DG_CK(cudaGetLastError());
+    MG<double> mg{h->root, &h->root->w64, act, n, s};
+    const int rc = mg.vcycle(0, h->rb.as<double>(), h->rx.as<double>());
+    if (rc != DG_OK) {
+      h->err = "root-grid V-cycle: " + h->root->err;
+      return rc;
+    }
+    const unsigned ge = (unsigned)std::min<long long>(4096, (h->E * 8LL + 255) / 256);
+    count_launch();
+    k_oct_prolong_root<<<dim3(ge, (unsigned)n), 256, 0, s>>>(h->rcell.as<int>(), h->rJ.as<double>(),
+                                                              h->rx.as<double>(), x, h->E, h->Nq_root, L.Nq, act);
+    DG_CK(cudaGetLastError());
+  }
+  DG_RET(oct_cheb(h, l, b, x, false, false, act, n, s));
+  return DG_OK;
+}
+
+// z = M r: the V-cycle (precond 1) or the leaf-block inverse (precond 0)
+static int oct_precond(dg_oct* h, const double* r, double* z, const int* act, int n, cudaStream_t s) {
+  if (h->precond == 0) {
+    DG_CK(launch_bjac(h, h->lv[0], r, z, act, n, s));
+    return DG_OK;
+  }
+  return oct_vcycle(h, 0, r, z, act, n, s);
+}
+
+// lambda_max(P^-1 A) of level l by 30 power iterations from a fixed
+// pseudo-random start (one field, the level's workspace of source 0)
+static int oct_lambda(dg_oct* h, int l, cudaStream_t s) {
+  OctLevel& L = h->lv[l];
+  std::vector<double> v(L.Nq);
+  uint64_t st = 0x9E3779B97F4A7C15ull;
+  for (auto& x : v) {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    x = double((st >> 11) & ((1ull << 53) - 1)) / double(1ull << 53) - 0.5;
+  }
+  double *x = L.d.as<double>(), *q = L.q.as<double>(), *z = L.z.as<double>();
+  DG_CK(cudaMemcpyAsync(x, v.data(), sizeof(double) * L.Nq, cudaMemcpyHostToDevice, s));
+  DG_RET(oct_act(h, std::vector<int>{0}, s));
+  const int* act = h->act.as<int>();
+  double* nrm = oslot(h, O_SE);
+  double lam = 0.0, nz = 0.0, nx = 0.0;
+  DG_CK(launch_dot(x, x, (const double*)nullptr, nrm, h->part.as<double>(), L.Nq, act, 1, s));
+  DG_CK(cudaMemcpyAsync(&nx, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  for (int it = 0; it < 30; ++it) {
+    DG_CK(oct_apply(h, L, x, q, act, 1, s));
+    DG_CK(launch_bjac(h, L, q, z, act, 1, s));
+    DG_CK(launch_dot(z, z, (const double*)nullptr, nrm, h->part.as<double>(), L.Nq, act, 1, s));
+    DG_CK(cudaMemcpyAsync(&nz, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    DG_CK(cudaStreamSynchronize(s));
+    if (!(nz > 0.0) || !std::isfinite(nz)) {
+      h->err = "power iteration of the smoother bound broke down";
+      return DG_ERR_BREAKDOWN;
+    }
+    lam = std::sqrt(nz / nx);
+    DG_CK(cudaMemcpyAsync(x, z, sizeof(double) * L.Nq, cudaMemcpyDeviceToDevice, s));
+    DG_CK(launch_scale(x, L.Nq, 1.0 / std::sqrt(nz), s));
+    nx = 1.0;
+  }
+  L.lam_max = lam;
+  return DG_OK;
+}
+
 }  // namespace dg
 
 namespace dg {
@@ -398,8 +687,7 @@ static int oct_pcg(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vec
   auto true_residual = [&](const std::vector<int>& a) -> int {
     DG_RET(oct_act(h, a, s));
     const int n = (int)a.size();
-    DG_CK(launch_octree_apply(h->n1, h->T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
-                              h->E, h->p, h->pform, h->eps, x, q, act, n, s));
+    DG_CK(oct_apply(h, h->lv[0], x, q, act, n, s));
     count_launch();
     k_oct_sub<<<vgrid_n(n), OT, 0, s>>>(r, b, q, Nq, act);
     DG_CK(cudaGetLastError());
@@ -415,7 +703,7 @@ static int oct_pcg(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vec
   k_oct_copy<<<vgrid_n(n), OT, 0, s>>>(r, b, Nq, act);
   DG_CK(cudaGetLastError());
   DG_CK(launch_dot(b, b, (const double*)nullptr, oslot(h, O_BB), part, Nq, act, n, s));
-  DG_CK(launch_bjac(h, r, z, act, n, s));
+  DG_RET(oct_precond(h, r, z, act, n, s));
   count_launch();
   k_oct_copy<<<vgrid_n(n), OT, 0, s>>>(p, z, Nq, act);
   DG_CK(cudaGetLastError());
@@ -430,8 +718,7 @@ static int oct_pcg(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vec
   for (int it = 1; it <= h->max_iter && !active.empty(); ++it) {
     DG_RET(oct_act(h, active, s));
     n = (int)active.size();
-    DG_CK(launch_octree_apply(h->n1, h->T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
-                              h->E, h->p, h->pform, h->eps, p, q, act, n, s));
+    DG_CK(oct_apply(h, h->lv[0], p, q, act, n, s));
     DG_CK(launch_dot(p, q, (const double*)nullptr, oslot(h, O_PQ), part, Nq, act, n, s));
     count_launch();
     k_oct_ratio<<<(n + 127) / 128, 128, 0, s>>>(oslot(h, O_RZ), oslot(h, O_PQ), oslot(h, O_AL), act, n, flags);
@@ -474,7 +761,7 @@ static int oct_pcg(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vec
     // z = P r, beta = (r, z) / rz, rz = (r, z), p = z + beta p (beta = 0 on a restart)
     DG_RET(oct_act(h, active, s));
     n = (int)active.size();
-    DG_CK(launch_bjac(h, r, z, act, n, s));
+    DG_RET(oct_precond(h, r, z, act, n, s));
     DG_CK(launch_dot(r, z, (const double*)nullptr, oslot(h, O_RZN), part, Nq, act, n, s));
     count_launch();
     k_oct_ratio<<<(n + 127) / 128, 128, 0, s>>>(oslot(h, O_RZN), oslot(h, O_RZ), oslot(h, O_BE), act, n, flags);
@@ -517,8 +804,11 @@ static int oct_self_energies(dg_oct* h, const double* f, int nsrc, std::vector<d
 }
 
 static int oct_cap(const dg_oct* h, long long want) {
-  // seven source vectors per source: at most about 4 GB of workspace, at most 64 sources per chunk
-  const long long per = 7LL * h->Nq * (long long)sizeof(double);
+  // per source: seven fine-level PCG vectors, four smoother vectors per level
+  // and two more on the coarser ones; at most about 4 GB, at most 64 sources
+  long long per = 7LL * h->Nq;
+  for (size_t l = 0; l < h->lv.size(); ++l) per += (l == 0 ? 4LL : 6LL) * h->lv[l].Nq;
+  per *= (long long)sizeof(double);
   long long c = std::max(1LL, std::min(64LL, (4LL << 30) / std::max(1LL, per)));
   return (int)std::max(1LL, std::min(c, want));
 }
@@ -530,17 +820,18 @@ using namespace dg;
 extern "C" {
 
 int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_leaves, int32_t penalty_form,
-                    double penalty_eps, double rtol, int32_t max_iter, dg_oct_handle* out) {
+                    double penalty_eps, double rtol, int32_t max_iter, int32_t precond, dg_oct_handle* out) {
   if (!out) return DG_ERR_INVALID_ARG;
   *out = nullptr;
   if (!root || !leaves || n_leaves < 1 || root->p < 1 || root->p > MAXN1 - 1 ||
       (penalty_form != 0 && penalty_form != 1) || !(penalty_eps > 0.0) || !(rtol > 0.0) || !(rtol < 1.0) ||
-      max_iter < 1)
+      max_iter < 1 || (precond != 0 && precond != 1))
     return DG_ERR_INVALID_ARG;
   const int E = n_leaves, n1 = root->p + 1, NPE = n1 * n1 * n1, NF = n1 * n1;
   std::vector<int32_t> kind(6 * (size_t)E), nb(24 * (size_t)E), pos(6 * (size_t)E);
   if (!octree_faces(root, leaves, n_leaves, kind.data(), nb.data(), pos.data())) return DG_ERR_INVALID_ARG;
   if ((long long)E * NPE > (1LL << 31)) return DG_ERR_UNSUPPORTED;
+  const long long n_root = (long long)root->n[0] * root->n[1] * root->n[2];
   DeviceWideGuard guard;
   dg_oct* h = new dg_oct();
   h->n1 = n1;
@@ -550,8 +841,8 @@ int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
   h->eps = penalty_eps;
   h->rtol = rtol;
   h->max_iter = max_iter;
+  h->precond = precond;
   h->Nq = (long long)E * NPE;
-  octree_tables(n1, h->T);
   double xi[MAXN1], w[MAXN1];
   gauss_legendre(n1, xi, w);
   // sizes, origins, nodes and weights
@@ -573,31 +864,71 @@ int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
       W[qi] = w[a] * w[b] * w[c] * hh[0] * hh[1] * hh[2] / 8.0;
     }
   }
-  // 1-D classes of the block preconditioner
-  std::map<OctClass, int> cmap;
-  std::vector<int> cls(3 * (size_t)E);
-  std::vector<double> Sv, lv;
-  for (int e = 0; e < E; ++e)
-    for (int d = 0; d < 3; ++d) {
-      int ty[2];
-      for (int r = 0; r < 2; ++r) {
-        const int k = kind[6 * (size_t)e + 2 * d + r];
-        ty[r] = k == 0 ? 0 : (k == 3 ? 2 : 1);
+  auto up = [&](DevBuf& dst, const void* src, size_t bytes) -> int {
+    DG_CK(dst.ensure(std::max<size_t>(bytes, 16)));
+    DG_CK(cudaMemcpy(dst.p, src, bytes, cudaMemcpyHostToDevice));
+    return DG_OK;
+  };
+  int rc = DG_OK;
+  auto fail = [&](int code) {
+    delete h;
+    return code;
+  };
+  // levels: degree p, then max(1, p / 2) down to 1 (precond 1), each with its
+  // operator tables and its leaf-block classes
+  for (int pl = root->p;;) {
+    h->lv.emplace_back();
+    OctLevel& L = h->lv.back();
+    L.p = pl;
+    L.n1 = pl + 1;
+    L.Nq = (long long)E * L.n1 * L.n1 * L.n1;
+    octree_tables(L.n1, L.T);
+    const int nf = L.n1 * L.n1;
+    std::map<OctClass, int> cmap;
+    std::vector<int> cls(3 * (size_t)E);
+    std::vector<double> Sv, lv;
+    for (int e = 0; e < E; ++e)
+      for (int d = 0; d < 3; ++d) {
+        int ty[2];
+        for (int r = 0; r < 2; ++r) {
+          const int k = kind[6 * (size_t)e + 2 * d + r];
+          ty[r] = k == 0 ? 0 : (k == 3 ? 2 : 1);
+        }
+        const OctClass key{d, leaves[4 * e], ty[0], ty[1]};
+        auto it = cmap.find(key);
+        if (it == cmap.end()) {
+          const int id = (int)cmap.size();
+          it = cmap.emplace(key, id).first;
+          Sv.resize((size_t)(id + 1) * nf);
+          lv.resize((size_t)(id + 1) * L.n1);
+          oct_class_fdm(L.T, L.n1, L.p, hq[3 * (size_t)e + d], ty[0], ty[1], penalty_form, penalty_eps,
+                        Sv.data() + (size_t)id * nf, lv.data() + (size_t)id * L.n1);
+        }
+        cls[3 * (size_t)e + d] = it->second;
       }
-      const OctClass key{d, leaves[4 * e], ty[0], ty[1]};
-      auto it = cmap.find(key);
-      if (it == cmap.end()) {
-        const int id = (int)cmap.size();
-        it = cmap.emplace(key, id).first;
-        Sv.resize((size_t)(id + 1) * NF);
-        lv.resize((size_t)(id + 1) * n1);
-        oct_class_fdm(h->T, n1, h->p, hq[3 * (size_t)e + d], ty[0], ty[1], penalty_form, penalty_eps,
-                      Sv.data() + (size_t)id * NF, lv.data() + (size_t)id * n1);
-      }
-      cls[3 * (size_t)e + d] = it->second;
+    L.ncls = (int)cmap.size();
+    if ((rc = up(L.cls, cls.data(), sizeof(int) * cls.size())) != DG_OK ||
+        (rc = up(L.S, Sv.data(), sizeof(double) * Sv.size())) != DG_OK ||
+        (rc = up(L.lam, lv.data(), sizeof(double) * lv.size())) != DG_OK)
+      return fail(rc);
+    if (precond == 0 || pl == 1) break;
+    pl = std::max(1, pl / 2);
+  }
+  // interpolation from each level to the next finer one
+  for (size_t l = 0; l + 1 < h->lv.size(); ++l) {
+    const int nf1 = h->lv[l].n1, nc1 = h->lv[l + 1].n1;
+    double xf[MAXN1], wf[MAXN1], xc[MAXN1], wc[MAXN1], Lc[MAXN1], dLc[MAXN1];
+    gauss_legendre(nf1, xf, wf);
+    gauss_legendre(nc1, xc, wc);
+    std::vector<double> I((size_t)nf1 * nc1);
+    for (int a = 0; a < nf1; ++a) {
+      lagrange(xc, nc1, xf[a], Lc, dLc);
+      for (int j = 0; j < nc1; ++j) I[(size_t)a * nc1 + j] = Lc[j];
     }
-  h->ncls = (int)cmap.size();
+    if ((rc = up(h->lv[l].I, I.data(), sizeof(double) * I.size())) != DG_OK) return fail(rc);
+  }
   // boundary faces: GL nodes, 1-D lift factors, and per leaf the face indices
+  const OctTables& T = h->lv[0].T;
   std::vector<double> xb, l1;
   std::vector<int> bl;
   for (int e = 0; e < E; ++e) {
@@ -621,33 +952,74 @@ int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
       const double sig = penalty(h->p, hh[d], penalty_form, penalty_eps);
       const double e1 = r ? 1.0 : -1.0;
       for (int a = 0; a < n1; ++a)
-        l1.push_back(hh[t0] * hh[t1] / 4.0 * (sig * h->T.Le[r][a] - e1 * (2.0 / hh[d]) * h->T.dLe[r][a]));
+        l1.push_back(hh[t0] * hh[t1] / 4.0 * (sig * T.Le[r][a] - e1 * (2.0 / hh[d]) * T.dLe[r][a]));
     }
     if (!any) continue;
     bl.push_back(e);
     bl.insert(bl.end(), fidx, fidx + 6);
     ++h->nbl;
   }
-  auto up = [&](DevBuf& dst, const void* src, size_t bytes) -> int {
-    DG_CK(dst.ensure(std::max<size_t>(bytes, 16)));
-    DG_CK(cudaMemcpy(dst.p, src, bytes, cudaMemcpyHostToDevice));
-    return DG_OK;
-  };
-  int rc = DG_OK;
   if ((rc = up(h->hq, hq.data(), sizeof(double) * hq.size())) != DG_OK ||
       (rc = up(h->kind, kind.data(), sizeof(int) * kind.size())) != DG_OK ||
       (rc = up(h->nb, nb.data(), sizeof(int) * nb.size())) != DG_OK ||
       (rc = up(h->pos, pos.data(), sizeof(int) * pos.size())) != DG_OK ||
-      (rc = up(h->cls, cls.data(), sizeof(int) * cls.size())) != DG_OK ||
-      (rc = up(h->S, Sv.data(), sizeof(double) * Sv.size())) != DG_OK ||
-      (rc = up(h->lam, lv.data(), sizeof(double) * lv.size())) != DG_OK ||
       (rc = up(h->xq, xq.data(), sizeof(double) * xq.size())) != DG_OK ||
       (rc = up(h->W, W.data(), sizeof(double) * W.size())) != DG_OK ||
       (rc = up(h->xb, xb.data(), sizeof(double) * xb.size())) != DG_OK ||
       (rc = up(h->lift1d, l1.data(), sizeof(double) * l1.size())) != DG_OK ||
-      (rc = up(h->wgl, w, sizeof(double) * n1)) != DG_OK || (rc = up(h->bleaf, bl.data(), sizeof(int) * bl.size())) != DG_OK) {
-    delete h;
-    return rc;
+      (rc = up(h->wgl, w, sizeof(double) * n1)) != DG_OK ||
+      (rc = up(h->bleaf, bl.data(), sizeof(int) * bl.size())) != DG_OK)
+    return fail(rc);
+  if (precond == 1) {
+    // the root grid at degree 1: each leaf's root cell, the root basis at the
+    // leaf's degree-1 nodes, the leaves of every root cell, and the uniform
+    // solver handle that carries the root grid's own multigrid hierarchy
+    double x2[2], w2[2], L2[2], dL2[2];
+    gauss_legendre(2, x2, w2);
+    h->n_root = (int)n_root;
+    h->Nq_root = n_root * 8;
+    std::vector<int> rcell(E), rptr(n_root + 1, 0), rlist(E);
+    std::vector<double> J(12 * (size_t)E);
+    for (int e = 0; e < E; ++e) {
+      const int lvl = leaves[4 * e];
+      int ci[3];
+      for (int d = 0; d < 3; ++d) {
+        ci[d] = leaves[4 * e + 1 + d] >> lvl;
+        const int loc = leaves[4 * e + 1 + d] - (ci[d] << lvl);
+        for (int a = 0; a < 2; ++a) {
+          const double eta = 2.0 * (loc + (x2[a] + 1.0) / 2.0) / double(1 << lvl) - 1.0;
+          lagrange(x2, 2, eta, L2, dL2);
+          for (int bq = 0; bq < 2; ++bq) J[12 * (size_t)e + 4 * d + 2 * a + bq] = L2[bq];
+        }
+      }
+      rcell[e] = ci[0] + root->n[0] * (ci[1] + root->n[1] * ci[2]);
+      ++rptr[rcell[e] + 1];
+    }
+    for (long long c = 0; c < n_root; ++c) rptr[c + 1] += rptr[c];
+    {
+      std::vector<int> fill(rptr.begin(), rptr.end() - 1);
+      for (int e = 0; e < E; ++e) rlist[fill[rcell[e]]++] = e;
+    }
+    if ((rc = up(h->rcell, rcell.data(), sizeof(int) * rcell.size())) != DG_OK ||
+        (rc = up(h->rJ, J.data(), sizeof(double) * J.size())) != DG_OK ||
+        (rc = up(h->rptr, rptr.data(), sizeof(int) * rptr.size())) != DG_OK ||
+        (rc = up(h->rlist, rlist.data(), sizeof(int) * rlist.size())) != DG_OK)
+      return fail(rc);
+    dg_mesh_desc rm = *root;
+    rm.p = 1;
+    dg_solver_opts o;
+    dg_default_opts(&o);
+    o.precision = DG_PREC_FP64;
+    o.penalty_form = penalty_form;
+    o.penalty_eps = penalty_eps;
+    if ((rc = dg_poisson_setup(&rm, &o, &h->root)) != DG_OK) {
+      h->err = "root-grid solver set-up failed";
+      return fail(rc);
+    }
+    // lambda_max(P^-1 A) of every octree level, for its Chebyshev smoother
+    if ((rc = oct_ws(h, 1)) != DG_OK) return fail(rc);
+    for (size_t l = 0; l < h->lv.size(); ++l)
+      if ((rc = oct_lambda(h, (int)l, nullptr)) != DG_OK) return fail(rc);
   }
   *out = h;
   return DG_OK;
@@ -678,8 +1050,7 @@ int dg_octree_operator(dg_oct_handle h, const double* u_dev, double* out_dev, in
   const char *u0 = (const char*)u_dev, *o0 = (const char*)out_dev;
   if (u0 < o0 + bytes && o0 < u0 + bytes) return DG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  DG_CK(launch_octree_apply(h->n1, h->T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
-                            h->E, h->p, h->pform, h->eps, u_dev, out_dev, nullptr, (int)B, s));
+  DG_CK(oct_apply(h, h->lv[0], u_dev, out_dev, nullptr, (int)B, s));
   return DG_OK;
 }
 
@@ -694,7 +1065,7 @@ int dg_octree_precond(dg_oct_handle h, const double* r_dev, double* z_dev, int64
     std::vector<int> a(nb);
     for (int k = 0; k < nb; ++k) a[k] = k;
     DG_RET(oct_act(h, a, s));
-    DG_CK(launch_bjac(h, r_dev + b0 * h->Nq, z_dev + b0 * h->Nq, h->act.as<int>(), nb, s));
+    DG_RET(oct_precond(h, r_dev + b0 * h->Nq, z_dev + b0 * h->Nq, h->act.as<int>(), nb, s));
   }
   DG_CK(cudaStreamSynchronize(s));
   return DG_OK;

@@ -135,7 +135,8 @@ def load():
     lib.dg_octree_faces.restype = C.c_int
     lib.dg_octree_apply.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, vp, vp, C.c_int64, vp]
     lib.dg_octree_apply.restype = C.c_int
-    lib.dg_octree_setup.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.POINTER(vp)]
+    lib.dg_octree_setup.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                    C.POINTER(vp)]
     lib.dg_octree_setup.restype = C.c_int
     lib.dg_octree_destroy.argtypes = [vp]
     lib.dg_octree_destroy.restype = None
@@ -745,7 +746,8 @@ class OctreeSolver:
     """Owns one octree solver handle (dg_octree_setup): the leaves [E, 4] of an
     octree over the root grid (lo, hi, n, p), FP64 fields [B, E (p+1)^3]."""
 
-    def __init__(self, lo, hi, n, p, leaves, penalty_form=0, penalty_eps=0.125, rtol=1e-10, max_iter=5000):
+    def __init__(self, lo, hi, n, p, leaves, penalty_form=0, penalty_eps=0.125, rtol=1e-10, max_iter=5000,
+                 precond=1):
         if np.isscalar(n):
             n = (n, n, n)
         self.leaves = np.ascontiguousarray(leaves, dtype=np.int32)
@@ -756,7 +758,8 @@ class OctreeSolver:
         desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), self.p)
         h = C.c_void_p()
         _check(load().dg_octree_setup(C.byref(desc), self.leaves.ctypes.data_as(C.c_void_p), self.leaves.shape[0],
-                                      penalty_form, penalty_eps, rtol, max_iter, C.byref(h)), "dg_octree_setup")
+                                      penalty_form, penalty_eps, rtol, max_iter, precond, C.byref(h)),
+               "dg_octree_setup")
         self.h = h
 
     def _ck(self, code, where, allow=()):
