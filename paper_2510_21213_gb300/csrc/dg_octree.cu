@@ -201,6 +201,29 @@ __device__ __forceinline__ double oct_penalty(int p, double h, int form, double 
   return form == 0 ? c / (eps * h) : c / (eps * h * h);
 }
 
+// Every face-quarter of the leaf is processed at once (a face with four smaller
+// neighbours has four, every other face one): 6 to 24 "face parts" per leaf,
+// each with six NF-sized buffers in dynamic shared memory. Interpolations to and
+// from the Gauss points are sum-factorised (one tangential axis at a time).
+// Phases, separated by block barriers:
+//   1. volume term; this leaf's six face traces; the neighbours' traces of
+//      every part, read from global memory
+//   2. first tangential contraction (t1) of the four traces of every part
+//   3. second contraction (t0) and the fluxes F1 (v-trace), F2 (d_n v)
+//   4, 5. the fluxes back onto this leaf's face nodes (t1, then t0)
+//   6. the face contributions added into the volume term, and the store
+template <int N1>
+__device__ __forceinline__ int oct_stride(int d) {
+  return d == 0 ? 1 : (d == 1 ? N1 : N1 * N1);
+}
+
+struct OctPart {
+  int f, L;          // face (2 d + side) and neighbour leaf (-1: boundary)
+  int tk0, tk1;      // this leaf's tables along t0, t1: 0 = Lq, 1 = Lh[0], 2 = Lh[1]
+  int tl0, tl1;      // the neighbour's
+  double sig, wsc;   // penalty and Jacobian of the part's face
+};
+
 template <int N1>
 __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const double* __restrict__ hq,
                                                       const int* __restrict__ kind, const int* __restrict__ nbr,
@@ -208,10 +231,12 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
                                                       double eps, const double* __restrict__ u,
                                                       double* __restrict__ out, const int* __restrict__ act) {
   constexpr int NPE = N1 * N1 * N1, NF = N1 * N1;
-  __shared__ double sLq[NF], sLh[2][NF], sS[NF], sLe[2][N1], sdLe[2][N1], sw[N1], swq[N1];
-  __shared__ double uK[NPE], acc[NPE], uN[NPE];
-  __shared__ double VK[NF], DK[NF], VL[NF], DL[NF], pv[NF], pd[NF], qv[NF], qd[NF], F1[NF], F2[NF], G1[NF],
-      G2[NF];
+  extern __shared__ double pbuf[];  // [nparts][6][NF]
+  __shared__ double sTab[3][NF], sS[NF], sLe[2][N1], sdLe[2][N1], sw[N1], swq[N1];
+  __shared__ double uK[NPE], acc[NPE], VK[6][2][NF];
+  __shared__ OctPart part[24];
+  __shared__ int npart;
+  __shared__ double hK[3];
   const int e = blockIdx.x;
   const int tid = threadIdx.x, NT = blockDim.x;
   const long long src = act ? act[blockIdx.y] : blockIdx.y;
@@ -219,9 +244,9 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   double* ob = out + src * E * NPE;
   for (int i = tid; i < NF; i += NT) {
     const int r = i / N1, c = i % N1;
-    sLq[i] = T.Lq[r * N1 + c];
-    sLh[0][i] = T.Lh[0][r * N1 + c];
-    sLh[1][i] = T.Lh[1][r * N1 + c];
+    sTab[0][i] = T.Lq[r * N1 + c];
+    sTab[1][i] = T.Lh[0][r * N1 + c];
+    sTab[2][i] = T.Lh[1][r * N1 + c];
     sS[i] = T.S[r * N1 + c];
   }
   for (int i = tid; i < N1; i += NT) {
@@ -233,9 +258,40 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
     swq[i] = T.wq[i];
   }
   for (int i = tid; i < NPE; i += NT) uK[i] = ub[(long long)e * NPE + i];
-  const double hK[3] = {hq[3LL * e], hq[3LL * e + 1], hq[3LL * e + 2]};
+  if (tid < 3) hK[tid] = hq[3LL * e + tid];
   __syncthreads();
-  // volume: sum_d (2/h_d)(h_t0 h_t1 / 4) (S_d (x) W (x) W) u
+  if (tid == 0) {
+    int n = 0;
+    for (int f = 0; f < 6; ++f) {
+      const int d = f >> 1, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+      const long long o = 6LL * e + f;
+      const int kd = kind[o];
+      const int nq = kd == 3 ? 4 : 1;
+      for (int qi = 0; qi < nq; ++qi) {
+        OctPart& P = part[n++];
+        P.f = f;
+        P.tk0 = kd == 3 ? 1 + (qi & 1) : 0;
+        P.tk1 = kd == 3 ? 1 + (qi >> 1) : 0;
+        const int ps = kd == 2 ? pos[o] : 0;
+        P.tl0 = kd == 2 ? 1 + (ps & 1) : 0;
+        P.tl1 = kd == 2 ? 1 + (ps >> 1) : 0;
+        if (kd == 0) {
+          P.L = -1;
+          P.sig = oct_penalty(p, hK[d], pform, eps);
+          P.wsc = hK[t0] * hK[t1] / 4.0;
+        } else {
+          P.L = kd == 3 ? nbr[4 * o + qi] : nbr[4 * o];
+          const double* hL = hq + 3LL * P.L;
+          P.sig = oct_penalty(p, fmin(hK[d], hL[d]), pform, eps);
+          P.wsc = kd == 3 ? hL[t0] * hL[t1] / 4.0 : hK[t0] * hK[t1] / 4.0;
+        }
+      }
+    }
+    npart = n;
+  }
+  __syncthreads();
+  const int np = npart;
+  // 1. volume: sum_d (2/h_d)(h_t0 h_t1 / 4) (S_d (x) W (x) W) u
   for (int i = tid; i < NPE; i += NT) {
     const int ix = i % N1, iy = (i / N1) % N1, iz = i / NF;
     double vx = 0.0, vy = 0.0, vz = 0.0;
@@ -249,134 +305,144 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
              vy * sw[ix] * sw[iz] * (2.0 / hK[1]) * (hK[0] * hK[2] / 4.0) +
              vz * sw[ix] * sw[iy] * (2.0 / hK[2]) * (hK[0] * hK[1] / 4.0);
   }
-  __syncthreads();
-  for (int f = 0; f < 6; ++f) {
-    const int d = f >> 1, r = f & 1;
-    const double s = r ? 1.0 : -1.0;
-    const int t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
-    const int str[3] = {1, N1, NF};
-    const int sd = str[d], s0 = str[t0], s1 = str[t1];
-    // this leaf's face trace and outward normal derivative on its face nodes [t0][t1]
-    for (int j = tid; j < NF; j += NT) {
-      const int b = j / N1, c = j % N1;
-      double v = 0.0, dv = 0.0;
+  // 1. this leaf's traces and outward normal derivatives on its face nodes [t0][t1]
+  for (int t = tid; t < 6 * NF; t += NT) {
+    const int f = t / NF, j = t - f * NF;
+    const int d = f >> 1, r = f & 1, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+    const int b = j / N1, c = j % N1;
+    const int sd = oct_stride<N1>(d), base = b * oct_stride<N1>(t0) + c * oct_stride<N1>(t1);
+    double v = 0.0, dv = 0.0;
 #pragma unroll
-      for (int a = 0; a < N1; ++a) {
-        const double x = uK[a * sd + b * s0 + c * s1];
-        v += sLe[r][a] * x;
-        dv += sdLe[r][a] * x;
-      }
-      VK[j] = v;
-      DK[j] = dv * (2.0 / hK[d]) * s;
+    for (int a = 0; a < N1; ++a) {
+      const double x = uK[a * sd + base];
+      v += sLe[r][a] * x;
+      dv += sdLe[r][a] * x;
     }
-    __syncthreads();
-    const long long o = 6LL * e + f;
-    const int kd = kind[o];
-    const int nq4 = kd == 3 ? 4 : 1;
-    for (int qi = 0; qi < nq4; ++qi) {
-      const double* T0K = kd == 3 ? sLh[qi & 1] : sLq;
-      const double* T1K = kd == 3 ? sLh[qi >> 1] : sLq;
-      for (int q = tid; q < NF; q += NT) {
-        const int i = q / N1, jj = q % N1;
-        double v = 0.0, dv = 0.0;
-        for (int b = 0; b < N1; ++b) {
-          double rv = 0.0, rd = 0.0;
-#pragma unroll
-          for (int c = 0; c < N1; ++c) {
-            rv += T1K[jj * N1 + c] * VK[b * N1 + c];
-            rd += T1K[jj * N1 + c] * DK[b * N1 + c];
-          }
-          v += T0K[i * N1 + b] * rv;
-          dv += T0K[i * N1 + b] * rd;
-        }
-        pv[q] = v;
-        pd[q] = dv;
-      }
-      double sig, wscale;
-      if (kd == 0) {
-        sig = oct_penalty(p, hK[d], pform, eps);
-        wscale = hK[t0] * hK[t1] / 4.0;
-      } else {
-        const int L = kd == 3 ? nbr[4 * o + qi] : nbr[4 * o];
-        const double hL[3] = {hq[3LL * L], hq[3LL * L + 1], hq[3LL * L + 2]};
-        for (int i = tid; i < NPE; i += NT) uN[i] = ub[(long long)L * NPE + i];
-        __syncthreads();
-        const int rl = 1 - r;  // the neighbour's face is on its other side
-        for (int j = tid; j < NF; j += NT) {
-          const int b = j / N1, c = j % N1;
-          double v = 0.0, dv = 0.0;
-#pragma unroll
-          for (int a = 0; a < N1; ++a) {
-            const double x = uN[a * sd + b * s0 + c * s1];
-            v += sLe[rl][a] * x;
-            dv += sdLe[rl][a] * x;
-          }
-          VL[j] = v;
-          DL[j] = dv * (2.0 / hL[d]) * s;
-        }
-        __syncthreads();
-        const int ps = kd == 2 ? pos[o] : 0;
-        const double* T0L = kd == 2 ? sLh[ps & 1] : sLq;
-        const double* T1L = kd == 2 ? sLh[ps >> 1] : sLq;
-        for (int q = tid; q < NF; q += NT) {
-          const int i = q / N1, jj = q % N1;
-          double v = 0.0, dv = 0.0;
-          for (int b = 0; b < N1; ++b) {
-            double rv = 0.0, rd = 0.0;
-#pragma unroll
-            for (int c = 0; c < N1; ++c) {
-              rv += T1L[jj * N1 + c] * VL[b * N1 + c];
-              rd += T1L[jj * N1 + c] * DL[b * N1 + c];
-            }
-            v += T0L[i * N1 + b] * rv;
-            dv += T0L[i * N1 + b] * rd;
-          }
-          qv[q] = v;
-          qd[q] = dv;
-        }
-        sig = oct_penalty(p, fmin(hK[d], hL[d]), pform, eps);
-        wscale = kd == 3 ? hL[t0] * hL[t1] / 4.0 : hK[t0] * hK[t1] / 4.0;
-      }
-      __syncthreads();
-      for (int q = tid; q < NF; q += NT) {
-        const int i = q / N1, jj = q % N1;
-        const double wt = swq[i] * swq[jj] * wscale;
-        if (kd == 0) {
-          F1[q] = wt * (-pd[q] + sig * pv[q]);
-          F2[q] = wt * (-pv[q]);
-        } else {
-          F1[q] = wt * (-0.5 * (pd[q] + qd[q]) + sig * (pv[q] - qv[q]));
-          F2[q] = wt * (-0.5 * (pv[q] - qv[q]));
-        }
-      }
-      __syncthreads();
-      // back onto this leaf's face nodes: G[b][c] = sum_ij T0K[i][b] T1K[j][c] F[i][j]
-      for (int j = tid; j < NF; j += NT) {
-        const int b = j / N1, c = j % N1;
-        double g1 = 0.0, g2 = 0.0;
-        for (int i = 0; i < N1; ++i) {
-          double r1 = 0.0, r2 = 0.0;
-#pragma unroll
-          for (int jj = 0; jj < N1; ++jj) {
-            r1 += F1[i * N1 + jj] * T1K[jj * N1 + c];
-            r2 += F2[i * N1 + jj] * T1K[jj * N1 + c];
-          }
-          g1 += T0K[i * N1 + b] * r1;
-          g2 += T0K[i * N1 + b] * r2;
-        }
-        G1[j] = g1;
-        G2[j] = g2;
-      }
-      __syncthreads();
-      for (int i = tid; i < NPE; i += NT) {
-        const int c3[3] = {i % N1, (i / N1) % N1, i / NF};
-        const int a = c3[d], b = c3[t0], c = c3[t1];
-        acc[i] += sLe[r][a] * G1[b * N1 + c] + sdLe[r][a] * (2.0 / hK[d]) * s * G2[b * N1 + c];
-      }
-      __syncthreads();
-    }
+    VK[f][0][j] = v;
+    VK[f][1][j] = dv * (2.0 / hK[d]) * (r ? 1.0 : -1.0);
   }
-  for (int i = tid; i < NPE; i += NT) ob[(long long)e * NPE + i] = acc[i];
+  // 1. the neighbours' traces (on the neighbour's own face nodes) into buffers 0, 1
+  for (int t = tid; t < np * NF; t += NT) {
+    const int k = t / NF, j = t - k * NF;
+    const OctPart& P = part[k];
+    const int L = P.L;
+    double* B = pbuf + (size_t)k * 6 * NF;
+    if (L < 0) continue;
+    const int d = P.f >> 1, r = P.f & 1, rl = 1 - r, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+    const int b = j / N1, c = j % N1;
+    const double* uL = ub + (long long)L * NPE + b * oct_stride<N1>(t0) + c * oct_stride<N1>(t1);
+    const int sd = oct_stride<N1>(d);
+    double v = 0.0, dv = 0.0;
+#pragma unroll
+    for (int a = 0; a < N1; ++a) {
+      const double x = uL[a * sd];
+      v += sLe[rl][a] * x;
+      dv += sdLe[rl][a] * x;
+    }
+    B[j] = v;
+    B[NF + j] = dv * (2.0 / hq[3LL * L + d]) * (r ? 1.0 : -1.0);
+  }
+  __syncthreads();
+  // 2. first contraction along t1: R_X[b][jj] = sum_c T1[jj][c] X[b][c] into buffers 2..5
+  //    (X = this leaf's value, derivative, the neighbour's value, derivative)
+  for (int t = tid; t < np * 4 * NF; t += NT) {
+    const int k = t / (4 * NF), rem = t - k * 4 * NF, x = rem / NF, q = rem - x * NF;
+    const OctPart& P = part[k];
+    double* B = pbuf + (size_t)k * 6 * NF;
+    if (x >= 2 && P.L < 0) continue;
+    const int b = q / N1, jj = q % N1;
+    const double* X = x < 2 ? VK[P.f][x] : B + (x - 2) * NF;
+    const double* T1 = sTab[x < 2 ? P.tk1 : P.tl1];
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < N1; ++c) s += T1[jj * N1 + c] * X[b * N1 + c];
+    B[(2 + x) * NF + q] = s;
+  }
+  __syncthreads();
+  // 3. second contraction along t0 at the Gauss point (i, jj), and the fluxes into buffers 0, 1
+  for (int t = tid; t < np * NF; t += NT) {
+    const int k = t / NF, q = t - k * NF;
+    const OctPart& P = part[k];
+    double* B = pbuf + (size_t)k * 6 * NF;
+    const int i = q / N1, jj = q % N1;
+    const double* T0K = sTab[P.tk0];
+    double pv = 0.0, pd = 0.0;
+#pragma unroll
+    for (int b = 0; b < N1; ++b) {
+      pv += T0K[i * N1 + b] * B[2 * NF + b * N1 + jj];
+      pd += T0K[i * N1 + b] * B[3 * NF + b * N1 + jj];
+    }
+    const double wt = swq[i] * swq[jj] * P.wsc;
+    double F1, F2;
+    if (P.L < 0) {
+      F1 = wt * (-pd + P.sig * pv);
+      F2 = wt * (-pv);
+    } else {
+      const double* T0L = sTab[P.tl0];
+      double qv = 0.0, qd = 0.0;
+#pragma unroll
+      for (int b = 0; b < N1; ++b) {
+        qv += T0L[i * N1 + b] * B[4 * NF + b * N1 + jj];
+        qd += T0L[i * N1 + b] * B[5 * NF + b * N1 + jj];
+      }
+      F1 = wt * (-0.5 * (pd + qd) + P.sig * (pv - qv));
+      F2 = wt * (-0.5 * (pv - qv));
+    }
+    B[q] = F1;
+    B[NF + q] = F2;
+  }
+  __syncthreads();
+  // 4. back along t1: H_Y[i][c] = sum_jj F_Y[i][jj] T1K[jj][c] into buffers 2, 3
+  for (int t = tid; t < np * 2 * NF; t += NT) {
+    const int k = t / (2 * NF), rem = t - k * 2 * NF, y = rem / NF, q = rem - y * NF;
+    const OctPart& P = part[k];
+    double* B = pbuf + (size_t)k * 6 * NF;
+    const int i = q / N1, c = q % N1;
+    const double* T1 = sTab[P.tk1];
+    double s = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < N1; ++jj) s += B[y * NF + i * N1 + jj] * T1[jj * N1 + c];
+    B[(2 + y) * NF + q] = s;
+  }
+  __syncthreads();
+  // 5. back along t0: G_Y[b][c] = sum_i T0K[i][b] H_Y[i][c] into buffers 4, 5
+  for (int t = tid; t < np * 2 * NF; t += NT) {
+    const int k = t / (2 * NF), rem = t - k * 2 * NF, y = rem / NF, q = rem - y * NF;
+    const OctPart& P = part[k];
+    double* B = pbuf + (size_t)k * 6 * NF;
+    const int b = q / N1, c = q % N1;
+    const double* T0 = sTab[P.tk0];
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < N1; ++i) s += T0[i * N1 + b] * B[(2 + y) * NF + i * N1 + c];
+    B[(4 + y) * NF + q] = s;
+  }
+  __syncthreads();
+  // 6. face contributions onto the leaf's nodes: l_a(e) G1 + l_a'(e) (2/h) s G2, parts in order
+  for (int i = tid; i < NPE; i += NT) {
+    const int ix = i % N1, iy = (i / N1) % N1, iz = i / NF;
+    double a_ = acc[i];
+    for (int k = 0; k < np; ++k) {
+      const OctPart& P = part[k];
+      const double* B = pbuf + (size_t)k * 6 * NF;
+      const int d = P.f >> 1, r = P.f & 1;
+      // (a, b, c) = the node's coordinates along d, t0, t1
+      const int a = d == 0 ? ix : (d == 1 ? iy : iz);
+      const int bc = d == 0 ? iy * N1 + iz : (d == 1 ? ix * N1 + iz : ix * N1 + iy);
+      a_ += sLe[r][a] * B[4 * NF + bc] + sdLe[r][a] * (2.0 / hK[d]) * (r ? 1.0 : -1.0) * B[5 * NF + bc];
+    }
+    ob[(long long)e * NPE + i] = a_;
+  }
+}
+
+int octree_max_parts(const int32_t* kind, int E) {
+  int m = 6;
+  for (int e = 0; e < E; ++e) {
+    int n = 0;
+    for (int f = 0; f < 6; ++f) n += kind[6 * (size_t)e + f] == 3 ? 4 : 1;
+    m = std::max(m, n);
+  }
+  return m;
 }
 
 void octree_tables(int n1, OctTables& T) {
@@ -419,15 +485,21 @@ void octree_tables(int n1, OctTables& T) {
 
 cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, const int* kind, const int* nb,
                                 const int* pos, int E, int p, int pform, double eps, const double* u, double* out,
-                                const int* act, int nact, cudaStream_t s) {
+                                const int* act, int nact, int maxparts, cudaStream_t s) {
   if (nact == 0 || E == 0) return cudaSuccess;
+  if (maxparts < 6 || maxparts > 24) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)E, (unsigned)nact);
+  const size_t smem = sizeof(double) * (size_t)maxparts * 6 * n1 * n1;
   count_launch();
   switch (n1) {
-#define DG_OCT_CASE(N)                                                                             \
-  case N:                                                                                          \
-    k_octree_apply<N><<<grid, 256, 0, s>>>(T, hq, kind, nb, pos, E, p, pform, eps, u, out, act); \
-    break;
+#define DG_OCT_CASE(N)                                                                                       \
+  case N: {                                                                                                  \
+    cudaError_t e0 = cudaFuncSetAttribute(k_octree_apply<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                          (int)smem);                                                        \
+    if (e0 != cudaSuccess) return e0;                                                                        \
+    k_octree_apply<N><<<grid, 256, smem, s>>>(T, hq, kind, nb, pos, E, p, pform, eps, u, out, act);          \
+    break;                                                                                                   \
+  }
     DG_OCT_CASE(2)
     DG_OCT_CASE(3)
     DG_OCT_CASE(4)
@@ -549,7 +621,8 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
   if ((rc = ck(cudaMemcpyAsync(dp.p, pos.data(), sizeof(int) * pos.size(), cudaMemcpyHostToDevice, s))) != DG_OK)
     return rc;
   if ((rc = ck(launch_octree_apply(n1, T, dh.as<double>(), dk.as<int>(), dn.as<int>(), dp.as<int>(), E, root->p,
-                                   penalty_form, penalty_eps, u, out, nullptr, (int)B, s))) != DG_OK)
+                                   penalty_form, penalty_eps, u, out, nullptr, (int)B, octree_max_parts(kind.data(), E),
+                                   s))) != DG_OK)
     return rc;
   // the tables and connectivity are call-local: wait before they are freed
   return ck(cudaStreamSynchronize(s));

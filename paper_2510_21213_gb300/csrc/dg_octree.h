@@ -29,10 +29,15 @@ void octree_tables(int n1, OctTables& T);
 bool octree_faces(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_leaves, int32_t* kind, int32_t* nb,
                   int32_t* pos);
 
+// largest number of face parts of a leaf (a face with four smaller neighbours
+// counts four, any other face one): 6..24, the operator's shared-memory size
+int octree_max_parts(const int32_t* kind, int E);
+
 // out[k] = A u[k] for the sources k = act[0..nact) (act null: k = 0..nact),
-// u and out [.][E][n1^3]; hq [E][3] leaf sizes, kind/nb/pos as octree_faces
+// u and out [.][E][n1^3]; hq [E][3] leaf sizes, kind/nb/pos as octree_faces;
+// maxparts = octree_max_parts of the mesh
 cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, const int* kind, const int* nb,
                                 const int* pos, int E, int p, int pform, double eps, const double* u, double* out,
-                                const int* act, int nact, cudaStream_t s);
+                                const int* act, int nact, int maxparts, cudaStream_t s);
 
 }  // namespace dg

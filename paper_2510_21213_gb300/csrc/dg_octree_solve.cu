@@ -61,6 +61,7 @@ struct OctLevel {
 struct dg_oct {
   std::string err;
   int n1 = 0, p = 0, E = 0, pform = 0, max_iter = 0, precond = 1;
+  int maxparts = 6;  // largest face-part count of a leaf (the operator's shared memory)
   double eps = 0.125, rtol = 1e-10;
   long long Nq = 0;
   dg::DevBuf hq, kind, nb, pos;  // leaf sizes [E][3]; connectivity [E][6], [E][6][4], [E][6]
@@ -85,7 +86,7 @@ struct dg_oct {
   double cheb_range = 10.0;      // its interval [lambda_max / range, lambda_max]
   // workspace, sized for `cap` sources
   int cap = 0;
-  dg::DevBuf f, g, b, x, r, z, pv, qv, scal, part, act, flags, pidx, lists, Wacc, kpart, Kdev;
+  dg::DevBuf f, g, gpart, b, x, r, z, pv, qv, scal, part, act, flags, pidx, lists, Wacc, kpart, Kdev;
   std::vector<int> act_host;
   ~dg_oct() {
     if (root) dg_destroy(root);
@@ -174,39 +175,80 @@ __global__ void __launch_bounds__(128) k_oct_bjac(const int* __restrict__ cls, c
   }
 }
 
-// g[k][j] = sum_q W_q f_k(q) / |xb_j - x_q| (Sec. 6.3): one thread per boundary
-// node, the nodes x_q staged through shared memory in a fixed order
-static constexpr int BDT = 128, BDQ = 256;
+// g[k][j] = sum_q W_q f_k(q) / |xb_j - x_q| (Sec. 6.3), direct quadrature. One
+// thread per boundary node and BDK sources per block: 1 / |xb_j - x_q| is
+// evaluated once for all the block's sources, so the cost per source is about
+// one FMA per pair. The nodes x_q and the weighted sources are staged through
+// shared memory; every sum runs over q in a fixed order. The reciprocal square
+// root: the FP32 hardware estimate (rsqrtf) refined by one Newton-Raphson step
+// y <- y (3 - d y^2) / 2 in FP64, which squares its relative error (about
+// 2^-22 before, 1e-13 after) at four FP64 operations instead of an FP64 square
+// root and division.
+static constexpr int BDT = 128, BDQ = 128, BDK = 16;
 __global__ void __launch_bounds__(BDT) k_oct_bdata(const double* __restrict__ xb, long long nbn,
                                                    const double* __restrict__ xq, const double* __restrict__ W,
-                                                   const double* __restrict__ f, long long Nq, double* __restrict__ g) {
-  __shared__ double sx[BDQ], sy[BDQ], sz[BDQ], sw[BDQ];
+                                                   const double* __restrict__ f, long long Nq, int nsrc,
+                                                   double* __restrict__ part) {
+  __shared__ double sx[BDQ], sy[BDQ], sz[BDQ], sw[BDK][BDQ];
   const long long j = (long long)blockIdx.x * BDT + threadIdx.x;
-  const int k = blockIdx.y;
-  const double* fk = f + (long long)k * Nq;
+  const int k0 = blockIdx.z * BDK;
+  const int nk = min(BDK, nsrc - k0);
+  // this block's chunk of the nodes q (chunk count fixed by the mesh, not the batch)
+  const long long per = (Nq + gridDim.y - 1) / gridDim.y;
+  const long long qa = (long long)blockIdx.y * per, qb = min(Nq, qa + per);
   double px = 0.0, py = 0.0, pz = 0.0;
   if (j < nbn) {
     px = xb[3 * j];
     py = xb[3 * j + 1];
     pz = xb[3 * j + 2];
   }
-  double acc = 0.0;
-  for (long long q0 = 0; q0 < Nq; q0 += BDQ) {
-    const int nq = (int)std::min<long long>(BDQ, Nq - q0);
+  double acc[BDK];
+#pragma unroll
+  for (int k = 0; k < BDK; ++k) acc[k] = 0.0;
+  for (long long q0 = qa; q0 < qb; q0 += BDQ) {
+    const int nq = (int)std::min<long long>(BDQ, qb - q0);
     __syncthreads();
     for (int i = threadIdx.x; i < nq; i += BDT) {
       sx[i] = xq[3 * (q0 + i)];
       sy[i] = xq[3 * (q0 + i) + 1];
       sz[i] = xq[3 * (q0 + i) + 2];
-      sw[i] = W[q0 + i] * fk[q0 + i];
+    }
+    for (int t = threadIdx.x; t < BDK * nq; t += BDT) {
+      const int k = t / nq, i = t - k * nq;
+      sw[k][i] = k < nk ? W[q0 + i] * f[(long long)(k0 + k) * Nq + q0 + i] : 0.0;
     }
     __syncthreads();
     for (int i = 0; i < nq; ++i) {
       const double dx = px - sx[i], dy = py - sy[i], dz = pz - sz[i];
-      acc += sw[i] / sqrt(dx * dx + dy * dy + dz * dz);
+      const double d2 = dx * dx + dy * dy + dz * dz;
+      double y = (double)rsqrtf((float)d2);
+      y = y * fma(-0.5, d2 * y * y, 1.5);
+#pragma unroll
+      for (int k = 0; k < BDK; ++k) acc[k] = fma(sw[k][i], y, acc[k]);
     }
   }
-  if (j < nbn) g[(long long)k * nbn + j] = acc;
+  if (j < nbn) {
+    double* pc = part + (long long)blockIdx.y * nsrc * nbn;
+#pragma unroll
+    for (int k = 0; k < BDK; ++k)
+      if (k < nk) pc[(long long)(k0 + k) * nbn + j] = acc[k];
+  }
+}
+
+// g[k][j] = the chunks' partial sums added in chunk order
+__global__ void k_oct_bdata_sum(const double* __restrict__ part, int nch, long long n, double* __restrict__ g) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nch; ++c) s += part[(long long)c * n + t];
+    g[t] = s;
+  }
+}
+
+// node chunks of the boundary-data sum: about four blocks per SM of a GB300 for
+// one source tile, at most 64
+static int oct_bdata_chunks(long long nbn) {
+  const long long bx = (nbn + BDT - 1) / BDT;
+  return (int)std::max(1LL, std::min(64LL, (4LL * 152 + bx - 1) / bx));
 }
 
 // b[k] += Nitsche load of the boundary data on every boundary face of the leaf
@@ -407,7 +449,7 @@ static cudaError_t launch_bjac(const dg_oct* h, const OctLevel& L, const double*
 static cudaError_t oct_apply(const dg_oct* h, const OctLevel& L, const double* u, double* out, const int* act,
                              int nact, cudaStream_t s) {
   return launch_octree_apply(L.n1, L.T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
-                             h->E, L.p, h->pform, h->eps, u, out, act, nact, s);
+                             h->E, L.p, h->pform, h->eps, u, out, act, nact, h->maxparts, s);
 }
 
 static cudaError_t launch_oct_lift(const dg_oct* h, const double* g, double* b, int nsrc, cudaStream_t s) {
@@ -482,6 +524,8 @@ static int oct_ws(dg_oct* h, int cap) {
     }
   }
   DG_CK(h->g.ensure(sizeof(double) * (size_t)cap * h->nbf * h->n1 * h->n1));
+  DG_CK(h->gpart.ensure(sizeof(double) * (size_t)oct_bdata_chunks((long long)h->nbf * h->n1 * h->n1) * cap * h->nbf *
+                        h->n1 * h->n1));
   DG_CK(h->scal.ensure(sizeof(double) * O_NSLOT * (size_t)cap));
   DG_CK(h->part.ensure(sizeof(double) * 304 * (size_t)cap));
   DG_CK(h->act.ensure(sizeof(int) * (size_t)cap));
@@ -506,8 +550,14 @@ static int oct_act(dg_oct* h, const std::vector<int>& a, cudaStream_t s) {
 static int oct_form_rhs(dg_oct* h, const double* f, int nsrc, cudaStream_t s) {
   const long long nbn = (long long)h->nbf * h->n1 * h->n1;
   count_launch();
-  k_oct_bdata<<<dim3((unsigned)((nbn + BDT - 1) / BDT), (unsigned)nsrc), BDT, 0, s>>>(
-      h->xb.as<double>(), nbn, h->xq.as<double>(), h->W.as<double>(), f, h->Nq, h->g.as<double>());
+  const int nch = oct_bdata_chunks(nbn);
+  k_oct_bdata<<<dim3((unsigned)((nbn + BDT - 1) / BDT), (unsigned)nch, (unsigned)((nsrc + BDK - 1) / BDK)), BDT, 0,
+                s>>>(h->xb.as<double>(), nbn, h->xq.as<double>(), h->W.as<double>(), f, h->Nq, nsrc,
+                     h->gpart.as<double>());
+  DG_CK(cudaGetLastError());
+  count_launch();
+  k_oct_bdata_sum<<<(unsigned)std::min<long long>(4096, (nsrc * nbn + 255) / 256), 256, 0, s>>>(
+      h->gpart.as<double>(), nch, nsrc * nbn, h->g.as<double>());
   DG_CK(cudaGetLastError());
   DG_CK(launch_rhs_volume(f, h->W.as<double>(), h->b.as<double>(), h->Nq, nsrc, s));
   DG_CK(launch_oct_lift(h, h->g.as<double>(), h->b.as<double>(), nsrc, s));
@@ -842,6 +892,7 @@ int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
   h->rtol = rtol;
   h->max_iter = max_iter;
   h->precond = precond;
+  h->maxparts = octree_max_parts(kind.data(), E);
   h->Nq = (long long)E * NPE;
   double xi[MAXN1], w[MAXN1];
   gauss_legendre(n1, xi, w);

@@ -205,3 +205,17 @@ def test_vcycle_cuts_iterations_on_a_refined_octree(dgx):
         its[pc] = st[0]["iters"]
     assert its[1] <= 30 and its[1] * 5 <= its[0], its
     assert float((sol[1] - sol[0]).abs().max()) <= 1e-7 * float(sol[0].abs().max())
+
+
+def test_solution_does_not_depend_on_the_batch(dgx):
+    """Every per-source sum runs in a fixed order that does not depend on how
+    many sources share the call (boundary-data tiles of 16 sources, dots,
+    operator blocks): the 18th source of a batch is bit-identical to the same
+    source solved alone."""
+    t = _three_levels(3)
+    s = _solver(dgx, t, rtol=1e-11)
+    f = np.stack([_gauss_source(t, (0.1 * k - 0.5, 0.2, -0.1), 1.0 + 0.1 * k) for k in range(18)])
+    v, _ = s.solve(torch.tensor(f, device="cuda"))
+    v1, _ = s.solve(torch.tensor(f[17:], device="cuda"))
+    s.close()
+    assert torch.equal(v[17], v1[0])
