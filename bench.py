@@ -622,9 +622,10 @@ def run_octree(args):
     dg_octree_exchange_build): the chain10 box [-12, 12]^3 with a 4^3 root grid
     at p = 6, refined by the density indicator of the chain system's orbitals
     (delta 1e-5, up to level 2), the chain's 10 orbitals evaluated at the
-    octree's nodes and orthonormalised with its weights; FP64, rtol 1e-8. One
-    step = one whole build (Hartree + 55 pairs), timed with CUDA events. Also
-    the operator alone on 8 fields (one kernel, CUDA events)."""
+    octree's nodes and orthonormalised with its weights; rtol 1e-8. One step =
+    one whole build (Hartree + 55 pairs), timed with CUDA events; value = the
+    mixed form (FP32 inner PCG in FP64 refinement), the FP64 form beside it.
+    Also the FP64 operator alone on 8 fields (one kernel, CUDA events)."""
     import torch
 
     from paper_2510_21213_gb300 import build, dgx, inputs
@@ -637,50 +638,59 @@ def run_octree(args):
         return np.sum((spec.coeffs @ inputs.eval_primitives(spec, P)) ** 2, axis=0)
 
     leaves = dgx.dg_octree_refine(lo, hi, n, p, rho, 1e-5, 2)
-    s = dgx.OctreeSolver(lo, hi, n, p, leaves, rtol=1e-8)
-    xyz, w = s.node_coords()
-    psi = torch.tensor(inputs.orbitals(spec, xyz.cpu().numpy(), w.cpu().numpy()), device="cuda")
-    N = psi.shape[0]
-    P = N * (N + 1) // 2
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(max(args.warmup, 3)):
-        K, EH, EX, st = s.exchange_build(psi)
-    torch.cuda.synchronize()
-    ms = []
-    for _ in range(args.steps):
-        ev0.record()
-        K, EH, EX, st = s.exchange_build(psi)
-        ev1.record()
+    res = {}
+    for prec in (dgx.DG_PREC_MIXED, dgx.DG_PREC_FP64):
+        s = dgx.OctreeSolver(lo, hi, n, p, leaves, rtol=1e-8, precision=prec)
+        xyz, w = s.node_coords()
+        psi = torch.tensor(inputs.orbitals(spec, xyz.cpu().numpy(), w.cpu().numpy()), device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            K, EH, EX, st = s.exchange_build(psi)
         torch.cuda.synchronize()
-        ms.append(ev0.elapsed_time(ev1))
-    t = sum(ms) / len(ms)
-    # the operator alone: 8 fields, one launch
-    B = 8
-    u = torch.randn(B, s.Nq, dtype=torch.float64, device="cuda")
-    out = torch.empty_like(u)
-    for _ in range(3):
-        s.apply(u, out)
-    torch.cuda.synchronize()
-    ev0.record()
-    for _ in range(20):
-        s.apply(u, out)
-    ev1.record()
-    torch.cuda.synchronize()
-    op_ms = ev0.elapsed_time(ev1) / 20
-    s.close()
+        ms = []
+        for _ in range(args.steps):
+            ev0.record()
+            K, EH, EX, st = s.exchange_build(psi)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        res[prec] = {"ms": sum(ms) / len(ms), "K": K, "E_H": EH, "E_X": EX,
+                     "iters": float(np.mean([x["iters"] for x in st])),
+                     "rounds": float(np.mean([x["outer_refinements"] for x in st]))}
+        if prec == dgx.DG_PREC_FP64:
+            B = 8
+            u = torch.randn(B, s.Nq, dtype=torch.float64, device="cuda")
+            out = torch.empty_like(u)
+            for _ in range(3):
+                s.apply(u, out)
+            torch.cuda.synchronize()
+            ev0.record()
+            for _ in range(20):
+                s.apply(u, out)
+            ev1.record()
+            torch.cuda.synchronize()
+            op_ms = ev0.elapsed_time(ev1) / 20
+            Nq = s.Nq
+        N = psi.shape[0]
+        s.close()
+    P = N * (N + 1) // 2
+    mx, fp = res[dgx.DG_PREC_MIXED], res[dgx.DG_PREC_FP64]
     levels = np.bincount(leaves[:, 0]).tolist()
-    print(json.dumps({"metric": "octree exchange build, pair solves/s", "value": (P + 1) / (t / 1e3),
-                      "unit": "pair_solves/s", "ms_per_step": t, "steps": args.steps, "warmup": max(args.warmup, 3),
-                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+    print(json.dumps({"metric": "octree exchange build, pair solves/s", "value": (P + 1) / (mx["ms"] / 1e3),
+                      "unit": "pair_solves/s", "ms_per_step": mx["ms"], "steps": args.steps,
+                      "warmup": max(args.warmup, 3), "higher_is_better": True, "dtype": "f32+f64",
+                      "data": "synthetic",
                       "config": {"workload": "octree: chain10 box, 4^3 roots, p=6, density-refined to level 2",
-                                 "leaves": int(leaves.shape[0]), "leaves_per_level": levels, "Nq": int(s.Nq),
-                                 "orbitals": N, "sources": P + 1, "rtol": 1e-8,
-                                 "mean_iters": float(np.mean([x["iters"] for x in st])),
-                                 "E_H": EH, "E_X": EX,
+                                 "leaves": int(leaves.shape[0]), "leaves_per_level": levels, "Nq": int(Nq),
+                                 "orbitals": N, "sources": P + 1, "rtol": 1e-8, "precision": "mixed",
+                                 "mean_inner_iters": mx["iters"], "mean_rounds": mx["rounds"],
+                                 "E_H": mx["E_H"], "E_X": mx["E_X"],
                                  "timing": "CUDA events around each whole build (host-synchronised PCG)"},
-                      "operator": {"fields": B, "ms_per_application": op_ms,
-                                   "dof_per_s": B * s.Nq / (op_ms / 1e3),
-                                   "timing": "CUDA events over 20 launches of the operator kernel"}}), flush=True)
+                      "fp64": {"value": (P + 1) / (fp["ms"] / 1e3), "ms_per_step": fp["ms"], "mean_iters": fp["iters"],
+                               "K_rel_diff_vs_mixed": float(np.abs(fp["K"] - mx["K"]).max() / np.abs(fp["K"]).max())},
+                      "operator": {"fields": 8, "ms_per_application": op_ms, "dof_per_s": 8 * Nq / (op_ms / 1e3),
+                                   "dtype": "f64", "timing": "CUDA events over 20 launches of the operator kernel"}}),
+          flush=True)
 
 
 def main():

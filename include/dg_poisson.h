@@ -466,7 +466,12 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * down to 1, then restricts to the uniform root grid at degree 1 (every leaf
  * lies in one root cell, so the root space is nested) and applies that grid's
  * own multigrid V-cycle (a uniform solver handle, h-coarsening and a dense
- * coarsest solve). Writes the handle to *out (NULL on
+ * coarsest solve). precision: DG_PREC_FP64 (PCG, V-cycle and operator in
+ * FP64) or DG_PREC_MIXED (the PCG and its V-cycle in FP32 inside FP64
+ * iterative refinement: each round solves A e = r for the FP64 residual r to a
+ * reduction of 1e-4, adds e in FP64 and recomputes r in FP64, until r meets
+ * rtol; the boundary data, right-hand side, residuals and results stay FP64;
+ * stats report the inner iterations and the rounds). Writes the handle to *out (NULL on
  * failure). Fields are [.][Nq] FP64 with Nq = n_leaves (p+1)^3, element-blocked
  * in leaf order, nodes x-fastest. DG_ERR_INVALID_ARG for a bad mesh, leaf set
  * or argument; DG_ERR_UNSUPPORTED beyond 2^31 nodes; DG_ERR_NO_MEMORY,
@@ -474,7 +479,8 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * handle must not overlap; each synchronises its stream before it returns. */
 typedef struct dg_oct* dg_oct_handle;
 int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves_host, int32_t n_leaves, int32_t penalty_form,
-                    double penalty_eps, double rtol, int32_t max_iter, int32_t precond, dg_oct_handle* out);
+                    double penalty_eps, double rtol, int32_t max_iter, int32_t precond, int32_t precision,
+                    dg_oct_handle* out);
 void dg_octree_destroy(dg_oct_handle h);
 /* Text of the last CUDA failure on the handle ("" if none). */
 const char* dg_octree_error_detail(dg_oct_handle h);

@@ -224,38 +224,41 @@ struct OctPart {
   double sig, wsc;   // penalty and Jacobian of the part's face
 };
 
-template <int N1>
+// V: the field type (double, or float in the FP32 inner solve); tables and
+// arithmetic in V too, the leaf sizes and penalties in FP64 until the final cast
+template <typename V, int N1>
 __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const double* __restrict__ hq,
                                                       const int* __restrict__ kind, const int* __restrict__ nbr,
                                                       const int* __restrict__ pos, int E, int p, int pform,
-                                                      double eps, const double* __restrict__ u,
-                                                      double* __restrict__ out, const int* __restrict__ act) {
+                                                      double eps, const V* __restrict__ u, V* __restrict__ out,
+                                                      const int* __restrict__ act) {
   constexpr int NPE = N1 * N1 * N1, NF = N1 * N1;
-  extern __shared__ double pbuf[];  // [nparts][6][NF]
-  __shared__ double sTab[3][NF], sS[NF], sLe[2][N1], sdLe[2][N1], sw[N1], swq[N1];
-  __shared__ double uK[NPE], acc[NPE], VK[6][2][NF];
+  extern __shared__ __align__(16) unsigned char pbuf_raw[];
+  V* pbuf = (V*)pbuf_raw;  // [nparts][6][NF]
+  __shared__ V sTab[3][NF], sS[NF], sLe[2][N1], sdLe[2][N1], sw[N1], swq[N1];
+  __shared__ V uK[NPE], acc[NPE], VK[6][2][NF];
   __shared__ OctPart part[24];
   __shared__ int npart;
   __shared__ double hK[3];
   const int e = blockIdx.x;
   const int tid = threadIdx.x, NT = blockDim.x;
   const long long src = act ? act[blockIdx.y] : blockIdx.y;
-  const double* ub = u + src * E * NPE;
-  double* ob = out + src * E * NPE;
+  const V* ub = u + src * E * NPE;
+  V* ob = out + src * E * NPE;
   for (int i = tid; i < NF; i += NT) {
     const int r = i / N1, c = i % N1;
-    sTab[0][i] = T.Lq[r * N1 + c];
-    sTab[1][i] = T.Lh[0][r * N1 + c];
-    sTab[2][i] = T.Lh[1][r * N1 + c];
-    sS[i] = T.S[r * N1 + c];
+    sTab[0][i] = (V)T.Lq[r * N1 + c];
+    sTab[1][i] = (V)T.Lh[0][r * N1 + c];
+    sTab[2][i] = (V)T.Lh[1][r * N1 + c];
+    sS[i] = (V)T.S[r * N1 + c];
   }
   for (int i = tid; i < N1; i += NT) {
-    sLe[0][i] = T.Le[0][i];
-    sLe[1][i] = T.Le[1][i];
-    sdLe[0][i] = T.dLe[0][i];
-    sdLe[1][i] = T.dLe[1][i];
-    sw[i] = T.w[i];
-    swq[i] = T.wq[i];
+    sLe[0][i] = (V)T.Le[0][i];
+    sLe[1][i] = (V)T.Le[1][i];
+    sdLe[0][i] = (V)T.dLe[0][i];
+    sdLe[1][i] = (V)T.dLe[1][i];
+    sw[i] = (V)T.w[i];
+    swq[i] = (V)T.wq[i];
   }
   for (int i = tid; i < NPE; i += NT) uK[i] = ub[(long long)e * NPE + i];
   if (tid < 3) hK[tid] = hq[3LL * e + tid];
@@ -294,16 +297,16 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   // 1. volume: sum_d (2/h_d)(h_t0 h_t1 / 4) (S_d (x) W (x) W) u
   for (int i = tid; i < NPE; i += NT) {
     const int ix = i % N1, iy = (i / N1) % N1, iz = i / NF;
-    double vx = 0.0, vy = 0.0, vz = 0.0;
+    V vx = 0, vy = 0, vz = 0;
 #pragma unroll
     for (int a = 0; a < N1; ++a) {
       vx += sS[ix * N1 + a] * uK[a + N1 * iy + NF * iz];
       vy += sS[iy * N1 + a] * uK[ix + N1 * a + NF * iz];
       vz += sS[iz * N1 + a] * uK[ix + N1 * iy + NF * a];
     }
-    acc[i] = vx * sw[iy] * sw[iz] * (2.0 / hK[0]) * (hK[1] * hK[2] / 4.0) +
-             vy * sw[ix] * sw[iz] * (2.0 / hK[1]) * (hK[0] * hK[2] / 4.0) +
-             vz * sw[ix] * sw[iy] * (2.0 / hK[2]) * (hK[0] * hK[1] / 4.0);
+    acc[i] = vx * sw[iy] * sw[iz] * (V)((2.0 / hK[0]) * (hK[1] * hK[2] / 4.0)) +
+             vy * sw[ix] * sw[iz] * (V)((2.0 / hK[1]) * (hK[0] * hK[2] / 4.0)) +
+             vz * sw[ix] * sw[iy] * (V)((2.0 / hK[2]) * (hK[0] * hK[1] / 4.0));
   }
   // 1. this leaf's traces and outward normal derivatives on its face nodes [t0][t1]
   for (int t = tid; t < 6 * NF; t += NT) {
@@ -311,36 +314,36 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
     const int d = f >> 1, r = f & 1, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
     const int b = j / N1, c = j % N1;
     const int sd = oct_stride<N1>(d), base = b * oct_stride<N1>(t0) + c * oct_stride<N1>(t1);
-    double v = 0.0, dv = 0.0;
+    V v = 0, dv = 0;
 #pragma unroll
     for (int a = 0; a < N1; ++a) {
-      const double x = uK[a * sd + base];
+      const V x = uK[a * sd + base];
       v += sLe[r][a] * x;
       dv += sdLe[r][a] * x;
     }
     VK[f][0][j] = v;
-    VK[f][1][j] = dv * (2.0 / hK[d]) * (r ? 1.0 : -1.0);
+    VK[f][1][j] = dv * (V)((2.0 / hK[d]) * (r ? 1.0 : -1.0));
   }
   // 1. the neighbours' traces (on the neighbour's own face nodes) into buffers 0, 1
   for (int t = tid; t < np * NF; t += NT) {
     const int k = t / NF, j = t - k * NF;
     const OctPart& P = part[k];
     const int L = P.L;
-    double* B = pbuf + (size_t)k * 6 * NF;
+    V* B = pbuf + (size_t)k * 6 * NF;
     if (L < 0) continue;
     const int d = P.f >> 1, r = P.f & 1, rl = 1 - r, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
     const int b = j / N1, c = j % N1;
-    const double* uL = ub + (long long)L * NPE + b * oct_stride<N1>(t0) + c * oct_stride<N1>(t1);
+    const V* uL = ub + (long long)L * NPE + b * oct_stride<N1>(t0) + c * oct_stride<N1>(t1);
     const int sd = oct_stride<N1>(d);
-    double v = 0.0, dv = 0.0;
+    V v = 0, dv = 0;
 #pragma unroll
     for (int a = 0; a < N1; ++a) {
-      const double x = uL[a * sd];
+      const V x = uL[a * sd];
       v += sLe[rl][a] * x;
       dv += sdLe[rl][a] * x;
     }
     B[j] = v;
-    B[NF + j] = dv * (2.0 / hq[3LL * L + d]) * (r ? 1.0 : -1.0);
+    B[NF + j] = dv * (V)((2.0 / hq[3LL * L + d]) * (r ? 1.0 : -1.0));
   }
   __syncthreads();
   // 2. first contraction along t1: R_X[b][jj] = sum_c T1[jj][c] X[b][c] into buffers 2..5
@@ -348,12 +351,12 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   for (int t = tid; t < np * 4 * NF; t += NT) {
     const int k = t / (4 * NF), rem = t - k * 4 * NF, x = rem / NF, q = rem - x * NF;
     const OctPart& P = part[k];
-    double* B = pbuf + (size_t)k * 6 * NF;
+    V* B = pbuf + (size_t)k * 6 * NF;
     if (x >= 2 && P.L < 0) continue;
     const int b = q / N1, jj = q % N1;
-    const double* X = x < 2 ? VK[P.f][x] : B + (x - 2) * NF;
-    const double* T1 = sTab[x < 2 ? P.tk1 : P.tl1];
-    double s = 0.0;
+    const V* X = x < 2 ? VK[P.f][x] : B + (x - 2) * NF;
+    const V* T1 = sTab[x < 2 ? P.tk1 : P.tl1];
+    V s = 0;
 #pragma unroll
     for (int c = 0; c < N1; ++c) s += T1[jj * N1 + c] * X[b * N1 + c];
     B[(2 + x) * NF + q] = s;
@@ -363,30 +366,31 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   for (int t = tid; t < np * NF; t += NT) {
     const int k = t / NF, q = t - k * NF;
     const OctPart& P = part[k];
-    double* B = pbuf + (size_t)k * 6 * NF;
+    V* B = pbuf + (size_t)k * 6 * NF;
     const int i = q / N1, jj = q % N1;
-    const double* T0K = sTab[P.tk0];
-    double pv = 0.0, pd = 0.0;
+    const V* T0K = sTab[P.tk0];
+    V pv = 0, pd = 0;
 #pragma unroll
     for (int b = 0; b < N1; ++b) {
       pv += T0K[i * N1 + b] * B[2 * NF + b * N1 + jj];
       pd += T0K[i * N1 + b] * B[3 * NF + b * N1 + jj];
     }
-    const double wt = swq[i] * swq[jj] * P.wsc;
-    double F1, F2;
+    const V wt = swq[i] * swq[jj] * (V)P.wsc;
+    const V sig = (V)P.sig;
+    V F1, F2;
     if (P.L < 0) {
-      F1 = wt * (-pd + P.sig * pv);
+      F1 = wt * (-pd + sig * pv);
       F2 = wt * (-pv);
     } else {
-      const double* T0L = sTab[P.tl0];
-      double qv = 0.0, qd = 0.0;
+      const V* T0L = sTab[P.tl0];
+      V qv = 0, qd = 0;
 #pragma unroll
       for (int b = 0; b < N1; ++b) {
         qv += T0L[i * N1 + b] * B[4 * NF + b * N1 + jj];
         qd += T0L[i * N1 + b] * B[5 * NF + b * N1 + jj];
       }
-      F1 = wt * (-0.5 * (pd + qd) + P.sig * (pv - qv));
-      F2 = wt * (-0.5 * (pv - qv));
+      F1 = wt * ((V)-0.5 * (pd + qd) + sig * (pv - qv));
+      F2 = wt * ((V)-0.5 * (pv - qv));
     }
     B[q] = F1;
     B[NF + q] = F2;
@@ -396,10 +400,10 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   for (int t = tid; t < np * 2 * NF; t += NT) {
     const int k = t / (2 * NF), rem = t - k * 2 * NF, y = rem / NF, q = rem - y * NF;
     const OctPart& P = part[k];
-    double* B = pbuf + (size_t)k * 6 * NF;
+    V* B = pbuf + (size_t)k * 6 * NF;
     const int i = q / N1, c = q % N1;
-    const double* T1 = sTab[P.tk1];
-    double s = 0.0;
+    const V* T1 = sTab[P.tk1];
+    V s = 0;
 #pragma unroll
     for (int jj = 0; jj < N1; ++jj) s += B[y * NF + i * N1 + jj] * T1[jj * N1 + c];
     B[(2 + y) * NF + q] = s;
@@ -409,10 +413,10 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   for (int t = tid; t < np * 2 * NF; t += NT) {
     const int k = t / (2 * NF), rem = t - k * 2 * NF, y = rem / NF, q = rem - y * NF;
     const OctPart& P = part[k];
-    double* B = pbuf + (size_t)k * 6 * NF;
+    V* B = pbuf + (size_t)k * 6 * NF;
     const int b = q / N1, c = q % N1;
-    const double* T0 = sTab[P.tk0];
-    double s = 0.0;
+    const V* T0 = sTab[P.tk0];
+    V s = 0;
 #pragma unroll
     for (int i = 0; i < N1; ++i) s += T0[i * N1 + b] * B[(2 + y) * NF + i * N1 + c];
     B[(4 + y) * NF + q] = s;
@@ -421,15 +425,15 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   // 6. face contributions onto the leaf's nodes: l_a(e) G1 + l_a'(e) (2/h) s G2, parts in order
   for (int i = tid; i < NPE; i += NT) {
     const int ix = i % N1, iy = (i / N1) % N1, iz = i / NF;
-    double a_ = acc[i];
+    V a_ = acc[i];
     for (int k = 0; k < np; ++k) {
       const OctPart& P = part[k];
-      const double* B = pbuf + (size_t)k * 6 * NF;
+      const V* B = pbuf + (size_t)k * 6 * NF;
       const int d = P.f >> 1, r = P.f & 1;
       // (a, b, c) = the node's coordinates along d, t0, t1
       const int a = d == 0 ? ix : (d == 1 ? iy : iz);
       const int bc = d == 0 ? iy * N1 + iz : (d == 1 ? ix * N1 + iz : ix * N1 + iy);
-      a_ += sLe[r][a] * B[4 * NF + bc] + sdLe[r][a] * (2.0 / hK[d]) * (r ? 1.0 : -1.0) * B[5 * NF + bc];
+      a_ += sLe[r][a] * B[4 * NF + bc] + sdLe[r][a] * (V)((2.0 / hK[d]) * (r ? 1.0 : -1.0)) * B[5 * NF + bc];
     }
     ob[(long long)e * NPE + i] = a_;
   }
@@ -483,21 +487,22 @@ void octree_tables(int n1, OctTables& T) {
     }
 }
 
+template <typename V>
 cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, const int* kind, const int* nb,
-                                const int* pos, int E, int p, int pform, double eps, const double* u, double* out,
+                                const int* pos, int E, int p, int pform, double eps, const V* u, V* out,
                                 const int* act, int nact, int maxparts, cudaStream_t s) {
   if (nact == 0 || E == 0) return cudaSuccess;
   if (maxparts < 6 || maxparts > 24) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)E, (unsigned)nact);
-  const size_t smem = sizeof(double) * (size_t)maxparts * 6 * n1 * n1;
+  const size_t smem = sizeof(V) * (size_t)maxparts * 6 * n1 * n1;
   count_launch();
   switch (n1) {
 #define DG_OCT_CASE(N)                                                                                       \
   case N: {                                                                                                  \
-    cudaError_t e0 = cudaFuncSetAttribute(k_octree_apply<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+    cudaError_t e0 = cudaFuncSetAttribute(k_octree_apply<V, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                           (int)smem);                                                        \
     if (e0 != cudaSuccess) return e0;                                                                        \
-    k_octree_apply<N><<<grid, 256, smem, s>>>(T, hq, kind, nb, pos, E, p, pform, eps, u, out, act);          \
+    k_octree_apply<V, N><<<grid, 256, smem, s>>>(T, hq, kind, nb, pos, E, p, pform, eps, u, out, act);          \
     break;                                                                                                   \
   }
     DG_OCT_CASE(2)
@@ -514,6 +519,12 @@ cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, co
   }
   return cudaGetLastError();
 }
+template cudaError_t launch_octree_apply<double>(int, const OctTables&, const double*, const int*, const int*,
+                                                 const int*, int, int, int, double, const double*, double*, const int*,
+                                                 int, int, cudaStream_t);
+template cudaError_t launch_octree_apply<float>(int, const OctTables&, const double*, const int*, const int*,
+                                                const int*, int, int, int, double, const float*, float*, const int*,
+                                                int, int, cudaStream_t);
 }  // namespace dg
 
 using namespace dg;
@@ -620,7 +631,7 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
     return rc;
   if ((rc = ck(cudaMemcpyAsync(dp.p, pos.data(), sizeof(int) * pos.size(), cudaMemcpyHostToDevice, s))) != DG_OK)
     return rc;
-  if ((rc = ck(launch_octree_apply(n1, T, dh.as<double>(), dk.as<int>(), dn.as<int>(), dp.as<int>(), E, root->p,
+  if ((rc = ck(launch_octree_apply<double>(n1, T, dh.as<double>(), dk.as<int>(), dn.as<int>(), dp.as<int>(), E, root->p,
                                    penalty_form, penalty_eps, u, out, nullptr, (int)B, octree_max_parts(kind.data(), E),
                                    s))) != DG_OK)
     return rc;

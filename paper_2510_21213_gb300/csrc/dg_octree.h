@@ -35,9 +35,11 @@ int octree_max_parts(const int32_t* kind, int E);
 
 // out[k] = A u[k] for the sources k = act[0..nact) (act null: k = 0..nact),
 // u and out [.][E][n1^3]; hq [E][3] leaf sizes, kind/nb/pos as octree_faces;
-// maxparts = octree_max_parts of the mesh
+// maxparts = octree_max_parts of the mesh; V = double or float (the fields and
+// the arithmetic)
+template <typename V>
 cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, const int* kind, const int* nb,
-                                const int* pos, int E, int p, int pform, double eps, const double* u, double* out,
+                                const int* pos, int E, int p, int pform, double eps, const V* u, V* out,
                                 const int* act, int nact, int maxparts, cudaStream_t s);
 
 }  // namespace dg

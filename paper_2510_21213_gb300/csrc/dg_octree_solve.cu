@@ -61,6 +61,8 @@ struct OctLevel {
 struct dg_oct {
   std::string err;
   int n1 = 0, p = 0, E = 0, pform = 0, max_iter = 0, precond = 1;
+  int mixed = 0;                 // 1: FP32 inner PCG (FP32 V-cycle) inside FP64 refinement
+  double inner_rtol = 1e-4;      // relative reduction of each inner solve
   int maxparts = 6;  // largest face-part count of a leaf (the operator's shared memory)
   double eps = 0.125, rtol = 1e-10;
   long long Nq = 0;
@@ -87,6 +89,7 @@ struct dg_oct {
   // workspace, sized for `cap` sources
   int cap = 0;
   dg::DevBuf f, g, gpart, b, x, r, z, pv, qv, scal, part, act, flags, pidx, lists, Wacc, kpart, Kdev;
+  dg::DevBuf b32, x32, r32, z32, p32, q32;  // FP32 inner solve (mixed)
   std::vector<int> act_host;
   ~dg_oct() {
     if (root) dg_destroy(root);
@@ -96,7 +99,8 @@ struct dg_oct {
 namespace dg {
 
 static constexpr int OT = 256;
-enum { O_BB = 0, O_RR, O_RZ, O_RZN, O_PQ, O_AL, O_BE, O_SE, O_NSLOT };
+// per-source scalar slots; I_*: those of the FP32 inner solve
+enum { O_BB = 0, O_RR, O_RZ, O_RZN, O_PQ, O_AL, O_BE, O_SE, I_BB, I_RR, I_RZ, I_RZN, I_PQ, I_AL, I_BE, O_NSLOT };
 
 static inline dim3 ogrid(long long n, int nsrc) {
   long long gx = (n + OT * 4 - 1) / (OT * 4);
@@ -106,28 +110,28 @@ static inline dim3 ogrid(long long n, int nsrc) {
 
 // z = P r on every leaf: the exact inverse of the leaf's diagonal block by
 // fast diagonalisation (one block per leaf and source)
-template <int N1>
+template <typename V, int N1>
 __global__ void __launch_bounds__(128) k_oct_bjac(const int* __restrict__ cls, const double* __restrict__ S,
-                                                  const double* __restrict__ lam, const double* __restrict__ r,
-                                                  double* __restrict__ z, long long Nq, const int* __restrict__ act) {
+                                                  const double* __restrict__ lam, const V* __restrict__ r,
+                                                  V* __restrict__ z, long long Nq, const int* __restrict__ act) {
   constexpr int NPE = N1 * N1 * N1, NF = N1 * N1;
-  __shared__ double sS[3][NF], sl[3][N1], u[NPE], t[NPE];
+  __shared__ V sS[3][NF], sl[3][N1], u[NPE], t[NPE];
   const int e = blockIdx.x;
   const long long off = (long long)act[blockIdx.y] * Nq + (long long)e * NPE;
   for (int i = threadIdx.x; i < 3 * NF; i += blockDim.x) {
     const int d = i / NF;
-    sS[d][i % NF] = S[(long long)cls[3 * e + d] * NF + i % NF];
+    sS[d][i % NF] = (V)S[(long long)cls[3 * e + d] * NF + i % NF];
   }
   for (int i = threadIdx.x; i < 3 * N1; i += blockDim.x) {
     const int d = i / N1;
-    sl[d][i % N1] = lam[(long long)cls[3 * e + d] * N1 + i % N1];
+    sl[d][i % N1] = (V)lam[(long long)cls[3 * e + d] * N1 + i % N1];
   }
   for (int i = threadIdx.x; i < NPE; i += blockDim.x) u[i] = r[off + i];
   __syncthreads();
   // forward: t = (S_x (x) S_y (x) S_z)^T u, one axis at a time (mode index replaces node index)
   for (int i = threadIdx.x; i < NPE; i += blockDim.x) {
     const int m = i % N1, rest = i - m;
-    double acc = 0.0;
+    V acc = 0;
 #pragma unroll
     for (int a = 0; a < N1; ++a) acc += sS[0][a * N1 + m] * u[rest + a];
     t[i] = acc;
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(128) k_oct_bjac(const int* __restrict__ cls, c
   __syncthreads();
   for (int i = threadIdx.x; i < NPE; i += blockDim.x) {
     const int m = (i / N1) % N1, rest = i - m * N1;
-    double acc = 0.0;
+    V acc = 0;
 #pragma unroll
     for (int b = 0; b < N1; ++b) acc += sS[1][b * N1 + m] * t[rest + b * N1];
     u[i] = acc;
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(128) k_oct_bjac(const int* __restrict__ cls, c
   __syncthreads();
   for (int i = threadIdx.x; i < NPE; i += blockDim.x) {
     const int m = i / NF, rest = i - m * NF;
-    double acc = 0.0;
+    V acc = 0;
 #pragma unroll
     for (int c = 0; c < N1; ++c) acc += sS[2][c * N1 + m] * u[rest + c * NF];
     t[i] = acc / (sl[0][i % N1] + sl[1][(i / N1) % N1] + sl[2][m]);
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(128) k_oct_bjac(const int* __restrict__ cls, c
   // back: u = (S_x (x) S_y (x) S_z) t
   for (int i = threadIdx.x; i < NPE; i += blockDim.x) {
     const int c = i / NF, rest = i - c * NF;
-    double acc = 0.0;
+    V acc = 0;
 #pragma unroll
     for (int m = 0; m < N1; ++m) acc += sS[2][c * N1 + m] * t[rest + m * NF];
     u[i] = acc;
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(128) k_oct_bjac(const int* __restrict__ cls, c
   __syncthreads();
   for (int i = threadIdx.x; i < NPE; i += blockDim.x) {
     const int b = (i / N1) % N1, rest = i - b * N1;
-    double acc = 0.0;
+    V acc = 0;
 #pragma unroll
     for (int m = 0; m < N1; ++m) acc += sS[1][b * N1 + m] * u[rest + m * N1];
     t[i] = acc;
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(128) k_oct_bjac(const int* __restrict__ cls, c
   __syncthreads();
   for (int i = threadIdx.x; i < NPE; i += blockDim.x) {
     const int a = i % N1, rest = i - a;
-    double acc = 0.0;
+    V acc = 0;
 #pragma unroll
     for (int m = 0; m < N1; ++m) acc += sS[0][a * N1 + m] * t[rest + m];
     z[off + i] = acc;
@@ -296,13 +300,15 @@ __global__ void k_oct_copy_slot(const double* src, double* dst, const int* act, 
 }
 
 // r = b - q (the true residual once q = A x), and p = z, on the active sources
-__global__ void k_oct_sub(double* __restrict__ r, const double* __restrict__ b, const double* __restrict__ q,
-                          long long Nq, const int* __restrict__ act) {
+template <typename V>
+__global__ void k_oct_sub(V* __restrict__ r, const V* __restrict__ b, const V* __restrict__ q, long long Nq,
+                          const int* __restrict__ act) {
   const long long off = (long long)act[blockIdx.y] * Nq;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Nq; i += (long long)gridDim.x * blockDim.x)
     r[off + i] = b[off + i] - q[off + i];
 }
-__global__ void k_oct_copy(double* __restrict__ dst, const double* __restrict__ src, long long Nq,
+template <typename V>
+__global__ void k_oct_copy(V* __restrict__ dst, const V* __restrict__ src, long long Nq,
                            const int* __restrict__ act) {
   const long long off = (long long)act[blockIdx.y] * Nq;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Nq; i += (long long)gridDim.x * blockDim.x)
@@ -313,69 +319,69 @@ __global__ void k_oct_copy(double* __restrict__ dst, const double* __restrict__ 
 // p-transfers between octree levels, one leaf and source per block, sum-factorised
 // with I [n1f][n1c] (the coarse basis at the fine nodes):
 //   prolongation  xf += (I (x) I (x) I) xc,  restriction  rc = (I (x) I (x) I)^T rf
+template <typename V>
 __global__ void __launch_bounds__(128) k_oct_prolong_p(const double* __restrict__ I, int n1f, int n1c,
-                                                       const double* __restrict__ xc, double* __restrict__ xf,
+                                                       const V* __restrict__ xc, V* __restrict__ xf,
                                                        long long Nqc, long long Nqf, const int* __restrict__ act) {
-  __shared__ double sI[MAXN1 * MAXN1], c0[MAXN1 * MAXN1 * MAXN1], t1[MAXN1 * MAXN1 * MAXN1],
-      t2[MAXN1 * MAXN1 * MAXN1];
+  __shared__ V sI[MAXN1 * MAXN1], c0[MAXN1 * MAXN1 * MAXN1], t1[MAXN1 * MAXN1 * MAXN1], t2[MAXN1 * MAXN1 * MAXN1];
   const int e = blockIdx.x;
   const long long k = act[blockIdx.y];
   const int npc = n1c * n1c * n1c, npf = n1f * n1f * n1f;
-  for (int i = threadIdx.x; i < n1f * n1c; i += blockDim.x) sI[i] = I[i];
+  for (int i = threadIdx.x; i < n1f * n1c; i += blockDim.x) sI[i] = (V)I[i];
   for (int i = threadIdx.x; i < npc; i += blockDim.x) c0[i] = xc[k * Nqc + (long long)e * npc + i];
   __syncthreads();
   for (int t = threadIdx.x; t < n1c * n1c * n1f; t += blockDim.x) {  // t1[c'][b'][a]
     const int a = t % n1f, r = t / n1f;
-    double acc = 0.0;
+    V acc = 0;
     for (int j = 0; j < n1c; ++j) acc += sI[a * n1c + j] * c0[r * n1c + j];
     t1[t] = acc;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < n1c * n1f * n1f; t += blockDim.x) {  // t2[c'][b][a]
     const int a = t % n1f, b = (t / n1f) % n1f, c = t / (n1f * n1f);
-    double acc = 0.0;
+    V acc = 0;
     for (int j = 0; j < n1c; ++j) acc += sI[b * n1c + j] * t1[(c * n1c + j) * n1f + a];
     t2[t] = acc;
   }
   __syncthreads();
-  double* dst = xf + k * Nqf + (long long)e * npf;
+  V* dst = xf + k * Nqf + (long long)e * npf;
   for (int t = threadIdx.x; t < npf; t += blockDim.x) {
     const int ab = t % (n1f * n1f), c = t / (n1f * n1f);
-    double acc = 0.0;
+    V acc = 0;
     for (int j = 0; j < n1c; ++j) acc += sI[c * n1c + j] * t2[j * n1f * n1f + ab];
     dst[t] += acc;
   }
 }
 
+template <typename V>
 __global__ void __launch_bounds__(128) k_oct_restrict_p(const double* __restrict__ I, int n1f, int n1c,
-                                                        const double* __restrict__ rf, double* __restrict__ rc,
+                                                        const V* __restrict__ rf, V* __restrict__ rc,
                                                         long long Nqf, long long Nqc, const int* __restrict__ act) {
-  __shared__ double sI[MAXN1 * MAXN1], f0[MAXN1 * MAXN1 * MAXN1], t1[MAXN1 * MAXN1 * MAXN1],
-      t2[MAXN1 * MAXN1 * MAXN1];
+  __shared__ V sI[MAXN1 * MAXN1], f0[MAXN1 * MAXN1 * MAXN1], t1[MAXN1 * MAXN1 * MAXN1], t2[MAXN1 * MAXN1 * MAXN1];
   const int e = blockIdx.x;
   const long long k = act[blockIdx.y];
   const int npc = n1c * n1c * n1c, npf = n1f * n1f * n1f;
-  for (int i = threadIdx.x; i < n1f * n1c; i += blockDim.x) sI[i] = I[i];
+  for (int i = threadIdx.x; i < n1f * n1c; i += blockDim.x) sI[i] = (V)I[i];
   for (int i = threadIdx.x; i < npf; i += blockDim.x) f0[i] = rf[k * Nqf + (long long)e * npf + i];
   __syncthreads();
   for (int t = threadIdx.x; t < n1f * n1f * n1c; t += blockDim.x) {  // t1[c][b][a']
     const int ac = t % n1c, r = t / n1c;
-    double acc = 0.0;
+    V acc = 0;
     for (int a = 0; a < n1f; ++a) acc += sI[a * n1c + ac] * f0[r * n1f + a];
     t1[t] = acc;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < n1f * n1c * n1c; t += blockDim.x) {  // t2[c][b'][a']
     const int ac = t % n1c, bc = (t / n1c) % n1c, c = t / (n1c * n1c);
-    double acc = 0.0;
+    V acc = 0;
     for (int b = 0; b < n1f; ++b) acc += sI[b * n1c + bc] * t1[(c * n1f + b) * n1c + ac];
     t2[t] = acc;
   }
   __syncthreads();
-  double* dst = rc + k * Nqc + (long long)e * npc;
+  V* dst = rc + k * Nqc + (long long)e * npc;
   for (int t = threadIdx.x; t < npc; t += blockDim.x) {
     const int ab = t % (n1c * n1c), cc = t / (n1c * n1c);
-    double acc = 0.0;
+    V acc = 0;
     for (int c = 0; c < n1f; ++c) acc += sI[c * n1c + cc] * t2[c * n1c * n1c + ab];
     dst[t] = acc;
   }
@@ -384,26 +390,28 @@ __global__ void __launch_bounds__(128) k_oct_restrict_p(const double* __restrict
 // degree-1 leaves <-> the degree-1 uniform root grid (each leaf lies in one
 // root cell; the root field restricted to a leaf is degree 1 there, so the
 // prolongation is exact): J[e][d][a][b] = root basis b at the leaf's node a
+template <typename V>
 __global__ void k_oct_prolong_root(const int* __restrict__ rcell, const double* __restrict__ J,
-                                   const double* __restrict__ xr, double* __restrict__ xf, int E, long long Nqr,
+                                   const V* __restrict__ xr, V* __restrict__ xf, int E, long long Nqr,
                                    long long Nqf, const int* __restrict__ act) {
   const long long k = act[blockIdx.y];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < E * 8; t += gridDim.x * blockDim.x) {
     const int e = t >> 3, a = t & 1, b = (t >> 1) & 1, c = t >> 2 & 1;
     const double* Je = J + 12LL * e;
-    const double* xe = xr + k * Nqr + 8LL * rcell[e];
+    const V* xe = xr + k * Nqr + 8LL * rcell[e];
     double acc = 0.0;
     for (int cc = 0; cc < 2; ++cc)
       for (int bb = 0; bb < 2; ++bb)
         for (int aa = 0; aa < 2; ++aa)
           acc += Je[0 + 2 * a + aa] * Je[4 + 2 * b + bb] * Je[8 + 2 * c + cc] * xe[aa + 2 * bb + 4 * cc];
-    xf[k * Nqf + t] += acc;
+    xf[k * Nqf + t] += (V)acc;
   }
 }
 
+template <typename V>
 __global__ void k_oct_restrict_root(const int* __restrict__ rptr, const int* __restrict__ rlist,
-                                    const double* __restrict__ J, const double* __restrict__ rf,
-                                    double* __restrict__ rr, int nroot, long long Nqr, long long Nqf,
+                                    const double* __restrict__ J, const V* __restrict__ rf,
+                                    V* __restrict__ rr, int nroot, long long Nqr, long long Nqf,
                                     const int* __restrict__ act) {
   const long long k = act[blockIdx.y];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nroot * 8; t += gridDim.x * blockDim.x) {
@@ -412,13 +420,13 @@ __global__ void k_oct_restrict_root(const int* __restrict__ rptr, const int* __r
     for (int i = rptr[rc]; i < rptr[rc + 1]; ++i) {
       const int e = rlist[i];
       const double* Je = J + 12LL * e;
-      const double* re = rf + k * Nqf + 8LL * e;
+      const V* re = rf + k * Nqf + 8LL * e;
       for (int c = 0; c < 2; ++c)
         for (int b = 0; b < 2; ++b)
           for (int a = 0; a < 2; ++a)
             acc += Je[0 + 2 * a + aa] * Je[4 + 2 * b + bb] * Je[8 + 2 * c + cc] * re[a + 2 * b + 4 * c];
     }
-    rr[k * Nqr + t] = acc;
+    rr[k * Nqr + t] = (V)acc;
   }
 }
 
@@ -426,8 +434,9 @@ __global__ void k_oct_restrict_root(const int* __restrict__ rptr, const int* __r
 
 namespace dg {
 
-static cudaError_t launch_bjac(const dg_oct* h, const OctLevel& L, const double* r, double* z, const int* act,
-                               int nact, cudaStream_t s) {
+template <typename V>
+static cudaError_t launch_bjac(const dg_oct* h, const OctLevel& L, const V* r, V* z, const int* act, int nact,
+                               cudaStream_t s) {
   if (nact == 0) return cudaSuccess;
   const dim3 grid((unsigned)h->E, (unsigned)nact);
   const int* c = L.cls.as<int>();
@@ -436,7 +445,7 @@ static cudaError_t launch_bjac(const dg_oct* h, const OctLevel& L, const double*
   switch (L.n1) {
 #define DG_BJ(N)                                                              \
   case N:                                                                     \
-    k_oct_bjac<N><<<grid, 128, 0, s>>>(c, S, l, r, z, L.Nq, act);             \
+    k_oct_bjac<V, N><<<grid, 128, 0, s>>>(c, S, l, r, z, L.Nq, act);          \
     break;
     DG_BJ(2) DG_BJ(3) DG_BJ(4) DG_BJ(5) DG_BJ(6) DG_BJ(7) DG_BJ(8) DG_BJ(9)
 #undef DG_BJ
@@ -446,9 +455,10 @@ static cudaError_t launch_bjac(const dg_oct* h, const OctLevel& L, const double*
   return cudaGetLastError();
 }
 
-static cudaError_t oct_apply(const dg_oct* h, const OctLevel& L, const double* u, double* out, const int* act,
-                             int nact, cudaStream_t s) {
-  return launch_octree_apply(L.n1, L.T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
+template <typename V>
+static cudaError_t oct_apply(const dg_oct* h, const OctLevel& L, const V* u, V* out, const int* act, int nact,
+                             cudaStream_t s) {
+  return launch_octree_apply<V>(L.n1, L.T, h->hq.as<double>(), h->kind.as<int>(), h->nb.as<int>(), h->pos.as<int>(),
                              h->E, L.p, h->pform, h->eps, u, out, act, nact, h->maxparts, s);
 }
 
@@ -514,10 +524,15 @@ static int oct_ws(dg_oct* h, int cap) {
     if (l > 0)
       for (DevBuf* v : {&L.x, &L.b}) DG_CK(v->ensure(lvec));
   }
+  if (h->mixed) {
+    const size_t v32 = sizeof(float) * (size_t)cap * (size_t)h->Nq;
+    for (DevBuf* v : {&h->b32, &h->x32, &h->r32, &h->z32, &h->p32, &h->q32}) DG_CK(v->ensure(v32));
+  }
   if (h->root) {
     DG_CK(h->rb.ensure(sizeof(double) * (size_t)cap * (size_t)h->Nq_root));
     DG_CK(h->rx.ensure(sizeof(double) * (size_t)cap * (size_t)h->Nq_root));
-    const int rc = prepare(h->root, cap);
+    int rc = prepare(h->root, cap);
+    if (rc == DG_OK && h->mixed) rc = ensure_prec<float>(h->root, h->root->w32, cap);
     if (rc != DG_OK) {
       h->err = "root-grid workspace: " + h->root->err;
       return rc;
@@ -581,10 +596,11 @@ static int oct_finite(dg_oct* h, const double* f, int nsrc, std::vector<int>& fi
 // P^-1 A (P the leaf-block preconditioner) over [lambda / range, lambda],
 // lambda = 1.1 x the level's power-iteration estimate. On exit, if want_res,
 // the level's res holds b - A x.
-static int oct_cheb(dg_oct* h, int l, const double* b, double* x, bool zero_init, bool want_res, const int* act,
-                    int n, cudaStream_t s) {
+template <typename V>
+static int oct_cheb(dg_oct* h, int l, const V* b, V* x, bool zero_init, bool want_res, const int* act, int n,
+                    cudaStream_t s) {
   OctLevel& L = h->lv[l];
-  double *res = L.res.as<double>(), *d = L.d.as<double>(), *z = L.z.as<double>(), *q = L.q.as<double>();
+  V *res = L.res.as<V>(), *d = L.d.as<V>(), *z = L.z.as<V>(), *q = L.q.as<V>();
   const double bmax = 1.1 * L.lam_max, amin = bmax / h->cheb_range;
   const double theta = 0.5 * (bmax + amin), delta = 0.5 * (bmax - amin), sig1 = theta / delta;
   const dim3 vg = ogrid(L.Nq, n);
@@ -595,19 +611,19 @@ static int oct_cheb(dg_oct* h, int l, const double* b, double* x, bool zero_init
     DG_CK(cudaGetLastError());
     return DG_OK;
   };
-  const double* r0 = b;
+  const V* r0 = b;
   if (!zero_init) {
     DG_RET(resid());
     r0 = res;
   }
   DG_CK(launch_bjac(h, L, r0, z, act, n, s));
-  DG_CK(launch_cheb_first<double>(x, d, z, nullptr, 1.0 / theta, zero_init ? 1 : 0, L.Nq, act, n, s));
+  DG_CK(launch_cheb_first<V>(x, d, z, nullptr, 1.0 / theta, zero_init ? 1 : 0, L.Nq, act, n, s));
   double rho_prev = 1.0 / sig1;
   for (int j = 2; j <= h->cheb_k; ++j) {
     DG_RET(resid());
     const double rho = 1.0 / (2.0 * sig1 - rho_prev);
     DG_CK(launch_bjac(h, L, res, z, act, n, s));
-    DG_CK(launch_cheb_step<double>(x, d, z, nullptr, rho * rho_prev, 2.0 * rho / delta, L.Nq, act, n, s));
+    DG_CK(launch_cheb_step<V>(x, d, z, nullptr, rho * rho_prev, 2.0 * rho / delta, L.Nq, act, n, s));
     rho_prev = rho;
   }
   if (want_res) DG_RET(resid());
@@ -617,51 +633,58 @@ static int oct_cheb(dg_oct* h, int l, const double* b, double* x, bool zero_init
 // x = V(b) on octree level l (x overwritten): smoothing, restriction to the
 // next coarser degree (or, from degree 1, to the uniform root grid and its own
 // V-cycle), prolongation of the correction, smoothing
-static int oct_vcycle(dg_oct* h, int l, const double* b, double* x, const int* act, int n, cudaStream_t s) {
+template <typename V>
+static int oct_vcycle(dg_oct* h, int l, const V* b, V* x, const int* act, int n, cudaStream_t s) {
   OctLevel& L = h->lv[l];
-  DG_RET(oct_cheb(h, l, b, x, true, true, act, n, s));
-  const double* res = L.res.as<double>();
+  DG_RET(oct_cheb<V>(h, l, b, x, true, true, act, n, s));
+  const V* res = L.res.as<V>();
   if (l + 1 < (int)h->lv.size()) {
     OctLevel& C = h->lv[l + 1];
     count_launch();
-    k_oct_restrict_p<<<dim3((unsigned)h->E, (unsigned)n), 128, 0, s>>>(L.I.as<double>(), L.n1, C.n1, res,
-                                                                        C.b.as<double>(), L.Nq, C.Nq, act);
+    k_oct_restrict_p<V><<<dim3((unsigned)h->E, (unsigned)n), 128, 0, s>>>(L.I.as<double>(), L.n1, C.n1, res,
+                                                                           C.b.as<V>(), L.Nq, C.Nq, act);
     DG_CK(cudaGetLastError());
-    DG_RET(oct_vcycle(h, l + 1, C.b.as<double>(), C.x.as<double>(), act, n, s));
+    DG_RET(oct_vcycle<V>(h, l + 1, C.b.as<V>(), C.x.as<V>(), act, n, s));
     count_launch();
-    k_oct_prolong_p<<<dim3((unsigned)h->E, (unsigned)n), 128, 0, s>>>(L.I.as<double>(), L.n1, C.n1,
-                                                                       C.x.as<double>(), x, C.Nq, L.Nq, act);
+    k_oct_prolong_p<V><<<dim3((unsigned)h->E, (unsigned)n), 128, 0, s>>>(L.I.as<double>(), L.n1, C.n1, C.x.as<V>(),
+                                                                          x, C.Nq, L.Nq, act);
     DG_CK(cudaGetLastError());
   } else {
     const unsigned gr = (unsigned)std::min<long long>(4096, (h->n_root * 8LL + 255) / 256);
     count_launch();
-    k_oct_restrict_root<<<dim3(gr, (unsigned)n), 256, 0, s>>>(h->rptr.as<int>(), h->rlist.as<int>(),
-                                                               h->rJ.as<double>(), res, h->rb.as<double>(),
-                                                               h->n_root, h->Nq_root, L.Nq, act);
+    k_oct_restrict_root<V><<<dim3(gr, (unsigned)n), 256, 0, s>>>(h->rptr.as<int>(), h->rlist.as<int>(),
+                                                                  h->rJ.as<double>(), res, h->rb.as<V>(),
+                                                                  h->n_root, h->Nq_root, L.Nq, act);
     DG_CK(cudaGetLastError());
-    MG<double> mg{h->root, &h->root->w64, act, n, s};
-    const int rc = mg.vcycle(0, h->rb.as<double>(), h->rx.as<double>());
+    PrecWork<V>* w;
+    if constexpr (sizeof(V) == 4)
+      w = &h->root->w32;
+    else
+      w = &h->root->w64;
+    MG<V> mg{h->root, w, act, n, s};
+    const int rc = mg.vcycle(0, h->rb.as<V>(), h->rx.as<V>());
     if (rc != DG_OK) {
       h->err = "root-grid V-cycle: " + h->root->err;
       return rc;
     }
     const unsigned ge = (unsigned)std::min<long long>(4096, (h->E * 8LL + 255) / 256);
     count_launch();
-    k_oct_prolong_root<<<dim3(ge, (unsigned)n), 256, 0, s>>>(h->rcell.as<int>(), h->rJ.as<double>(),
-                                                              h->rx.as<double>(), x, h->E, h->Nq_root, L.Nq, act);
+    k_oct_prolong_root<V><<<dim3(ge, (unsigned)n), 256, 0, s>>>(h->rcell.as<int>(), h->rJ.as<double>(),
+                                                                 h->rx.as<V>(), x, h->E, h->Nq_root, L.Nq, act);
     DG_CK(cudaGetLastError());
   }
-  DG_RET(oct_cheb(h, l, b, x, false, false, act, n, s));
+  DG_RET(oct_cheb<V>(h, l, b, x, false, false, act, n, s));
   return DG_OK;
 }
 
 // z = M r: the V-cycle (precond 1) or the leaf-block inverse (precond 0)
-static int oct_precond(dg_oct* h, const double* r, double* z, const int* act, int n, cudaStream_t s) {
+template <typename V>
+static int oct_precond(dg_oct* h, const V* r, V* z, const int* act, int n, cudaStream_t s) {
   if (h->precond == 0) {
-    DG_CK(launch_bjac(h, h->lv[0], r, z, act, n, s));
+    DG_CK(launch_bjac<V>(h, h->lv[0], r, z, act, n, s));
     return DG_OK;
   }
-  return oct_vcycle(h, 0, r, z, act, n, s);
+  return oct_vcycle<V>(h, 0, r, z, act, n, s);
 }
 
 // lambda_max(P^-1 A) of level l by 30 power iterations from a fixed
@@ -710,8 +733,12 @@ namespace dg {
 // FP64 relative residual rtol. Convergence of the recursive residual is
 // confirmed on the true residual b - A x; where the two disagree the
 // iteration restarts from the true residual (at most 3 times per source).
+static int oct_pcg_mixed(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vector<dg_solve_stats>& st,
+                         cudaStream_t s);
+
 static int oct_pcg(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vector<dg_solve_stats>& st,
                    cudaStream_t s) {
+  if (h->mixed) return oct_pcg_mixed(h, nsrc, finite, st, s);
   const long long Nq = h->Nq;
   double *b = h->b.as<double>(), *x = h->x.as<double>(), *r = h->r.as<double>(), *z = h->z.as<double>();
   double *p = h->pv.as<double>(), *q = h->qv.as<double>(), *part = h->part.as<double>();
@@ -832,6 +859,134 @@ static int oct_pcg(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vec
   return DG_OK;
 }
 
+// Inner PCG in precision V (the FP32 inner solve of the mixed mode) on the
+// sources `srcs`: x = A^-1 b from x = 0 until the recursive residual falls by
+// itol or imax iterations; iters[k] += the iterations of source k
+template <typename V>
+static int oct_cg_inner(dg_oct* h, const V* b, V* x, V* r, V* z, V* p, V* q, const std::vector<int>& srcs,
+                        double itol, int imax, std::vector<int>& iters, cudaStream_t s) {
+  const long long Nq = h->Nq;
+  double* part = h->part.as<double>();
+  int* flags = h->flags.as<int>();
+  const int* act = h->act.as<int>();
+  const dim3 vg = ogrid(Nq, 1);
+  std::vector<double> bb(h->cap), rr(h->cap);
+  std::vector<int> fl(h->cap);
+  DG_RET(oct_act(h, srcs, s));
+  int n = (int)srcs.size();
+  DG_CK(launch_zero<V>(x, Nq, act, n, s));
+  count_launch();
+  k_oct_copy<V><<<dim3(vg.x, (unsigned)n), OT, 0, s>>>(r, b, Nq, act);
+  DG_CK(cudaGetLastError());
+  DG_CK(launch_dot<V>(b, b, (const double*)nullptr, oslot(h, I_BB), part, Nq, act, n, s));
+  DG_RET(oct_precond<V>(h, r, z, act, n, s));
+  count_launch();
+  k_oct_copy<V><<<dim3(vg.x, (unsigned)n), OT, 0, s>>>(p, z, Nq, act);
+  DG_CK(cudaGetLastError());
+  DG_CK(launch_dot<V>(r, z, (const double*)nullptr, oslot(h, I_RZ), part, Nq, act, n, s));
+  DG_CK(cudaMemcpyAsync(bb.data(), oslot(h, I_BB), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  std::vector<int> active;
+  for (int k : srcs)
+    if (bb[k] > 0.0) active.push_back(k);
+  for (int it = 1; it <= imax && !active.empty(); ++it) {
+    DG_RET(oct_act(h, active, s));
+    n = (int)active.size();
+    DG_CK(oct_apply<V>(h, h->lv[0], p, q, act, n, s));
+    DG_CK(launch_dot<V>(p, q, (const double*)nullptr, oslot(h, I_PQ), part, Nq, act, n, s));
+    count_launch();
+    k_oct_ratio<<<(n + 127) / 128, 128, 0, s>>>(oslot(h, I_RZ), oslot(h, I_PQ), oslot(h, I_AL), act, n, flags);
+    DG_CK(cudaGetLastError());
+    DG_CK(launch_cg_xr<V>(x, r, p, q, oslot(h, I_AL), Nq, act, n, s));
+    DG_CK(launch_dot<V>(r, r, (const double*)nullptr, oslot(h, I_RR), part, Nq, act, n, s));
+    DG_CK(cudaMemcpyAsync(rr.data(), oslot(h, I_RR), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+    DG_CK(cudaMemcpyAsync(fl.data(), flags, sizeof(int) * h->cap, cudaMemcpyDeviceToHost, s));
+    DG_CK(cudaStreamSynchronize(s));
+    std::vector<int> next;
+    for (int k : active) {
+      ++iters[k];
+      if (!(fl[k] & 2) && rr[k] > itol * itol * bb[k]) next.push_back(k);
+    }
+    active = next;
+    if (active.empty()) break;
+    DG_RET(oct_act(h, active, s));
+    n = (int)active.size();
+    DG_RET(oct_precond<V>(h, r, z, act, n, s));
+    DG_CK(launch_dot<V>(r, z, (const double*)nullptr, oslot(h, I_RZN), part, Nq, act, n, s));
+    count_launch();
+    k_oct_ratio<<<(n + 127) / 128, 128, 0, s>>>(oslot(h, I_RZN), oslot(h, I_RZ), oslot(h, I_BE), act, n, flags);
+    DG_CK(cudaGetLastError());
+    count_launch();
+    k_oct_copy_slot<<<(n + 127) / 128, 128, 0, s>>>(oslot(h, I_RZN), oslot(h, I_RZ), act, n);
+    DG_CK(cudaGetLastError());
+    DG_CK(launch_cg_p<V>(p, z, oslot(h, I_BE), Nq, act, n, s));
+  }
+  return DG_OK;
+}
+
+// Mixed mode: FP64 iterative refinement around the FP32 inner PCG. Each round
+// takes the FP64 residual r = b - A x in FP32, solves A e = r to a reduction
+// of inner_rtol, adds e to x in FP64 and recomputes the FP64 residual; a
+// source stops when that residual meets rtol (at most 30 rounds).
+static int oct_pcg_mixed(dg_oct* h, int nsrc, const std::vector<int>& finite, std::vector<dg_solve_stats>& st,
+                         cudaStream_t s) {
+  const long long Nq = h->Nq;
+  double *b = h->b.as<double>(), *x = h->x.as<double>(), *r = h->r.as<double>(), *q = h->qv.as<double>();
+  double* part = h->part.as<double>();
+  const int* act = h->act.as<int>();
+  st.assign(nsrc, dg_solve_stats{});
+  DG_CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)nsrc * Nq, s));
+  DG_CK(cudaMemsetAsync(h->flags.p, 0, sizeof(int) * nsrc, s));
+  std::vector<int> all;
+  for (int k = 0; k < nsrc; ++k) {
+    st[k].guess_rel_residual = 1.0;
+    if (finite[k])
+      all.push_back(k);
+    else
+      st[k].status = DG_ERR_NONFINITE;
+  }
+  if (all.empty()) return DG_OK;
+  const dim3 vg = ogrid(Nq, 1);
+  std::vector<double> bb(h->cap), rr(h->cap);
+  DG_RET(oct_act(h, all, s));
+  int n = (int)all.size();
+  count_launch();
+  k_oct_copy<double><<<dim3(vg.x, (unsigned)n), OT, 0, s>>>(r, b, Nq, act);
+  DG_CK(cudaGetLastError());
+  DG_CK(launch_dot<double>(b, b, (const double*)nullptr, oslot(h, O_BB), part, Nq, act, n, s));
+  DG_CK(cudaMemcpyAsync(bb.data(), oslot(h, O_BB), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+  DG_CK(cudaStreamSynchronize(s));
+  std::vector<int> active, iters(h->cap, 0);
+  for (int k : all)
+    if (bb[k] > 0.0) active.push_back(k);
+  for (int round = 1; round <= 30 && !active.empty(); ++round) {
+    DG_RET(oct_act(h, active, s));
+    n = (int)active.size();
+    DG_CK((launch_convert<float, double>(h->b32.as<float>(), r, Nq, act, n, 1.0, 0, s)));
+    DG_RET(oct_cg_inner<float>(h, h->b32.as<float>(), h->x32.as<float>(), h->r32.as<float>(), h->z32.as<float>(),
+                               h->p32.as<float>(), h->q32.as<float>(), active, h->inner_rtol, h->max_iter, iters, s));
+    DG_RET(oct_act(h, active, s));
+    DG_CK((launch_convert<double, float>(x, h->x32.as<float>(), Nq, act, n, 1.0, 1, s)));
+    DG_CK(oct_apply<double>(h, h->lv[0], x, q, act, n, s));
+    count_launch();
+    k_oct_sub<double><<<dim3(vg.x, (unsigned)n), OT, 0, s>>>(r, b, q, Nq, act);
+    DG_CK(cudaGetLastError());
+    DG_CK(launch_dot<double>(r, r, (const double*)nullptr, oslot(h, O_RR), part, Nq, act, n, s));
+    DG_CK(cudaMemcpyAsync(rr.data(), oslot(h, O_RR), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+    DG_CK(cudaStreamSynchronize(s));
+    std::vector<int> next;
+    for (int k : active) {
+      st[k].outer_refinements = round;
+      st[k].iters = iters[k];
+      st[k].rel_residual = std::sqrt(rr[k] / bb[k]);
+      if (!(st[k].rel_residual <= h->rtol)) next.push_back(k);
+    }
+    active = next;
+  }
+  for (int k : active) st[k].status = DG_ERR_NOT_CONVERGED;
+  return DG_OK;
+}
+
 static int worst_of(const std::vector<dg_solve_stats>& st) {
   int w = DG_OK;
   for (const auto& x : st)
@@ -859,6 +1014,7 @@ static int oct_cap(const dg_oct* h, long long want) {
   long long per = 7LL * h->Nq;
   for (size_t l = 0; l < h->lv.size(); ++l) per += (l == 0 ? 4LL : 6LL) * h->lv[l].Nq;
   per *= (long long)sizeof(double);
+  if (h->mixed) per += 6LL * h->Nq * (long long)sizeof(float);
   long long c = std::max(1LL, std::min(64LL, (4LL << 30) / std::max(1LL, per)));
   return (int)std::max(1LL, std::min(c, want));
 }
@@ -870,12 +1026,13 @@ using namespace dg;
 extern "C" {
 
 int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_leaves, int32_t penalty_form,
-                    double penalty_eps, double rtol, int32_t max_iter, int32_t precond, dg_oct_handle* out) {
+                    double penalty_eps, double rtol, int32_t max_iter, int32_t precond, int32_t precision,
+                    dg_oct_handle* out) {
   if (!out) return DG_ERR_INVALID_ARG;
   *out = nullptr;
   if (!root || !leaves || n_leaves < 1 || root->p < 1 || root->p > MAXN1 - 1 ||
       (penalty_form != 0 && penalty_form != 1) || !(penalty_eps > 0.0) || !(rtol > 0.0) || !(rtol < 1.0) ||
-      max_iter < 1 || (precond != 0 && precond != 1))
+      max_iter < 1 || (precond != 0 && precond != 1) || (precision != DG_PREC_FP64 && precision != DG_PREC_MIXED))
     return DG_ERR_INVALID_ARG;
   const int E = n_leaves, n1 = root->p + 1, NPE = n1 * n1 * n1, NF = n1 * n1;
   std::vector<int32_t> kind(6 * (size_t)E), nb(24 * (size_t)E), pos(6 * (size_t)E);
@@ -892,6 +1049,7 @@ int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
   h->rtol = rtol;
   h->max_iter = max_iter;
   h->precond = precond;
+  h->mixed = precision == DG_PREC_MIXED;
   h->maxparts = octree_max_parts(kind.data(), E);
   h->Nq = (long long)E * NPE;
   double xi[MAXN1], w[MAXN1];

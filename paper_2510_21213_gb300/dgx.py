@@ -136,7 +136,7 @@ def load():
     lib.dg_octree_apply.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, vp, vp, C.c_int64, vp]
     lib.dg_octree_apply.restype = C.c_int
     lib.dg_octree_setup.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_int32, C.c_int32,
-                                    C.POINTER(vp)]
+                                    C.c_int32, C.POINTER(vp)]
     lib.dg_octree_setup.restype = C.c_int
     lib.dg_octree_destroy.argtypes = [vp]
     lib.dg_octree_destroy.restype = None
@@ -747,7 +747,7 @@ class OctreeSolver:
     octree over the root grid (lo, hi, n, p), FP64 fields [B, E (p+1)^3]."""
 
     def __init__(self, lo, hi, n, p, leaves, penalty_form=0, penalty_eps=0.125, rtol=1e-10, max_iter=5000,
-                 precond=1):
+                 precond=1, precision=DG_PREC_FP64):
         if np.isscalar(n):
             n = (n, n, n)
         self.leaves = np.ascontiguousarray(leaves, dtype=np.int32)
@@ -758,7 +758,7 @@ class OctreeSolver:
         desc = dg_mesh_desc((C.c_double * 3)(*lo), (C.c_double * 3)(*hi), (C.c_int32 * 3)(*n), self.p)
         h = C.c_void_p()
         _check(load().dg_octree_setup(C.byref(desc), self.leaves.ctypes.data_as(C.c_void_p), self.leaves.shape[0],
-                                      penalty_form, penalty_eps, rtol, max_iter, precond, C.byref(h)),
+                                      penalty_form, penalty_eps, rtol, max_iter, precond, precision, C.byref(h)),
                "dg_octree_setup")
         self.h = h
 

@@ -219,3 +219,41 @@ def test_solution_does_not_depend_on_the_batch(dgx):
     v1, _ = s.solve(torch.tensor(f[17:], device="cuda"))
     s.close()
     assert torch.equal(v[17], v1[0])
+
+
+@pytest.mark.parametrize("mesh,p", [("three", 3), ("one", 7)])
+def test_mixed_precision_solve_matches_the_oracle(dgx, mesh, p):
+    """Mixed mode (FP32 inner PCG and V-cycle inside FP64 refinement; boundary
+    data, residuals and results in FP64): refined to a 1e-12 FP64 residual the
+    potentials equal the oracle's exact solve as the FP64 mode's do."""
+    t = _three_levels(p) if mesh == "three" else _one_split(p)
+    f = np.stack([_gauss_source(t), _gauss_source(t, (-0.4, 0.5, 0.9), 1.5)])
+    ref = np.stack([octree.poisson(t, fk) for fk in f])
+    s = _solver(dgx, t, rtol=1e-12, precision=dgx.DG_PREC_MIXED)
+    v, st = s.solve(torch.tensor(f, device="cuda"))
+    s.close()
+    assert all(x["status"] == 0 and x["rel_residual"] <= 1e-12 and x["outer_refinements"] >= 2 for x in st)
+    assert np.abs(v.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_mixed_precision_exchange_build_matches_the_oracle(dgx):
+    """The mixed mode's exchange build on the density-refined octree of the
+    two-atom system: K, E_H, E_X equal the oracle's at rtol 1e-10."""
+    from paper_2510_21213_gb300 import inputs
+
+    spec = inputs.tiny_system()
+    t = octree.OctreeMesh(list(spec.mesh.lo), list(spec.mesh.hi), (2, 2, 2), 3)
+
+    def rho(P):
+        return np.sum(inputs.orbitals(spec, P) ** 2, axis=0)
+
+    octree.refine_to_density(t, rho, 1e-3, 2)
+    psi = inputs.orbitals(spec, t.node_coords())
+    ref = octree.exchange_build(t, psi)
+    s = _solver(dgx, t, rtol=1e-10, precision=dgx.DG_PREC_MIXED)
+    K, EH, EX, st = s.exchange_build(torch.tensor(psi, device="cuda"))
+    s.close()
+    assert all(x["status"] == 0 for x in st)
+    assert np.abs(K - ref["K"]).max() <= 1e-8 * np.abs(ref["K"]).max()
+    assert abs(EH - ref["E_H"]) <= 1e-8 * abs(ref["E_H"])
+    assert abs(EX - ref["E_X"]) <= 1e-8 * abs(ref["E_X"])

@@ -269,24 +269,24 @@ def test_octree_setup_rejects_bad_arguments_without_a_device():
     def desc(p=2, n=(2, 2, 2)):
         return dgx.dg_mesh_desc((C.c_double * 3)(*LO), (C.c_double * 3)(*HI), (C.c_int32 * 3)(*n), p)
 
-    good = dict(form=0, eps=0.125, rtol=1e-10, it=100, pc=1)
+    good = dict(form=0, eps=0.125, rtol=1e-10, it=100, pc=1, prec=0)
     cases = [dict(good, form=2), dict(good, eps=0.0), dict(good, rtol=0.0), dict(good, rtol=1.0),
-             dict(good, it=0), dict(good, pc=2), dict(good, pc=-1)]
+             dict(good, it=0), dict(good, pc=2), dict(good, pc=-1), dict(good, prec=2), dict(good, prec=-1)]
     for c in cases:
         h = C.c_void_p(1)
         rc = lib.dg_octree_setup(C.byref(desc()), lp, len(leaves), c["form"], c["eps"], c["rtol"], c["it"], c["pc"],
-                                 C.byref(h))
+                                 c["prec"], C.byref(h))
         assert rc == dgx.DG_ERR_INVALID_ARG and not h.value
     h = C.c_void_p(1)
-    assert lib.dg_octree_setup(C.byref(desc(p=9)), lp, len(leaves), 0, 0.125, 1e-10, 100, 1,
+    assert lib.dg_octree_setup(C.byref(desc(p=9)), lp, len(leaves), 0, 0.125, 1e-10, 100, 1, 0,
                                C.byref(h)) == dgx.DG_ERR_INVALID_ARG and not h.value
     # a leaf set that is not 2:1 balanced
     bad = octree.OctreeMesh(LO, HI, (2, 2, 2), 2)
     bad.refine([(0, 0, 0, 0)])
     bad.refine([(1, 1, 1, 1)])
     bl = np.array(bad.leaf_list(), dtype=np.int32)
-    assert lib.dg_octree_setup(C.byref(desc()), bl.ctypes.data_as(C.c_void_p), len(bl), 0, 0.125, 1e-10, 100, 1,
+    assert lib.dg_octree_setup(C.byref(desc()), bl.ctypes.data_as(C.c_void_p), len(bl), 0, 0.125, 1e-10, 100, 1, 0,
                                C.byref(h)) == dgx.DG_ERR_INVALID_ARG and not h.value
-    assert lib.dg_octree_setup(C.byref(desc()), lp, len(leaves), 0, 0.125, 1e-10, 100, 1, None) == \
+    assert lib.dg_octree_setup(C.byref(desc()), lp, len(leaves), 0, 0.125, 1e-10, 100, 1, 0, None) == \
         dgx.DG_ERR_INVALID_ARG
     lib.dg_octree_destroy(None)
