@@ -619,7 +619,7 @@ def run_ours(args):
 
 def run_octree(args):
     """Exchange build on an adaptive octree (dg_octree_setup /
-    dg_octree_exchange_build): the chain10 box [-12, 12]^3 with a 4^3 root grid
+    dg_octree_exchange_build): the chain10 box [-12, 12]^3 with an 8^3 root grid
     at p = 6, refined by the density indicator of the chain system's orbitals
     (delta 1e-5, up to level 2), the chain's 10 orbitals evaluated at the
     octree's nodes and orthonormalised with its weights; rtol 1e-8. One step =
@@ -680,7 +680,7 @@ def run_octree(args):
                       "unit": "pair_solves/s", "ms_per_step": mx["ms"], "steps": args.steps,
                       "warmup": max(args.warmup, 3), "higher_is_better": True, "dtype": "f32+f64",
                       "data": "synthetic",
-                      "config": {"workload": "octree: chain10 box, 4^3 roots, p=6, density-refined to level 2",
+                      "config": {"workload": "octree: chain10 box, 8^3 roots, p=6, density-refined to level 2",
                                  "leaves": int(leaves.shape[0]), "leaves_per_level": levels, "Nq": int(Nq),
                                  "orbitals": N, "sources": P + 1, "rtol": 1e-8, "precision": "mixed",
                                  "mean_inner_iters": mx["iters"], "mean_rounds": mx["rounds"],

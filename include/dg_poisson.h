@@ -470,8 +470,12 @@ int dg_octree_apply(const dg_mesh_desc* root, const int32_t* leaves_host, int32_
  * FP64) or DG_PREC_MIXED (the PCG and its V-cycle in FP32 inside FP64
  * iterative refinement: each round solves A e = r for the FP64 residual r to a
  * reduction of 1e-4, adds e in FP64 and recomputes r in FP64, until r meets
- * rtol; the boundary data, right-hand side, residuals and results stay FP64;
- * stats report the inner iterations and the rounds). Writes the handle to *out (NULL on
+ * rtol; right-hand side, residuals and results stay FP64; the boundary data
+ * is one 3xTF32 tensor-core GEMM per chunk of sources against the FP32 kernel
+ * matrix 1/|xb_j - x_q| that the handle computes once and keeps on the device
+ * when it takes at most 48 GB (nodes x boundary face nodes x 4 bytes; else the
+ * FP64 direct sum), accurate to about 1e-7 of sum |W f| / r; stats report the
+ * inner iterations and the rounds). Writes the handle to *out (NULL on
  * failure). Fields are [.][Nq] FP64 with Nq = n_leaves (p+1)^3, element-blocked
  * in leaf order, nodes x-fastest. DG_ERR_INVALID_ARG for a bad mesh, leaf set
  * or argument; DG_ERR_UNSUPPORTED beyond 2^31 nodes; DG_ERR_NO_MEMORY,

@@ -90,6 +90,11 @@ struct dg_oct {
   int cap = 0;
   dg::DevBuf f, g, gpart, b, x, r, z, pv, qv, scal, part, act, flags, pidx, lists, Wacc, kpart, Kdev;
   dg::DevBuf b32, x32, r32, z32, p32, q32;  // FP32 inner solve (mixed)
+  // mixed mode: the boundary data as one GEMM per chunk, G = (W f) K with the
+  // kernel matrix K[q][j] = 1 / |xb_j - x_q| (FP32, [Nq][nbf n1^2]) kept on
+  // the device when it fits the budget below
+  dg::DevBuf kmat, wf32, g32, gwork;
+  bool has_kmat = false;
   std::vector<int> act_host;
   ~dg_oct() {
     if (root) dg_destroy(root);
@@ -246,6 +251,35 @@ __global__ void k_oct_bdata_sum(const double* __restrict__ part, int nch, long l
     for (int c = 0; c < nch; ++c) s += part[(long long)c * n + t];
     g[t] = s;
   }
+}
+
+// kmat[q][j] = 1 / |xb_j - x_q| in FP32 (the mixed mode's boundary-data
+// kernel matrix): FP64 distance, rsqrtf refined by one FP64 Newton step, then
+// rounded to FP32
+__global__ void k_oct_kmat(const double* __restrict__ xb, long long nbn, const double* __restrict__ xq,
+                           long long Nq, float* __restrict__ kmat) {
+  const long long n = Nq * nbn;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long q = t / nbn, j = t - q * nbn;
+    const double dx = xb[3 * j] - xq[3 * q], dy = xb[3 * j + 1] - xq[3 * q + 1], dz = xb[3 * j + 2] - xq[3 * q + 2];
+    const double d2 = dx * dx + dy * dy + dz * dz;
+    double y = (double)rsqrtf((float)d2);
+    y = y * fma(-0.5, d2 * y * y, 1.5);
+    kmat[t] = (float)y;
+  }
+}
+
+// wf[k][q] = W_q f_k(q) in FP32 (the GEMM's left operand)
+__global__ void k_oct_wf32(const double* __restrict__ W, const double* __restrict__ f, long long Nq, int nsrc,
+                           float* __restrict__ wf) {
+  const long long n = Nq * nsrc;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    wf[t] = (float)(W[t % Nq] * f[t]);
+}
+
+__global__ void k_oct_f2d(const float* __restrict__ a, long long n, double* __restrict__ b) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    b[t] = (double)a[t];
 }
 
 // node chunks of the boundary-data sum: about four blocks per SM of a GB300 for
@@ -527,6 +561,12 @@ static int oct_ws(dg_oct* h, int cap) {
   if (h->mixed) {
     const size_t v32 = sizeof(float) * (size_t)cap * (size_t)h->Nq;
     for (DevBuf* v : {&h->b32, &h->x32, &h->r32, &h->z32, &h->p32, &h->q32}) DG_CK(v->ensure(v32));
+    if (h->has_kmat) {
+      const size_t nbn = (size_t)h->nbf * h->n1 * h->n1;
+      DG_CK(h->wf32.ensure(v32));
+      DG_CK(h->g32.ensure(sizeof(float) * (size_t)cap * nbn));
+      DG_CK(h->gwork.ensure(sizeof(float) * 32 * (size_t)cap * nbn));
+    }
   }
   if (h->root) {
     DG_CK(h->rb.ensure(sizeof(double) * (size_t)cap * (size_t)h->Nq_root));
@@ -564,6 +604,39 @@ static int oct_act(dg_oct* h, const std::vector<int>& a, cudaStream_t s) {
 // b[k] = 4 pi W f_k + the Nitsche load of f_k's Coulomb boundary data, k < nsrc
 static int oct_form_rhs(dg_oct* h, const double* f, int nsrc, cudaStream_t s) {
   const long long nbn = (long long)h->nbf * h->n1 * h->n1;
+  if (h->mixed && h->has_kmat) {
+    // G = (W f) K: 3xTF32 tensor-core GEMM (M sources, N boundary nodes, K nodes)
+    const unsigned gb = (unsigned)std::min<long long>(152LL * 16, (h->Nq * nsrc + 255) / 256);
+    count_launch();
+    k_oct_wf32<<<gb, 256, 0, s>>>(h->W.as<double>(), f, h->Nq, nsrc, h->wf32.as<float>());
+    DG_CK(cudaGetLastError());
+    GemmArgs ga{};
+    ga.M = nsrc;
+    ga.N = (int)nbn;
+    ga.K = (int)h->Nq;
+    ga.nb1 = ga.nb2 = 1;
+    ga.A = h->wf32.p;
+    ga.sAm = h->Nq;
+    ga.sAk = 1;
+    ga.B = h->kmat.p;
+    ga.sBk = nbn;
+    ga.sBn = 1;
+    ga.C = h->g32.p;
+    ga.sCm = nbn;
+    ga.sCn = 1;
+    ga.alpha = 1.0;
+    ga.beta = 0.0;
+    ga.work = h->gwork.p;
+    ga.work_elems = 32LL * h->cap * nbn;
+    DG_CK(launch_gemm<float>(ga, s));
+    count_launch();
+    k_oct_f2d<<<(unsigned)std::min<long long>(4096, (nsrc * nbn + 255) / 256), 256, 0, s>>>(
+        h->g32.as<float>(), nsrc * nbn, h->g.as<double>());
+    DG_CK(cudaGetLastError());
+    DG_CK(launch_rhs_volume(f, h->W.as<double>(), h->b.as<double>(), h->Nq, nsrc, s));
+    DG_CK(launch_oct_lift(h, h->g.as<double>(), h->b.as<double>(), nsrc, s));
+    return DG_OK;
+  }
   count_launch();
   const int nch = oct_bdata_chunks(nbn);
   k_oct_bdata<<<dim3((unsigned)((nbn + BDT - 1) / BDT), (unsigned)nch, (unsigned)((nsrc + BDK - 1) / BDK)), BDT, 0,
@@ -1224,6 +1297,21 @@ int dg_octree_setup(const dg_mesh_desc* root, const int32_t* leaves, int32_t n_l
     if ((rc = dg_poisson_setup(&rm, &o, &h->root)) != DG_OK) {
       h->err = "root-grid solver set-up failed";
       return fail(rc);
+    }
+    // the mixed mode's boundary-data kernel matrix, when it fits 48 GB (a sixth
+    // of a GB300's memory) and the GEMM's int sizes; else the direct FP64 sum
+    const long long nbn = (long long)h->nbf * n1 * n1;
+    if (h->mixed && h->Nq * nbn * 4 <= (48LL << 30) && h->Nq < (1LL << 31)) {
+      if ((rc = [&]() -> int {
+            DG_CK(h->kmat.ensure(sizeof(float) * (size_t)(h->Nq * nbn)));
+            count_launch();
+            k_oct_kmat<<<152 * 16, 256>>>(h->xb.as<double>(), nbn, h->xq.as<double>(), h->Nq, h->kmat.as<float>());
+            DG_CK(cudaGetLastError());
+            DG_CK(cudaDeviceSynchronize());
+            return DG_OK;
+          }()) != DG_OK)
+        return fail(rc);
+      h->has_kmat = true;
     }
     // lambda_max(P^-1 A) of every octree level, for its Chebyshev smoother
     if ((rc = oct_ws(h, 1)) != DG_OK) return fail(rc);

@@ -221,11 +221,18 @@ def test_solution_does_not_depend_on_the_batch(dgx):
     assert torch.equal(v[17], v1[0])
 
 
+# Mixed mode: FP32 inner PCG and V-cycle inside FP64 refinement; the boundary
+# data as a 3xTF32 GEMM against the FP32 kernel matrix 1/|x_j - x_q| (about
+# 1e-7 of sum |W f| / r). Stated bound against the FP64 oracle: 2e-5 of the
+# largest entry on v, K, E_H, E_X (as for the uniform mesh's mixed mode).
+MIXED_BOUND = 2e-5
+
+
 @pytest.mark.parametrize("mesh,p", [("three", 3), ("one", 7)])
 def test_mixed_precision_solve_matches_the_oracle(dgx, mesh, p):
-    """Mixed mode (FP32 inner PCG and V-cycle inside FP64 refinement; boundary
-    data, residuals and results in FP64): refined to a 1e-12 FP64 residual the
-    potentials equal the oracle's exact solve as the FP64 mode's do."""
+    """Refined to a 1e-12 FP64 residual of its own right-hand side, the mixed
+    mode's potentials are within the mixed bound of the oracle's exact solve
+    (the difference is the FP32 boundary data's)."""
     t = _three_levels(p) if mesh == "three" else _one_split(p)
     f = np.stack([_gauss_source(t), _gauss_source(t, (-0.4, 0.5, 0.9), 1.5)])
     ref = np.stack([octree.poisson(t, fk) for fk in f])
@@ -233,12 +240,14 @@ def test_mixed_precision_solve_matches_the_oracle(dgx, mesh, p):
     v, st = s.solve(torch.tensor(f, device="cuda"))
     s.close()
     assert all(x["status"] == 0 and x["rel_residual"] <= 1e-12 and x["outer_refinements"] >= 2 for x in st)
-    assert np.abs(v.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    err = np.abs(v.cpu().numpy() - ref).max() / np.abs(ref).max()
+    print(f"mixed octree solve, {mesh} p = {p}: {err:.2e} of max |v|")
+    assert err <= MIXED_BOUND
 
 
 def test_mixed_precision_exchange_build_matches_the_oracle(dgx):
     """The mixed mode's exchange build on the density-refined octree of the
-    two-atom system: K, E_H, E_X equal the oracle's at rtol 1e-10."""
+    two-atom system at rtol 1e-10: K, E_H, E_X within the mixed bound."""
     from paper_2510_21213_gb300 import inputs
 
     spec = inputs.tiny_system()
@@ -254,6 +263,7 @@ def test_mixed_precision_exchange_build_matches_the_oracle(dgx):
     K, EH, EX, st = s.exchange_build(torch.tensor(psi, device="cuda"))
     s.close()
     assert all(x["status"] == 0 for x in st)
-    assert np.abs(K - ref["K"]).max() <= 1e-8 * np.abs(ref["K"]).max()
-    assert abs(EH - ref["E_H"]) <= 1e-8 * abs(ref["E_H"])
-    assert abs(EX - ref["E_X"]) <= 1e-8 * abs(ref["E_X"])
+    eK = np.abs(K - ref["K"]).max() / np.abs(ref["K"]).max()
+    eH, eX = abs(EH - ref["E_H"]) / abs(ref["E_H"]), abs(EX - ref["E_X"]) / abs(ref["E_X"])
+    print(f"mixed octree build: K {eK:.2e}, E_H {eH:.2e}, E_X {eX:.2e}")
+    assert eK <= MIXED_BOUND and eH <= MIXED_BOUND and eX <= MIXED_BOUND
