@@ -263,34 +263,41 @@ __global__ void __launch_bounds__(256) k_octree_apply(const OctTables T, const d
   for (int i = tid; i < NPE; i += NT) uK[i] = ub[(long long)e * NPE + i];
   if (tid < 3) hK[tid] = hq[3LL * e + tid];
   __syncthreads();
-  if (tid == 0) {
-    int n = 0;
-    for (int f = 0; f < 6; ++f) {
+  // the leaf's face parts, one thread per (face f, quarter qi) slot: part index =
+  // the parts of the faces before f, plus qi
+  if (tid < 24) {
+    const int f = tid >> 2, qi = tid & 3;
+    int kd = 0, start = 0, total = 0;
+#pragma unroll
+    for (int g = 0; g < 6; ++g) {
+      const int kg = kind[6LL * e + g];
+      const int ng = kg == 3 ? 4 : 1;
+      if (g < f) start += ng;
+      if (g == f) kd = kg;
+      total += ng;
+    }
+    if (tid == 0) npart = total;
+    if (qi < (kd == 3 ? 4 : 1)) {
       const int d = f >> 1, t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
       const long long o = 6LL * e + f;
-      const int kd = kind[o];
-      const int nq = kd == 3 ? 4 : 1;
-      for (int qi = 0; qi < nq; ++qi) {
-        OctPart& P = part[n++];
-        P.f = f;
-        P.tk0 = kd == 3 ? 1 + (qi & 1) : 0;
-        P.tk1 = kd == 3 ? 1 + (qi >> 1) : 0;
-        const int ps = kd == 2 ? pos[o] : 0;
-        P.tl0 = kd == 2 ? 1 + (ps & 1) : 0;
-        P.tl1 = kd == 2 ? 1 + (ps >> 1) : 0;
-        if (kd == 0) {
-          P.L = -1;
-          P.sig = oct_penalty(p, hK[d], pform, eps);
-          P.wsc = hK[t0] * hK[t1] / 4.0;
-        } else {
-          P.L = kd == 3 ? nbr[4 * o + qi] : nbr[4 * o];
-          const double* hL = hq + 3LL * P.L;
-          P.sig = oct_penalty(p, fmin(hK[d], hL[d]), pform, eps);
-          P.wsc = kd == 3 ? hL[t0] * hL[t1] / 4.0 : hK[t0] * hK[t1] / 4.0;
-        }
+      OctPart& P = part[start + qi];
+      P.f = f;
+      P.tk0 = kd == 3 ? 1 + (qi & 1) : 0;
+      P.tk1 = kd == 3 ? 1 + (qi >> 1) : 0;
+      const int ps = kd == 2 ? pos[o] : 0;
+      P.tl0 = kd == 2 ? 1 + (ps & 1) : 0;
+      P.tl1 = kd == 2 ? 1 + (ps >> 1) : 0;
+      if (kd == 0) {
+        P.L = -1;
+        P.sig = oct_penalty(p, hK[d], pform, eps);
+        P.wsc = hK[t0] * hK[t1] / 4.0;
+      } else {
+        P.L = kd == 3 ? nbr[4 * o + qi] : nbr[4 * o];
+        const double* hL = hq + 3LL * P.L;
+        P.sig = oct_penalty(p, fmin(hK[d], hL[d]), pform, eps);
+        P.wsc = kd == 3 ? hL[t0] * hL[t1] / 4.0 : hK[t0] * hK[t1] / 4.0;
       }
     }
-    npart = n;
   }
   __syncthreads();
   const int np = npart;
@@ -495,6 +502,8 @@ cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, co
   if (maxparts < 6 || maxparts > 24) return cudaErrorInvalidValue;
   const dim3 grid((unsigned)E, (unsigned)nact);
   const size_t smem = sizeof(V) * (size_t)maxparts * 6 * n1 * n1;
+  // threads per block by degree: the phases have (p+1)^2 to 24 (p+1)^2 work items
+  const int nthr = n1 <= 3 ? 64 : (n1 <= 5 ? 128 : 256);
   count_launch();
   switch (n1) {
 #define DG_OCT_CASE(N)                                                                                       \
@@ -502,7 +511,7 @@ cudaError_t launch_octree_apply(int n1, const OctTables& T, const double* hq, co
     cudaError_t e0 = cudaFuncSetAttribute(k_octree_apply<V, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                           (int)smem);                                                        \
     if (e0 != cudaSuccess) return e0;                                                                        \
-    k_octree_apply<V, N><<<grid, 256, smem, s>>>(T, hq, kind, nb, pos, E, p, pform, eps, u, out, act);          \
+    k_octree_apply<V, N><<<grid, nthr, smem, s>>>(T, hq, kind, nb, pos, E, p, pform, eps, u, out, act);         \
     break;                                                                                                   \
   }
     DG_OCT_CASE(2)
