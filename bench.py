@@ -369,13 +369,19 @@ def run_batched(args):
     clk.start()
     l0 = dgx.dg_kernel_launch_count()
     times = []
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush_l2(flush)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Ks, ehs, exs, sts = dgx.dg_exchange_build_multi(systems, opts=opts, lanes=4)
-        torch.cuda.synchronize()
-        times.append(time.perf_counter() - t0)
+        # every lane's build is ordered after e0 and before e1 on this stream
+        # (each waits on the stream at entry and the stream waits on it at exit)
+        e0.record(stream)
+        Ks, ehs, exs, sts = dgx.dg_exchange_build_multi(systems, opts=opts, lanes=4, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
     launches = (dgx.dg_kernel_launch_count() - l0) // args.steps
     clocks = clk.stop()
     pd.barrier()
@@ -394,7 +400,8 @@ def run_batched(args):
         "config": {"workload": f"batched32: 32 systems per GPU, seeds 4000-4031 (+1000 per rank), "
                                f"{total_pairs} pair solves + 32 Hartree on rank 0",
                    "sizes": [[sp.mesh.n[0], sp.mesh.p, sp.N] for sp in specs], "lanes": 4,
-                   "timing": "host wall clock around each multi-system call (several streams)"},
+                   "timing": "CUDA events on the calling stream around each multi-system call (the lanes' "
+                             "streams are ordered between them)"},
         "gpu_launches": int(launches), "clocks": clocks,
         "solver": {"mean_iters": float(np.mean(iters)), "max_iters": int(max(iters)),
                    "all_converged": all(x["status"] == 0 for st in sts for x in st)},
