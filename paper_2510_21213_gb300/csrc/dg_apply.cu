@@ -123,8 +123,29 @@ __device__ __forceinline__ void ap_traces(const T* __restrict__ u, const long lo
       const int base = D == 0 ? N1 * t1 + NF * t2 : (D == 1 ? t1 + NF * t2 : t1 + N1 * t2);
       const T* un = u + b0 + (long long)nb * (N1 * NF) + base;
       T vals[N1];
+      // an x-line is N1 contiguous values: with N1 * sizeof(T) a multiple of 16
+      // bytes (and the field 16-byte aligned, as the library's are) it is read
+      // with 16-byte loads, so that a warp's load touches each sector once
+      constexpr bool VEC = D == 0 && (N1 * (int)sizeof(T)) % 16 == 0;
+      if (VEC && (reinterpret_cast<uintptr_t>(un) & 15) == 0) {
+        const uint4* p4 = reinterpret_cast<const uint4*>(un);
 #pragma unroll
-      for (int i = 0; i < N1; ++i) vals[i] = un[i * SD];
+        for (int w = 0; w < (N1 * (int)sizeof(T)) / 16; ++w) {
+          const uint4 q = __ldg(p4 + w);
+          if constexpr (sizeof(T) == 4) {
+            vals[4 * w] = __uint_as_float(q.x);
+            vals[4 * w + 1] = __uint_as_float(q.y);
+            vals[4 * w + 2] = __uint_as_float(q.z);
+            vals[4 * w + 3] = __uint_as_float(q.w);
+          } else {
+            vals[2 * w] = __hiloint2double((int)q.y, (int)q.x);
+            vals[2 * w + 1] = __hiloint2double((int)q.w, (int)q.z);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N1; ++i) vals[i] = un[i * SD];
+      }
       // the -d neighbour meets us at its right end, the +d neighbour at its left end
       const T* tv = side == 0 ? sTr[1] : sTr[0];
       const T* td = side == 0 ? sTr[3] : sTr[2];
