@@ -28,7 +28,7 @@ namespace dg {
 #define DG_APPLY_THREADS 256  // threads per block (at least)
 #endif
 #ifndef DG_APPLY_SMEM
-#define DG_APPLY_SMEM 36864   // shared-memory budget of the element slots (bytes)
+#define DG_APPLY_SMEM 38912   // shared-memory budget of the element slots (bytes)
 #endif
 #ifndef DG_SMEM_CARVEOUT
 #define DG_SMEM_CARVEOUT -1  // shared-memory carveout (percent) asked for the operator and patch kernels; -1: default
@@ -36,13 +36,25 @@ namespace dg {
 #ifndef DG_APPLY_MINB32
 #define DG_APPLY_MINB32 4     // resident blocks per SM asked of ptxas, FP32
 #endif
+// Element values in shared memory: node (a, b, c) at a + PB b + PB N1 c. With
+// an even N1 the rows are padded by one (PB = N1 + 1), so that the x-pass's
+// threads, which own consecutive x-lines, fall on different banks.
+template <int N1>
+struct ApplyPad {
+  static constexpr int PB = N1 % 2 == 0 ? N1 + 1 : N1;
+  static constexpr int PNPE = PB * N1 * N1;
+  // shared-memory index of the element-local node loc = a + N1 b + N1^2 c
+  __device__ static __forceinline__ int idx(int loc) { return loc + (PB - N1) * (loc / N1); }
+};
+
 template <typename T, int N1>
 struct ApplyCfg {
   static constexpr int NPE = N1 * N1 * N1;
   static constexpr int NF = N1 * N1;
+  static constexpr int PNPE = ApplyPad<N1>::PNPE;
   static constexpr int LPT = sizeof(T) == 4 ? DG_APPLY_LPT32 : 1;
   static constexpr int TPE = (NF + LPT - 1) / LPT;
-  static constexpr int PER_ELEM = (2 * NPE + 12 * NF + 3) * (int)sizeof(T);
+  static constexpr int PER_ELEM = (2 * PNPE + 12 * NF + 3) * (int)sizeof(T);
   static constexpr int EPB_T = DG_APPLY_THREADS / TPE < 1 ? 1 : DG_APPLY_THREADS / TPE;
   static constexpr int EPB_S = DG_APPLY_SMEM / PER_ELEM < 1 ? 1 : DG_APPLY_SMEM / PER_ELEM;
   static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;
@@ -60,7 +72,8 @@ __device__ __forceinline__ void ap_pass(const T* __restrict__ su, T* __restrict_
                                         const T* __restrict__ cc, const T* __restrict__ tr,
                                         const T* __restrict__ mA, const T* __restrict__ mB, int lt) {
   constexpr int NF = N1 * N1;
-  constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? N1 : NF);
+  constexpr int PB = ApplyPad<N1>::PB;
+  constexpr int stride = DIR == 0 ? 1 : (DIR == 1 ? PB : PB * N1);
   T v[LPT][N1];
   int base[LPT], tt[LPT];
   bool ok[LPT];
@@ -71,7 +84,7 @@ __device__ __forceinline__ void ap_pass(const T* __restrict__ su, T* __restrict_
     ok[s] = l < NF;
     const int l1 = ok[s] ? l % N1 : 0, l2 = ok[s] ? l / N1 : 0;
     // line (l1, l2) = (b, c) for x, (a, c) for y, (a, b) for z
-    base[s] = DIR == 0 ? N1 * l1 + NF * l2 : (DIR == 1 ? l1 + NF * l2 : l1 + N1 * l2);
+    base[s] = DIR == 0 ? PB * l1 + PB * N1 * l2 : (DIR == 1 ? l1 + PB * N1 * l2 : l1 + PB * l2);
     tt[s] = l1 + N1 * l2;
     scale[s] = mA[l1] * mB[l2];
     tvm[s] = tr[(0 * 2 + 0) * NF + tt[s]];
@@ -171,8 +184,8 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS, ApplyCfg<T, N1>::MIN
   __shared__ T sC[3][4][N1];
   __shared__ T sM[3][N1];
   __shared__ T sTr[4][N1];
-  __shared__ T su[EPB][NPE];
-  __shared__ T sacc[EPB][NPE];
+  __shared__ T su[EPB][C::PNPE];
+  __shared__ T sacc[EPB][C::PNPE];
   __shared__ T st[EPB][6][2][NF];
   __shared__ long long sbase[EPB];  // rhs * Nq + e * NPE of the slot, or -1
   __shared__ int snb[EPB][6];       // neighbour element offset (elements) per face, 0 = none
@@ -231,7 +244,7 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS, ApplyCfg<T, N1>::MIN
     for (int t = tid; t < EPB * NPE; t += NT) {
       const int sl = t / NPE, loc = t - sl * NPE;
       const long long b0 = sbase[sl];
-      su[sl][loc] = b0 >= 0 ? u[b0 + loc] : (T)0;
+      su[sl][ApplyPad<N1>::idx(loc)] = b0 >= 0 ? u[b0 + loc] : (T)0;
     }
     // neighbour traces: face f = 2 d + side (side 0: -d neighbour, side 1: +d),
     // one direction at a time so that the line stride is a constant
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(ApplyCfg<T, N1>::THREADS, ApplyCfg<T, N1>::MIN
       const long long b0 = sbase[sl];
       if (b0 >= 0) {
         const long long gi = b0 + loc;
-        const T Au = sacc[sl][loc];
+        const T Au = sacc[sl][ApplyPad<N1>::idx(loc)];
         if (MODE == 0) {
           out[gi] = Au;
         } else if (MODE == 1) {
