@@ -125,6 +125,12 @@ typedef struct {
   int32_t nn_use_net;    /* MIXED_LEARNED: 1 (default) starts from the network's guess; 0 from the same
                             guess without the network (the prolongated degree-1 coarse solution, smoothed and
                             scaled), to measure what the network itself adds */
+  int32_t device_loop;   /* PCG iterations driven from the device: 1: each launch of a captured graph runs
+                            iterations in a conditional while-node that tests convergence on the device and
+                            stops when a source converges, after which the host drops it and launches the
+                            continuation (one host round trip per convergence event, results bit-identical
+                            to 0); 0: two graph launches and one host read of the residual norms per
+                            iteration; 2 (default): 1 for batches of at most 2^24 unknowns, else 0 */
 } dg_solver_opts;
 
 typedef struct {

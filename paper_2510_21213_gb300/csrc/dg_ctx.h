@@ -2,6 +2,8 @@
 // shared by the host driver and the allocation-free entry point.
 #pragma once
 
+#include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -104,12 +106,33 @@ struct PhaseGraph {
   }
 };
 
+// PCG iterations captured as one graph: the first iteration (variant 0) or
+// the preconditioner phase that continues an interrupted solve (variant 1),
+// then a conditional while-node whose body runs the preconditioner phase, the
+// next operator phase and the device-side convergence test. The loop stops
+// when a source converges (so that the host can drop it from the batch), when
+// none is left, or at the iteration limit. Valid for one active source count
+// and one generation of the workspace buffers; the tolerances and the limit
+// are read from device memory.
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long gen = -1;
+  long long nk_first = 0, nk_body = 0;  // kernels before the loop and of the loop body
+  LoopGraph() = default;
+  LoopGraph(const LoopGraph&) = delete;
+  LoopGraph& operator=(const LoopGraph&) = delete;
+  ~LoopGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
 template <typename T>
 struct PrecWork {
   std::vector<LevelWork> lev;            // per level (level 0: res, d, invD only)
   DevBuf x, r, z, p, q;                  // CG vectors on the fine level
   int cap = 0;
   PhaseGraph gA, gB;                     // captured PCG phases (operator / preconditioner)
+  std::map<std::pair<int, int>, std::unique_ptr<LoopGraph>> gL;  // device-side loops by (variant, sources)
 };
 
 struct Level {
@@ -171,6 +194,7 @@ struct dg_ctx {
   dg::DevBuf f64, b64, x64, r64;   // [cap][Nq]
   dg::DevBuf flex, T1, T2, g;      // boundary data
   dg::DevBuf part, scal, act, flags, pidx;
+  dg::DevBuf loop;  // device-side PCG loop state: done[cap], iters[cap], counter, limit, tol[cap], relres[cap]
   dg::DevBuf tc_err;               // device word: a tensor-core kernel's wait gave up (DG_ERR_TIMEOUT)
   dg::DevBuf Wacc, kpart, Kdev;
   int cap = 0;

@@ -75,6 +75,17 @@ int ensure_prec(dg_ctx* h, PrecWork<T>& w, int cap) {
 template int ensure_prec<double>(dg_ctx*, PrecWork<double>&, int);
 template int ensure_prec<float>(dg_ctx*, PrecWork<float>&, int);
 
+// layout of the device-side loop state: done[cap], iters[cap], counter, limit, then
+// (8-byte aligned) tol[cap], relres[cap]
+static size_t loop_ints(int cap) { return ((size_t)2 * cap + 2 + 1) / 2 * 2; }
+size_t loop_bytes(int cap) { return sizeof(int) * loop_ints(cap) + sizeof(double) * 2 * (size_t)cap; }
+static int* loop_done(dg_ctx* h) { return h->loop.as<int>(); }
+static int* loop_iters(dg_ctx* h) { return h->loop.as<int>() + h->cap; }
+static int* loop_counter(dg_ctx* h) { return h->loop.as<int>() + 2 * h->cap; }
+static int* loop_limit(dg_ctx* h) { return h->loop.as<int>() + 2 * h->cap + 1; }
+static double* loop_tol(dg_ctx* h) { return (double*)(h->loop.as<int>() + loop_ints(h->cap)); }
+static double* loop_relres(dg_ctx* h) { return loop_tol(h) + h->cap; }
+
 int ensure_common(dg_ctx* h, int cap) {
   if (h->cap >= cap) return DG_OK;
   DeviceWideGuard guard;
@@ -89,6 +100,7 @@ int ensure_common(dg_ctx* h, int cap) {
   DG_CK(h->act.ensure(sizeof(int) * cap));
   h->act_host.clear();
   DG_CK(h->flags.ensure(sizeof(int) * cap));
+  DG_CK(h->loop.ensure(loop_bytes(cap)));
   DG_CK(h->pidx.ensure(sizeof(int) * 2 * cap));
   DG_CK(h->g.ensure(sizeof(double) * h->nface * cap));
   h->cap = cap;
@@ -155,6 +167,57 @@ __global__ void k_copy_slot(const double* src, double* dst, const int* act, int 
   if (k < nact) dst[act[k]] = src[act[k]];
 }
 
+// k_ratio for the device-side loop: a source marked done takes a zero step
+__global__ void k_ratio_masked(const double* num, const double* den, double* out, const int* act, int nact,
+                               int* flags, int check, const int* done) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nact) return;
+  const int r = act[k];
+  if (done[r]) {
+    out[r] = 0.0;
+    return;
+  }
+  const double dn = den[r];
+  if (!(dn > 0.0) || !isfinite(dn) || !isfinite(num[r])) {
+    out[r] = 0.0;
+    if (check) flags[r] |= 2;
+  } else {
+    out[r] = num[r] / dn;
+  }
+}
+
+// Device-side convergence test after the operator phase of an iteration (one
+// block): every source not yet done records the iteration and its relative
+// residual and is done once that meets its tolerance (or is not finite). The
+// loop goes on while no source became done in this test, some are left and the
+// iteration limit is not reached.
+__global__ void k_pcg_check(const double* rr, const double* bn, const double* tol, const int* act, int nact,
+                            int* done, int* iters, double* relres, int* counter, const int* limit,
+                            cudaGraphConditionalHandle hnd) {
+  const int it = *counter + 1;
+  const int maxit = *limit;
+  int left = 0, now = 0;
+  for (int k = threadIdx.x; k < nact; k += blockDim.x) {
+    const int r = act[k];
+    if (done[r]) continue;
+    iters[r] = it;
+    const double rel = sqrt(fmax(rr[r], 0.0) / bn[r]);
+    relres[r] = rel;
+    if (!(rel <= tol[r]) && isfinite(rel)) {
+      left = 1;
+    } else {
+      done[r] = 1;
+      now = 1;
+    }
+  }
+  left = __syncthreads_or(left);
+  now = __syncthreads_or(now);
+  if (threadIdx.x == 0) {
+    *counter = it;
+    cudaGraphSetConditional(hnd, (left && !now && it < maxit) ? 1u : 0u);
+  }
+}
+
 // Active source list on the device; re-uploaded only when it changes.
 int upload_act(dg_ctx* h, const std::vector<int>& a, cudaStream_t s) {
   if (a.empty()) return DG_OK;
@@ -181,14 +244,13 @@ static int run_phase(dg_ctx* h, PhaseGraph& g, int nact, cudaStream_t s, F&& bod
     g.exec = nullptr;
   }
   CaptureGuard cap_guard;  // no device-wide operation of another thread during the capture
-  const long long l0 = g_launch_count.load();
+  const long long l0 = t_launch_count;
   DG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   const int rc = body();
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(s, &graph);
   // kernels counted while capturing did not run; they are counted at replay
-  const long long nk = g_launch_count.load() - l0;
-  g_launch_count.fetch_sub(nk);
+  const long long nk = uncount_captured(l0);
   if (rc != DG_OK) {
     if (graph) cudaGraphDestroy(graph);
     return rc;
@@ -272,6 +334,139 @@ static int pcg(dg_ctx* h, PrecWork<T>& w, const std::vector<int>& act0, const st
     DG_CK(launch_cg_p<T>(p, z, scal(h, S_BE), Nq, dact, nact, s));
     return DG_OK;
   };
+  // device-side loop: always (1), or (2, the default) where an iteration is
+  // short enough for the host round trip to matter (at most 2^24 unknowns in
+  // the batch)
+  const bool dev_loop =
+      h->opts.device_loop == 1 || (h->opts.device_loop == 2 && (long long)Nq * nact <= (1LL << 24));
+  if (h->use_graphs && s != nullptr && dev_loop) {
+    // iterations in graph launches with a device-side loop: each launch runs
+    // until a source converges, then the host drops the converged sources and
+    // launches the continuation for the others
+    int* done = loop_done(h);
+    const std::vector<double> tolv(tol.begin(), tol.begin() + h->cap);
+    DG_CK(cudaMemcpyAsync(loop_tol(h), tolv.data(), sizeof(double) * h->cap, cudaMemcpyHostToDevice, s));
+    DG_CK(cudaMemsetAsync(done, 0, sizeof(int) * h->cap, s));
+    const int lim[2] = {0, maxit};  // counter, iteration limit
+    DG_CK(cudaMemcpyAsync(loop_counter(h), lim, sizeof(lim), cudaMemcpyHostToDevice, s));
+    auto phaseAm = [&]() -> int {
+      DG_CK(launch_apply<T>(h->levels[0].op, h->levels[0].dop, 0, p, q, nullptr, dact, nact, s));
+      DG_CK(launch_dot<T>(p, q, nullptr, scal(h, S_PQ), part, Nq, dact, nact, s));
+      count_launch();
+      k_ratio_masked<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZ), scal(h, S_PQ), scal(h, S_AL), dact, nact,
+                                                         flags, 1, done);
+      DG_CK(launch_cg_xr<T>(x, r, p, q, scal(h, S_AL), Nq, dact, nact, s));
+      DG_CK(launch_dot<T>(r, r, nullptr, scal(h, S_RR), part, Nq, dact, nact, s));
+      return DG_OK;
+    };
+    auto phaseBm = [&]() -> int {
+      DG_RET(mg.vcycle(0, r, z));
+      DG_CK(launch_dot<T>(r, z, nullptr, scal(h, S_RZN), part, Nq, dact, nact, s));
+      count_launch();
+      k_ratio_masked<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), scal(h, S_BE), dact, nact,
+                                                         flags, 0, done);
+      count_launch();
+      k_copy_slot<<<(nact + 127) / 128, 128, 0, s>>>(scal(h, S_RZN), scal(h, S_RZ), dact, nact);
+      DG_CK(launch_cg_p<T>(p, z, scal(h, S_BE), Nq, dact, nact, s));
+      return DG_OK;
+    };
+    std::vector<int> ibuf(2 * (size_t)h->cap + 1);
+    std::vector<double> rel(h->cap);
+    for (int variant = 0;; variant = 1) {
+      std::unique_ptr<LoopGraph>& slot = w.gL[{variant, nact}];
+      if (!slot || slot->gen != h->buf_gen) {
+        slot.reset(new LoopGraph());
+        LoopGraph& L = *slot;
+        CaptureGuard cap_guard;  // no device-wide operation of another thread during the capture
+        cudaGraph_t g = nullptr;
+        DG_CK(cudaGraphCreate(&g, 0));
+        struct GraphOwner {
+          cudaGraph_t g;
+          ~GraphOwner() {
+            if (g) cudaGraphDestroy(g);
+          }
+        } owner{g};
+        cudaGraphConditionalHandle hnd;
+        DG_CK(cudaGraphConditionalHandleCreate(&hnd, g, 1, cudaGraphCondAssignDefault));
+        auto check = [&]() -> int {
+          count_launch();
+          k_pcg_check<<<1, 256, 0, s>>>(scal(h, S_RR), scal(h, S_BN), loop_tol(h), dact, nact, done,
+                                        loop_iters(h), loop_relres(h), loop_counter(h), loop_limit(h), hnd);
+          DG_CK(cudaGetLastError());
+          return DG_OK;
+        };
+        // before the loop: the first operator phase (variant 0) or the
+        // preconditioner phase and the next operator phase (variant 1)
+        const long long l0 = t_launch_count;
+        DG_CK(cudaStreamBeginCaptureToGraph(s, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        int rc = variant == 0 ? DG_OK : phaseBm();
+        if (rc == DG_OK) rc = phaseAm();
+        if (rc == DG_OK) rc = check();
+        std::vector<cudaGraphNode_t> sink;
+        {
+          cudaStreamCaptureStatus cst;
+          const cudaGraphNode_t* deps = nullptr;
+          size_t nd = 0;
+          if (cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess && deps)
+            sink.assign(deps, deps + nd);
+        }
+        cudaGraph_t g_out = nullptr;
+        const cudaError_t e1 = cudaStreamEndCapture(s, &g_out);
+        const long long nk_first = uncount_captured(l0);  // counted at replay
+        if (rc != DG_OK) {
+          slot.reset();
+          return rc;
+        }
+        DG_CK(e1);
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hnd;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cnode;
+        DG_CK(cudaGraphAddNode(&cnode, g, sink.data(), nullptr, sink.size(), &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        const long long l1 = t_launch_count;
+        DG_CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        rc = phaseBm();
+        if (rc == DG_OK) rc = phaseAm();
+        if (rc == DG_OK) rc = check();
+        cudaGraph_t b_out = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &b_out);
+        const long long nk_body = uncount_captured(l1);
+        if (rc != DG_OK) {
+          slot.reset();
+          return rc;
+        }
+        DG_CK(e2);
+        DG_CK(cudaGraphInstantiate(&L.exec, g, 0));
+        L.gen = h->buf_gen;
+        L.nk_first = nk_first;
+        L.nk_body = nk_body;
+      }
+      const int it0 = variant == 0 ? 0 : ibuf[2 * (size_t)h->cap];
+      DG_CK(cudaGraphLaunch(slot->exec, s));
+      DG_CK(cudaMemcpyAsync(ibuf.data(), h->loop.p, sizeof(int) * ibuf.size(), cudaMemcpyDeviceToHost, s));
+      DG_CK(cudaMemcpyAsync(rel.data(), loop_relres(h), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
+      DG_CK(cudaStreamSynchronize(s));
+      const int nit = ibuf[2 * (size_t)h->cap];
+      count_launch((int)(slot->nk_first + (long long)std::max(0, nit - it0 - 1) * slot->nk_body));
+      std::vector<int> a2;
+      for (int k : act) {
+        iters[k] = ibuf[(size_t)h->cap + k];
+        relres[k] = rel[k];
+        if (!ibuf[k]) a2.push_back(k);
+      }
+      if (a2.empty() || nit >= maxit) break;
+      if (a2.size() != act.size()) {
+        act = a2;
+        nact = (int)act.size();
+        DG_RET(upload_act(h, act, s));
+        mg.nact = nact;
+      }
+    }
+    return DG_OK;
+  }
   for (int it = 1; it <= maxit; ++it) {
     DG_RET(run_phase(h, w.gA, nact, s, phaseA));
     DG_CK(cudaMemcpyAsync(rr.data(), scal(h, S_RR), sizeof(double) * h->cap, cudaMemcpyDeviceToHost, s));
@@ -884,6 +1079,7 @@ static int setup(dg_ctx* h) {
 
 namespace dg {
 std::atomic<long long> g_launch_count{0};
+thread_local long long t_launch_count = 0;
 
 template <typename T>
 static int apply_smoother_t(dg_ctx* h, PrecWork<T>& w, int level, const T* r, T* z, int nb, cudaStream_t s) {
@@ -933,6 +1129,7 @@ void dg_default_opts(dg_solver_opts* o) {
   o->gauss_construction = 0;
   o->tc_smoother = 1;
   o->nn_use_net = 1;
+  o->device_loop = 2;
 }
 
 const char* dg_error_string(int status) {
@@ -974,7 +1171,7 @@ int dg_poisson_setup(const dg_mesh_desc* mesh, const dg_solver_opts* opts, dg_ha
       (o.smoother != DG_SMOOTH_JACOBI && o.smoother != DG_SMOOTH_SCHWARZ) ||
       (o.coarse_penalty != 0 && o.coarse_penalty != 1) || o.coarse_smoother_degree < 0 ||
       o.coarse_smoother_degree > 16 || o.p1_smoother < -1 || o.p1_smoother > 1 ||
-      (o.gauss_construction != 0 && o.gauss_construction != 1))
+      (o.gauss_construction != 0 && o.gauss_construction != 1) || o.device_loop < 0 || o.device_loop > 2)
     return DG_ERR_INVALID_ARG;
   if (o.cheb_range <= 1.0) o.cheb_range = 10.0;
   if (o.inner_rtol <= 0.0) o.inner_rtol = 1e-4;

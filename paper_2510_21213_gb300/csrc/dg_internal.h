@@ -23,9 +23,23 @@
 
 namespace dg {
 
-// kernels launched by this library in this process (profiling / benchmark evidence)
+// kernels launched by this library in this process (profiling / benchmark
+// evidence), and by the calling thread (so that a thread capturing a graph can
+// take back exactly the launches it recorded, while other threads launch)
 extern std::atomic<long long> g_launch_count;
-inline void count_launch(int n = 1) { g_launch_count.fetch_add(n, std::memory_order_relaxed); }
+extern thread_local long long t_launch_count;
+inline void count_launch(int n = 1) {
+  g_launch_count.fetch_add(n, std::memory_order_relaxed);
+  t_launch_count += n;
+}
+// launches recorded by this thread since `since` (a t_launch_count value) are
+// removed from the process count: captured kernels are counted when replayed
+inline long long uncount_captured(long long since) {
+  const long long n = t_launch_count - since;
+  g_launch_count.fetch_sub(n, std::memory_order_relaxed);
+  t_launch_count = since;
+  return n;
+}
 
 constexpr int MAXN1 = 9;    // p <= 8
 constexpr int MAXLEV = 16;

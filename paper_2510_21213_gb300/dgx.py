@@ -62,6 +62,7 @@ class dg_solver_opts(C.Structure):
         ("gauss_construction", C.c_int32),
         ("tc_smoother", C.c_int32),
         ("nn_use_net", C.c_int32),
+        ("device_loop", C.c_int32),
     ]
 
 

@@ -44,3 +44,18 @@ def test_binding_loads_and_error_strings():
     assert lib.dg_error_string(-3) == b"not converged"
     o = dgx.dg_default_opts()
     assert o.rtol == pytest.approx(1e-8) and o.penalty_eps == pytest.approx(0.125) and o.smoother_degree == 4 and o.smoother == 1
+
+
+def test_options_are_checked_before_any_device_work():
+    """dg_poisson_setup refuses out-of-range options on the host (no GPU
+    needed): the device-loop switch takes 0, 1 or 2 (2, adaptive, by default)."""
+    from paper_2510_21213_gb300 import dgx
+
+    lib = dgx.load()
+    C = dgx.C
+    assert dgx.dg_default_opts().device_loop == 2
+    desc = dgx.dg_mesh_desc((C.c_double * 3)(-1, -1, -1), (C.c_double * 3)(1, 1, 1), (C.c_int32 * 3)(2, 2, 2), 2)
+    for bad in (-1, 3):
+        o = dgx.dg_default_opts(device_loop=bad)
+        h = C.c_void_p()
+        assert lib.dg_poisson_setup(C.byref(desc), C.byref(o), C.byref(h)) == dgx.DG_ERR_INVALID_ARG and not h.value
