@@ -294,17 +294,23 @@ struct GatherCfg {
 };
 
 // mode 0: z = M r; 1: d = c1 M r, x = d; 2: d = c1 M r, x += d; 3: d = c1 d + c2 M r, x += d
-// (d is passed in z). GE elements per block and iteration (grid-stride), one thread per node.
+// (d is passed in z). GE elements per block and iteration (grid-stride), one thread per node,
+// GS sources per thread (the node's position, neighbour tests and offsets shared by them).
+#ifndef DG_GATHER_SOURCES
+#define DG_GATHER_SOURCES 4
+#endif
 template <typename T, int N1, int MODE>
 __global__ void __launch_bounds__(GatherCfg<N1>::THREADS)
     k_schwarz_gather(const LevelOp* __restrict__ op, const T* __restrict__ zp, T* __restrict__ z, T* __restrict__ x,
-                     T c1, T c2, const int* __restrict__ act) {
-  constexpr int MP = N1 + 2, MP3 = MP * MP * MP, NPE = N1 * N1 * N1, GE = GatherCfg<N1>::GE;
+                     T c1, T c2, const int* __restrict__ act, int nact) {
+  constexpr int MP = N1 + 2, MP2 = MP * MP, MP3 = MP2 * MP, NPE = N1 * N1 * N1, GE = GatherCfg<N1>::GE;
+  constexpr int GS = DG_GATHER_SOURCES;
   const int nx = op->n[0], ny = op->n[1], nz = op->n[2];
   const int E = op->E;
   const long long Nq = op->Nq;
-  const long long rhs = act[blockIdx.y];
-  const T* zr = zp + rhs * E * (long long)MP3;
+  // this block's sources (GS consecutive entries of the active list)
+  const int k0 = blockIdx.y * GS;
+  const int ns = min(GS, nact - k0);
   const int slot = threadIdx.x / NPE, loc = threadIdx.x % NPE;
   const int a = loc % N1, bb = (loc / N1) % N1, c = loc / (N1 * N1);
   // element position, advanced by the grid stride without runtime divisions
@@ -333,29 +339,47 @@ __global__ void __launch_bounds__(GatherCfg<N1>::THREADS)
     } else if (c == N1 - 1 && ez < nz - 1) {
       dz = nx * ny;
     }
-    T acc = zr[(long long)e * MP3 + ix + MP * (iy + MP * iz)];
-    if (dx) acc += zr[(long long)(e + dx) * MP3 + jx + MP * (iy + MP * iz)];
-    if (dy) acc += zr[(long long)(e + dy) * MP3 + ix + MP * (jy + MP * iz)];
-    if (dz) acc += zr[(long long)(e + dz) * MP3 + ix + MP * (iy + MP * jz)];
-    if (dx && dy) acc += zr[(long long)(e + dx + dy) * MP3 + jx + MP * (jy + MP * iz)];
-    if (dx && dz) acc += zr[(long long)(e + dx + dz) * MP3 + jx + MP * (iy + MP * jz)];
-    if (dy && dz) acc += zr[(long long)(e + dy + dz) * MP3 + ix + MP * (jy + MP * jz)];
-    if (dx && dy && dz) acc += zr[(long long)(e + dx + dy + dz) * MP3 + jx + MP * (jy + MP * jz)];
-    const long long gi = rhs * Nq + (long long)e * NPE + loc;
-    if (MODE == 0) {
-      z[gi] = acc;
-    } else if (MODE == 1) {
-      const T v = c1 * acc;
-      z[gi] = v;
-      x[gi] = v;
-    } else if (MODE == 2) {
-      const T v = c1 * acc;
-      z[gi] = v;
-      x[gi] += v;
-    } else {
-      const T v = c1 * z[gi] + c2 * acc;
-      z[gi] = v;
-      x[gi] += v;
+    // offsets (values, within one source's patch buffer) of every contribution;
+    // a source's patch buffer holds E MP^3 < 2^31 values
+    const int o0 = e * MP3 + ix + MP * iy + MP2 * iz;
+    const int ox = (e + dx) * MP3 + jx + MP * iy + MP2 * iz;
+    const int oy = (e + dy) * MP3 + ix + MP * jy + MP2 * iz;
+    const int oz = (e + dz) * MP3 + ix + MP * iy + MP2 * jz;
+    const int oxy = (e + dx + dy) * MP3 + jx + MP * jy + MP2 * iz;
+    const int oxz = (e + dx + dz) * MP3 + jx + MP * iy + MP2 * jz;
+    const int oyz = (e + dy + dz) * MP3 + ix + MP * jy + MP2 * jz;
+    const int oxyz = (e + dx + dy + dz) * MP3 + jx + MP * jy + MP2 * jz;
+    const int gi = e * NPE + loc;
+#pragma unroll
+    for (int j = 0; j < GS; ++j) {
+      if (j >= ns) break;
+      const long long rhs = act[k0 + j];
+      const T* zs = zp + rhs * E * (long long)MP3;
+      T* zg = z + rhs * Nq;
+      T* xg = x + rhs * Nq;
+      T acc = zs[o0];
+      if (dx) acc += zs[ox];
+      if (dy) acc += zs[oy];
+      if (dz) acc += zs[oz];
+      if (dx && dy) acc += zs[oxy];
+      if (dx && dz) acc += zs[oxz];
+      if (dy && dz) acc += zs[oyz];
+      if (dx && dy && dz) acc += zs[oxyz];
+      if (MODE == 0) {
+        zg[gi] = acc;
+      } else if (MODE == 1) {
+        const T v = c1 * acc;
+        zg[gi] = v;
+        xg[gi] = v;
+      } else if (MODE == 2) {
+        const T v = c1 * acc;
+        zg[gi] = v;
+        xg[gi] += v;
+      } else {
+        const T v = c1 * zg[gi] + c2 * acc;
+        zg[gi] = v;
+        xg[gi] += v;
+      }
     }
     ex += sx;
     int carry = ex >= nx;
@@ -389,18 +413,21 @@ static cudaError_t schwarz_n1(const LevelOp& hop, const LevelOp* dop, const doub
                                                                                            nact);
   }
   constexpr int GT = GatherCfg<N1>::THREADS;
+  // the gather indexes one source's patch buffer with 32-bit offsets
+  if ((long long)hop.E * (N1 + 2) * (N1 + 2) * (N1 + 2) >= (1LL << 31)) return cudaErrorInvalidValue;
   long long gx = (hop.E + GatherCfg<N1>::GE - 1) / GatherCfg<N1>::GE;
 #if DG_GATHER_WAVE > 0
-  const long long cap = 152LL * DG_GATHER_WAVE / (nact > 0 ? nact : 1) + 1;
+  const long long ngroups = (nact + DG_GATHER_SOURCES - 1) / DG_GATHER_SOURCES;
+  const long long cap = 152LL * DG_GATHER_WAVE / (ngroups > 0 ? ngroups : 1) + 1;
   if (gx > cap) gx = cap;
 #endif
-  const dim3 grid((unsigned)gx, (unsigned)nact);
+  const dim3 grid((unsigned)gx, (unsigned)((nact + DG_GATHER_SOURCES - 1) / DG_GATHER_SOURCES));
   count_launch();
   switch (mode) {
-    case 0: k_schwarz_gather<T, N1, 0><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
-    case 1: k_schwarz_gather<T, N1, 1><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
-    case 2: k_schwarz_gather<T, N1, 2><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
-    default: k_schwarz_gather<T, N1, 3><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act); break;
+    case 0: k_schwarz_gather<T, N1, 0><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act, nact); break;
+    case 1: k_schwarz_gather<T, N1, 1><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act, nact); break;
+    case 2: k_schwarz_gather<T, N1, 2><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act, nact); break;
+    default: k_schwarz_gather<T, N1, 3><<<grid, GT, 0, s>>>(dop, zp, z, x, (T)c1, (T)c2, act, nact); break;
   }
   return cudaGetLastError();
 }
