@@ -49,6 +49,20 @@ inline float host_tf32(float x) {
 
 }  // namespace
 
+// K slot of patch node (j, l) in the residual operand of the n1 = 8 kernel,
+// for an x position class with left overlap oLx and mx patch nodes: own
+// x-node a = l - oLx of row j at 8 j + a (two 16-byte groups per row, filled
+// by 16-byte copies of the element row), the left / right x-halo node of row
+// j at 8 MP + 2 j + 0 / 1; -1 for a node outside the patch
+int swtc_fill_k(int j, int l, int oLx, int mx) {
+  constexpr int N1 = 8, MP = N1 + 2;
+  const int a = l - oLx;
+  if (a >= 0 && a < N1) return N1 * j + a;
+  if (l == 0 && oLx == 1) return N1 * MP + 2 * j;
+  if (l == oLx + N1 && l < mx) return N1 * MP + 2 * j + 1;
+  return -1;
+}
+
 bool swtc_geometry(int n1, SwTcGeom& g, int np) {
   g.mp = n1 + 2;
   const int mp2 = g.mp * g.mp;
@@ -65,7 +79,10 @@ bool swtc_geometry(int n1, SwTcGeom& g, int np) {
   g.np = np > 0 ? np : np_max;
   g.ncol = (g.np * SWTC_CS + 15) / 16 * 16;
   g.b_bytes = (g.ncol / 8) * g.sbo;
-  return 2 * (size_t)g.a_bytes + SWTC_BSLOTS * (size_t)g.b_bytes + sizeof(SwTcShared) <= 232448 &&
+  // the static shared memory counts in whole kilobytes (the dynamic part is
+  // 1024-byte aligned after it)
+  const size_t stat = (sizeof(SwTcShared) + 1023) / 1024 * 1024;
+  return 2 * (size_t)g.a_bytes + SWTC_BSLOTS * (size_t)g.b_bytes + stat <= 232448 &&
          g.np <= SWTC_NPMAX && SWTC_DSLOTS * g.ncol <= SWTC_TMEM_COLS;
 }
 
@@ -97,7 +114,7 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
       }
       cls[d][e] = c;
     }
-    if ((int)rep[d].size() > SWTC_MAXCLS) return {};
+    if ((int)rep[d].size() > (d == 2 ? SWTC_MAXZCLS : SWTC_MAXCLS)) return {};
     off += (size_t)L.n[d] * STR;
   }
   if (L.n[0] * L.n[1] > SWTC_MAXCOLS || L.n[2] > SWTC_MAXNZ) return {};
@@ -153,12 +170,17 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
   std::memcpy(blob.data() + H.off_cols, cols.data(), sizeof(int) * cols.size());
   std::memcpy(blob.data() + H.off_zcls, cls[2], sizeof(int) * L.n[2]);
   float* zt = (float*)(blob.data() + H.off_z);
+  const int MPP = SWTC_MPP(MP);
   for (int c = 0; c < ncz; ++c) {
     const double* t = tab(2, rep[2][c]);
     float* o = zt + (size_t)c * SWTC_ZSTR(MP);
-    for (int i = 0; i < MP * MP; ++i) o[i] = (float)t[2 + i];
-    for (int k = 0; k < MP; ++k) o[MP * MP + k] = (float)t[2 + MP * MP + k];
-    o[MP * MP + MP] = (float)t[0];
+    for (int a = 0; a < MP; ++a)
+      for (int k = 0; k < MP; ++k) {
+        o[a * MPP + k] = (float)t[2 + a * MP + k];
+        o[MP * MPP + k * MPP + a] = (float)t[2 + a * MP + k];
+      }
+    for (int k = 0; k < MP; ++k) o[2 * MP * MPP + k] = (float)t[2 + MP * MP + k];
+    o[2 * MP * MPP + MPP] = (float)t[0];
   }
   float* xy = (float*)(blob.data() + H.off_xy);
   for (int d = 0; d < 2; ++d)
@@ -169,21 +191,27 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
       o[MP] = (float)t[0];
     }
   // Kronecker factors per segment: forward (rows = modes (j',l'), K = nodes
-  // (j,l)) and inverse (rows = nodes, K = modes), value Sy[j][j'] Sx[l][l']
+  // (j,l)) and inverse (rows = nodes, K = modes), value Sy[j][j'] Sx[l][l'].
+  // At n1 = 8 the forward factor's K order is the one the residual fill
+  // writes (swtc_fill_k): each patch row's own x-nodes as two aligned 16-byte
+  // groups, the x-halo nodes after all rows.
   for (int s = 0; s < H.nseg; ++s) {
     const double* tx = tab(0, rep[0][H.seg_cx[s]]);
     const double* ty = tab(1, rep[1][H.seg_cy[s]]);
+    const int oLx = (int)tx[1], mx = (int)tx[0];
     unsigned char* af = blob.data() + H.off_a + (size_t)s * 2 * g.a_bytes;
     unsigned char* ai = af + g.a_bytes;
     for (int j = 0; j < MP; ++j)
-      for (int l = 0; l < MP; ++l)
+      for (int l = 0; l < MP; ++l) {
+        const int kf = L.n1 == 8 && DG_SWTC_ROWFILL ? swtc_fill_k(j, l, oLx, mx) : j * MP + l;
         for (int jp = 0; jp < MP; ++jp)
           for (int lp = 0; lp < MP; ++lp) {
             const float v = host_tf32((float)(ty[2 + j * MP + jp] * tx[2 + l * MP + lp]));
             const int node = j * MP + l, mode = jp * MP + lp;
-            std::memcpy(af + opnd_off(mode, node, g.sbo), &v, 4);
+            if (kf >= 0) std::memcpy(af + opnd_off(mode, kf, g.sbo), &v, 4);
             std::memcpy(ai + opnd_off(node, mode, g.sbo), &v, 4);
           }
+      }
   }
   std::memcpy(blob.data(), &H, sizeof(H));
   return blob;
@@ -208,10 +236,11 @@ __device__ __forceinline__ bool swtc_wait(SwTcShared& sh, const SwTcHead* H, uns
 }
 
 template <int N1>
-__global__ void __launch_bounds__(SWTC_THREADS, 1)
+__global__ void __launch_bounds__(swtc_threads(N1), 1)
     k_schwarz_patch_tc(const LevelOp* __restrict__ op, const unsigned char* __restrict__ blob, const SwTcGeom geom,
                        const float* __restrict__ r, float* __restrict__ zp, const int* __restrict__ act, int nact) {
-  constexpr int MP = N1 + 2, MP2 = MP * MP, MP3 = MP2 * MP, NPE = N1 * N1 * N1;
+  constexpr int MP = N1 + 2, MP2 = MP * MP, MP3 = MP2 * MP, NPE = N1 * N1 * N1, MPP = SWTC_MPP(MP);
+  constexpr int CONS = swtc_consumers(N1), THREADS = swtc_threads(N1), NPAR = CONS / 128;
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ SwTcShared sh;
   const SwTcHead* H = (const SwTcHead*)blob;
@@ -229,12 +258,12 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
   if (tid == 0) {
     for (int b = 0; b < SWTC_BSLOTS; ++b) {
       tc::mbar_init(tc::smem_addr(&sh.full[b]), SWTC_PRODUCERS);
-      tc::mbar_init(tc::smem_addr(&sh.b2[b]), SWTC_CONSUMERS);
+      tc::mbar_init(tc::smem_addr(&sh.b2[b]), CONS);
     }
     for (int d = 0; d < SWTC_DSLOTS; ++d) {
       tc::mbar_init(tc::smem_addr(&sh.d1[d]), 1);
       tc::mbar_init(tc::smem_addr(&sh.d2[d]), 1);
-      tc::mbar_init(tc::smem_addr(&sh.empty[d]), SWTC_CONSUMERS);
+      tc::mbar_init(tc::smem_addr(&sh.empty[d]), CONS);
     }
     tc::mbar_init(tc::smem_addr(&sh.tma_f), 1);
     tc::mbar_init(tc::smem_addr(&sh.tma_i), 1);
@@ -250,26 +279,26 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
   if (warp == 0) tc::tmem_alloc(&sh.tmem, SWTC_TMEM_COLS);
   {
     const float* zt = (const float*)(blob + H->off_z);
-    for (int i = tid; i < H->ncz * SWTC_ZSTR(MP); i += SWTC_THREADS) sh.z[i] = zt[i];
-    for (int i = tid; i < nseg; i += SWTC_THREADS) {
+    for (int i = tid; i < H->ncz * SWTC_ZSTR(MP); i += THREADS) sh.z[i] = zt[i];
+    for (int i = tid; i < nseg; i += THREADS) {
       sh.seg_col0[i] = H->seg_col0[i];
       sh.seg_ncol[i] = H->seg_ncol[i];
       sh.seg_cx[i] = (unsigned char)H->seg_cx[i];
       sh.seg_cy[i] = (unsigned char)H->seg_cy[i];
     }
     const int* cols = (const int*)(blob + H->off_cols);
-    for (int i = tid; i < nx * ny; i += SWTC_THREADS) sh.cols[i] = make_short2((short)cols[2 * i], (short)cols[2 * i + 1]);
+    for (int i = tid; i < nx * ny; i += THREADS) sh.cols[i] = make_short2((short)cols[2 * i], (short)cols[2 * i + 1]);
     const int* zc = (const int*)(blob + H->off_zcls);
-    for (int i = tid; i < nz; i += SWTC_THREADS) sh.zcls[i] = (unsigned char)zc[i];
-    for (int i = tid; i < nact && i < SWTC_MAXACT; i += SWTC_THREADS) sh.act[i] = (unsigned short)act[i];
+    for (int i = tid; i < nz; i += THREADS) sh.zcls[i] = (unsigned char)zc[i];
+    for (int i = tid; i < nact && i < SWTC_MAXACT; i += THREADS) sh.act[i] = (unsigned short)act[i];
     const float* xy = (const float*)(blob + H->off_xy);
-    for (int i = tid; i < 2 * SWTC_MAXCLS * (MP + 1); i += SWTC_THREADS) {
+    for (int i = tid; i < 2 * SWTC_MAXCLS * (MP + 1); i += THREADS) {
       const int d = i / (SWTC_MAXCLS * (MP + 1)), rem = i % (SWTC_MAXCLS * (MP + 1));
       const int c = rem / (MP + 1), k = rem % (MP + 1);
       if (c < (d == 0 ? H->ncx : H->ncy)) sh.lxy[d][c][k] = xy[(d == 0 ? 0 : H->off_y) + (size_t)c * (MP + 1) + k];
     }
     uint4* b4 = (uint4*)sB0;
-    for (int i = tid; i < SWTC_BSLOTS * b_bytes / 16; i += SWTC_THREADS) b4[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < SWTC_BSLOTS * b_bytes / 16; i += THREADS) b4[i] = make_uint4(0, 0, 0, 0);
   }
   tc::fence_proxy_async();
   tc::fence_before_sync();
@@ -283,10 +312,31 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
   const int first = (int)blockIdx.x * per_cta;
   const int nmine = max(0, min(per_cta, total - first));
 
-  if (tid >= SWTC_CONSUMERS && tid < SWTC_CONSUMERS + SWTC_PRODUCERS) {
+  if (tid >= CONS && tid < CONS + SWTC_PRODUCERS) {
     // ================= producers: decode and fill =================
-    const int L = tid - SWTC_CONSUMERS;  // B column (j, l) this thread fills
+    const int L = tid - CONS;  // B column (j, l) this thread fills (n1 != 8)
     const int jj = L / MP, ll = L % MP;
+    // row fill (n1 = 8): slots (zk, jj, half) L and L + 128 of the 2 MP^2 per
+    // patch, with the y offset of row jj relative to the patch's element for
+    // a patch without (0) and with (1) left overlap along y
+    int f_zk[2], f_j[2], f_h[2], f_own[2], f_halo[2];
+    long long f_yoff[2][2];
+    bool f_ok[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if constexpr (N1 != 8 || !DG_SWTC_ROWFILL) break;
+      const int sl = L + SWTC_PRODUCERS * u;
+      f_ok[u] = sl < 2 * MP2;
+      f_zk[u] = sl / (2 * MP);
+      f_j[u] = (sl % (2 * MP)) >> 1;
+      f_h[u] = sl & 1;
+      const int j = f_j[u], kh = N1 * MP + 2 * j + f_h[u];
+      f_own[u] = (2 * j + f_h[u]) * SWTC_LBO;
+      f_halo[u] = (kh >> 2) * SWTC_LBO + (kh & 3) * 4;
+      f_yoff[u][0] = (long long)(j / N1) * nx * NPE + (j % N1) * N1;
+      f_yoff[u][1] = j == 0 ? -(long long)nx * NPE + (N1 - 1) * N1
+                            : (long long)((j - 1) / N1) * nx * NPE + ((j - 1) % N1) * N1;
+    }
     for (int li = 0; li < nmine; ++li) {
       const int b = li % SWTC_BSLOTS;
       // B slot free once MMA 2 of item li - 2 is done; description slot free
@@ -320,6 +370,18 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
         I.ez[L] = (short)ez;
         I.cz[L] = (short)sh.zcls[ez];
         I.elem[L] = c.x + nx * (c.y + ny * ez);
+        if constexpr (N1 == 8 && DG_SWTC_ROWFILL) {
+          // x-halos shared with the neighbouring patch of the item: the same
+          // source, y and z position and the adjacent x position (patch q - 1
+          // or q + 1 of the same column run)
+          const short2* cs = sh.cols + sh.seg_col0[seg];
+          const bool lsh = L > 0 && colrel > 0 && cs[colrel - 1].x == c.x - 1 && cs[colrel - 1].y == c.y;
+          const bool rsh = L + 1 < np && colrel + 1 < ncs && cs[colrel + 1].x == c.x + 1 && cs[colrel + 1].y == c.y;
+          const int oLy = c.y > 0, my = N1 + oLy + (c.y < ny - 1);
+          I.rbase[L] = (long long)I.src[L] * Nq + (long long)(c.x + nx * c.y) * NPE;
+          I.pf[L] = (unsigned short)(oLy | (my << 1) | (lsh << 6) | (rsh << 7) | ((c.x > 0) << 8) |
+                                     ((c.x < nx - 1) << 9));
+        }
       }
       // z offsets of every (patch, z-node): the same for all (x, y) of the patch
       if (L < np * MP) {
@@ -336,7 +398,58 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       }
       tc::named_barrier(1, SWTC_PRODUCERS);
       unsigned char* sB = sB0 + b * b_bytes;
-      if (L < MP2) {
+      if constexpr (N1 == 8 && DG_SWTC_ROWFILL) {
+        // Residual rows by 16-byte copies: row (zk, jj) of patch i holds its
+        // 8 own x-nodes (one element row, 32 bytes) at K slots 8 jj .. 8 jj + 7
+        // and its x-halo nodes at 8 MP + 2 jj + side (swtc_fill_k). This
+        // thread's slots (zk, jj, half) are fixed: per patch it copies one
+        // half row and the x-halo node on side `half`, unless that node is an
+        // own node of the item's neighbouring patch (copied in shared memory
+        // below). Outside the domain the copies fill zeros. The values land
+        // as FP32 and the tensor core takes their TF32 part.
+#pragma unroll
+        for (int i = 0; i < SWTC_NPMAX; ++i) {
+          if (i < np) {
+            const long long rb = I.rbase[i];
+            const int pf = I.pf[i];
+            const int oLy = pf & 1, my = (pf >> 1) & 15;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (f_ok[u]) {
+                const int zo = I.zoff[i][f_zk[u]];
+                const bool valid = f_j[u] < my && zo >= 0;
+                const long long o = rb + (oLy ? f_yoff[u][1] : f_yoff[u][0]) + zo;
+                const int row = i * SWTC_CS + f_zk[u];
+                unsigned char* rowp = sB + (row >> 3) * sbo + (row & 7) * 16;
+                tc::cp_async16(rowp + f_own[u], valid ? r + o + 4 * f_h[u] : r, valid ? 16 : 0);
+                if (!((pf >> (6 + f_h[u])) & 1)) {
+                  const bool ok_x = valid && ((pf >> (8 + f_h[u])) & 1);
+                  tc::cp_async4(rowp + f_halo[u], ok_x ? r + o + (f_h[u] ? NPE : N1 - 1 - NPE) : r, ok_x ? 4 : 0);
+                }
+              }
+            }
+          }
+        }
+        tc::cp_async_wait_all();
+        tc::named_barrier(1, SWTC_PRODUCERS);
+#pragma unroll
+        for (int i = 0; i < SWTC_NPMAX; ++i) {
+          if (i < np) {
+            const int pf = I.pf[i];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              if (f_ok[u] && ((pf >> (6 + f_h[u])) & 1)) {
+                const int row = i * SWTC_CS + f_zk[u];
+                const int rs = row + (f_h[u] ? SWTC_CS : -SWTC_CS);
+                const int ks = N1 * f_j[u] + (f_h[u] ? 0 : N1 - 1);
+                const float v =
+                    *(const float*)(sB + (rs >> 3) * sbo + (ks >> 2) * SWTC_LBO + (rs & 7) * 16 + (ks & 3) * 4);
+                *(float*)(sB + (row >> 3) * sbo + (row & 7) * 16 + f_halo[u]) = v;
+              }
+            }
+          }
+        }
+      } else if (L < MP2) {
         // this thread's column of B: byte offset of row 0 in its 4-column group.
         // Every value of the item is loaded first (all in flight at once), then
         // rounded to TF32 and stored: coalesced loads, not one-element copies
@@ -374,9 +487,9 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       tc::fence_proxy_async();
       tc::mbar_arrive(tc::smem_addr(&sh.full[b]));
     }
-  } else if (tid >= SWTC_CONSUMERS + SWTC_PRODUCERS) {
+  } else if (tid >= CONS + SWTC_PRODUCERS) {
     // ================= MMA issuer (one thread) =================
-    if (tid == SWTC_CONSUMERS + SWTC_PRODUCERS) {
+    if (tid == CONS + SWTC_PRODUCERS) {
       const uint32_t idesc = tc::idesc_tf32(128, ncol);
       int seg_f = -1, seg_i = -1;
       uint32_t ph_f = 0, ph_i = 0;
@@ -431,15 +544,20 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
     }
   } else {
     // ================= consumers: z-step of item li, output of item li - 1 =================
-    const int L = tid;  // TMEM lane: mode (j', l') for the z-step, node (j, l) for the output
+    // TMEM lane L: mode (j', l') for the z-step, node (j, l) for the output.
+    // With two consumer warps per lane quarter, warp group `par` takes the
+    // item's patches par, par + NPAR, ...
+    const int L = tid & 127, par = tid >> 7;
     const int jj = L / MP, ll = L % MP;
     const bool active = L < MP2;
-    const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
-    float S[MP][MP], inv[MP];
+    const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    constexpr bool SREG = NPAR == 1;  // z factor in registers (one warp per lane quarter)
+    float S[SREG ? MP : 1][SREG ? MP : 1];
+    float inv[MP];
     float lxy = 0.f;
     bool vxy = false;
     int cur_seg = -1, cur_cz = -1;
-    // output of item k: patch node (l, j, k') of each patch
+    // output of item k: patch node (l, j, k') of each of this warp's patches
     auto output = [&](int k) -> bool {
       const int d = k % SWTC_DSLOTS;
       const bool ok = swtc_wait(sh, H, &sh.d2[d], (k / SWTC_DSLOTS) & 1);
@@ -449,13 +567,13 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       const uint32_t tcol = tlane + d * ncol;
       const int np = I.np;
       uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
-      tc::tmem_ld12_async(tcol, nx12);
-      for (int i = 0; i < np; ++i) {
+      if (par < np) tc::tmem_ld12_async(tcol + par * SWTC_CS, nx12);
+      for (int i = par; i < np; i += NPAR) {
         tc::tmem_wait12(nx12);
         float v[SWTC_CS];
 #pragma unroll
         for (int c = 0; c < SWTC_CS; ++c) v[c] = __uint_as_float(nx12[c]);
-        if (i + 1 < np) tc::tmem_ld12_async(tcol + (i + 1) * SWTC_CS, nx12);
+        if (i + NPAR < np) tc::tmem_ld12_async(tcol + (i + NPAR) * SWTC_CS, nx12);
         if (active) {
           // streaming stores: the patch solutions are read once, by the gather,
           // long after; evict-first keeps L2 for the residual rows that
@@ -492,27 +610,30 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
       unsigned char* sB = sB0 + b * b_bytes;
       const uint32_t tcol = tlane + d * ncol;
       // z-step: Sz^T, scaling, Sz along each patch's z line, back into B as TF32
+      // (the z factor's rows from shared memory, 16 bytes at a time)
       uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
-      tc::tmem_ld12_async(tcol, nx12);
-      for (int i = 0; i < np; ++i) {
+      if (par < np) tc::tmem_ld12_async(tcol + par * SWTC_CS, nx12);
+      for (int i = par; i < np; i += NPAR) {
         tc::tmem_wait12(nx12);
         float t[SWTC_CS];
 #pragma unroll
         for (int c = 0; c < SWTC_CS; ++c) t[c] = __uint_as_float(nx12[c]);
-        if (i + 1 < np) tc::tmem_ld12_async(tcol + (i + 1) * SWTC_CS, nx12);
+        if (i + NPAR < np) tc::tmem_ld12_async(tcol + (i + NPAR) * SWTC_CS, nx12);
         const int cz = I.cz[i];
+        const float* zt = sh.z + cz * SWTC_ZSTR(MP);
         if (cz != cur_cz) {
           cur_cz = cz;
-          const float* zt = sh.z + cz * SWTC_ZSTR(MP);
-          const int mzc = (int)zt[MP2 + MP];
+          const int mzc = (int)zt[2 * MP * MPP + MPP];
 #pragma unroll
-          for (int a = 0; a < MP; ++a)
+          for (int c = 0; c < MP; ++c) inv[c] = (vxy && c < mzc) ? 1.0f / (lxy + zt[2 * MP * MPP + c]) : 0.0f;
+          if constexpr (SREG) {
 #pragma unroll
-            for (int c = 0; c < MP; ++c) S[a][c] = zt[a * MP + c];
+            for (int a = 0; a < MP; ++a)
 #pragma unroll
-          for (int c = 0; c < MP; ++c) inv[c] = (vxy && c < mzc) ? 1.0f / (lxy + zt[MP2 + c]) : 0.0f;
+              for (int c = 0; c < MP; ++c) S[a][c] = zt[a * MPP + c];
+          }
         }
-        if (active) {
+        if (active && SREG) {
           // both contractions as MP independent accumulators updated per step
           float u[MP], w[MP];
 #pragma unroll
@@ -529,6 +650,45 @@ __global__ void __launch_bounds__(SWTC_THREADS, 1)
           for (int c = 1; c < MP; ++c)
 #pragma unroll
             for (int a = 0; a < MP; ++a) w[a] = fmaf(S[a][c], u[c], w[a]);
+          unsigned char* col = sB + (L / 4) * SWTC_LBO + (L % 4) * 4;
+#pragma unroll
+          for (int a = 0; a < MP; ++a) {
+            const int row = i * SWTC_CS + a;
+            *(float*)(col + (row >> 3) * sbo + (row & 7) * 16) = tc::to_tf32(w[a]);
+          }
+        } else if (active) {
+          // the same with the z factor's rows read from shared memory
+          float u[MP], w[MP];
+#pragma unroll
+          for (int a = 0; a < MP; ++a) {
+            float s[MPP];
+#pragma unroll
+            for (int q = 0; q < MPP / 4; ++q) {
+              const float4 f = *(const float4*)(zt + a * MPP + 4 * q);
+              s[4 * q] = f.x;
+              s[4 * q + 1] = f.y;
+              s[4 * q + 2] = f.z;
+              s[4 * q + 3] = f.w;
+            }
+#pragma unroll
+            for (int c = 0; c < MP; ++c) u[c] = a == 0 ? s[c] * t[0] : fmaf(s[c], t[a], u[c]);
+          }
+#pragma unroll
+          for (int c = 0; c < MP; ++c) u[c] *= inv[c];
+#pragma unroll
+          for (int c = 0; c < MP; ++c) {
+            float s[MPP];  // row c of Sz^T: Sz[a][c] for every a
+#pragma unroll
+            for (int q = 0; q < MPP / 4; ++q) {
+              const float4 f = *(const float4*)(zt + MP * MPP + c * MPP + 4 * q);
+              s[4 * q] = f.x;
+              s[4 * q + 1] = f.y;
+              s[4 * q + 2] = f.z;
+              s[4 * q + 3] = f.w;
+            }
+#pragma unroll
+            for (int a = 0; a < MP; ++a) w[a] = c == 0 ? s[a] * u[0] : fmaf(s[a], u[c], w[a]);
+          }
           unsigned char* col = sB + (L / 4) * SWTC_LBO + (L % 4) * 4;
 #pragma unroll
           for (int a = 0; a < MP; ++a) {
@@ -563,7 +723,7 @@ static cudaError_t launch_tc_n1(const LevelOp* dop, const unsigned char* blob, c
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(items, nsm));
   count_launch();
-  k_schwarz_patch_tc<N1><<<grid, SWTC_THREADS, smem, s>>>(dop, blob, g, r, zp, act, nact);
+  k_schwarz_patch_tc<N1><<<grid, swtc_threads(N1), smem, s>>>(dop, blob, g, r, zp, act, nact);
   return cudaGetLastError();
 }
 

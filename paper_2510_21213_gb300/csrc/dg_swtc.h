@@ -11,22 +11,42 @@
 namespace dg {
 
 constexpr int SWTC_LBO = 144;        // byte stride of K-adjacent core matrices (128 + 16: conflict-free stores)
-// warp roles: 0-3 consumers (one thread per TMEM lane: z-step and output),
-// 4-7 producers (item decode and the residual fill), 8 the MMA issuer
-constexpr int SWTC_CONSUMERS = 128, SWTC_PRODUCERS = 128;
-constexpr int SWTC_THREADS = SWTC_CONSUMERS + SWTC_PRODUCERS + 32;
+// warp roles: consumers first (one thread per TMEM lane: z-step and output;
+// at n1 = 8 two warps per lane quarter, each taking every other patch of an
+// item), then 4 producer warps (item decode and the residual fill), then the
+// MMA issuer
+// Tuning switches (compile-time; defaults chosen by timing on a GB300):
+// DG_SWTC_ROWFILL: at n1 = 8 fill the residual operand by 16-byte copies of
+// element rows (K order permuted, x-halos shared within an item); 0: one
+// 4-byte load per operand entry, as at the other degrees.
+// DG_SWTC_WIDE: at n1 = 8 two consumer warps per TMEM lane quarter (z factor
+// read from shared memory); 0: one warp per quarter with the z factor in
+// registers.
+#ifndef DG_SWTC_ROWFILL
+#define DG_SWTC_ROWFILL 1
+#endif
+#ifndef DG_SWTC_WIDE
+#define DG_SWTC_WIDE 0
+#endif
+constexpr int SWTC_PRODUCERS = 128;
+__host__ __device__ constexpr int swtc_consumers(int n1) { return n1 == 8 && DG_SWTC_WIDE ? 256 : 128; }
+__host__ __device__ constexpr int swtc_threads(int n1) { return swtc_consumers(n1) + SWTC_PRODUCERS + 32; }
 // rings of the pipeline: B operands in shared memory, FP32 accumulators in
 // tensor memory, item descriptions
 constexpr int SWTC_BSLOTS = 2, SWTC_DSLOTS = 3, SWTC_ISLOTS = 4;
 constexpr int SWTC_TMEM_COLS = 512;  // three accumulators of up to 128 columns
 constexpr int SWTC_MAXCLS = 8;       // position classes per axis
+constexpr int SWTC_MAXZCLS = 5;      // position classes along z (at most 5 on a uniform mesh)
 constexpr int SWTC_MAXSEG = SWTC_MAXCLS * SWTC_MAXCLS;
 constexpr int SWTC_CS = 12;          // B rows / D columns per patch (MP <= 11, padded to a multiple of 4)
 constexpr int SWTC_NPMAX = 10;       // patches per work item
-constexpr int SWTC_MAXCOLS = 1024;   // element columns (nx * ny) staged in shared memory
+constexpr int SWTC_MAXCOLS = 768;    // element columns (nx * ny) staged in shared memory
 constexpr int SWTC_MAXNZ = 256;      // elements along z
 constexpr int SWTC_MAXACT = 256;     // active sources staged in shared memory (more are read from global)
-#define SWTC_ZSTR(MP) ((MP) * (MP) + (MP) + 1)  // floats per z class: S, lambda, m
+// floats per z class: S and S^T with rows padded to a multiple of 4 (16-byte
+// row loads), lambda (padded), m
+#define SWTC_MPP(MP) (((MP) + 3) / 4 * 4)
+#define SWTC_ZSTR(MP) (2 * (MP) * SWTC_MPP(MP) + SWTC_MPP(MP) + 4)
 
 // operand geometry for one degree
 struct SwTcGeom {
@@ -49,7 +69,7 @@ struct SwTcHead {
   int* err;             // device word set to DG_ERR_TIMEOUT when a wait gives up
   long long off_cols;   // int [ncol][2]: element columns (ex, ey), grouped by segment
   long long off_zcls;   // int [nz]: class of each z position
-  long long off_z;      // float [ncz][SWTC_ZSTR]: Sz (row node, col mode), lambda_z, m_z
+  long long off_z;      // float [ncz][SWTC_ZSTR]: Sz [node][mode], Sz^T [mode][node] (rows of SWTC_MPP), lambda_z, m_z
   long long off_xy;     // float [ncx][mp + 1] then [ncy][mp + 1]: lambda, m
   long long off_y;      // float offset of the y classes inside off_xy
   long long off_a;      // per segment: forward factor then inverse factor, a_bytes each
@@ -63,6 +83,12 @@ struct SwTcItem {
   short ex[SWTC_NPMAX], ey[SWTC_NPMAX], ez[SWTC_NPMAX], cz[SWTC_NPMAX];
   // residual offset of patch z-node k relative to its plane (x, y) part, -1 outside the domain
   int zoff[SWTC_NPMAX][SWTC_CS];
+  // row fill at n1 = 8: offset of the patch's element in the residual, and
+  // flags: bit 0 left overlap along y, bits 1-4 patch nodes along y, bits 6 / 7
+  // x-halo left / right taken from the neighbouring patch of the item, bits 8 / 9
+  // a left / right neighbour element exists
+  long long rbase[SWTC_NPMAX];
+  unsigned short pf[SWTC_NPMAX];
 };
 
 // static shared memory of the kernel
@@ -77,7 +103,7 @@ struct SwTcShared {
   int abort;
   int item0[SWTC_MAXSEG + 1];
   SwTcItem item[SWTC_ISLOTS];
-  float z[SWTC_MAXCLS * SWTC_ZSTR(11)];
+  alignas(16) float z[SWTC_MAXZCLS * SWTC_ZSTR(11)];
   // the level's tables, staged once per launch (no global loads on the item path)
   int seg_col0[SWTC_MAXSEG], seg_ncol[SWTC_MAXSEG];
   unsigned char seg_cx[SWTC_MAXSEG], seg_cy[SWTC_MAXSEG];
@@ -100,6 +126,8 @@ struct SwTcPlan {
 // operand geometry for degree n1 - 1 with np patches per item (0: the default,
 // the largest count that fits); false if the degree or count does not fit
 bool swtc_geometry(int n1, SwTcGeom& g, int np = 0);
+// K slot of patch node (j, l) in the residual operand at n1 = 8 (-1: no node)
+int swtc_fill_k(int j, int l, int oLx, int mx);
 std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<double>& tabs, int* err_dev);
 cudaError_t schwarz_tc_prepare(int n1);
 cudaError_t launch_schwarz_patch_tc(const LevelOp& hop, const LevelOp* dop, const SwTcPlan& plan, const float* r,

@@ -150,6 +150,12 @@ __device__ __forceinline__ void cp_async4(void* dst_smem, const void* src, uint3
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "r"(src_bytes)
                : "memory");
 }
+// 16-byte asynchronous global -> shared copy through L2 (both addresses
+// 16-byte aligned); src_bytes = 0 fills zeros and reads nothing
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst_smem)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // barrier over the `count` threads of the warps that use barrier `id` (1..15)
