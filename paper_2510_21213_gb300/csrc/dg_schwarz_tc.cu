@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
     k_schwarz_patch_tc(const LevelOp* __restrict__ op, const unsigned char* __restrict__ blob, const SwTcGeom geom,
                        const float* __restrict__ r, float* __restrict__ zp, const int* __restrict__ act, int nact) {
   constexpr int MP = N1 + 2, MP2 = MP * MP, MP3 = MP2 * MP, NPE = N1 * N1 * N1, MPP = SWTC_MPP(MP);
-  constexpr int CONS = swtc_consumers(N1), THREADS = swtc_threads(N1), NPAR = CONS / 128;
+  constexpr int CONS = swtc_consumers(N1), PROD = swtc_producers(N1), THREADS = swtc_threads(N1);
+  constexpr int NPAR = CONS / 128;
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ SwTcShared sh;
   const SwTcHead* H = (const SwTcHead*)blob;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
   // ---- set-up: barriers, tensor memory, staged tables, item offsets, zeroed B
   if (tid == 0) {
     for (int b = 0; b < SWTC_BSLOTS; ++b) {
-      tc::mbar_init(tc::smem_addr(&sh.full[b]), SWTC_PRODUCERS);
+      tc::mbar_init(tc::smem_addr(&sh.full[b]), PROD);
       tc::mbar_init(tc::smem_addr(&sh.b2[b]), CONS);
     }
     for (int d = 0; d < SWTC_DSLOTS; ++d) {
@@ -312,20 +313,21 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
   const int first = (int)blockIdx.x * per_cta;
   const int nmine = max(0, min(per_cta, total - first));
 
-  if (tid >= CONS && tid < CONS + SWTC_PRODUCERS) {
+  if (tid >= CONS && tid < CONS + PROD) {
     // ================= producers: decode and fill =================
     const int L = tid - CONS;  // B column (j, l) this thread fills (n1 != 8)
     const int jj = L / MP, ll = L % MP;
-    // row fill (n1 = 8): slots (zk, jj, half) L and L + 128 of the 2 MP^2 per
-    // patch, with the y offset of row jj relative to the patch's element for
+    // row fill (n1 = 8): slots (zk, jj, half) L, L + PROD, ... of the 2 MP^2
+    // per patch, with the y offset of row jj relative to the patch's element for
     // a patch without (0) and with (1) left overlap along y
-    int f_zk[2], f_j[2], f_h[2], f_own[2], f_halo[2];
-    long long f_yoff[2][2];
-    bool f_ok[2];
+    constexpr int NSL = (2 * MP2 + PROD - 1) / PROD;
+    int f_zk[NSL], f_j[NSL], f_h[NSL], f_own[NSL], f_halo[NSL];
+    long long f_yoff[NSL][2];
+    bool f_ok[NSL];
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < NSL; ++u) {
       if constexpr (N1 != 8 || !DG_SWTC_ROWFILL) break;
-      const int sl = L + SWTC_PRODUCERS * u;
+      const int sl = L + PROD * u;
       f_ok[u] = sl < 2 * MP2;
       f_zk[u] = sl / (2 * MP);
       f_j[u] = (sl % (2 * MP)) >> 1;
@@ -337,19 +339,18 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       f_yoff[u][1] = j == 0 ? -(long long)nx * NPE + (N1 - 1) * N1
                             : (long long)((j - 1) / N1) * nx * NPE + ((j - 1) % N1) * N1;
     }
+    int seg = 0;  // segment of the current item (items ascend)
     for (int li = 0; li < nmine; ++li) {
       const int b = li % SWTC_BSLOTS;
-      // B slot free once MMA 2 of item li - 2 is done; description slot free
-      // once item li - 4 is read out
-      bool ok = li < SWTC_BSLOTS ||
-                swtc_wait(sh, H, &sh.d2[(li - SWTC_BSLOTS) % SWTC_DSLOTS], ((li - SWTC_BSLOTS) / SWTC_DSLOTS) & 1);
-      ok = ok && (li < SWTC_ISLOTS || swtc_wait(sh, H, &sh.empty[(li - SWTC_ISLOTS) % SWTC_DSLOTS],
-                                                ((li - SWTC_ISLOTS) / SWTC_DSLOTS) & 1));
-      // all producers leave together (they share a named barrier)
-      if (tc::named_barrier_or(1, SWTC_PRODUCERS, !ok || sh.abort != 0)) break;
+      // The item is decoded as soon as its description slot is free (item
+      // li - 4 read out), before the wait for its B slot (MMA 2 of item li - 2
+      // done), which is the longer one: the decode stays off the B slots'
+      // critical path. All producers leave together (they share a named barrier).
+      bool ok = li < SWTC_ISLOTS || swtc_wait(sh, H, &sh.empty[(li - SWTC_ISLOTS) % SWTC_DSLOTS],
+                                              ((li - SWTC_ISLOTS) / SWTC_DSLOTS) & 1);
+      if (tc::named_barrier_or(1, PROD, !ok || sh.abort != 0)) break;
       const int it = first + li;
       SwTcItem& I = sh.item[li % SWTC_ISLOTS];
-      int seg = 0;
       while (sh.item0[seg + 1] <= it) ++seg;
       // patch q of a segment: column fastest, then z, then source: each CTA
       // sweeps a slab of one source's elements, so the residual rows it
@@ -384,8 +385,8 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
         }
       }
       // z offsets of every (patch, z-node): the same for all (x, y) of the patch
-      if (L < np * MP) {
-        const int i = L / MP, k = L - (L / MP) * MP;
+      for (int e = L; e < np * MP; e += PROD) {
+        const int i = e / MP, k = e - (e / MP) * MP;
         const int ez = ((q0 + i) / ncs) % nz;
         const int oLz = ez > 0, mz = N1 + oLz + (ez < nz - 1);
         const int Z = ez * N1 - oLz + k;
@@ -396,7 +397,9 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
         I.np = np;
         I.seg = seg;
       }
-      tc::named_barrier(1, SWTC_PRODUCERS);
+      ok = li < SWTC_BSLOTS ||
+           swtc_wait(sh, H, &sh.d2[(li - SWTC_BSLOTS) % SWTC_DSLOTS], ((li - SWTC_BSLOTS) / SWTC_DSLOTS) & 1);
+      if (tc::named_barrier_or(1, PROD, !ok || sh.abort != 0)) break;
       unsigned char* sB = sB0 + b * b_bytes;
       if constexpr (N1 == 8 && DG_SWTC_ROWFILL) {
         // Residual rows by 16-byte copies: row (zk, jj) of patch i holds its
@@ -414,7 +417,7 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
             const int pf = I.pf[i];
             const int oLy = pf & 1, my = (pf >> 1) & 15;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < NSL; ++u) {
               if (f_ok[u]) {
                 const int zo = I.zoff[i][f_zk[u]];
                 const bool valid = f_j[u] < my && zo >= 0;
@@ -431,13 +434,13 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
           }
         }
         tc::cp_async_wait_all();
-        tc::named_barrier(1, SWTC_PRODUCERS);
+        tc::named_barrier(1, PROD);
 #pragma unroll
         for (int i = 0; i < SWTC_NPMAX; ++i) {
           if (i < np) {
             const int pf = I.pf[i];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < NSL; ++u) {
               if (f_ok[u] && ((pf >> (6 + f_h[u])) & 1)) {
                 const int row = i * SWTC_CS + f_zk[u];
                 const int rs = row + (f_h[u] ? SWTC_CS : -SWTC_CS);
@@ -487,9 +490,9 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       tc::fence_proxy_async();
       tc::mbar_arrive(tc::smem_addr(&sh.full[b]));
     }
-  } else if (tid >= CONS + SWTC_PRODUCERS) {
+  } else if (tid >= CONS + PROD) {
     // ================= MMA issuer (one thread) =================
-    if (tid == CONS + SWTC_PRODUCERS) {
+    if (tid == CONS + PROD) {
       const uint32_t idesc = tc::idesc_tf32(128, ncol);
       int seg_f = -1, seg_i = -1;
       uint32_t ph_f = 0, ph_i = 0;
@@ -552,6 +555,9 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
     const bool active = L < MP2;
     const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
     constexpr bool SREG = NPAR == 1;  // z factor in registers (one warp per lane quarter)
+    // patches per batch of tensor-memory loads (more than one only where the
+    // CTA has 8 warps and the registers for it)
+    constexpr int LDG = PROD == 96 ? DG_SWTC_LDG : 1;
     float S[SREG ? MP : 1][SREG ? MP : 1];
     float inv[MP];
     float lxy = 0.f;
@@ -566,21 +572,34 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       const SwTcItem& I = sh.item[k % SWTC_ISLOTS];
       const uint32_t tcol = tlane + d * ncol;
       const int np = I.np;
-      uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
-      if (par < np) tc::tmem_ld12_async(tcol + par * SWTC_CS, nx12);
-      for (int i = par; i < np; i += NPAR) {
-        tc::tmem_wait12(nx12);
-        float v[SWTC_CS];
+      // tensor-memory loads in batches of LDG patches, the next batch in
+      // flight while this one is stored
+      uint32_t nxb[LDG][SWTC_CS];
 #pragma unroll
-        for (int c = 0; c < SWTC_CS; ++c) v[c] = __uint_as_float(nx12[c]);
-        if (i + NPAR < np) tc::tmem_ld12_async(tcol + (i + NPAR) * SWTC_CS, nx12);
-        if (active) {
-          // streaming stores: the patch solutions are read once, by the gather,
-          // long after; evict-first keeps L2 for the residual rows that
-          // neighbouring patches still gather
-          float* out = zp + ((long long)I.src[i] * E + I.elem[i]) * MP3 + L;
+      for (int g = 0; g < LDG; ++g)
+        if (par + g * NPAR < np) tc::tmem_ld12_async(tcol + (par + g * NPAR) * SWTC_CS, nxb[g]);
+      for (int i0 = par; i0 < np; i0 += LDG * NPAR) {
+        float vb[LDG][SWTC_CS];
 #pragma unroll
-          for (int c = 0; c < MP; ++c) __stcs(out + c * MP2, v[c]);
+        for (int g = 0; g < LDG; ++g) {
+          tc::tmem_wait12(nxb[g]);
+#pragma unroll
+          for (int c = 0; c < SWTC_CS; ++c) vb[g][c] = __uint_as_float(nxb[g][c]);
+        }
+#pragma unroll
+        for (int g = 0; g < LDG; ++g)
+          if (i0 + (LDG + g) * NPAR < np) tc::tmem_ld12_async(tcol + (i0 + (LDG + g) * NPAR) * SWTC_CS, nxb[g]);
+#pragma unroll
+        for (int g = 0; g < LDG; ++g) {
+          const int i = i0 + g * NPAR;
+          if (i < np && active) {
+            // streaming stores: the patch solutions are read once, by the gather,
+            // long after; evict-first keeps L2 for the residual rows that
+            // neighbouring patches still gather
+            float* out = zp + ((long long)I.src[i] * E + I.elem[i]) * MP3 + L;
+#pragma unroll
+            for (int c = 0; c < MP; ++c) __stcs(out + c * MP2, vb[g][c]);
+          }
         }
       }
       tc::fence_before_sync();
@@ -611,14 +630,26 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       const uint32_t tcol = tlane + d * ncol;
       // z-step: Sz^T, scaling, Sz along each patch's z line, back into B as TF32
       // (the z factor's rows from shared memory, 16 bytes at a time)
-      uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
-      if (par < np) tc::tmem_ld12_async(tcol + par * SWTC_CS, nx12);
-      for (int i = par; i < np; i += NPAR) {
-        tc::tmem_wait12(nx12);
-        float t[SWTC_CS];
+      uint32_t nxb[LDG][SWTC_CS];  // the next batch's columns, in flight
 #pragma unroll
-        for (int c = 0; c < SWTC_CS; ++c) t[c] = __uint_as_float(nx12[c]);
-        if (i + NPAR < np) tc::tmem_ld12_async(tcol + (i + NPAR) * SWTC_CS, nx12);
+      for (int g = 0; g < LDG; ++g)
+        if (par + g * NPAR < np) tc::tmem_ld12_async(tcol + (par + g * NPAR) * SWTC_CS, nxb[g]);
+      for (int i0 = par; i0 < np; i0 += LDG * NPAR) {
+       float tb[LDG][SWTC_CS];
+#pragma unroll
+       for (int g = 0; g < LDG; ++g) {
+         tc::tmem_wait12(nxb[g]);
+#pragma unroll
+         for (int c = 0; c < SWTC_CS; ++c) tb[g][c] = __uint_as_float(nxb[g][c]);
+       }
+#pragma unroll
+       for (int g = 0; g < LDG; ++g)
+         if (i0 + (LDG + g) * NPAR < np) tc::tmem_ld12_async(tcol + (i0 + (LDG + g) * NPAR) * SWTC_CS, nxb[g]);
+#pragma unroll
+       for (int g = 0; g < LDG; ++g) {
+        const int i = i0 + g * NPAR;
+        if (i >= np) break;
+        const float* t = tb[g];
         const int cz = I.cz[i];
         const float* zt = sh.z + cz * SWTC_ZSTR(MP);
         if (cz != cur_cz) {
@@ -696,6 +727,7 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
             *(float*)(col + (row >> 3) * sbo + (row & 7) * 16) = tc::to_tf32(w[a]);
           }
         }
+       }
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();

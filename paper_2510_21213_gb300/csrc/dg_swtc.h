@@ -25,12 +25,21 @@ constexpr int SWTC_LBO = 144;        // byte stride of K-adjacent core matrices 
 #ifndef DG_SWTC_ROWFILL
 #define DG_SWTC_ROWFILL 1
 #endif
+// DG_SWTC_LDG: patches per batch of tensor-memory loads in the consumer warps
+// (the next batch is in flight while one is processed).
+#ifndef DG_SWTC_LDG
+#define DG_SWTC_LDG 1
+#endif
 #ifndef DG_SWTC_WIDE
 #define DG_SWTC_WIDE 0
 #endif
-constexpr int SWTC_PRODUCERS = 128;
 __host__ __device__ constexpr int swtc_consumers(int n1) { return n1 == 8 && DG_SWTC_WIDE ? 256 : 128; }
-__host__ __device__ constexpr int swtc_threads(int n1) { return swtc_consumers(n1) + SWTC_PRODUCERS + 32; }
+// producers: 4 warps (one thread per operand column in the 4-byte fill), 3 with
+// the row fill, so that the CTA has 8 warps: two per SM sub-partition, whose
+// register file (16 K registers) then allows up to 255 registers a thread
+// (with 9 warps one sub-partition holds three, and the cap is 168)
+__host__ __device__ constexpr int swtc_producers(int n1) { return n1 == 8 && DG_SWTC_ROWFILL && !DG_SWTC_WIDE ? 96 : 128; }
+__host__ __device__ constexpr int swtc_threads(int n1) { return swtc_consumers(n1) + swtc_producers(n1) + 32; }
 // rings of the pipeline: B operands in shared memory, FP32 accumulators in
 // tensor memory, item descriptions
 constexpr int SWTC_BSLOTS = 2, SWTC_DSLOTS = 3, SWTC_ISLOTS = 4;
