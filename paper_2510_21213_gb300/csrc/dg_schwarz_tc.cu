@@ -1,5 +1,7 @@
 // Tensor-core patch solve of the overlapping Schwarz smoother (FP32 inner
-// solve, levels of degree 6-8).
+// solve, levels of degree 6-8): tables, geometry and the kernel (a variant at
+// degree 7 that also runs the z factor on the tensor cores, off by default,
+// is in dg_schwarz_tc8.cu).
 //
 // Each patch problem of the smoother is solved exactly by fast
 // diagonalisation (Sec. 3.4: the SIPDG operator is a Kronecker sum, so its
@@ -71,19 +73,26 @@ bool swtc_geometry(int n1, SwTcGeom& g, int np) {
   g.kc = g.kpad / 4;
   g.sbo = g.kc * SWTC_LBO;
   g.a_bytes = ((mp2 + 7) / 8) * g.sbo;
-  // patches per item: MP rows of the B operand each, at a stride of SWTC_CS rows
-  // (D columns), so that every tensor-memory load starts at a multiple of 4;
-  // two stages of B must fit next to the two factors
-  const int np_max = g.mp == 11 ? 4 : 10;
+  // patches per item: MP rows of the B operand each, at a stride of cs rows
+  // (D columns), so that every tensor-memory load starts at a multiple of 4
+  // (degree 7: 16, one z-factor MMA operand per patch); two stages of B must
+  // fit next to the two factors (and, at degree 7, the z-factor operands)
+  const bool ztc = n1 == 8 && DG_SWTC_ZTC;
+  g.cs = ztc ? SWTC8_CS : SWTC_CS;
+  const int np_max = ztc ? SWTC8_NPMAX : g.mp == 11 ? 4 : 10;
   if (np < 0 || np > np_max) return false;
   g.np = np > 0 ? np : np_max;
-  g.ncol = (g.np * SWTC_CS + 15) / 16 * 16;
+  g.ncol = (g.np * g.cs + 15) / 16 * 16;
   g.b_bytes = (g.ncol / 8) * g.sbo;
+  g.zb_bytes = ztc ? SWTC_MAXZCLS * 2 * SWTC_ZB_BYTES : 0;
   // the static shared memory counts in whole kilobytes (the dynamic part is
   // 1024-byte aligned after it)
   const size_t stat = (sizeof(SwTcShared) + 1023) / 1024 * 1024;
-  return 2 * (size_t)g.a_bytes + SWTC_BSLOTS * (size_t)g.b_bytes + stat <= 232448 &&
-         g.np <= SWTC_NPMAX && SWTC_DSLOTS * g.ncol <= SWTC_TMEM_COLS;
+  // tensor memory: three accumulators, or at degree 7 two items of two
+  // 128-column accumulators each
+  const bool tmem_ok = ztc ? g.ncol <= 128 : SWTC_DSLOTS * g.ncol <= SWTC_TMEM_COLS;
+  return 2 * (size_t)g.a_bytes + SWTC_BSLOTS * (size_t)g.b_bytes + g.zb_bytes + stat <= 232448 &&
+         g.np <= SWTC_NPMAX && tmem_ok;
 }
 
 // Host tables of the tensor-core patch solve of one level (layout in
@@ -164,6 +173,8 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
   H.off_xy = pos;  // per x class, then per y class: lambda [MP], m (as float)
   pos = align(pos + sizeof(float) * (size_t)(ncx + ncy) * (MP + 1));
   H.off_y = ncx * (MP + 1);
+  H.off_zb = pos;  // degree 7: per z class Sz^T and Sz as MMA operands
+  pos = align(pos + (L.n1 == 8 && DG_SWTC_ZTC ? (size_t)ncz * 2 * SWTC_ZB_BYTES : 0));
   H.off_a = pos;
   pos += (size_t)H.nseg * 2 * g.a_bytes;
   std::vector<unsigned char> blob(pos, 0);
@@ -175,12 +186,27 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
     const double* t = tab(2, rep[2][c]);
     float* o = zt + (size_t)c * SWTC_ZSTR(MP);
     for (int a = 0; a < MP; ++a)
-      for (int k = 0; k < MP; ++k) {
-        o[a * MPP + k] = (float)t[2 + a * MP + k];
-        o[MP * MPP + k * MPP + a] = (float)t[2 + a * MP + k];
-      }
-    for (int k = 0; k < MP; ++k) o[2 * MP * MPP + k] = (float)t[2 + MP * MP + k];
-    o[2 * MP * MPP + MPP] = (float)t[0];
+      for (int k = 0; k < MP; ++k) o[a * MPP + k] = (float)t[2 + a * MP + k];
+    for (int k = 0; k < MP; ++k) o[MP * MPP + k] = (float)t[2 + MP * MP + k];
+    o[MP * MPP + MPP] = (float)t[0];
+  }
+  if (L.n1 == 8 && DG_SWTC_ZTC) {
+    // z-factor MMA operands per z class: Sz^T [n = mode][k = node] (forward)
+    // and Sz [n = node][k = mode] (inverse), 16 x 16, zero outside the patch
+    auto zoff = [](int n, int k) {
+      return (size_t)(n / 8) * SWTC_ZB_SBO + (size_t)(k / 4) * SWTC_ZB_LBO + (size_t)(n % 8) * 16 + (size_t)(k % 4) * 4;
+    };
+    for (int c = 0; c < ncz; ++c) {
+      const double* t = tab(2, rep[2][c]);
+      unsigned char* fw = blob.data() + H.off_zb + (size_t)c * 2 * SWTC_ZB_BYTES;
+      unsigned char* iv = fw + SWTC_ZB_BYTES;
+      for (int node = 0; node < MP; ++node)
+        for (int mode = 0; mode < MP; ++mode) {
+          const float v = host_tf32((float)t[2 + node * MP + mode]);
+          std::memcpy(fw + zoff(mode, node), &v, 4);
+          std::memcpy(iv + zoff(node, mode), &v, 4);
+        }
+    }
   }
   float* xy = (float*)(blob.data() + H.off_xy);
   for (int d = 0; d < 2; ++d)
@@ -203,7 +229,7 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
     unsigned char* ai = af + g.a_bytes;
     for (int j = 0; j < MP; ++j)
       for (int l = 0; l < MP; ++l) {
-        const int kf = L.n1 == 8 && DG_SWTC_ROWFILL ? swtc_fill_k(j, l, oLx, mx) : j * MP + l;
+        const int kf = L.n1 == 8 ? swtc_fill_k(j, l, oLx, mx) : j * MP + l;
         for (int jp = 0; jp < MP; ++jp)
           for (int lp = 0; lp < MP; ++lp) {
             const float v = host_tf32((float)(ty[2 + j * MP + jp] * tx[2 + l * MP + lp]));
@@ -225,23 +251,12 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
 // read out item i - 1 (accumulators in 3 TMEM slots, item descriptions in 4).
 // Every hand-off is an mbarrier; every wait is bounded.
 // ---------------------------------------------------------------------------
-constexpr long long kWaitLimit = 1LL << 31;  // clock cycles (about a second) before a wait gives up
-
-__device__ __forceinline__ bool swtc_wait(SwTcShared& sh, const SwTcHead* H, unsigned long long* bar,
-                                          uint32_t parity) {
-  if (tc::mbar_wait(tc::smem_addr(bar), parity, kWaitLimit)) return true;
-  atomicExch(H->err, DG_ERR_TIMEOUT);
-  atomicExch(&sh.abort, 1);
-  return false;
-}
-
 template <int N1>
 __global__ void __launch_bounds__(swtc_threads(N1), 1)
     k_schwarz_patch_tc(const LevelOp* __restrict__ op, const unsigned char* __restrict__ blob, const SwTcGeom geom,
                        const float* __restrict__ r, float* __restrict__ zp, const int* __restrict__ act, int nact) {
   constexpr int MP = N1 + 2, MP2 = MP * MP, MP3 = MP2 * MP, NPE = N1 * N1 * N1, MPP = SWTC_MPP(MP);
-  constexpr int CONS = swtc_consumers(N1), PROD = swtc_producers(N1), THREADS = swtc_threads(N1);
-  constexpr int NPAR = CONS / 128;
+  constexpr int CONS = SWTC_CONSUMERS, PROD = swtc_producers(N1), THREADS = swtc_threads(N1);
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ SwTcShared sh;
   const SwTcHead* H = (const SwTcHead*)blob;
@@ -326,7 +341,7 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
     bool f_ok[NSL];
 #pragma unroll
     for (int u = 0; u < NSL; ++u) {
-      if constexpr (N1 != 8 || !DG_SWTC_ROWFILL) break;
+      if constexpr (N1 != 8) break;
       const int sl = L + PROD * u;
       f_ok[u] = sl < 2 * MP2;
       f_zk[u] = sl / (2 * MP);
@@ -371,7 +386,7 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
         I.ez[L] = (short)ez;
         I.cz[L] = (short)sh.zcls[ez];
         I.elem[L] = c.x + nx * (c.y + ny * ez);
-        if constexpr (N1 == 8 && DG_SWTC_ROWFILL) {
+        if constexpr (N1 == 8) {
           // x-halos shared with the neighbouring patch of the item: the same
           // source, y and z position and the adjacent x position (patch q - 1
           // or q + 1 of the same column run)
@@ -401,7 +416,7 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
            swtc_wait(sh, H, &sh.d2[(li - SWTC_BSLOTS) % SWTC_DSLOTS], ((li - SWTC_BSLOTS) / SWTC_DSLOTS) & 1);
       if (tc::named_barrier_or(1, PROD, !ok || sh.abort != 0)) break;
       unsigned char* sB = sB0 + b * b_bytes;
-      if constexpr (N1 == 8 && DG_SWTC_ROWFILL) {
+      if constexpr (N1 == 8) {
         // Residual rows by 16-byte copies: row (zk, jj) of patch i holds its
         // 8 own x-nodes (one element row, 32 bytes) at K slots 8 jj .. 8 jj + 7
         // and its x-halo nodes at 8 MP + 2 jj + side (swtc_fill_k). This
@@ -547,23 +562,15 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
     }
   } else {
     // ================= consumers: z-step of item li, output of item li - 1 =================
-    // TMEM lane L: mode (j', l') for the z-step, node (j, l) for the output.
-    // With two consumer warps per lane quarter, warp group `par` takes the
-    // item's patches par, par + NPAR, ...
-    const int L = tid & 127, par = tid >> 7;
+    const int L = tid;  // TMEM lane: mode (j', l') for the z-step, node (j, l) for the output
     const int jj = L / MP, ll = L % MP;
     const bool active = L < MP2;
-    const uint32_t tlane = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    constexpr bool SREG = NPAR == 1;  // z factor in registers (one warp per lane quarter)
-    // patches per batch of tensor-memory loads (more than one only where the
-    // CTA has 8 warps and the registers for it)
-    constexpr int LDG = PROD == 96 ? DG_SWTC_LDG : 1;
-    float S[SREG ? MP : 1][SREG ? MP : 1];
-    float inv[MP];
+    const uint32_t tlane = tmem + ((uint32_t)(32 * warp) << 16);
+    float S[MP][MP], inv[MP];
     float lxy = 0.f;
     bool vxy = false;
     int cur_seg = -1, cur_cz = -1;
-    // output of item k: patch node (l, j, k') of each of this warp's patches
+    // output of item k: patch node (l, j, k') of each patch
     auto output = [&](int k) -> bool {
       const int d = k % SWTC_DSLOTS;
       const bool ok = swtc_wait(sh, H, &sh.d2[d], (k / SWTC_DSLOTS) & 1);
@@ -572,34 +579,21 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       const SwTcItem& I = sh.item[k % SWTC_ISLOTS];
       const uint32_t tcol = tlane + d * ncol;
       const int np = I.np;
-      // tensor-memory loads in batches of LDG patches, the next batch in
-      // flight while this one is stored
-      uint32_t nxb[LDG][SWTC_CS];
+      uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
+      tc::tmem_ld12_async(tcol, nx12);
+      for (int i = 0; i < np; ++i) {
+        tc::tmem_wait12(nx12);
+        float v[SWTC_CS];
 #pragma unroll
-      for (int g = 0; g < LDG; ++g)
-        if (par + g * NPAR < np) tc::tmem_ld12_async(tcol + (par + g * NPAR) * SWTC_CS, nxb[g]);
-      for (int i0 = par; i0 < np; i0 += LDG * NPAR) {
-        float vb[LDG][SWTC_CS];
+        for (int c = 0; c < SWTC_CS; ++c) v[c] = __uint_as_float(nx12[c]);
+        if (i + 1 < np) tc::tmem_ld12_async(tcol + (i + 1) * SWTC_CS, nx12);
+        if (active) {
+          // streaming stores: the patch solutions are read once, by the gather,
+          // long after; evict-first keeps L2 for the residual rows that
+          // neighbouring patches still gather
+          float* out = zp + ((long long)I.src[i] * E + I.elem[i]) * MP3 + L;
 #pragma unroll
-        for (int g = 0; g < LDG; ++g) {
-          tc::tmem_wait12(nxb[g]);
-#pragma unroll
-          for (int c = 0; c < SWTC_CS; ++c) vb[g][c] = __uint_as_float(nxb[g][c]);
-        }
-#pragma unroll
-        for (int g = 0; g < LDG; ++g)
-          if (i0 + (LDG + g) * NPAR < np) tc::tmem_ld12_async(tcol + (i0 + (LDG + g) * NPAR) * SWTC_CS, nxb[g]);
-#pragma unroll
-        for (int g = 0; g < LDG; ++g) {
-          const int i = i0 + g * NPAR;
-          if (i < np && active) {
-            // streaming stores: the patch solutions are read once, by the gather,
-            // long after; evict-first keeps L2 for the residual rows that
-            // neighbouring patches still gather
-            float* out = zp + ((long long)I.src[i] * E + I.elem[i]) * MP3 + L;
-#pragma unroll
-            for (int c = 0; c < MP; ++c) __stcs(out + c * MP2, vb[g][c]);
-          }
+          for (int c = 0; c < MP; ++c) __stcs(out + c * MP2, v[c]);
         }
       }
       tc::fence_before_sync();
@@ -629,42 +623,27 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       unsigned char* sB = sB0 + b * b_bytes;
       const uint32_t tcol = tlane + d * ncol;
       // z-step: Sz^T, scaling, Sz along each patch's z line, back into B as TF32
-      // (the z factor's rows from shared memory, 16 bytes at a time)
-      uint32_t nxb[LDG][SWTC_CS];  // the next batch's columns, in flight
+      uint32_t nx12[SWTC_CS];  // the next patch's columns, in flight
+      tc::tmem_ld12_async(tcol, nx12);
+      for (int i = 0; i < np; ++i) {
+        tc::tmem_wait12(nx12);
+        float t[SWTC_CS];
 #pragma unroll
-      for (int g = 0; g < LDG; ++g)
-        if (par + g * NPAR < np) tc::tmem_ld12_async(tcol + (par + g * NPAR) * SWTC_CS, nxb[g]);
-      for (int i0 = par; i0 < np; i0 += LDG * NPAR) {
-       float tb[LDG][SWTC_CS];
-#pragma unroll
-       for (int g = 0; g < LDG; ++g) {
-         tc::tmem_wait12(nxb[g]);
-#pragma unroll
-         for (int c = 0; c < SWTC_CS; ++c) tb[g][c] = __uint_as_float(nxb[g][c]);
-       }
-#pragma unroll
-       for (int g = 0; g < LDG; ++g)
-         if (i0 + (LDG + g) * NPAR < np) tc::tmem_ld12_async(tcol + (i0 + (LDG + g) * NPAR) * SWTC_CS, nxb[g]);
-#pragma unroll
-       for (int g = 0; g < LDG; ++g) {
-        const int i = i0 + g * NPAR;
-        if (i >= np) break;
-        const float* t = tb[g];
+        for (int c = 0; c < SWTC_CS; ++c) t[c] = __uint_as_float(nx12[c]);
+        if (i + 1 < np) tc::tmem_ld12_async(tcol + (i + 1) * SWTC_CS, nx12);
         const int cz = I.cz[i];
-        const float* zt = sh.z + cz * SWTC_ZSTR(MP);
         if (cz != cur_cz) {
           cur_cz = cz;
-          const int mzc = (int)zt[2 * MP * MPP + MPP];
+          const float* zt = sh.z + cz * SWTC_ZSTR(MP);
+          const int mzc = (int)zt[MP * MPP + MPP];
 #pragma unroll
-          for (int c = 0; c < MP; ++c) inv[c] = (vxy && c < mzc) ? 1.0f / (lxy + zt[2 * MP * MPP + c]) : 0.0f;
-          if constexpr (SREG) {
+          for (int a = 0; a < MP; ++a)
 #pragma unroll
-            for (int a = 0; a < MP; ++a)
+            for (int c = 0; c < MP; ++c) S[a][c] = zt[a * MPP + c];
 #pragma unroll
-              for (int c = 0; c < MP; ++c) S[a][c] = zt[a * MPP + c];
-          }
+          for (int c = 0; c < MP; ++c) inv[c] = (vxy && c < mzc) ? 1.0f / (lxy + zt[MP * MPP + c]) : 0.0f;
         }
-        if (active && SREG) {
+        if (active) {
           // both contractions as MP independent accumulators updated per step
           float u[MP], w[MP];
 #pragma unroll
@@ -687,47 +666,7 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
             const int row = i * SWTC_CS + a;
             *(float*)(col + (row >> 3) * sbo + (row & 7) * 16) = tc::to_tf32(w[a]);
           }
-        } else if (active) {
-          // the same with the z factor's rows read from shared memory
-          float u[MP], w[MP];
-#pragma unroll
-          for (int a = 0; a < MP; ++a) {
-            float s[MPP];
-#pragma unroll
-            for (int q = 0; q < MPP / 4; ++q) {
-              const float4 f = *(const float4*)(zt + a * MPP + 4 * q);
-              s[4 * q] = f.x;
-              s[4 * q + 1] = f.y;
-              s[4 * q + 2] = f.z;
-              s[4 * q + 3] = f.w;
-            }
-#pragma unroll
-            for (int c = 0; c < MP; ++c) u[c] = a == 0 ? s[c] * t[0] : fmaf(s[c], t[a], u[c]);
-          }
-#pragma unroll
-          for (int c = 0; c < MP; ++c) u[c] *= inv[c];
-#pragma unroll
-          for (int c = 0; c < MP; ++c) {
-            float s[MPP];  // row c of Sz^T: Sz[a][c] for every a
-#pragma unroll
-            for (int q = 0; q < MPP / 4; ++q) {
-              const float4 f = *(const float4*)(zt + MP * MPP + c * MPP + 4 * q);
-              s[4 * q] = f.x;
-              s[4 * q + 1] = f.y;
-              s[4 * q + 2] = f.z;
-              s[4 * q + 3] = f.w;
-            }
-#pragma unroll
-            for (int a = 0; a < MP; ++a) w[a] = c == 0 ? s[a] * u[0] : fmaf(s[a], u[c], w[a]);
-          }
-          unsigned char* col = sB + (L / 4) * SWTC_LBO + (L % 4) * 4;
-#pragma unroll
-          for (int a = 0; a < MP; ++a) {
-            const int row = i * SWTC_CS + a;
-            *(float*)(col + (row >> 3) * sbo + (row & 7) * 16) = tc::to_tf32(w[a]);
-          }
         }
-       }
       }
       tc::fence_proxy_async();
       tc::fence_before_sync();
@@ -767,7 +706,9 @@ cudaError_t schwarz_tc_prepare(int n1) {
   const int smem = 2 * g.a_bytes + SWTC_BSLOTS * g.b_bytes;
   switch (n1) {
     case 7: return cudaFuncSetAttribute(k_schwarz_patch_tc<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    case 8: return cudaFuncSetAttribute(k_schwarz_patch_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    case 8:
+      if (DG_SWTC_ZTC) return schwarz_tc8_prepare(g);
+      return cudaFuncSetAttribute(k_schwarz_patch_tc<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     case 9: return cudaFuncSetAttribute(k_schwarz_patch_tc<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     default: return cudaErrorInvalidValue;
   }
@@ -782,7 +723,9 @@ cudaError_t launch_schwarz_patch_tc(const LevelOp& hop, const LevelOp* dop, cons
   const unsigned char* b = (const unsigned char*)plan.blob;
   switch (hop.n1) {
     case 7: return launch_tc_n1<7>(dop, b, g, r, zp, act, nact, items, s);
-    case 8: return launch_tc_n1<8>(dop, b, g, r, zp, act, nact, items, s);
+    case 8:
+      if (DG_SWTC_ZTC) return launch_schwarz_patch_tc8(plan, r, zp, act, nact, s);
+      return launch_tc_n1<8>(dop, b, g, r, zp, act, nact, items, s);
     case 9: return launch_tc_n1<9>(dop, b, g, r, zp, act, nact, items, s);
     default: return cudaErrorInvalidValue;
   }

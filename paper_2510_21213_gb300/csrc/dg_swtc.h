@@ -7,39 +7,28 @@
 #include <vector>
 
 #include "dg_internal.h"
+#include "dg_tc.h"
 
 namespace dg {
 
 constexpr int SWTC_LBO = 144;        // byte stride of K-adjacent core matrices (128 + 16: conflict-free stores)
-// warp roles: consumers first (one thread per TMEM lane: z-step and output;
-// at n1 = 8 two warps per lane quarter, each taking every other patch of an
-// item), then 4 producer warps (item decode and the residual fill), then the
-// MMA issuer
-// Tuning switches (compile-time; defaults chosen by timing on a GB300):
-// DG_SWTC_ROWFILL: at n1 = 8 fill the residual operand by 16-byte copies of
-// element rows (K order permuted, x-halos shared within an item); 0: one
-// 4-byte load per operand entry, as at the other degrees.
-// DG_SWTC_WIDE: at n1 = 8 two consumer warps per TMEM lane quarter (z factor
-// read from shared memory); 0: one warp per quarter with the z factor in
-// registers.
-#ifndef DG_SWTC_ROWFILL
-#define DG_SWTC_ROWFILL 1
+// Warp roles: 4 consumer warps (one thread per TMEM lane), then the producer
+// warps (item decode and the residual fill: 4, one thread per operand column,
+// in the kernel of degrees 6 and 8; 3 in the degree-7 kernel, so that its CTA
+// has 8 warps, two per SM sub-partition, whose 16 K registers then allow up
+// to 255 registers a thread; with 9 warps one sub-partition holds three and
+// the cap is 168), then one warp whose first thread issues the MMAs.
+constexpr int SWTC_CONSUMERS = 128;
+// DG_SWTC_ZTC (compile-time): at degree 7 run the z factor on the tensor cores
+// too (dg_schwarz_tc8.cu: A operand read from tensor memory, 7 patches per
+// item). Measured slower than the FP32 z-step at 16^3 p = 7 with 42 sources
+// (1.08 against 0.92 ms per launch: its two-slot pipeline waits on the chain
+// fill -> MMA 1 -> z1 -> scaling -> MMA 2 -> z2), so it is off by default.
+#ifndef DG_SWTC_ZTC
+#define DG_SWTC_ZTC 0
 #endif
-// DG_SWTC_LDG: patches per batch of tensor-memory loads in the consumer warps
-// (the next batch is in flight while one is processed).
-#ifndef DG_SWTC_LDG
-#define DG_SWTC_LDG 1
-#endif
-#ifndef DG_SWTC_WIDE
-#define DG_SWTC_WIDE 0
-#endif
-__host__ __device__ constexpr int swtc_consumers(int n1) { return n1 == 8 && DG_SWTC_WIDE ? 256 : 128; }
-// producers: 4 warps (one thread per operand column in the 4-byte fill), 3 with
-// the row fill, so that the CTA has 8 warps: two per SM sub-partition, whose
-// register file (16 K registers) then allows up to 255 registers a thread
-// (with 9 warps one sub-partition holds three, and the cap is 168)
-__host__ __device__ constexpr int swtc_producers(int n1) { return n1 == 8 && DG_SWTC_ROWFILL && !DG_SWTC_WIDE ? 96 : 128; }
-__host__ __device__ constexpr int swtc_threads(int n1) { return swtc_consumers(n1) + swtc_producers(n1) + 32; }
+__host__ __device__ constexpr int swtc_producers(int n1) { return n1 == 8 ? 96 : 128; }
+__host__ __device__ constexpr int swtc_threads(int n1) { return SWTC_CONSUMERS + swtc_producers(n1) + 32; }
 // rings of the pipeline: B operands in shared memory, FP32 accumulators in
 // tensor memory, item descriptions
 constexpr int SWTC_BSLOTS = 2, SWTC_DSLOTS = 3, SWTC_ISLOTS = 4;
@@ -49,13 +38,20 @@ constexpr int SWTC_MAXZCLS = 5;      // position classes along z (at most 5 on a
 constexpr int SWTC_MAXSEG = SWTC_MAXCLS * SWTC_MAXCLS;
 constexpr int SWTC_CS = 12;          // B rows / D columns per patch (MP <= 11, padded to a multiple of 4)
 constexpr int SWTC_NPMAX = 10;       // patches per work item
+// degree 7 with DG_SWTC_ZTC: 16 rows / columns per patch, so that each patch's z line
+// is one 16-wide operand of the z-factor MMAs; at most 7 patches per item
+// (two items in flight, each with two 128-column accumulators)
+constexpr int SWTC8_CS = 16, SWTC8_NPMAX = 7;
+// z-factor operands of the degree-7 kernel: per z class Sz^T and Sz as 16 x 16
+// TF32 matrices, K-major core matrices (16-byte groups of K 128 bytes apart,
+// 8-row groups 512 bytes apart)
+constexpr int SWTC_ZB_BYTES = 1024, SWTC_ZB_LBO = 128, SWTC_ZB_SBO = 512;
 constexpr int SWTC_MAXCOLS = 768;    // element columns (nx * ny) staged in shared memory
 constexpr int SWTC_MAXNZ = 256;      // elements along z
 constexpr int SWTC_MAXACT = 256;     // active sources staged in shared memory (more are read from global)
-// floats per z class: S and S^T with rows padded to a multiple of 4 (16-byte
-// row loads), lambda (padded), m
+// floats per z class: S (rows padded to a multiple of 4), lambda (padded), m
 #define SWTC_MPP(MP) (((MP) + 3) / 4 * 4)
-#define SWTC_ZSTR(MP) (2 * (MP) * SWTC_MPP(MP) + SWTC_MPP(MP) + 4)
+#define SWTC_ZSTR(MP) ((MP) * SWTC_MPP(MP) + SWTC_MPP(MP) + 4)
 
 // operand geometry for one degree
 struct SwTcGeom {
@@ -67,6 +63,8 @@ struct SwTcGeom {
   int np;       // patches per work item
   int ncol;     // N of the MMAs: np * SWTC_CS rounded up to a multiple of 16
   int b_bytes;  // the B operand of one stage (ncol / 8 row groups)
+  int cs;       // B rows / D columns per patch
+  int zb_bytes; // z-factor operands in shared memory (degree 7), 0 otherwise
 };
 
 // Header of a level's table blob (device memory, read by the kernel). Offsets
@@ -78,7 +76,8 @@ struct SwTcHead {
   int* err;             // device word set to DG_ERR_TIMEOUT when a wait gives up
   long long off_cols;   // int [ncol][2]: element columns (ex, ey), grouped by segment
   long long off_zcls;   // int [nz]: class of each z position
-  long long off_z;      // float [ncz][SWTC_ZSTR]: Sz [node][mode], Sz^T [mode][node] (rows of SWTC_MPP), lambda_z, m_z
+  long long off_z;      // float [ncz][SWTC_ZSTR]: Sz [node][mode] (rows of SWTC_MPP), lambda_z, m_z
+  long long off_zb;     // degree 7: per z class the operands Sz^T then Sz (SWTC_ZB_BYTES each)
   long long off_xy;     // float [ncx][mp + 1] then [ncy][mp + 1]: lambda, m
   long long off_y;      // float offset of the y classes inside off_xy
   long long off_a;      // per segment: forward factor then inverse factor, a_bytes each
@@ -108,9 +107,15 @@ struct SwTcShared {
   unsigned long long full[SWTC_BSLOTS], b2[SWTC_BSLOTS];
   unsigned long long d1[SWTC_DSLOTS], d2[SWTC_DSLOTS], empty[SWTC_DSLOTS];
   unsigned long long tma_f, tma_i;
+  // degree-7 kernel: z-forward MMAs done (e), z-inverse MMAs done (f), item
+  // description slot free (ifree)
+  unsigned long long e[2], f[2], ifree[SWTC_ISLOTS];
   uint32_t tmem;
   int abort;
   int item0[SWTC_MAXSEG + 1];
+  // degree-7 kernel: this CTA's share of every segment (first item in the
+  // segment, count of its items before the segment)
+  int mine0[SWTC_MAXSEG], mcum[SWTC_MAXSEG + 1];
   SwTcItem item[SWTC_ISLOTS];
   alignas(16) float z[SWTC_MAXZCLS * SWTC_ZSTR(11)];
   // the level's tables, staged once per launch (no global loads on the item path)
@@ -139,6 +144,21 @@ bool swtc_geometry(int n1, SwTcGeom& g, int np = 0);
 int swtc_fill_k(int j, int l, int oLx, int mx);
 std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<double>& tabs, int* err_dev);
 cudaError_t schwarz_tc_prepare(int n1);
+cudaError_t schwarz_tc8_prepare(const SwTcGeom& g);
+cudaError_t launch_schwarz_patch_tc8(const SwTcPlan& plan, const float* r, float* zp, const int* act, int nact,
+                                     cudaStream_t s);
+
+// Bounded wait on a shared-memory mbarrier phase (about a second); on a
+// timeout the kernel's error word gets DG_ERR_TIMEOUT and the CTA's abort flag
+// is set, so that every role leaves its loop.
+constexpr long long kSwtcWaitLimit = 1LL << 31;  // clock cycles
+__device__ __forceinline__ bool swtc_wait(SwTcShared& sh, const SwTcHead* H, unsigned long long* bar,
+                                          uint32_t parity) {
+  if (tc::mbar_wait(tc::smem_addr(bar), parity, kSwtcWaitLimit)) return true;
+  atomicExch(H->err, DG_ERR_TIMEOUT);
+  atomicExch(&sh.abort, 1);
+  return false;
+}
 cudaError_t launch_schwarz_patch_tc(const LevelOp& hop, const LevelOp* dop, const SwTcPlan& plan, const float* r,
                                     float* zp, const int* act, int nact, cudaStream_t s);
 
