@@ -547,7 +547,8 @@ def run_ours(args):
         kpad = (rf["m"] ** 2 + 7) // 8 * 8
         tc_flops = rf["B"] * rf["E"] * 2 * 2 * 128 * 12 * kpad
         ideal["tensor"] = tc_flops / (bf16 * TF32_OVER_BF16 * 1e12)
-        ideal["alu"] = rf["B"] * rf["E"] * 2 * 2 * rf["m"] ** 3 / (alu_peak * 1e12)  # the z factor in FP32
+        # the z factor in FP32: per patch m^2 z lines, each two m x m contractions
+        ideal["alu"] = rf["B"] * rf["E"] * 2 * 2 * rf["m"] ** 4 / (alu_peak * 1e12)
     else:
         ideal["alu"] = rf["patch_flops"] / (alu_peak * 1e12)
     bound = max(ideal, key=ideal.get)
