@@ -291,6 +291,24 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       acc += (int)(((long long)H->seg_ncol[sg] * nz * nact + NP - 1) / NP);
     }
     sh.item0[nseg] = acc;
+    if (DG_SWTC_SPLIT) {
+      // Every CTA takes the same share of every segment (class pair), so that
+      // all CTAs get the same mix of interior items and the costlier items of
+      // the boundary classes; its position in the split rotates from segment
+      // to segment, so that the CTAs that take one item more of a small
+      // segment differ. A CTA's share of a segment is a contiguous run.
+      int mine = 0;
+      const long long G = gridDim.x;
+      for (int sg = 0; sg < nseg; ++sg) {
+        const long long n = sh.item0[sg + 1] - sh.item0[sg];
+        const long long c = (blockIdx.x + 37LL * sg) % G;
+        const int lo = (int)(c * n / G), hi = (int)((c + 1) * n / G);
+        sh.mine0[sg] = sh.item0[sg] + lo;
+        sh.mcum[sg] = mine;
+        mine += hi - lo;
+      }
+      sh.mcum[nseg] = mine;
+    }
   }
   if (warp == 0) tc::tmem_alloc(&sh.tmem, SWTC_TMEM_COLS);
   {
@@ -321,12 +339,13 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = sh.tmem;
-  // each CTA takes a contiguous range of items, so that it rarely crosses into
-  // another class pair (a new pair costs a reload of both factors)
+  // without DG_SWTC_SPLIT each CTA takes a contiguous range of items, so that
+  // it rarely crosses into another class pair (a new pair costs a reload of
+  // both factors)
   const int total = sh.item0[nseg];
   const int per_cta = (total + (int)gridDim.x - 1) / (int)gridDim.x;
   const int first = (int)blockIdx.x * per_cta;
-  const int nmine = max(0, min(per_cta, total - first));
+  const int nmine = DG_SWTC_SPLIT ? sh.mcum[nseg] : max(0, min(per_cta, total - first));
 
   if (tid >= CONS && tid < CONS + PROD) {
     // ================= producers: decode and fill =================
@@ -364,9 +383,15 @@ __global__ void __launch_bounds__(swtc_threads(N1), 1)
       bool ok = li < SWTC_ISLOTS || swtc_wait(sh, H, &sh.empty[(li - SWTC_ISLOTS) % SWTC_DSLOTS],
                                               ((li - SWTC_ISLOTS) / SWTC_DSLOTS) & 1);
       if (tc::named_barrier_or(1, PROD, !ok || sh.abort != 0)) break;
-      const int it = first + li;
       SwTcItem& I = sh.item[li % SWTC_ISLOTS];
-      while (sh.item0[seg + 1] <= it) ++seg;
+      int it;  // item index in the launch's item list
+      if (DG_SWTC_SPLIT) {
+        while (sh.mcum[seg + 1] <= li) ++seg;
+        it = sh.mine0[seg] + li - sh.mcum[seg];
+      } else {
+        it = first + li;
+        while (sh.item0[seg + 1] <= it) ++seg;
+      }
       // patch q of a segment: column fastest, then z, then source: each CTA
       // sweeps a slab of one source's elements, so the residual rows it
       // gathers as halos were loaded shortly before (by itself or by the CTAs

@@ -27,6 +27,12 @@ constexpr int SWTC_CONSUMERS = 128;
 #ifndef DG_SWTC_ZTC
 #define DG_SWTC_ZTC 0
 #endif
+// DG_SWTC_SPLIT (compile-time): 1 = every CTA takes a share of every class
+// pair (balanced mix of item costs, a factor reload per class pair); 0 = each
+// CTA a contiguous range of the item list.
+#ifndef DG_SWTC_SPLIT
+#define DG_SWTC_SPLIT 1
+#endif
 __host__ __device__ constexpr int swtc_producers(int n1) { return n1 == 8 ? 96 : 128; }
 __host__ __device__ constexpr int swtc_threads(int n1) { return SWTC_CONSUMERS + swtc_producers(n1) + 32; }
 // rings of the pipeline: B operands in shared memory, FP32 accumulators in
