@@ -20,9 +20,13 @@
 // D in tensor memory (FP32). The Kronecker factors depend on the x and y
 // position classes of the element (boundary, next to the boundary, interior),
 // so a work item holds patches of one class pair; its factors arrive by bulk
-// copy, its residual entries by coalesced loads (zero outside the domain),
-// rounded to TF32 on their way into shared memory. The output goes to the same patch buffer as the SIMT
-// kernel's, [source][element][MP^3] (x fastest), for k_schwarz_gather.
+// copy. The residual entries arrive, at degree 7 (element rows of 32 bytes),
+// by 16-byte asynchronous copies of whole element rows into a permuted K
+// order (swtc_fill_k), the x-halos shared between the x-neighbouring patches
+// of an item; at degrees 6 and 8 by coalesced 4-byte loads rounded to TF32 on
+// their way into shared memory; zero outside the domain. The output goes to
+// the same patch buffer as the SIMT kernel's, [source][element][MP^3]
+// (x fastest), for k_schwarz_gather.
 #include <algorithm>
 #include <cstring>
 
@@ -244,7 +248,8 @@ std::vector<unsigned char> schwarz_tc_blob(const LevelOp& L, const std::vector<d
 }
 
 // ---------------------------------------------------------------------------
-// kernel: a pipeline over work items, each CTA taking a contiguous range.
+// kernel: a pipeline over work items, each CTA taking a share of every class
+// pair (or, with DG_SWTC_SPLIT = 0, a contiguous range of the item list).
 // Warp roles: producers decode an item and fill its B operand (2 slots),
 // the MMA thread issues MMA 1 as soon as a B is full and MMA 2 as soon as the
 // consumers have rewritten it, consumers run the z-step of item i and then
