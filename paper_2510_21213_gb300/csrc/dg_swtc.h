@@ -22,7 +22,7 @@ constexpr int SWTC_CONSUMERS = 128;
 // DG_SWTC_ZTC (compile-time): at degree 7 run the z factor on the tensor cores
 // too (dg_schwarz_tc8.cu: A operand read from tensor memory, 7 patches per
 // item). Measured slower than the FP32 z-step at 16^3 p = 7 with 42 sources
-// (1.08 against 0.92 ms per launch: its two-slot pipeline waits on the chain
+// (1.08 against 0.84 ms per launch: its two-slot pipeline waits on the chain
 // fill -> MMA 1 -> z1 -> scaling -> MMA 2 -> z2), so it is off by default.
 #ifndef DG_SWTC_ZTC
 #define DG_SWTC_ZTC 0
